@@ -1,0 +1,322 @@
+#!/usr/bin/env python
+"""Benchmark of the IterNCGP hot path on GB300; prints one JSON line.
+
+Step = one kernel product K(X, X) S on the kernel-bench workload (N = 60000 points of
+784-D sparse clusters, Matern-3/2 l = 28, S of N x 80 standard normals), computed through
+the C ABI (itergp_kmatvec) in the FP32-accurate tensor-core precision (bf16x3).  The
+metric is kernel pairs per second (N^2 / step time).  The same JSON line carries the
+end-to-end number (host buffers, copies inside the timed region), the roofline of the
+fused product kernel, the other precisions, Newton-step times of the full fit on the
+same data (plain FP32 path vs tensor-core paths), clocks sampled during the timed region
+and the FP64 oracle's throughput on the host cores.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+N_DEFAULT, D, P = 60000, 784, 80
+ELL, OUT = 28.0, 1.0
+METRIC = "K·S kernel-pairs/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--precision", default="bf16x3")
+    ap.add_argument("--n", type=int, default=N_DEFAULT)
+    ap.add_argument("--no-extras", action="store_true", help="skip other precisions and fit timings")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    return ap.parse_args()
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            d = json.load(fh)
+        return d, "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0,
+                "sm_max_mhz": 2070.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples every 200 ms while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        with open(self.path) as fh:
+            for line in fh:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.path)
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(rows)}
+
+
+def cpu_baseline(X, S, seconds: float):
+    """The FP64 oracle's k(X, X) S on a bounded sample of output rows (host cores)."""
+    import numpy as np
+
+    import oracle.itergp_oracle as O
+    kern = O.Kernel(O.MATERN32, ELL, OUT)
+    X64 = X.astype(np.float64)
+    S64 = S.astype(np.float64)
+    rows, t0 = 0, time.perf_counter()
+    chunk = 64
+    while time.perf_counter() - t0 < seconds and rows < X.shape[0]:
+        O.kmatvec(X64[rows:rows + chunk], X64, S64, kern)
+        rows += chunk
+    dt = time.perf_counter() - t0
+    return {"value": rows * X.shape[0] / dt, "unit": "kernel-pairs/s", "cores": os.cpu_count(),
+            "kind": "oracle",
+            "sample": f"{rows} of {X.shape[0]} output rows of k(X,X)S (FP64 NumPy, D={X.shape[1]}, P={S.shape[1]})",
+            "seconds": round(dt, 2)}
+
+
+def reference_arm(args):
+    """Oracle on the host cores as the reference implementation (rank 0 only)."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    from paper_2310_20285_gb300 import datagen
+    X, _, _, _, S = datagen.workload_kernel_bench(n=args.n)
+    import numpy as np
+
+    import oracle.itergp_oracle as O
+    kern = O.Kernel(O.MATERN32, ELL, OUT)
+    X64, S64 = X.astype(np.float64), S.astype(np.float64)
+    rows_per_step = 32
+    for w in range(args.warmup):
+        O.kmatvec(X64[:8], X64, S64, kern)
+    times = []
+    for k in range(args.steps):
+        r0 = (k * rows_per_step) % X.shape[0]
+        t0 = time.perf_counter()
+        O.kmatvec(X64[r0:r0 + rows_per_step], X64, S64, kern)
+        times.append(time.perf_counter() - t0)
+    t = sum(times) / len(times)
+    value = rows_per_step * X.shape[0] / t
+    out = {"metric": METRIC, "value": value, "unit": "kernel-pairs/s", "impl": "reference",
+           "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": t * 1e3, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": f"kernel product K(X,X)S, N={args.n}, D={D}, P={P}, Matern-3/2 l=28 "
+                                  f"(bounded sample: {rows_per_step} output rows per step)"},
+           "cpu_baseline": {"value": value, "unit": "kernel-pairs/s", "cores": os.cpu_count(),
+                            "kind": "oracle",
+                            "sample": f"{rows_per_step} output rows of k(X,X)S per step"},
+           "e2e": {"value": value, "unit": "kernel-pairs/s", "h2d_bytes_per_step": 0,
+                   "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        reference_arm(args)
+        return
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl")
+    from paper_2310_20285_gb300 import datagen, native
+
+    dev = torch.device("cuda", local)
+    # rank r works on its own independent problem (weak scaling)
+    X, y, Xs, ys, S = datagen.workload_kernel_bench(n=args.n, seed=2 + 1000 * rank)
+    n = X.shape[0]
+    tX = torch.as_tensor(X, device=dev)
+    tS = torch.as_tensor(S, device=dev)
+    Y = torch.empty((n, P), device=dev)
+
+    def step(prec=args.precision):
+        native.kmatvec(tX, tX, tS, kind="matern32", lengthscale=ELL, outputscale=OUT,
+                       precision=prec, out=Y)
+
+    def barrier():
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    assert native.sync_status() == 0
+    clocks = ClockSampler(local)
+    barrier()
+    clocks.start()
+    native.timing_read()
+    native.timing_enable(True)
+    l0 = native.launch_count()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record()
+    for _ in range(args.steps):
+        step()
+    ev1.record()
+    barrier()
+    launches = native.launch_count() - l0
+    native.timing_enable(False)
+    kern_ms, kern_n = native.timing_read()
+    clk = clocks.stop()
+    t_step = ev0.elapsed_time(ev1) / 1e3 / args.steps
+    t_max = t_step
+    if world > 1:
+        tt = torch.tensor([t_step], device=dev, dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_max = float(tt.item())
+    value = world * n * n / t_max
+    assert native.sync_status() == 0
+
+    # ---- end to end through the C ABI with host buffers (copies in the timed region)
+    hX = torch.as_tensor(X).pin_memory()
+    hS = torch.as_tensor(S).pin_memory()
+    hY = torch.empty((n, P), dtype=torch.float32).pin_memory()
+    dX = torch.empty_like(tX)
+    dS = torch.empty_like(tS)
+    dY = torch.empty_like(Y)
+
+    def e2e_step():
+        dX.copy_(hX, non_blocking=True)
+        dS.copy_(hS, non_blocking=True)
+        native.kmatvec(dX, dX, dS, kind="matern32", lengthscale=ELL, outputscale=OUT,
+                       precision=args.precision, out=dY)
+        hY.copy_(dY, non_blocking=True)
+
+    e2e_steps = max(1, min(args.steps, 5))
+    e2e_step()
+    barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(e2e_steps):
+        e2e_step()
+    e1.record()
+    barrier()
+    t_e2e = e0.elapsed_time(e1) / 1e3 / e2e_steps
+    if world > 1:
+        tt = torch.tensor([t_e2e], device=dev, dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_e2e = float(tt.item())
+
+    pk, pk_kind = peaks()
+    flops = 2.0 * n * n * (D + P)
+    kernel_s = (kern_ms / max(kern_n, 1)) / 1e3
+    achieved = flops / kernel_s / 1e12
+    roof = {"bound": "tensor", "achieved": achieved, "peak": pk["bf16_tflops"], "unit": "TFLOP/s",
+            "frac": achieved / pk["bf16_tflops"], "traffic": None,
+            "peak_kind": f"{pk_kind} bf16 dense (burst)",
+            "frac_of_sustained": achieved / pk.get("bf16_tflops_sustained", pk["bf16_tflops"]),
+            "kernel": "kmv_tc_kernel", "kernel_ms": kernel_s * 1e3,
+            "algorithmic_flops_per_launch": flops,
+            "tensor_flops_issued_per_launch": flops * (3.0 if args.precision == "bf16x3" else 1.0)}
+
+    out = {"metric": METRIC, "value": value, "unit": "kernel-pairs/s", "n_gpus": world,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_max * 1e3,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+           "dtype": "bf16x3 (BF16 hi/lo split operands, FP32 accumulate; FP32-accurate)",
+           "data": "synthetic",
+           "config": {"workload": f"kernel product K(X,X)S, N={n}, D={D}, P={P}, Matern-3/2 l=28, s=1; "
+                                  "784-D sparse clusters (19% non-zero), S ~ N(0,1)",
+                      "precision": args.precision, "l2": "inputs exceed L2 (X is 188 MB FP32, 200 MB BF16 hi+lo)",
+                      "parallelism": f"{world} independent problem(s), one per GPU"},
+           "roofline": roof, "clocks": clk, "gpu_launches": int(launches),
+           "e2e": {"value": world * n * n / t_e2e, "unit": "kernel-pairs/s",
+                   "h2d_bytes_per_step": int(hX.numel() * 4 + hS.numel() * 4),
+                   "d2h_bytes_per_step": int(hY.numel() * 4), "ms_per_step": t_e2e * 1e3}}
+
+    if rank == 0 and not args.no_extras:
+        paths = {}
+        for prec, k in (("bf16", 5), ("bf16_comp", 5), ("fp32", 2)):
+            step(prec)
+            torch.cuda.synchronize()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            for _ in range(k):
+                step(prec)
+            b.record()
+            torch.cuda.synchronize()
+            tp = a.elapsed_time(b) / 1e3 / k
+            paths[prec] = {"kernel_pairs_per_s": n * n / tp, "ms": tp * 1e3}
+        paths[args.precision] = {"kernel_pairs_per_s": n * n / t_step, "ms": t_step * 1e3}
+        out["paths"] = paths
+        # full IterNCGP fit on the same data: 5 Newton steps x <= 5 iterations, R = 200
+        fits = {}
+        ty = torch.as_tensor(y, device=dev)
+        for prec in ("bf16x3", "bf16", "fp32"):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            m = native.fit(tX, ty, 10, kind="matern32", lengthscale=ELL, outputscale=OUT,
+                           precision=prec, max_newton=5, max_iters=5, rank=200)
+            torch.cuda.synchronize()
+            dt = time.perf_counter() - t0
+            mean, var, probs = m.predict(torch.as_tensor(Xs, device=dev))
+            acc = float((probs.argmax(1).cpu().numpy() == ys).mean())
+            fits[prec] = {"newton_step_ms": dt * 1e3 / max(m.report.newton_steps, 1),
+                          "fit_s": dt, "iters": int(m.report.total_iters), "test_acc": acc}
+            m.free()
+        out["fit"] = {"workload": "IterNCGP fit, same data, C=10, 5 Newton steps x 5 iterations, R=200",
+                      **fits}
+    if rank == 0 and world == 1:
+        out["cpu_baseline"] = cpu_baseline(X, S, args.cpu_seconds)
+    if rank == 0:
+        print(json.dumps(out))
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

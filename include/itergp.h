@@ -1,0 +1,224 @@
+/*
+ * itergp.h -- C ABI of the IterNCGP hot path for NVIDIA GB300 (sm_103a).
+ *
+ * IterNCGP (Tatzel, Wenger, Schneider, Hennig, arXiv 2310.20285) fits a multi-class GP
+ * classifier with a softmax likelihood by Newton steps (Alg. 1).  Each step is a GP
+ * regression problem with pseudo targets y_hat = f + W^+ grad log p(y|f) and noise
+ * W^+ (Eqs. 6-7, footnote on the pseudo-inverse, Lemma A.6), solved approximately by
+ * IterGP (Alg. 2) with actions recycled between steps and compressed to rank R (Alg. 3).
+ * All of its cost sits in products with the kernel matrix K (Sec. 3.5, App. B.3.1),
+ * which this library evaluates on the fly and never stores.
+ *
+ * Conventions shared by every entry point
+ *  - Matrices are row-major and contiguous.  Vectors over the training set are N x C
+ *    arrays in the paper's CN ordering (class index fastest, App. B.1).  The multi-output
+ *    prior is K = k(X, X) kron I_C, one kernel shared by the C independent latent GPs
+ *    (App. C.3), so K w is k(X, X) @ w for w viewed as N x C.
+ *  - Pointers named "device" must point to memory of the current CUDA device.  The
+ *    caller owns every pointer argument; the library never frees caller memory.
+ *  - Every call is stream-ordered on `stream` (a cudaStream_t; NULL = legacy default
+ *    stream) and returns without waiting for the GPU, except where stated.
+ *  - Errors: functions return ITERGP_OK (0) or a negative itergp_status.  Arguments are
+ *    validated on the host before any launch; nothing is launched when validation
+ *    fails.  Faults detected on the device (a bounded wait that expired, a non-finite
+ *    value) are recorded in a per-device status word that itergp_sync_status() reads.
+ *    No function aborts the process or throws across the ABI.
+ *  - Thread safety: calls may come from several host threads on different streams.
+ *    Scratch memory is drawn stream-ordered from a library-owned pool per device.
+ */
+#ifndef ITERGP_H_
+#define ITERGP_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  ITERGP_OK = 0,
+  ITERGP_EINVAL = -1,       /* invalid argument (host-side check, nothing launched)      */
+  ITERGP_ENOMEM = -2,       /* device allocation failed                                   */
+  ITERGP_ECUDA = -3,        /* a CUDA runtime call failed                                 */
+  ITERGP_ENUMERIC = -4,     /* a non-finite value was produced on the device              */
+  ITERGP_ETIMEOUT = -5,     /* a device-side wait exceeded its bound; the kernel returned */
+  ITERGP_EUNSUPPORTED = -6  /* the current device is not sm_103a / sm_100 family          */
+} itergp_status;
+
+/* Kernel functions (App. C.1 / C.3 use GPyTorch's RBF and Matern-3/2 kernels):
+ *   RBF        k(r) = s exp(-r^2 / (2 l^2))
+ *   Matern-3/2 k(r) = s (1 + sqrt(3) r / l) exp(-sqrt(3) r / l)
+ * with r^2 = max(0, |a|^2 + |b|^2 - 2 a.b), lengthscale l > 0, outputscale s > 0. */
+typedef enum { ITERGP_RBF = 0, ITERGP_MATERN32 = 1 } itergp_kernel_kind;
+
+typedef struct {
+  int32_t kind;         /* itergp_kernel_kind */
+  float lengthscale;    /* l */
+  float outputscale;    /* s */
+} itergp_kernel;
+
+/* Arithmetic of the two contractions inside the kernel product (distance over D and the
+ * kernel-weighted sum over the data points).  Accumulation is FP32 in every mode.
+ *   ITERGP_FP32      plain FP32 SIMT (FFMA) for both contractions.
+ *   ITERGP_BF16X3    tensor cores; each operand split into BF16 hi + lo parts and each
+ *                    contraction formed from the three products hi*hi + hi*lo + lo*hi.
+ *                    FP32-level accuracy (normwise relative error ~1e-5).
+ *   ITERGP_BF16      tensor cores; one BF16 product per contraction; the squared distance
+ *                    uses the norms of the BF16-rounded rows.
+ *   ITERGP_BF16_COMP tensor cores; split-precision (3-product) distance with FP32 norms,
+ *                    one-product BF16 kernel-weighted sum. */
+typedef enum {
+  ITERGP_FP32 = 0,
+  ITERGP_BF16X3 = 1,
+  ITERGP_BF16 = 2,
+  ITERGP_BF16_COMP = 3
+} itergp_precision;
+
+typedef void* itergp_stream; /* cudaStream_t */
+
+/* ----------------------------------------------------------------------------------
+ * Kernel matrix times block of vectors (App. B.3.1 "Products with K"; Alg. 2 t_j = K s_j;
+ * Eq. 9 predictive mean).
+ *
+ *   Y[i, :] = sum_j k(A[i, :], B[j, :]) S[j, :]        i < m, j < n
+ *
+ * A: device, m x d FP32.  B: device, n x d FP32.  S: device, n x p FP32.
+ * Y: device, m x p FP32, overwritten (Y = 0 when n == 0).  k is never stored: each CTA
+ * evaluates tiles of it on the fly and contracts them with S.  m, n, p >= 0, d >= 1,
+ * d <= 4096, p <= 65536.  Y must not alias A, B or S.  Scratch (BF16 copies, norms,
+ * split partial sums) comes from the library's stream-ordered pool.
+ * Returns ITERGP_EINVAL for bad sizes/pointers, ITERGP_EUNSUPPORTED if a tensor-core
+ * precision is requested on a device without tcgen05. */
+int itergp_kmatvec(const itergp_kernel* kernel, int32_t precision, const float* A, int64_t m,
+                   const float* B, int64_t n, int64_t d, const float* S, int64_t p, float* Y,
+                   itergp_stream stream);
+
+/* ----------------------------------------------------------------------------------
+ * Softmax-likelihood building blocks (Alg. 1 lines "W(f)^-1" and "y_hat"; Lemma A.6).
+ * f, x, out: device, n x c FP32; y: device, n int32 labels in [0, c); c >= 2.
+ *
+ * itergp_winv_apply:     out_n = P diag(1/pi_n) P x_n,  pi_n = softmax(f_n),
+ *                        P = I - 11^T / c  (the pseudo-inverse W(f)^+ of Lemma A.6);
+ *                        1/pi is formed as exp(logsumexp(f_n) - f_n).
+ * itergp_pseudo_targets: out = f + W(f)^+ (onehot(y) - softmax(f))   (Alg. 1 / Eq. 6).
+ * Labels outside [0, c) set ITERGP_EINVAL in the device status word. */
+int itergp_winv_apply(const float* f, int64_t n, int32_t c, const float* x, float* out,
+                      itergp_stream stream);
+int itergp_pseudo_targets(const float* f, const int32_t* y, int64_t n, int32_t c, float* out,
+                          itergp_stream stream);
+
+/* ----------------------------------------------------------------------------------
+ * Symmetric eigendecomposition of the projected Gram matrix of Alg. 3 in FP64 on the
+ * device (cyclic Jacobi, one CTA).  M: device, b x b FP64 (only its symmetric part is
+ * used); lam: device, b FP64, eigenvalues in descending order (ties by index);
+ * U: device, b x b FP64 row-major, column k = eigenvector of lam[k].  1 <= b <= 512.
+ * M is not modified. */
+int itergp_sym_eig(const double* M, int32_t b, double* lam, double* U, itergp_stream stream);
+
+/* ----------------------------------------------------------------------------------
+ * IterNCGP fit (Alg. 1 with Alg. 2 inner solves and Alg. 3 recycling/compression).
+ * Prior mean m = 0 and f_0 = m (App. C.3); buffers start empty. */
+
+typedef enum { ITERGP_POLICY_CG = 0, ITERGP_POLICY_UNIT = 1 } itergp_policy;
+
+typedef enum {
+  ITERGP_STOP_MAXITER = 0,  /* inner solver ran max_iters iterations            */
+  ITERGP_STOP_TOL = 1,      /* |r| < max(tol_abs, tol_rel |y_hat - m|)  (App. B.2) */
+  ITERGP_STOP_ETA = 2       /* eta_j <= 0: action not kept                        */
+} itergp_stop_reason;
+
+typedef struct {
+  int64_t n;              /* number of training points, >= 1                       */
+  int64_t d;              /* input dimension, 1 .. 4096                            */
+  int32_t c;              /* number of classes, 2 .. 64                            */
+  const float* X;         /* device, n x d FP32 (copied into the model)           */
+  const int32_t* y;       /* device, n labels in [0, c)                           */
+  itergp_kernel kernel;
+  int32_t precision;      /* itergp_precision of every kernel product             */
+  int32_t policy;         /* itergp_policy: residual actions (CG) or unit vectors */
+  int32_t max_newton;     /* Newton steps (outer iterations), >= 1                */
+  int32_t max_iters;      /* solver iterations per Newton step (j_max), >= 0       */
+  int32_t rank;           /* compression limit R (Alg. 3); < 0 means no limit      */
+  int32_t recycle;        /* 1: virtual solver run (Alg. 3); 0: fresh buffers       */
+  int32_t literal_kv;     /* 0: K v_{j-1} is carried from the T buffer (one K product
+                             per iteration); 1: recomputed by a K product as printed
+                             in Alg. 2 (two per iteration, plus f_{i+1} = K v + m)  */
+  double tol_newton;      /* outer stop on |g_i - g_{i-1}| / |g_i| <= tol (<= 0: off)*/
+  double tol_abs;         /* inner stop, absolute (paper default 1e-5)             */
+  double tol_rel;         /* inner stop, relative to |y_hat - m| (default 1e-5)     */
+} itergp_fit_params;
+
+#define ITERGP_MAX_REPORT_STEPS 64
+
+typedef struct {
+  int32_t newton_steps;   /* Newton steps taken                                   */
+  int32_t total_iters;    /* solver iterations over all steps                     */
+  int32_t buffer_cols;    /* columns of S, T, Q at the end                        */
+  int32_t stop_reason;    /* of the last inner solve (itergp_stop_reason)         */
+  int32_t iters[ITERGP_MAX_REPORT_STEPS];       /* per Newton step                 */
+  int32_t stops[ITERGP_MAX_REPORT_STEPS];       /* per Newton step                 */
+  int32_t kept[ITERGP_MAX_REPORT_STEPS];        /* buffer columns after Alg. 3     */
+  double objective[ITERGP_MAX_REPORT_STEPS];    /* Psi(f_i), Eq. 2, per step       */
+  double rel_change[ITERGP_MAX_REPORT_STEPS];   /* |g_i - g_{i-1}|/|g_i| (i >= 1)  */
+  double resid_norm;      /* |r| at the last residual evaluation                   */
+  int64_t device_bytes;   /* bytes held by the model and its buffers              */
+} itergp_fit_report;
+
+typedef struct itergp_model itergp_model;
+
+/* Runs the whole fit on `stream` and waits for it (the report needs the device's
+ * counters).  On success *out owns device memory until itergp_model_free.
+ * Returns ITERGP_ENUMERIC if a non-finite value appeared during the fit. */
+int itergp_fit(const itergp_fit_params* params, itergp_model** out, itergp_fit_report* report,
+               itergp_stream stream);
+
+/* Posterior predictive of the fitted model (Eqs. 9-10 with C_j = Q Q^T) and the probit
+ * approximation of App. C.3:
+ *   mean[i, c]  = sum_n k(x*_i, x_n) v[n, c]
+ *   var[i, c]   = s - sum_b (sum_n k(x*_i, x_n) Q_b[n, c])^2
+ *   probs[i, :] = softmax(mean[i, :] / sqrt(1 + pi/8 var[i, :]))
+ * Xs: device, m x d FP32; mean: device m x c (required); var, probs: device m x c or
+ * NULL.  One fused kernel product against the stacked columns [v | Q]. */
+int itergp_predict(const itergp_model* model, const float* Xs, int64_t m, float* mean,
+                   float* var, float* probs, itergp_stream stream);
+
+/* Read-only view of the model's device arrays (valid until itergp_model_free). */
+typedef struct {
+  int64_t n, d;
+  int32_t c, buffer_cols;
+  itergp_kernel kernel;
+  const float* X;   /* n x d                                   */
+  const float* v;   /* n x c representer weights v_j           */
+  const float* f;   /* n x c latest Newton iterate f_{i+1}     */
+  const float* Q;   /* buffer_cols blocks of n x c: root of C_j */
+} itergp_model_view;
+
+int itergp_model_get_view(const itergp_model* model, itergp_model_view* view);
+void itergp_model_free(itergp_model* model);
+
+/* ----------------------------------------------------------------------------------
+ * Instrumentation (off by default).
+ * itergp_timing_enable(1): every launch of the fused kernel-product kernel (the tile
+ *   kernel inside itergp_kmatvec / itergp_fit / itergp_predict) is bracketed by a pair of
+ *   CUDA events recorded on the stream it is launched on.
+ * itergp_timing_read: waits for the recorded events, returns the summed device time (ms)
+ *   and number of those launches since the previous read, and clears them.
+ * itergp_launch_count: total number of CUDA kernels this library has launched in the
+ *   process (all kernels, not only the product). */
+int itergp_timing_enable(int enable);
+int itergp_timing_read(double* kernel_ms, int64_t* launches);
+int64_t itergp_launch_count(void);
+
+/* Waits for `stream`, then returns and clears the current device's status word:
+ * ITERGP_OK, ITERGP_ETIMEOUT, ITERGP_ENUMERIC or ITERGP_EINVAL (bad label). */
+int itergp_sync_status(itergp_stream stream);
+
+const char* itergp_status_string(int status);
+
+/* Library version "major.minor.patch". */
+const char* itergp_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* ITERGP_H_ */

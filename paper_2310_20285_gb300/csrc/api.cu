@@ -1,0 +1,434 @@
+// C-ABI entry points of libitergp: argument validation, per-device context, the model
+// object and the predictive epilogue.
+#include <algorithm>
+#include <cmath>
+#include <cstdlib>
+#include <cstring>
+#include <atomic>
+#include <mutex>
+#include <vector>
+
+#include "internal.h"
+
+namespace itergp {
+
+int fit_run(DeviceContext* ctx, const itergp_fit_params& prm, const KParams& kp,
+            const RowOperand& Xop, const int32_t* y, float* v, float* f, float* Q, int bcap,
+            cudaStream_t stream, itergp_fit_report* rep, int* final_B);
+int winv_apply_launch(DeviceContext* ctx, const float* f, int64_t n, int c, const float* x,
+                      float* out, cudaStream_t s);
+int pseudo_targets_launch(DeviceContext* ctx, const float* f, const int32_t* y, int64_t n, int c,
+                          float* out, cudaStream_t s);
+int sym_eig_launch(DeviceContext* ctx, const double* M, int b, double* lam, double* U,
+                   cudaStream_t s);
+
+void record_cuda_error(cudaError_t err, const char* expr, const char* file, int line) {
+  static const bool verbose = std::getenv("ITERGP_DEBUG") != nullptr;
+  if (verbose)
+    std::fprintf(stderr, "[itergp] %s failed: %s (%s:%d)\n", expr, cudaGetErrorString(err), file, line);
+}
+
+namespace {
+std::mutex g_ctx_mu;
+DeviceContext* g_ctx[64] = {};
+
+std::atomic<int64_t> g_launches{0};
+std::atomic<bool> g_timing{false};
+std::mutex g_timing_mu;
+std::vector<std::pair<cudaEvent_t, cudaEvent_t>> g_timed;   // recorded (begin, end) pairs
+thread_local cudaEvent_t t_begin = nullptr;
+}  // namespace
+
+void note_launch(int64_t n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+
+void timing_begin(cudaStream_t s) {
+  if (!g_timing.load(std::memory_order_relaxed)) return;
+  cudaEvent_t e;
+  if (cudaEventCreate(&e) != cudaSuccess) return;
+  cudaEventRecord(e, s);
+  t_begin = e;
+}
+
+void timing_end(cudaStream_t s) {
+  if (!t_begin) return;
+  cudaEvent_t e;
+  if (cudaEventCreate(&e) != cudaSuccess) return;
+  cudaEventRecord(e, s);
+  std::lock_guard<std::mutex> lk(g_timing_mu);
+  g_timed.emplace_back(t_begin, e);
+  t_begin = nullptr;
+}
+
+DeviceContext* current_context() {
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+  std::lock_guard<std::mutex> lk(g_ctx_mu);
+  if (g_ctx[dev]) return g_ctx[dev];
+  auto* c = new DeviceContext();
+  c->device = dev;
+  cudaDeviceProp prop;
+  if (cudaGetDeviceProperties(&prop, dev) != cudaSuccess) {
+    delete c;
+    return nullptr;
+  }
+  c->num_sms = prop.multiProcessorCount;
+  c->cc_major = prop.major;
+  c->cc_minor = prop.minor;
+  c->smem_optin = prop.sharedMemPerBlockOptin;
+  c->tcgen05 = (prop.major == 10);   // sm_100 / sm_103 family: tcgen05, TMEM, TMA
+  if (cudaMalloc(&c->status, sizeof(int)) != cudaSuccess || cudaMemset(c->status, 0, sizeof(int)) != cudaSuccess) {
+    delete c;
+    return nullptr;
+  }
+  cudaMemPoolProps props = {};
+  props.allocType = cudaMemAllocationTypePinned;
+  props.location.type = cudaMemLocationTypeDevice;
+  props.location.id = dev;
+  if (cudaMemPoolCreate(&c->pool, &props) != cudaSuccess) {
+    cudaFree(c->status);
+    delete c;
+    return nullptr;
+  }
+  uint64_t threshold = UINT64_MAX;
+  cudaMemPoolSetAttribute(c->pool, cudaMemPoolAttrReleaseThreshold, &threshold);
+  g_ctx[dev] = c;
+  return c;
+}
+
+cudaError_t scratch_alloc(DeviceContext* ctx, void** p, size_t bytes, cudaStream_t s) {
+  return cudaMallocFromPoolAsync(p, bytes, ctx->pool, s);
+}
+
+void scratch_free(void* p, cudaStream_t s) { cudaFreeAsync(p, s); }
+
+namespace {
+
+bool kernel_ok(const itergp_kernel* k) {
+  return k && (k->kind == ITERGP_RBF || k->kind == ITERGP_MATERN32) && std::isfinite(k->lengthscale) &&
+         k->lengthscale > 0.f && std::isfinite(k->outputscale) && k->outputscale > 0.f;
+}
+
+bool precision_ok(int p) { return p >= ITERGP_FP32 && p <= ITERGP_BF16_COMP; }
+
+// mean = Y[:, :C]; var_c = s - sum_b Y[:, C + b C + c]^2; probs = softmax(mean / sqrt(1 + pi/8 var))
+__global__ void predict_epilogue_kernel(const float* __restrict__ Y, int64_t m, int C, int B,
+                                        int64_t P, float s, float* __restrict__ mean,
+                                        float* __restrict__ var, float* __restrict__ probs) {
+  for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < m;
+       i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const float* yi = Y + i * P;
+    float mx = -INFINITY;
+    for (int c = 0; c < C; ++c) {
+      mean[i * C + c] = yi[c];
+      if (var || probs) {
+        float acc = 0.f;
+        for (int b = 0; b < B; ++b) {
+          const float q = yi[C + b * C + c];
+          acc = fmaf(q, q, acc);
+        }
+        const float vc = s - acc;
+        if (var) var[i * C + c] = vc;
+        if (probs) {
+          const float a = yi[c] / sqrtf(1.f + 0.39269908169872414f * vc);
+          probs[i * C + c] = a;
+          mx = fmaxf(mx, a);
+        }
+      }
+    }
+    if (probs) {
+      float se = 0.f;
+      for (int c = 0; c < C; ++c) {
+        const float e = expf(probs[i * C + c] - mx);
+        probs[i * C + c] = e;
+        se += e;
+      }
+      for (int c = 0; c < C; ++c) probs[i * C + c] /= se;
+    }
+  }
+}
+
+// S_view[n][col]: col < C -> v[n][col]; col = C + b C + c -> Q[b][n][c]
+__global__ void gather_vq_kernel(const float* __restrict__ v, const float* __restrict__ Q,
+                                 int64_t n, int C, int B, float* __restrict__ out) {
+  const int64_t P = static_cast<int64_t>(C) * (1 + B);
+  const int64_t total = n * P;
+  const int64_t nc = n * C;
+  for (int64_t e = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; e < total;
+       e += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const int64_t i = e / P, col = e % P;
+    float x;
+    if (col < C) {
+      x = v[i * C + col];
+    } else {
+      const int64_t b = (col - C) / C, c = (col - C) % C;
+      x = Q[b * nc + i * C + c];
+    }
+    out[e] = x;
+  }
+}
+
+}  // namespace
+}  // namespace itergp
+
+using namespace itergp;
+
+struct itergp_model {
+  int device = -1;
+  int64_t n = 0, d = 0;
+  int c = 0, bcap = 0, B = 0;
+  itergp_kernel kernel{};
+  int precision = 0;
+  void* mem = nullptr;
+  float* X = nullptr;
+  float* v = nullptr;
+  float* f = nullptr;
+  float* Q = nullptr;
+  RowOperand xop;
+  int64_t bytes = 0;
+};
+
+extern "C" {
+
+const char* itergp_version(void) { return "0.1.0"; }
+
+int itergp_timing_enable(int enable) {
+  g_timing.store(enable != 0);
+  return ITERGP_OK;
+}
+
+int itergp_timing_read(double* kernel_ms, int64_t* launches) {
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev;
+  {
+    std::lock_guard<std::mutex> lk(g_timing_mu);
+    ev.swap(g_timed);
+  }
+  double total = 0.0;
+  int rc = ITERGP_OK;
+  for (auto& pr : ev) {
+    float ms = 0.f;
+    if (cudaEventSynchronize(pr.second) != cudaSuccess ||
+        cudaEventElapsedTime(&ms, pr.first, pr.second) != cudaSuccess)
+      rc = ITERGP_ECUDA;
+    total += ms;
+    cudaEventDestroy(pr.first);
+    cudaEventDestroy(pr.second);
+  }
+  if (kernel_ms) *kernel_ms = total;
+  if (launches) *launches = static_cast<int64_t>(ev.size());
+  return rc;
+}
+
+int64_t itergp_launch_count(void) { return g_launches.load(); }
+
+const char* itergp_status_string(int status) {
+  switch (status) {
+    case ITERGP_OK: return "ok";
+    case ITERGP_EINVAL: return "invalid argument";
+    case ITERGP_ENOMEM: return "out of device memory";
+    case ITERGP_ECUDA: return "CUDA runtime error";
+    case ITERGP_ENUMERIC: return "non-finite value on the device";
+    case ITERGP_ETIMEOUT: return "device-side wait exceeded its bound";
+    case ITERGP_EUNSUPPORTED: return "unsupported device (needs sm_100 family / sm_103a)";
+    default: return "unknown status";
+  }
+}
+
+int itergp_sync_status(itergp_stream stream) {
+  DeviceContext* ctx = current_context();
+  if (!ctx) return ITERGP_ECUDA;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  ITERGP_CUDA_TRY(cudaStreamSynchronize(s));
+  int h = 0;
+  ITERGP_CUDA_TRY(cudaMemcpy(&h, ctx->status, sizeof(int), cudaMemcpyDeviceToHost));
+  ITERGP_CUDA_TRY(cudaMemset(ctx->status, 0, sizeof(int)));
+  return h;
+}
+
+int itergp_kmatvec(const itergp_kernel* kernel, int32_t precision, const float* A, int64_t m,
+                   const float* B, int64_t n, int64_t d, const float* S, int64_t p, float* Y,
+                   itergp_stream stream) {
+  if (!kernel_ok(kernel) || !precision_ok(precision)) return ITERGP_EINVAL;
+  if (m < 0 || n < 0 || p < 0 || d < 1 || d > 4096 || p > 65536) return ITERGP_EINVAL;
+  if (m == 0 || p == 0) return ITERGP_OK;
+  if (!Y || (n > 0 && (!A || !B || !S))) return ITERGP_EINVAL;
+  if (n > 0 && m > 0 && !A) return ITERGP_EINVAL;
+  DeviceContext* ctx = current_context();
+  if (!ctx) return ITERGP_ECUDA;
+  if (precision_is_tensor(precision) && !ctx->tcgen05) return ITERGP_EUNSUPPORTED;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const KParams kp = make_kparams(*kernel);
+  const bool same = (A == B) && (m == n);
+  const size_t ba = rows_workspace_bytes(precision, m, static_cast<int>(d));
+  const size_t bb = same ? 0 : rows_workspace_bytes(precision, n, static_cast<int>(d));
+  Scratch ws;
+  ITERGP_CUDA_TRY(ws.alloc(ctx, ba + bb, s));
+  RowOperand opA, opB;
+  int rc = prepare_rows(precision, A, m, static_cast<int>(d), d, ws.as<void>(), &opA, s);
+  if (rc != ITERGP_OK) return rc;
+  if (same) {
+    opB = opA;
+  } else {
+    rc = prepare_rows(precision, B, n, static_cast<int>(d), d, ws.as<char>(ba), &opB, s);
+    if (rc != ITERGP_OK) return rc;
+  }
+  return kmv_execute(ctx, kp, opA, opB, S, p, p, Y, p, s, nullptr);
+}
+
+int itergp_winv_apply(const float* f, int64_t n, int32_t c, const float* x, float* out,
+                      itergp_stream stream) {
+  if (n < 0 || c < 2 || c > 64) return ITERGP_EINVAL;
+  if (n > 0 && (!f || !x || !out)) return ITERGP_EINVAL;
+  DeviceContext* ctx = current_context();
+  if (!ctx) return ITERGP_ECUDA;
+  return winv_apply_launch(ctx, f, n, c, x, out, static_cast<cudaStream_t>(stream));
+}
+
+int itergp_pseudo_targets(const float* f, const int32_t* y, int64_t n, int32_t c, float* out,
+                          itergp_stream stream) {
+  if (n < 0 || c < 2 || c > 64) return ITERGP_EINVAL;
+  if (n > 0 && (!f || !y || !out)) return ITERGP_EINVAL;
+  DeviceContext* ctx = current_context();
+  if (!ctx) return ITERGP_ECUDA;
+  return pseudo_targets_launch(ctx, f, y, n, c, out, static_cast<cudaStream_t>(stream));
+}
+
+int itergp_sym_eig(const double* M, int32_t b, double* lam, double* U, itergp_stream stream) {
+  if (b < 1 || b > 512 || !M || !lam || !U) return ITERGP_EINVAL;
+  DeviceContext* ctx = current_context();
+  if (!ctx) return ITERGP_ECUDA;
+  return sym_eig_launch(ctx, M, b, lam, U, static_cast<cudaStream_t>(stream));
+}
+
+int itergp_fit(const itergp_fit_params* prm, itergp_model** out, itergp_fit_report* report,
+               itergp_stream stream) {
+  if (!prm || !out) return ITERGP_EINVAL;
+  *out = nullptr;
+  if (prm->n < 1 || prm->d < 1 || prm->d > 4096 || prm->c < 2 || prm->c > 64 || !prm->X || !prm->y)
+    return ITERGP_EINVAL;
+  if (!kernel_ok(&prm->kernel) || !precision_ok(prm->precision)) return ITERGP_EINVAL;
+  if (prm->policy != ITERGP_POLICY_CG && prm->policy != ITERGP_POLICY_UNIT) return ITERGP_EINVAL;
+  if (prm->max_newton < 1 || prm->max_iters < 0 || prm->max_newton > 100000) return ITERGP_EINVAL;
+  if (!(prm->tol_abs >= 0) || !(prm->tol_rel >= 0)) return ITERGP_EINVAL;
+  DeviceContext* ctx = current_context();
+  if (!ctx) return ITERGP_ECUDA;
+  if (precision_is_tensor(prm->precision) && !ctx->tcgen05) return ITERGP_EUNSUPPORTED;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+
+  const int64_t n = prm->n, nc = n * prm->c;
+  int64_t bcap = static_cast<int64_t>(prm->max_newton) * prm->max_iters;
+  if (prm->recycle && prm->rank >= 0) bcap = std::min<int64_t>(bcap, static_cast<int64_t>(prm->rank) + prm->max_iters);
+  if (!prm->recycle) bcap = std::min<int64_t>(bcap, prm->max_iters);
+  bcap = std::min<int64_t>(bcap, nc);
+  bcap = std::max<int64_t>(bcap, 1);
+  if (bcap > 512) return ITERGP_EINVAL;
+
+  auto* mdl = new itergp_model();
+  mdl->device = ctx->device;
+  mdl->n = n;
+  mdl->d = prm->d;
+  mdl->c = prm->c;
+  mdl->bcap = static_cast<int>(bcap);
+  mdl->kernel = prm->kernel;
+  mdl->precision = prm->precision;
+  const size_t xb = align_up(sizeof(float) * n * prm->d, 256);
+  const size_t rb = rows_workspace_bytes(prm->precision, n, static_cast<int>(prm->d));
+  const size_t vb = align_up(sizeof(float) * nc, 256);
+  const size_t qb = align_up(sizeof(float) * nc * bcap, 256);
+  mdl->bytes = static_cast<int64_t>(xb + rb + 2 * vb + qb);
+  if (cudaMalloc(&mdl->mem, mdl->bytes) != cudaSuccess) {
+    delete mdl;
+    return ITERGP_ENOMEM;
+  }
+  char* base = static_cast<char*>(mdl->mem);
+  mdl->X = reinterpret_cast<float*>(base);
+  mdl->v = reinterpret_cast<float*>(base + xb + rb);
+  mdl->f = reinterpret_cast<float*>(base + xb + rb + vb);
+  mdl->Q = reinterpret_cast<float*>(base + xb + rb + 2 * vb);
+  int rc = ITERGP_OK;
+  if (cudaMemcpyAsync(mdl->X, prm->X, sizeof(float) * n * prm->d, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+    rc = ITERGP_ECUDA;
+  if (rc == ITERGP_OK)
+    rc = prepare_rows(prm->precision, mdl->X, n, static_cast<int>(prm->d), prm->d, base + xb, &mdl->xop, s);
+  itergp_fit_report rep{};
+  int finalB = 0;
+  if (rc == ITERGP_OK)
+    rc = fit_run(ctx, *prm, make_kparams(prm->kernel), mdl->xop, prm->y, mdl->v, mdl->f, mdl->Q,
+                 static_cast<int>(bcap), s, &rep, &finalB);
+  if (rc == ITERGP_OK) {
+    const int st = itergp_sync_status(stream);
+    if (st != ITERGP_OK) rc = st;
+  }
+  if (rc != ITERGP_OK) {
+    cudaStreamSynchronize(s);
+    cudaFree(mdl->mem);
+    delete mdl;
+    return rc;
+  }
+  mdl->B = finalB;
+  rep.device_bytes = mdl->bytes;
+  if (report) *report = rep;
+  *out = mdl;
+  return ITERGP_OK;
+}
+
+int itergp_predict(const itergp_model* mdl, const float* Xs, int64_t m, float* mean, float* var,
+                   float* probs, itergp_stream stream) {
+  if (!mdl || m < 0 || (m > 0 && (!Xs || !mean))) return ITERGP_EINVAL;
+  if (m == 0) return ITERGP_OK;
+  DeviceContext* ctx = current_context();
+  if (!ctx) return ITERGP_ECUDA;
+  if (ctx->device != mdl->device) return ITERGP_EINVAL;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const int C = mdl->c;
+  const int B = (var || probs) ? mdl->B : 0;
+  const int64_t P = static_cast<int64_t>(C) * (1 + B);
+  const size_t rb = rows_workspace_bytes(mdl->precision, m, static_cast<int>(mdl->d));
+  const size_t sb = align_up(sizeof(float) * mdl->n * P, 256);
+  const size_t yb = align_up(sizeof(float) * m * P, 256);
+  Scratch ws;
+  ITERGP_CUDA_TRY(ws.alloc(ctx, rb + sb + yb, s));
+  RowOperand op;
+  int rc = prepare_rows(mdl->precision, Xs, m, static_cast<int>(mdl->d), mdl->d, ws.as<void>(), &op, s);
+  if (rc != ITERGP_OK) return rc;
+  float* Sv = ws.as<float>(rb);
+  float* Y = ws.as<float>(rb + sb);
+  {
+    const int64_t total = mdl->n * P;
+    const unsigned blocks = static_cast<unsigned>(std::min<int64_t>(ceil_div(total, 256), 8LL * ctx->num_sms));
+    gather_vq_kernel<<<blocks, 256, 0, s>>>(mdl->v, mdl->Q, mdl->n, C, B, Sv), ::itergp::note_launch();
+    ITERGP_CUDA_TRY(cudaGetLastError());
+  }
+  rc = kmv_execute(ctx, make_kparams(mdl->kernel), op, mdl->xop, Sv, P, P, Y, P, s, nullptr);
+  if (rc != ITERGP_OK) return rc;
+  const unsigned blocks = static_cast<unsigned>(std::min<int64_t>(ceil_div(m, 256), 8LL * ctx->num_sms));
+  predict_epilogue_kernel<<<blocks, 256, 0, s>>>(Y, m, C, B, P, mdl->kernel.outputscale, mean, var, probs), ::itergp::note_launch();
+  ITERGP_CUDA_TRY(cudaGetLastError());
+  return ITERGP_OK;
+}
+
+int itergp_model_get_view(const itergp_model* mdl, itergp_model_view* view) {
+  if (!mdl || !view) return ITERGP_EINVAL;
+  view->n = mdl->n;
+  view->d = mdl->d;
+  view->c = mdl->c;
+  view->buffer_cols = mdl->B;
+  view->kernel = mdl->kernel;
+  view->X = mdl->X;
+  view->v = mdl->v;
+  view->f = mdl->f;
+  view->Q = mdl->Q;
+  return ITERGP_OK;
+}
+
+void itergp_model_free(itergp_model* mdl) {
+  if (!mdl) return;
+  int prev = -1;
+  cudaGetDevice(&prev);
+  if (prev != mdl->device) cudaSetDevice(mdl->device);
+  cudaDeviceSynchronize();
+  cudaFree(mdl->mem);
+  if (prev >= 0 && prev != mdl->device) cudaSetDevice(prev);
+  delete mdl;
+}
+
+}  // extern "C"

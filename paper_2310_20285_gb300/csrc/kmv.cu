@@ -1,0 +1,130 @@
+// Operand preparation and dispatch of the kernel product Y = k(A, B) S.
+#include <algorithm>
+
+#include "internal.h"
+
+namespace itergp {
+namespace {
+
+// One warp per row: BF16 hi (and lo = bf16(x - hi)) copies zero-padded to d_pad, and the
+// squared row norm used by r^2 = |a|^2 + |b|^2 - 2 a.b.  NORM_ROUNDED selects the norm of
+// the BF16-rounded row, which keeps r^2 the exact distance between the rounded points
+// when the dot product is formed from the hi parts only.
+template <bool SPLIT, bool NORM_ROUNDED>
+__global__ void prep_rows_kernel(const float* __restrict__ X, int64_t ldX, int64_t rows, int d,
+                                 int64_t rows_pad, int d_pad, __nv_bfloat16* __restrict__ hi,
+                                 __nv_bfloat16* __restrict__ lo, float* __restrict__ norms) {
+  const int64_t row = static_cast<int64_t>(blockIdx.x) * (blockDim.x / 32) + threadIdx.x / 32;
+  const int lane = threadIdx.x % 32;
+  if (row >= rows_pad) return;
+  double acc = 0.0;
+  for (int col = lane; col < d_pad; col += 32) {
+    const float x = (row < rows && col < d) ? X[row * ldX + col] : 0.f;
+    const __nv_bfloat16 h = __float2bfloat16_rn(x);
+    const float hf = __bfloat162float(h);
+    hi[row * d_pad + col] = h;
+    if (SPLIT) lo[row * d_pad + col] = __float2bfloat16_rn(x - hf);
+    const float nv = NORM_ROUNDED ? hf : x;
+    acc += static_cast<double>(nv) * nv;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if (lane == 0) norms[row] = static_cast<float>(acc);
+}
+
+// FP32 path: squared row norms only.
+__global__ void row_norms_kernel(const float* __restrict__ X, int64_t ldX, int64_t rows, int d,
+                                 float* __restrict__ norms) {
+  const int64_t row = static_cast<int64_t>(blockIdx.x) * (blockDim.x / 32) + threadIdx.x / 32;
+  const int lane = threadIdx.x % 32;
+  if (row >= rows) return;
+  double acc = 0.0;
+  for (int col = lane; col < d; col += 32) {
+    const float x = X[row * ldX + col];
+    acc += static_cast<double>(x) * x;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if (lane == 0) norms[row] = static_cast<float>(acc);
+}
+
+__global__ void zero_rows_kernel(float* __restrict__ Y, int64_t m, int64_t p, int64_t ldY,
+                                 const int* __restrict__ active) {
+  if (active != nullptr && *active == 0) return;
+  const int64_t total = m * p;
+  for (int64_t e = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; e < total;
+       e += static_cast<int64_t>(gridDim.x) * blockDim.x)
+    Y[(e / p) * ldY + e % p] = 0.f;
+}
+
+}  // namespace
+
+size_t rows_workspace_bytes(int precision, int64_t rows, int d) {
+  const int64_t rows_pad = (rows + kRowTile - 1) / kRowTile * kRowTile;
+  size_t bytes = align_up(sizeof(float) * std::max<int64_t>(rows_pad, 1), 256);
+  if (precision_is_tensor(precision)) {
+    const int64_t d_pad = (d + 63) / 64 * 64;
+    const size_t plane = align_up(static_cast<size_t>(rows_pad) * d_pad * 2, 256);
+    bytes += plane * (precision_splits_rows(precision) ? 2 : 1);
+  }
+  return bytes;
+}
+
+int prepare_rows(int precision, const float* X, int64_t rows, int d, int64_t ldX, void* mem,
+                 RowOperand* op, cudaStream_t stream) {
+  op->X = X;
+  op->rows = rows;
+  op->d = d;
+  op->ldX = ldX;
+  op->precision = precision;
+  op->rows_pad = (rows + kRowTile - 1) / kRowTile * kRowTile;
+  char* base = static_cast<char*>(mem);
+  float* norms = reinterpret_cast<float*>(base);
+  op->norms = norms;
+  const size_t norm_bytes = align_up(sizeof(float) * std::max<int64_t>(op->rows_pad, 1), 256);
+  if (!precision_is_tensor(precision)) {
+    op->d_pad = d;
+    op->hi = op->lo = nullptr;
+    if (rows > 0) {
+      row_norms_kernel<<<static_cast<unsigned>(ceil_div(rows, 8)), 256, 0, stream>>>(X, ldX, rows, d, norms), ::itergp::note_launch();
+      ITERGP_CUDA_TRY(cudaGetLastError());
+    }
+    return ITERGP_OK;
+  }
+  op->d_pad = (d + 63) / 64 * 64;
+  const size_t plane = align_up(static_cast<size_t>(op->rows_pad) * op->d_pad * 2, 256);
+  __nv_bfloat16* hi = reinterpret_cast<__nv_bfloat16*>(base + norm_bytes);
+  __nv_bfloat16* lo = precision_splits_rows(precision)
+                          ? reinterpret_cast<__nv_bfloat16*>(base + norm_bytes + plane)
+                          : nullptr;
+  op->hi = hi;
+  op->lo = lo;
+  if (op->rows_pad == 0) return ITERGP_OK;
+  const unsigned blocks = static_cast<unsigned>(ceil_div(op->rows_pad, 8));
+  if (lo)
+    prep_rows_kernel<true, false><<<blocks, 256, 0, stream>>>(X, ldX, rows, d, op->rows_pad, op->d_pad, hi, lo, norms), ::itergp::note_launch();
+  else
+    prep_rows_kernel<false, true><<<blocks, 256, 0, stream>>>(X, ldX, rows, d, op->rows_pad, op->d_pad, hi, lo, norms), ::itergp::note_launch();
+  ITERGP_CUDA_TRY(cudaGetLastError());
+  return ITERGP_OK;
+}
+
+int kmv_execute(DeviceContext* ctx, const KParams& kp, const RowOperand& A, const RowOperand& B,
+                const float* S, int64_t ldS, int64_t p, float* Y, int64_t ldY,
+                cudaStream_t stream, const int* active) {
+  if (A.rows == 0 || p == 0) return ITERGP_OK;
+  if (B.rows == 0) {
+    const int64_t total = A.rows * p;
+    const unsigned blocks = static_cast<unsigned>(std::min<int64_t>(ceil_div(total, 256), 4096));
+    zero_rows_kernel<<<blocks, 256, 0, stream>>>(Y, A.rows, p, ldY, active), ::itergp::note_launch();
+    ITERGP_CUDA_TRY(cudaGetLastError());
+    return ITERGP_OK;
+  }
+  if (precision_is_tensor(A.precision)) {
+    if (!ctx->tcgen05) return ITERGP_EUNSUPPORTED;
+    return kmv_tc(ctx, kp, A, B, S, ldS, p, Y, ldY, stream, active);
+  }
+  return kmv_simt(ctx, kp, A, B, S, ldS, p, Y, ldY, stream, active);
+}
+
+}  // namespace itergp

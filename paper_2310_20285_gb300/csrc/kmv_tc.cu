@@ -1,0 +1,522 @@
+// Tensor-core kernel product Y = k(A, B) S for sm_103a (tcgen05 + TMEM + TMA).
+//
+// The product of App. B.3.1 is evaluated flash-style and K is never stored:
+//   for each CTA-owned (row tile of A, column chunk of B):
+//     G   = A_tile . B_chunk^T        tcgen05.mma, BF16 operands, FP32 accumulator in TMEM
+//     P   = k(|a|^2 + |b|^2 - 2 G)    epilogue warps: TMEM -> registers -> BF16 -> TMEM
+//     O  += P . S_chunk               tcgen05.mma with P read from TMEM (A operand)
+// Operands are staged by TMA with 128-byte swizzle.  Split precisions use BF16 hi/lo
+// parts: a.b ~ ah.bh + ah.bl + al.bh and P S ~ Ph Sh + Ph Sl + Pl Sh.
+//
+// Warp roles (256 threads): warp 0 issues TMA loads, warp 1 issues the MMAs (one thread),
+// warp 2 owns the TMEM allocation, warps 4-7 (one per TMEM lane quadrant) run the kernel
+// evaluation and the output stores.  TMEM columns: G0 [0,128), G1 [128,256) (double
+// buffer, P aliases the G it came from), O [256, 256 + p_tile).
+//
+// Work partition: U = row_tiles x column_chunks units, CTA g owns the contiguous range
+// [g U / G, (g+1) U / G).  A CTA accumulates O over a run of chunks of one row tile; a
+// run covering a whole row tile is stored directly, partial runs (at most the first and
+// last of a CTA) go to scratch and a fix-up kernel adds them in CTA order, so results
+// are deterministic.
+#include <algorithm>
+
+#include "internal.h"
+#include "tc_ptx.cuh"
+#include "tma_host.h"
+
+namespace itergp {
+namespace {
+
+constexpr int BM = 128;   // rows of A per tile (MMA M)
+constexpr int BN = 128;   // rows of B per chunk (MMA N of the distance GEMM, K of the product)
+constexpr int BK = 64;    // D slice per stage (one 128-byte swizzle row of BF16)
+constexpr int kThreads = 256;
+constexpr uint32_t kTmemCols = 512;
+constexpr uint32_t kOCol = 256;
+constexpr uint64_t kWaitLimitNs = 4000000000ull;   // 4 s per wait
+
+struct TcArgs {
+  const float* na;        // [A.rows_pad] row norms of A
+  const float* nb;        // [B.rows_pad] row norms of B
+  int64_t m;              // valid rows of A
+  int64_t units;          // row_tiles * chunks
+  int chunks;             // J
+  int nk;                 // D slices (d_pad / 64)
+  int p_pad;              // MMA N of the product (multiple of 16, <= 128)
+  int p_valid;            // valid output columns of this P tile
+  int s_row0;             // first row of this P tile in the transposed S
+  float* Y;               // output, already offset to the tile's first column
+  int64_t ldY;
+  float* partial;         // [2 G][BM][p_pad]
+  KParams kp;
+  int* status;
+  const int* active;
+};
+
+__host__ __device__ constexpr uint32_t stage_bytes(int nt1) {
+  return (nt1 == 3 ? 2u : 1u) * (BM * BK * 2u) + (nt1 == 3 ? 2u : 1u) * (BN * BK * 2u);
+}
+__host__ __device__ constexpr uint32_t s_box_bytes(int p_pad) { return static_cast<uint32_t>(p_pad) * 128u; }
+__host__ __device__ constexpr uint32_t s_buf_bytes(int nt2, int p_pad) {
+  return 2u * s_box_bytes(p_pad) * (nt2 == 3 ? 2u : 1u);
+}
+constexpr uint32_t kSmemExtra = 1024 /*alignment*/ + 2048 /*per-warp nb staging*/;
+
+template <int KIND, int NT1, int NT2, int NSTAGE>
+__global__ void __launch_bounds__(kThreads, 1)
+kmv_tc_kernel(const __grid_constant__ CUtensorMap mAh, const __grid_constant__ CUtensorMap mAl,
+              const __grid_constant__ CUtensorMap mBh, const __grid_constant__ CUtensorMap mBl,
+              const __grid_constant__ CUtensorMap mSh, const __grid_constant__ CUtensorMap mSl,
+              const TcArgs args) {
+  if (args.active != nullptr && *args.active == 0) return;
+  const int64_t G = gridDim.x, g = blockIdx.x;
+  const int64_t u_begin = part_start(g, args.units, G), u_end = part_start(g + 1, args.units, G);
+  if (u_begin >= u_end) return;
+  const int64_t T = u_end - u_begin;
+  const int J = args.chunks;
+
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
+                                             ~static_cast<uintptr_t>(1023));
+  constexpr uint32_t SB = stage_bytes(NT1);
+  constexpr uint32_t A_PART = BM * BK * 2, B_PART = BN * BK * 2;
+  const uint32_t SBOX = s_box_bytes(args.p_pad);
+  const uint32_t SBUF = s_buf_bytes(NT2, args.p_pad);
+  uint8_t* s_region = smem + NSTAGE * SB;
+  float* nb_all = reinterpret_cast<float*>(s_region + 2 * SBUF);   // [4 warps][128]
+
+  __shared__ __align__(8) uint64_t full_bar[NSTAGE], empty_bar[NSTAGE];
+  __shared__ __align__(8) uint64_t gfull[2], pfull[2], sfull[2], sempty[2], ofull, oempty, drain;
+  __shared__ uint32_t tmem_base_s;
+  __shared__ int abort_s;
+
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+  if (threadIdx.x == 0) {
+    abort_s = 0;
+    for (int i = 0; i < NSTAGE; ++i) {
+      mbar_init(&full_bar[i], 1);
+      mbar_init(&empty_bar[i], 1);
+    }
+    for (int i = 0; i < 2; ++i) {
+      mbar_init(&gfull[i], 1);
+      mbar_init(&pfull[i], 128);
+      mbar_init(&sfull[i], 1);
+      mbar_init(&sempty[i], 1);
+    }
+    mbar_init(&ofull, 1);
+    mbar_init(&oempty, 128);
+    mbar_init(&drain, 1);
+    fence_mbar_init();
+  }
+  if (warp == 2) {
+    tmem_alloc(&tmem_base_s, kTmemCols);
+    tmem_relinquish();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tb = tmem_base_s;
+  volatile int* ab = &abort_s;
+
+  if (warp == 0) {
+    // ------------------------------------------------------------------ TMA producer
+    if (lane == 0) {
+      tma_prefetch_desc(&mAh);
+      tma_prefetch_desc(&mBh);
+      tma_prefetch_desc(&mSh);
+      int stage = 0;
+      uint32_t phase = 0;
+      uint32_t armed = 0, armed_par = 0;      // bit i: stage i armed / parity of last arm
+      uint32_t s_armed = 0, s_par = 0;
+      for (int64_t t = 0; t < T && !*ab; ++t) {
+        const int64_t u = u_begin + t;
+        const int32_t a_y = static_cast<int32_t>((u / J) * BM);
+        const int32_t c = static_cast<int32_t>(u % J);
+        const int32_t b_y = c * BN;
+        for (int ks = 0; ks < args.nk; ++ks) {
+          if (!mbar_wait(&empty_bar[stage], phase ^ 1u, ab, kWaitLimitNs)) break;
+          mbar_arrive_expect_tx(&full_bar[stage], SB);
+          armed |= 1u << stage;
+          armed_par = (armed_par & ~(1u << stage)) | (phase << stage);
+          uint8_t* base = smem + stage * SB;
+          tma_load_2d(base, &mAh, &full_bar[stage], ks * BK, a_y);
+          if (NT1 == 3) tma_load_2d(base + A_PART, &mAl, &full_bar[stage], ks * BK, a_y);
+          uint8_t* bbase = base + (NT1 == 3 ? 2 : 1) * A_PART;
+          tma_load_2d(bbase, &mBh, &full_bar[stage], ks * BK, b_y);
+          if (NT1 == 3) tma_load_2d(bbase + B_PART, &mBl, &full_bar[stage], ks * BK, b_y);
+          if (++stage == NSTAGE) {
+            stage = 0;
+            phase ^= 1u;
+          }
+        }
+        if (*ab) break;
+        const int sb = static_cast<int>(t & 1);
+        if (!mbar_wait(&sempty[sb], static_cast<uint32_t>((t >> 1) & 1) ^ 1u, ab, kWaitLimitNs)) break;
+        mbar_arrive_expect_tx(&sfull[sb], SBUF);
+        s_armed |= 1u << sb;
+        s_par = (s_par & ~(1u << sb)) | (static_cast<uint32_t>((t >> 1) & 1) << sb);
+        uint8_t* sbase = s_region + sb * SBUF;
+        tma_load_2d(sbase, &mSh, &sfull[sb], b_y, args.s_row0);
+        tma_load_2d(sbase + SBOX, &mSh, &sfull[sb], b_y + 64, args.s_row0);
+        if (NT2 == 3) {
+          tma_load_2d(sbase + 2 * SBOX, &mSl, &sfull[sb], b_y, args.s_row0);
+          tma_load_2d(sbase + 3 * SBOX, &mSl, &sfull[sb], b_y + 64, args.s_row0);
+        }
+      }
+      if (*ab) {
+        // let every load this thread issued land before the CTA can exit
+        for (int i = 0; i < NSTAGE; ++i)
+          if (armed & (1u << i)) mbar_wait_drain(&full_bar[i], (armed_par >> i) & 1u, kWaitLimitNs);
+        for (int i = 0; i < 2; ++i)
+          if (s_armed & (1u << i)) mbar_wait_drain(&sfull[i], (s_par >> i) & 1u, kWaitLimitNs);
+      }
+    }
+  } else if (warp == 1) {
+    // ------------------------------------------------------------------ MMA issuer
+    if (lane == 0) {
+      const uint32_t idesc1 = idesc_bf16_f32(BM, BN);
+      const uint32_t idesc2 = idesc_bf16_f32(BM, static_cast<uint32_t>(args.p_pad));
+      int stage = 0;
+      uint32_t phase = 0;
+      int64_t seg = -1;
+      bool ok = true;
+      auto gemm2 = [&](int64_t t) -> bool {
+        const int64_t u = u_begin + t;
+        const int c = static_cast<int>(u % J);
+        const bool first = (t == 0) || (c == 0);
+        const bool last = (t == T - 1) || (c == J - 1);
+        if (first) {
+          ++seg;
+          if (seg >= 1 && !mbar_wait(&oempty, static_cast<uint32_t>((seg - 1) & 1), ab, kWaitLimitNs))
+            return false;
+        }
+        const int gb = static_cast<int>(t & 1);
+        const uint32_t par = static_cast<uint32_t>((t >> 1) & 1);
+        if (!mbar_wait(&pfull[gb], par, ab, kWaitLimitNs)) return false;
+        if (!mbar_wait(&sfull[gb], par, ab, kWaitLimitNs)) return false;
+        tc_fence_after();
+        const uint32_t sbase = smem_u32(s_region + gb * SBUF);
+#pragma unroll
+        for (int ks2 = 0; ks2 < BN / 16; ++ks2) {
+          const int grp = ks2 >> 1, h = ks2 & 1;
+          const uint32_t a_hi = tb + gb * BN + 32 * grp + 8 * h;
+          const uint32_t boff = static_cast<uint32_t>(ks2 >> 2) * SBOX;
+          const uint64_t koff = static_cast<uint64_t>((ks2 & 3) * 32) >> 4;
+          const uint64_t dSh = sdesc_kmajor_sw128(sbase + boff) + koff;
+          mma_ts(tb + kOCol, a_hi, dSh, idesc2, (first && ks2 == 0) ? 0u : 1u);
+          if (NT2 == 3) {
+            const uint64_t dSl = sdesc_kmajor_sw128(sbase + 2 * SBOX + boff) + koff;
+            mma_ts(tb + kOCol, a_hi, dSl, idesc2, 1u);
+            mma_ts(tb + kOCol, a_hi + 16, dSh, idesc2, 1u);
+          }
+        }
+        mma_commit(&sempty[gb]);
+        if (last) mma_commit(&ofull);
+        return true;
+      };
+      for (int64_t t = 0; t < T && ok; ++t) {
+        const int gb = static_cast<int>(t & 1);
+        const uint32_t gt = tb + gb * BN;
+        for (int ks = 0; ks < args.nk; ++ks) {
+          if (!mbar_wait(&full_bar[stage], phase, ab, kWaitLimitNs)) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t base = smem_u32(smem + stage * SB);
+          const uint32_t bbase = base + (NT1 == 3 ? 2 : 1) * A_PART;
+          const uint64_t dAh = sdesc_kmajor_sw128(base);
+          const uint64_t dBh = sdesc_kmajor_sw128(bbase);
+#pragma unroll
+          for (int kk = 0; kk < BK / 16; ++kk) {
+            const uint32_t acc = (ks | kk) != 0 ? 1u : 0u;
+            mma_ss(gt, dAh + 2 * kk, dBh + 2 * kk, idesc1, acc);
+            if (NT1 == 3) {
+              const uint64_t dAl = sdesc_kmajor_sw128(base + A_PART);
+              const uint64_t dBl = sdesc_kmajor_sw128(bbase + B_PART);
+              mma_ss(gt, dAh + 2 * kk, dBl + 2 * kk, idesc1, 1u);
+              mma_ss(gt, dAl + 2 * kk, dBh + 2 * kk, idesc1, 1u);
+            }
+          }
+          mma_commit(&empty_bar[stage]);
+          if (++stage == NSTAGE) {
+            stage = 0;
+            phase ^= 1u;
+          }
+        }
+        if (!ok) break;
+        mma_commit(&gfull[gb]);
+        if (t >= 1 && !gemm2(t - 1)) ok = false;
+      }
+      if (ok) gemm2(T - 1);
+      // all issued MMAs must retire before TMEM is released
+      mma_commit(&drain);
+      mbar_wait_drain(&drain, 0, kWaitLimitNs);
+    }
+  } else if (warp >= 4) {
+    // ------------------------------------------------------------------ epilogue
+    const int q = warp - 4;
+    const int row = 32 * q + lane;
+    const uint32_t lane_base = static_cast<uint32_t>(32 * q) << 16;
+    int64_t seg = -1;
+    int seg_c0 = 0;
+    float na_r = 0.f;
+    int64_t grow = 0;
+    const KParams kp = args.kp;
+    for (int64_t t = 0; t < T; ++t) {
+      const int64_t u = u_begin + t;
+      const int64_t r = u / J;
+      const int c = static_cast<int>(u % J);
+      const bool first = (t == 0) || (c == 0);
+      const bool last = (t == T - 1) || (c == J - 1);
+      if (first) {
+        ++seg;
+        seg_c0 = c;
+        grow = r * BM + row;
+        na_r = args.na[grow];
+      }
+      float* nb_s = nb_all + q * BN;
+      __syncwarp();
+#pragma unroll
+      for (int k = 0; k < BN / 32; ++k) nb_s[lane + 32 * k] = args.nb[static_cast<int64_t>(c) * BN + lane + 32 * k];
+      __syncwarp();
+      const int gb = static_cast<int>(t & 1);
+      if (!mbar_wait_warp(&gfull[gb], static_cast<uint32_t>((t >> 1) & 1), ab, kWaitLimitNs)) break;
+      tc_fence_after();
+      const uint32_t gcol = tb + lane_base + gb * BN;
+#pragma unroll 1
+      for (int grp = 0; grp < BN / 32; ++grp) {
+        uint32_t v[32];
+        tmem_ld32(gcol + 32 * grp, v);
+        tmem_ld_wait();
+        uint32_t ph[16], pl[16];
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+          const float r0 = fmaxf(fmaf(-2.f, __uint_as_float(v[2 * i]), na_r + nb_s[32 * grp + 2 * i]), 0.f);
+          const float r1 = fmaxf(fmaf(-2.f, __uint_as_float(v[2 * i + 1]), na_r + nb_s[32 * grp + 2 * i + 1]), 0.f);
+          const float k0 = kernel_eval_fast<KIND>(r0, kp);
+          const float k1 = kernel_eval_fast<KIND>(r1, kp);
+          ph[i] = pack_bf16x2(k0, k1);
+          if (NT2 == 3) {
+            const float h0 = __uint_as_float(ph[i] << 16);
+            const float h1 = __uint_as_float(ph[i] & 0xFFFF0000u);
+            pl[i] = pack_bf16x2(k0 - h0, k1 - h1);
+          }
+        }
+        tmem_st16(gcol + 32 * grp, ph);
+        if (NT2 == 3) tmem_st16(gcol + 32 * grp + 16, pl);
+      }
+      tmem_st_wait();
+      tc_fence_before();
+      mbar_arrive(&pfull[gb]);
+      if (last) {
+        if (!mbar_wait_warp(&ofull, static_cast<uint32_t>(seg & 1), ab, kWaitLimitNs)) break;
+        tc_fence_after();
+        const bool full_row = (seg_c0 == 0) && (c == J - 1);
+        float* dst;
+        int64_t ld;
+        bool valid;
+        if (full_row) {
+          dst = args.Y + grow * args.ldY;
+          ld = args.ldY;
+          valid = grow < args.m;
+        } else {
+          const int64_t slot = 2 * g + (seg == 0 ? 0 : 1);
+          dst = args.partial + (slot * BM + row) * args.p_pad;
+          ld = args.p_pad;
+          valid = true;
+        }
+        (void)ld;
+        for (int c16 = 0; c16 < args.p_pad / 16; ++c16) {
+          uint32_t o[16];
+          tmem_ld16(tb + lane_base + kOCol + 16 * c16, o);
+          tmem_ld_wait();
+          if (valid) {
+            const int lim = full_row ? args.p_valid : args.p_pad;
+#pragma unroll
+            for (int i = 0; i < 16; ++i)
+              if (16 * c16 + i < lim) dst[16 * c16 + i] = __uint_as_float(o[i]);
+          }
+        }
+        tc_fence_before();
+        mbar_arrive(&oempty);
+      }
+    }
+  }
+
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 2) {
+    tc_fence_after();
+    tmem_dealloc(tb, kTmemCols);
+  }
+  if (threadIdx.x == 0 && abort_s) atomicExch(args.status, ITERGP_ETIMEOUT);
+}
+
+// Adds the partial runs of row tiles shared by several CTAs, in CTA order.
+__global__ void tc_fixup_kernel(const float* __restrict__ partial, int64_t units, int64_t G, int J,
+                                int64_t m, int p_pad, int p_valid, float* __restrict__ Y,
+                                int64_t ldY, const int* __restrict__ active) {
+  if (active != nullptr && *active == 0) return;
+  const int64_t r = blockIdx.x;
+  const int64_t u0 = r * J, u1 = u0 + J - 1;
+  const int64_t g_lo = part_owner(u0, units, G), g_hi = part_owner(u1, units, G);
+  if (g_lo == g_hi) return;
+  for (int e = threadIdx.x; e < BM * p_valid; e += blockDim.x) {
+    const int row = e / p_valid, col = e % p_valid;
+    const int64_t grow = r * BM + row;
+    if (grow >= m) continue;
+    float acc = 0.f;
+    for (int64_t gg = g_lo; gg <= g_hi; ++gg) {
+      const int64_t slot = 2 * gg + (part_start(gg, units, G) < u0 ? 1 : 0);
+      acc += partial[(slot * BM + row) * p_pad + col];
+    }
+    Y[grow * ldY + col] = acc;
+  }
+}
+
+// S (n x p, row pitch ldS) -> transposed BF16 hi [p16][n_pad] (+ lo), zero padded.
+template <bool SPLIT>
+__global__ void prep_s_kernel(const float* __restrict__ S, int64_t ldS, int64_t n, int64_t p,
+                              int64_t n_pad, int64_t p16, __nv_bfloat16* __restrict__ hi,
+                              __nv_bfloat16* __restrict__ lo, const int* __restrict__ active) {
+  if (active != nullptr && *active == 0) return;
+  __shared__ float tile[32][33];
+  const int64_t j0 = static_cast<int64_t>(blockIdx.x) * 32, c0 = static_cast<int64_t>(blockIdx.y) * 32;
+  for (int i = threadIdx.y; i < 32; i += 8) {
+    const int64_t j = j0 + i, cc = c0 + threadIdx.x;
+    tile[i][threadIdx.x] = (j < n && cc < p) ? S[j * ldS + cc] : 0.f;
+  }
+  __syncthreads();
+  for (int i = threadIdx.y; i < 32; i += 8) {
+    const int64_t cc = c0 + i, j = j0 + threadIdx.x;
+    if (cc < p16 && j < n_pad) {
+      const float x = tile[threadIdx.x][i];
+      const __nv_bfloat16 h = __float2bfloat16_rn(x);
+      hi[cc * n_pad + j] = h;
+      if (SPLIT) lo[cc * n_pad + j] = __float2bfloat16_rn(x - __bfloat162float(h));
+    }
+  }
+}
+
+template <int KIND, int NT1, int NT2, int NSTAGE>
+cudaError_t launch_tc(int grid, size_t smem, cudaStream_t st, const CUtensorMap* maps,
+                      const TcArgs& a) {
+  auto fn = kmv_tc_kernel<KIND, NT1, NT2, NSTAGE>;
+  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  timing_begin(st);
+  fn<<<grid, kThreads, smem, st>>>(maps[0], maps[1], maps[2], maps[3], maps[4], maps[5], a), ::itergp::note_launch();
+  timing_end(st);
+  return cudaGetLastError();
+}
+
+template <int KIND, int NT1, int NT2>
+cudaError_t launch_stages(int nstage, int grid, size_t smem, cudaStream_t st,
+                          const CUtensorMap* maps, const TcArgs& a) {
+  switch (nstage) {
+    case 2: return launch_tc<KIND, NT1, NT2, 2>(grid, smem, st, maps, a);
+    case 3: return launch_tc<KIND, NT1, NT2, 3>(grid, smem, st, maps, a);
+    default: return launch_tc<KIND, NT1, NT2, 4>(grid, smem, st, maps, a);
+  }
+}
+
+template <int KIND>
+cudaError_t launch_prec(int prec, int nstage, int grid, size_t smem, cudaStream_t st,
+                        const CUtensorMap* maps, const TcArgs& a) {
+  switch (prec) {
+    case ITERGP_BF16X3: return launch_stages<KIND, 3, 3>(nstage, grid, smem, st, maps, a);
+    case ITERGP_BF16_COMP: return launch_stages<KIND, 3, 1>(nstage, grid, smem, st, maps, a);
+    default: return launch_stages<KIND, 1, 1>(nstage, grid, smem, st, maps, a);
+  }
+}
+
+}  // namespace
+
+int kmv_tc(DeviceContext* ctx, const KParams& kp, const RowOperand& A, const RowOperand& B,
+           const float* S, int64_t ldS, int64_t p, float* Y, int64_t ldY, cudaStream_t stream,
+           const int* active) {
+  const int prec = A.precision;
+  const int nt1 = precision_splits_rows(prec) ? 3 : 1;
+  const int nt2 = precision_splits_weights(prec) ? 3 : 1;
+  const size_t smem_cap = std::min<size_t>(ctx->smem_optin, 232448) - 2048;
+
+  // P tile: the largest multiple of 16 (<= 128) that leaves room for >= 2 stages.
+  const int64_t p16 = (p + 15) / 16 * 16;
+  int p_tile = static_cast<int>(std::min<int64_t>(p16, 128));
+  int nstage = 0;
+  for (; p_tile >= 16; p_tile -= 16) {
+    const size_t fixed = 2 * s_buf_bytes(nt2, p_tile) + kSmemExtra;
+    const size_t room = smem_cap > fixed ? smem_cap - fixed : 0;
+    nstage = static_cast<int>(std::min<size_t>(room / stage_bytes(nt1), 4));
+    if (nstage >= 2) break;
+  }
+  if (nstage < 2) return ITERGP_EUNSUPPORTED;
+  const size_t smem = nstage * stage_bytes(nt1) + 2 * s_buf_bytes(nt2, p_tile) + kSmemExtra;
+
+  // transposed, split S
+  const int64_t n_pad = B.rows_pad;
+  Scratch sbuf;
+  const size_t s_elems = static_cast<size_t>(p16) * n_pad;
+  ITERGP_CUDA_TRY(sbuf.alloc(ctx, s_elems * 2 * (nt2 == 3 ? 2 : 1), stream));
+  __nv_bfloat16* s_hi = sbuf.as<__nv_bfloat16>();
+  __nv_bfloat16* s_lo = nt2 == 3 ? s_hi + s_elems : nullptr;
+  {
+    dim3 grid(static_cast<unsigned>(n_pad / 32), static_cast<unsigned>(ceil_div(p16, 32)));
+    if (nt2 == 3)
+      prep_s_kernel<true><<<grid, dim3(32, 8), 0, stream>>>(S, ldS, B.rows, p, n_pad, p16, s_hi, s_lo, active), ::itergp::note_launch();
+    else
+      prep_s_kernel<false><<<grid, dim3(32, 8), 0, stream>>>(S, ldS, B.rows, p, n_pad, p16, s_hi, s_lo, active), ::itergp::note_launch();
+    ITERGP_CUDA_TRY(cudaGetLastError());
+  }
+
+  CUtensorMap maps[6];
+  bool ok = encode_bf16_sw128(&maps[0], A.hi, A.rows_pad, A.d_pad, A.d_pad, BM) &&
+            encode_bf16_sw128(&maps[1], nt1 == 3 ? A.lo : A.hi, A.rows_pad, A.d_pad, A.d_pad, BM) &&
+            encode_bf16_sw128(&maps[2], B.hi, B.rows_pad, B.d_pad, B.d_pad, BN) &&
+            encode_bf16_sw128(&maps[3], nt1 == 3 ? B.lo : B.hi, B.rows_pad, B.d_pad, B.d_pad, BN);
+  if (!ok) return ITERGP_ECUDA;
+
+  const int64_t row_tiles = ceil_div(A.rows, BM);
+  const int64_t chunks = ceil_div(B.rows, BN);
+  const int64_t units = row_tiles * chunks;
+  const int64_t G = std::min<int64_t>(ctx->num_sms, units);
+  Scratch part;
+  ITERGP_CUDA_TRY(part.alloc(ctx, sizeof(float) * 2 * G * BM * p_tile, stream));
+
+  for (int64_t p0 = 0; p0 < p; p0 += p_tile) {
+    const int pw = static_cast<int>(std::min<int64_t>(p_tile, p - p0));
+    const int pp = (pw + 15) / 16 * 16;
+    ok = encode_bf16_sw128(&maps[4], s_hi, p16, n_pad, n_pad, pp) &&
+         encode_bf16_sw128(&maps[5], nt2 == 3 ? s_lo : s_hi, p16, n_pad, n_pad, pp);
+    if (!ok) return ITERGP_ECUDA;
+    TcArgs a;
+    a.na = A.norms;
+    a.nb = B.norms;
+    a.m = A.rows;
+    a.units = units;
+    a.chunks = static_cast<int>(chunks);
+    a.nk = A.d_pad / BK;
+    a.p_pad = pp;
+    a.p_valid = pw;
+    a.s_row0 = static_cast<int>(p0);
+    a.Y = Y + p0;
+    a.ldY = ldY;
+    a.partial = part.as<float>();
+    a.kp = kp;
+    a.status = ctx->status;
+    a.active = active;
+    const size_t smem_t = nstage * stage_bytes(nt1) + 2 * s_buf_bytes(nt2, pp) + kSmemExtra;
+    (void)smem;
+    cudaError_t e = kp.kind == ITERGP_RBF
+                        ? launch_prec<ITERGP_RBF>(prec, nstage, (int)G, smem_t, stream, maps, a)
+                        : launch_prec<ITERGP_MATERN32>(prec, nstage, (int)G, smem_t, stream, maps, a);
+    ITERGP_CUDA_TRY(e);
+    tc_fixup_kernel<<<static_cast<unsigned>(row_tiles), 256, 0, stream>>>(
+        part.as<float>(), units, G, (int)chunks, A.rows, pp, pw, Y + p0, ldY, active), ::itergp::note_launch();
+    ITERGP_CUDA_TRY(cudaGetLastError());
+  }
+  return ITERGP_OK;
+}
+
+}  // namespace itergp

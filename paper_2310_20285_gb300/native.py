@@ -1,0 +1,267 @@
+"""ctypes binding of libitergp (the C ABI declared in include/itergp.h).
+
+Argument marshalling only: every step of the computation runs in the library's CUDA
+kernels.  PyTorch provides device memory and the current CUDA stream.  If the shared
+library is missing this module raises at import; there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes as ct
+import os
+
+import torch
+
+_LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libitergp.so")
+
+OK, EINVAL, ENOMEM, ECUDA, ENUMERIC, ETIMEOUT, EUNSUPPORTED = 0, -1, -2, -3, -4, -5, -6
+RBF, MATERN32 = 0, 1
+FP32, BF16X3, BF16, BF16_COMP = 0, 1, 2, 3
+POLICY_CG, POLICY_UNIT = 0, 1
+STOP_MAXITER, STOP_TOL, STOP_ETA = 0, 1, 2
+MAX_REPORT_STEPS = 64
+
+PRECISIONS = {"fp32": FP32, "bf16x3": BF16X3, "bf16": BF16, "bf16_comp": BF16_COMP}
+KERNELS = {"rbf": RBF, "matern32": MATERN32}
+
+
+class ItergpError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        super().__init__(f"{where}: {status_string(code)} ({code})")
+        self.code = code
+
+
+class Kernel(ct.Structure):
+    _fields_ = [("kind", ct.c_int32), ("lengthscale", ct.c_float), ("outputscale", ct.c_float)]
+
+
+class FitParams(ct.Structure):
+    _fields_ = [("n", ct.c_int64), ("d", ct.c_int64), ("c", ct.c_int32),
+                ("X", ct.c_void_p), ("y", ct.c_void_p), ("kernel", Kernel),
+                ("precision", ct.c_int32), ("policy", ct.c_int32),
+                ("max_newton", ct.c_int32), ("max_iters", ct.c_int32), ("rank", ct.c_int32),
+                ("recycle", ct.c_int32), ("literal_kv", ct.c_int32),
+                ("tol_newton", ct.c_double), ("tol_abs", ct.c_double), ("tol_rel", ct.c_double)]
+
+
+class FitReport(ct.Structure):
+    _fields_ = [("newton_steps", ct.c_int32), ("total_iters", ct.c_int32),
+                ("buffer_cols", ct.c_int32), ("stop_reason", ct.c_int32),
+                ("iters", ct.c_int32 * MAX_REPORT_STEPS), ("stops", ct.c_int32 * MAX_REPORT_STEPS),
+                ("kept", ct.c_int32 * MAX_REPORT_STEPS),
+                ("objective", ct.c_double * MAX_REPORT_STEPS),
+                ("rel_change", ct.c_double * MAX_REPORT_STEPS),
+                ("resid_norm", ct.c_double), ("device_bytes", ct.c_int64)]
+
+
+class ModelView(ct.Structure):
+    _fields_ = [("n", ct.c_int64), ("d", ct.c_int64), ("c", ct.c_int32),
+                ("buffer_cols", ct.c_int32), ("kernel", Kernel),
+                ("X", ct.c_void_p), ("v", ct.c_void_p), ("f", ct.c_void_p), ("Q", ct.c_void_p)]
+
+
+def _load():
+    if not os.path.exists(_LIB_PATH):
+        raise ImportError(f"libitergp.so not built ({_LIB_PATH}); run "
+                          "`python -c 'import __graft_entry__ as g; g.build()'`")
+    lib = ct.CDLL(_LIB_PATH)
+    vp, i64, i32 = ct.c_void_p, ct.c_int64, ct.c_int32
+    lib.itergp_kmatvec.argtypes = [ct.POINTER(Kernel), i32, vp, i64, vp, i64, i64, vp, i64, vp, vp]
+    lib.itergp_winv_apply.argtypes = [vp, i64, i32, vp, vp, vp]
+    lib.itergp_pseudo_targets.argtypes = [vp, vp, i64, i32, vp, vp]
+    lib.itergp_sym_eig.argtypes = [vp, i32, vp, vp, vp]
+    lib.itergp_fit.argtypes = [ct.POINTER(FitParams), ct.POINTER(vp), ct.POINTER(FitReport), vp]
+    lib.itergp_predict.argtypes = [vp, vp, i64, vp, vp, vp, vp]
+    lib.itergp_model_get_view.argtypes = [vp, ct.POINTER(ModelView)]
+    lib.itergp_model_free.argtypes = [vp]
+    lib.itergp_model_free.restype = None
+    lib.itergp_sync_status.argtypes = [vp]
+    lib.itergp_status_string.argtypes = [i32]
+    lib.itergp_status_string.restype = ct.c_char_p
+    lib.itergp_version.restype = ct.c_char_p
+    lib.itergp_timing_enable.argtypes = [ct.c_int]
+    lib.itergp_timing_read.argtypes = [ct.POINTER(ct.c_double), ct.POINTER(ct.c_int64)]
+    lib.itergp_launch_count.restype = ct.c_int64
+    lib.itergp_launch_count.argtypes = []
+    for name in ("itergp_kmatvec", "itergp_winv_apply", "itergp_pseudo_targets",
+                 "itergp_sym_eig", "itergp_fit", "itergp_predict", "itergp_model_get_view",
+                 "itergp_sync_status"):
+        getattr(lib, name).restype = ct.c_int
+    return lib
+
+
+lib = _load()
+
+
+def status_string(code: int) -> str:
+    return lib.itergp_status_string(int(code)).decode()
+
+
+def _check(code: int, where: str):
+    if code != OK:
+        raise ItergpError(code, where)
+
+
+def _stream(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ct.c_void_p(s.cuda_stream)
+
+
+def _dev(t: torch.Tensor, dtype, name: str):
+    if not isinstance(t, torch.Tensor) or not t.is_cuda or t.dtype != dtype or not t.is_contiguous():
+        raise ValueError(f"{name} must be a contiguous CUDA tensor of {dtype}")
+    return ct.c_void_p(t.data_ptr())
+
+
+def _kernel(kind, lengthscale, outputscale) -> Kernel:
+    k = KERNELS[kind] if isinstance(kind, str) else int(kind)
+    return Kernel(k, float(lengthscale), float(outputscale))
+
+
+def _prec(p) -> int:
+    return PRECISIONS[p] if isinstance(p, str) else int(p)
+
+
+def kmatvec(A, B, S, kind="rbf", lengthscale=1.0, outputscale=1.0, precision="fp32",
+            out=None, stream=None):
+    """Y = k(A, B) @ S on the GPU, k never stored.  A: m x d, B: n x d, S: n x p (float32)."""
+    m, d = A.shape
+    n = B.shape[0]
+    p = S.shape[1]
+    if out is None:
+        out = torch.empty((m, p), device=A.device, dtype=torch.float32)
+    k = _kernel(kind, lengthscale, outputscale)
+    rc = lib.itergp_kmatvec(ct.byref(k), _prec(precision), _dev(A, torch.float32, "A"), m,
+                            _dev(B, torch.float32, "B"), n, d, _dev(S, torch.float32, "S"), p,
+                            _dev(out, torch.float32, "out"), _stream(stream))
+    _check(rc, "itergp_kmatvec")
+    return out
+
+
+def winv_apply(f, x, out=None, stream=None):
+    n, c = f.shape
+    out = torch.empty_like(x) if out is None else out
+    _check(lib.itergp_winv_apply(_dev(f, torch.float32, "f"), n, c, _dev(x, torch.float32, "x"),
+                                 _dev(out, torch.float32, "out"), _stream(stream)), "itergp_winv_apply")
+    return out
+
+
+def pseudo_targets(f, y, out=None, stream=None):
+    n, c = f.shape
+    out = torch.empty_like(f) if out is None else out
+    _check(lib.itergp_pseudo_targets(_dev(f, torch.float32, "f"), _dev(y, torch.int32, "y"), n, c,
+                                     _dev(out, torch.float32, "out"), _stream(stream)),
+           "itergp_pseudo_targets")
+    return out
+
+
+def sym_eig(M, stream=None):
+    b = M.shape[0]
+    lam = torch.empty(b, device=M.device, dtype=torch.float64)
+    U = torch.empty((b, b), device=M.device, dtype=torch.float64)
+    _check(lib.itergp_sym_eig(_dev(M, torch.float64, "M"), b, _dev(lam, torch.float64, "lam"),
+                              _dev(U, torch.float64, "U"), _stream(stream)), "itergp_sym_eig")
+    return lam, U
+
+
+def timing_enable(on: bool = True):
+    """Bracket every fused kernel-product launch with CUDA events on its stream."""
+    lib.itergp_timing_enable(1 if on else 0)
+
+
+def timing_read():
+    """(summed device ms, number of fused kernel-product launches) since the last read."""
+    ms, n = ct.c_double(), ct.c_int64()
+    _check(lib.itergp_timing_read(ct.byref(ms), ct.byref(n)), "itergp_timing_read")
+    return ms.value, n.value
+
+
+def launch_count() -> int:
+    """Total kernels the library has launched in this process."""
+    return int(lib.itergp_launch_count())
+
+
+def sync_status(stream=None) -> int:
+    return int(lib.itergp_sync_status(_stream(stream)))
+
+
+class Model:
+    """A fitted IterNCGP model living in device memory (owned by the library)."""
+
+    def __init__(self, handle: ct.c_void_p, report: FitReport, device):
+        self._h = handle
+        self.report = report
+        self.device = device
+
+    def view(self) -> ModelView:
+        v = ModelView()
+        _check(lib.itergp_model_get_view(self._h, ct.byref(v)), "itergp_model_get_view")
+        return v
+
+    def _wrap(self, ptr, shape):
+        """Copy a device array owned by the model into a new torch tensor."""
+        if any(x == 0 for x in shape):
+            return torch.empty(shape, device=self.device, dtype=torch.float32)
+        view = torch.as_tensor(_CudaArray(ptr, shape), device=self.device)
+        return view.clone()
+
+    def arrays(self):
+        v = self.view()
+        n, c, B = v.n, v.c, v.buffer_cols
+        return {"v": self._wrap(v.v, (n, c)), "f": self._wrap(v.f, (n, c)),
+                "Q": self._wrap(v.Q, (B, n, c))}
+
+    def predict(self, Xs, want_var=True, want_probs=True, stream=None):
+        m = Xs.shape[0]
+        c = self.view().c
+        mean = torch.empty((m, c), device=Xs.device, dtype=torch.float32)
+        var = torch.empty_like(mean) if want_var else None
+        probs = torch.empty_like(mean) if want_probs else None
+        rc = lib.itergp_predict(self._h, _dev(Xs, torch.float32, "Xs"), m,
+                                _dev(mean, torch.float32, "mean"),
+                                None if var is None else _dev(var, torch.float32, "var"),
+                                None if probs is None else _dev(probs, torch.float32, "probs"),
+                                _stream(stream))
+        _check(rc, "itergp_predict")
+        return mean, var, probs
+
+    def free(self):
+        if self._h:
+            lib.itergp_model_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+class _CudaArray:
+    """Minimal __cuda_array_interface__ holder for a float32 device array."""
+
+    def __init__(self, ptr: int, shape):
+        self.__cuda_array_interface__ = {"shape": tuple(int(x) for x in shape), "typestr": "<f4",
+                                         "data": (int(ptr), True), "version": 3, "strides": None}
+
+
+def fit(X, y, c, kind="rbf", lengthscale=1.0, outputscale=1.0, precision="fp32",
+        policy="cg", max_newton=10, max_iters=50, rank=-1, recycle=True, literal_kv=False,
+        tol_newton=0.0, tol_abs=1e-5, tol_rel=1e-5, stream=None) -> Model:
+    """IterNCGP fit (Alg. 1-3) of a softmax GP classifier on the GPU."""
+    n, d = X.shape
+    prm = FitParams()
+    prm.n, prm.d, prm.c = n, d, int(c)
+    prm.X = _dev(X, torch.float32, "X").value
+    prm.y = _dev(y, torch.int32, "y").value
+    prm.kernel = _kernel(kind, lengthscale, outputscale)
+    prm.precision = _prec(precision)
+    prm.policy = POLICY_CG if policy in ("cg", POLICY_CG) else POLICY_UNIT
+    prm.max_newton, prm.max_iters = int(max_newton), int(max_iters)
+    prm.rank = -1 if rank is None else int(rank)
+    prm.recycle, prm.literal_kv = int(bool(recycle)), int(bool(literal_kv))
+    prm.tol_newton, prm.tol_abs, prm.tol_rel = float(tol_newton), float(tol_abs), float(tol_rel)
+    h = ct.c_void_p()
+    rep = FitReport()
+    rc = lib.itergp_fit(ct.byref(prm), ct.byref(h), ct.byref(rep), _stream(stream))
+    _check(rc, "itergp_fit")
+    return Model(h, rep, X.device)

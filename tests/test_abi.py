@@ -1,0 +1,109 @@
+"""The C-ABI library loads and exports every symbol include/itergp.h declares; host-side
+argument validation rejects bad input before any launch (no GPU needed)."""
+import ctypes as ct
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "itergp.h")
+LIB = os.path.join(ROOT, "paper_2310_20285_gb300", "libitergp.so")
+
+
+def declared_functions():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(itergp_[a-z_0-9]+)\s*\(", src)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    if not os.path.exists(LIB):
+        from paper_2310_20285_gb300 import build
+        build.build()
+    return ct.CDLL(LIB)
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for required in ("itergp_fit", "itergp_kmatvec", "itergp_predict", "itergp_model_free",
+                     "itergp_status_string"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    missing = [n for n in declared_functions() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_status_strings(lib):
+    lib.itergp_status_string.restype = ct.c_char_p
+    lib.itergp_status_string.argtypes = [ct.c_int]
+    assert lib.itergp_status_string(0) == b"ok"
+    assert b"bound" in lib.itergp_status_string(-5)
+    assert lib.itergp_status_string(12345) == b"unknown status"
+
+
+class Kernel(ct.Structure):
+    _fields_ = [("kind", ct.c_int32), ("lengthscale", ct.c_float), ("outputscale", ct.c_float)]
+
+
+@pytest.mark.parametrize("kind,ell,s,prec,m,n,d,p", [
+    (7, 1.0, 1.0, 0, 4, 4, 2, 1),      # unknown kernel
+    (0, 0.0, 1.0, 0, 4, 4, 2, 1),      # zero lengthscale
+    (0, 1.0, -1.0, 0, 4, 4, 2, 1),     # negative outputscale
+    (0, 1.0, 1.0, 9, 4, 4, 2, 1),      # unknown precision
+    (0, 1.0, 1.0, 0, -1, 4, 2, 1),     # negative m
+    (0, 1.0, 1.0, 0, 4, 4, 0, 1),      # d = 0
+    (0, 1.0, 1.0, 0, 4, 4, 5000, 1),   # d too large
+])
+def test_kmatvec_rejects_bad_arguments_on_the_host(lib, kind, ell, s, prec, m, n, d, p):
+    k = Kernel(kind, ell, s)
+    f = lib.itergp_kmatvec
+    f.restype = ct.c_int
+    f.argtypes = [ct.POINTER(Kernel), ct.c_int32, ct.c_void_p, ct.c_int64, ct.c_void_p, ct.c_int64,
+                  ct.c_int64, ct.c_void_p, ct.c_int64, ct.c_void_p, ct.c_void_p]
+    dummy = ct.c_void_p(16)
+    assert f(ct.byref(k), prec, dummy, m, dummy, n, d, dummy, p, dummy, None) == -1
+
+
+def test_kmatvec_null_output_rejected(lib):
+    k = Kernel(0, 1.0, 1.0)
+    f = lib.itergp_kmatvec
+    f.restype = ct.c_int
+    f.argtypes = [ct.POINTER(Kernel), ct.c_int32, ct.c_void_p, ct.c_int64, ct.c_void_p, ct.c_int64,
+                  ct.c_int64, ct.c_void_p, ct.c_int64, ct.c_void_p, ct.c_void_p]
+    dummy = ct.c_void_p(16)
+    assert f(ct.byref(k), 0, dummy, 4, dummy, 4, 2, dummy, 3, None, None) == -1
+
+
+def test_fit_rejects_bad_arguments_on_the_host(lib):
+    from paper_2310_20285_gb300.native import FitParams, FitReport, Kernel as K
+    f = lib.itergp_fit
+    f.restype = ct.c_int
+    f.argtypes = [ct.POINTER(FitParams), ct.POINTER(ct.c_void_p), ct.POINTER(FitReport), ct.c_void_p]
+    base = dict(n=10, d=2, c=3, X=16, y=16, kernel=K(0, 1.0, 1.0), precision=0, policy=0,
+                max_newton=1, max_iters=1, rank=-1, recycle=1, literal_kv=0, tol_newton=0.0,
+                tol_abs=1e-5, tol_rel=1e-5)
+    for bad in (dict(n=0), dict(c=1), dict(c=65), dict(d=0), dict(X=None), dict(y=None),
+                dict(policy=5), dict(max_newton=0), dict(max_iters=-1), dict(precision=8),
+                dict(kernel=K(0, -1.0, 1.0)), dict(tol_abs=-1.0)):
+        prm = FitParams(**{**base, **bad})
+        h = ct.c_void_p()
+        assert f(ct.byref(prm), ct.byref(h), None, None) == -1, bad
+        assert not h.value
+    assert f(None, None, None, None) == -1
+
+
+def test_predict_rejects_null_model(lib):
+    f = lib.itergp_predict
+    f.restype = ct.c_int
+    f.argtypes = [ct.c_void_p] * 7
+    assert f(None, ct.c_void_p(16), 3, ct.c_void_p(16), None, None, None) == -1
+
+
+def test_model_free_accepts_null(lib):
+    lib.itergp_model_free.argtypes = [ct.c_void_p]
+    lib.itergp_model_free.restype = None
+    lib.itergp_model_free(None)

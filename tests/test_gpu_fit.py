@@ -1,0 +1,229 @@
+"""Parity of the CUDA IterNCGP fit (Alg. 1-3), its building blocks (Lemma A.6 W^+,
+Alg. 1 pseudo targets, Alg. 3 eigendecomposition) and the predictive (Eqs. 9-10, probit)
+against the FP64 oracle.  FP32 paths: relative error <= 1e-4; BF16 paths: predictive mean
+within 1e-2."""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import oracle.itergp_oracle as O
+from paper_2310_20285_gb300 import datagen
+
+pytestmark = pytest.mark.gpu
+DEV = torch.device("cuda:0")
+
+
+def t32(x):
+    return torch.as_tensor(np.ascontiguousarray(x), dtype=torch.float32, device=DEV)
+
+
+def rel(a, b):
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+# ------------------------------------------------------------------- building blocks
+
+@pytest.mark.parametrize("c", [2, 3, 10, 64])
+def test_winv_apply_matches_lemma_a6(native, c):
+    g = np.random.default_rng(c)
+    n = 1000 + c
+    f = (2 * g.standard_normal((n, c))).astype(np.float32)
+    x = g.standard_normal((n, c)).astype(np.float32)
+    out = native.winv_apply(t32(f), t32(x)).cpu().numpy()
+    assert native.sync_status() == 0
+    lik = O.Softmax(np.zeros(n, int), c)
+    ref = lik.Winv_apply(f.astype(np.float64), x.astype(np.float64))
+    assert rel(out, ref) <= 1e-4
+    assert np.allclose(out.sum(axis=1), 0.0, atol=1e-3 * np.abs(out).max())
+
+
+@pytest.mark.parametrize("c", [2, 3, 10])
+def test_pseudo_targets_match_alg1(native, c):
+    g = np.random.default_rng(10 + c)
+    n = 777
+    f = g.standard_normal((n, c)).astype(np.float32)
+    y = g.integers(0, c, n).astype(np.int32)
+    out = native.pseudo_targets(t32(f), torch.as_tensor(y, device=DEV)).cpu().numpy()
+    assert native.sync_status() == 0
+    ref = O.pseudo_targets(O.Softmax(y, c), f.astype(np.float64))
+    assert rel(out, ref) <= 1e-4
+
+
+def test_bad_label_sets_device_status(native):
+    f = t32(np.zeros((4, 3)))
+    y = torch.tensor([0, 1, 7, 2], dtype=torch.int32, device=DEV)
+    native.pseudo_targets(f, y)
+    assert native.sync_status() == native.EINVAL
+    assert native.sync_status() == 0      # cleared
+
+
+@pytest.mark.parametrize("b", [1, 2, 7, 33, 100])
+def test_sym_eig_fp64(native, b):
+    g = np.random.default_rng(b)
+    A = g.standard_normal((b, b))
+    M = A @ A.T + np.diag(np.linspace(0, 3, b))
+    lam, U = native.sym_eig(torch.as_tensor(M, device=DEV))
+    lam, U = lam.cpu().numpy(), U.cpu().numpy()
+    ref = np.sort(np.linalg.eigvalsh(M))[::-1]
+    assert np.allclose(lam, ref, rtol=1e-10, atol=1e-10 * ref[0])
+    assert np.allclose(U.T @ U, np.eye(b), atol=1e-10)
+    assert np.allclose(M @ U, U * lam[None, :], atol=1e-9 * ref[0])
+
+
+# ------------------------------------------------------------------- fit + predict
+
+SMALL_KERN = dict(kind="rbf", lengthscale=1.0, outputscale=1.0)
+
+
+def oracle_fit(X, y, c, kern, **kw):
+    return O.iterncgp_fit(X.astype(np.float32).astype(np.float64), O.Softmax(y, c), c, kern, **kw)
+
+
+def gpu_fit(native, X, y, c, **kw):
+    args = dict(SMALL_KERN)
+    args.update(kw)
+    m = native.fit(t32(X), torch.as_tensor(y, dtype=torch.int32, device=DEV), c, **args)
+    return m
+
+
+def test_fit_fixed_schedule_with_truncation_matches_oracle(native):
+    """Small workload, 10 Newton steps x 12 iterations, R = 50 (truncation from step 5)."""
+    X, y, Xs, ys = datagen.workload_small()
+    kern = O.Kernel(O.RBF, 1.0, 1.0)
+    ref = oracle_fit(X, y, 3, kern, max_newton=10, max_iters=12, R=50, tol_abs=0, tol_rel=0)
+    m = gpu_fit(native, X, y, 3, max_newton=10, max_iters=12, rank=50, tol_abs=0.0, tol_rel=0.0)
+    rep = m.report
+    assert rep.newton_steps == 10
+    assert [rep.iters[i] for i in range(10)] == [inf.iters for inf in ref.infos]
+    assert [rep.kept[i] for i in range(1, 10)] == [inf.B0 for inf in ref.infos[1:]]
+    arr = m.arrays()
+    assert rel(arr["f"].cpu(), ref.f) <= 1e-4
+    assert rel(arr["v"].cpu(), ref.v) <= 1e-4
+    for i in range(10):
+        assert abs(rep.objective[i] - ref.objectives[i]) <= 1e-4 * abs(ref.objectives[i])
+    # C_j = Q Q^T on probe vectors (basis independent)
+    Qg = arr["Q"].cpu().numpy().reshape(arr["Q"].shape[0], -1).T.astype(np.float64)
+    w = np.random.default_rng(0).standard_normal((Qg.shape[0], 4))
+    assert rel(Qg @ (Qg.T @ w), ref.Q @ (ref.Q.T @ w)) <= 1e-4
+    mean, var, probs = m.predict(t32(Xs))
+    em, ev, ep = O.predict(Xs.astype(np.float32).astype(np.float64), X.astype(np.float32).astype(np.float64),
+                           ref.v, ref.Q, kern, 3)
+    assert rel(mean.cpu(), em) <= 1e-4
+    assert np.max(np.abs(var.cpu().numpy() - ev)) <= 1e-4 * kern.outputscale
+    assert np.max(np.abs(probs.cpu().numpy() - ep)) <= 1e-4
+    m.free()
+
+
+def test_fit_paper_default_tolerances_matches_oracle(native):
+    """Default inner tolerances 1e-5 (App. B.2), up to 50 iterations, R = 50."""
+    X, y, Xs, ys = datagen.workload_small()
+    kern = O.Kernel(O.RBF, 1.0, 1.0)
+    ref = oracle_fit(X, y, 3, kern, max_newton=10, max_iters=50, R=50)
+    m = gpu_fit(native, X, y, 3, max_newton=10, max_iters=50, rank=50)
+    arr = m.arrays()
+    assert rel(arr["f"].cpu(), ref.f) <= 1e-4
+    mean, var, probs = m.predict(t32(Xs))
+    em, ev, ep = O.predict(Xs.astype(np.float64), X.astype(np.float32).astype(np.float64), ref.v, ref.Q, kern, 3)
+    assert rel(mean.cpu(), em) <= 1e-4
+    acc = (probs.cpu().numpy().argmax(1) == ys).mean()
+    assert acc >= 0.95
+    iters = [m.report.iters[i] for i in range(m.report.newton_steps)]
+    ref_iters = [inf.iters for inf in ref.infos]
+    assert all(abs(a - b) <= 2 for a, b in zip(iters, ref_iters)), (iters, ref_iters)
+    m.free()
+
+
+@pytest.mark.parametrize("prec", ["bf16x3", "bf16_comp", "bf16"])
+def test_fit_precisions(native, prec):
+    X, y, Xs, ys = datagen.workload_small()
+    kern = O.Kernel(O.RBF, 1.0, 1.0)
+    ref = oracle_fit(X, y, 3, kern, max_newton=5, max_iters=12, R=50, tol_abs=0, tol_rel=0)
+    m = gpu_fit(native, X, y, 3, max_newton=5, max_iters=12, rank=50, tol_abs=0.0, tol_rel=0.0,
+                precision=prec)
+    mean, _, _ = m.predict(t32(Xs))
+    em, _, _ = O.predict(Xs.astype(np.float64), X.astype(np.float32).astype(np.float64), ref.v, ref.Q, kern, 3)
+    tol = 1e-4 if prec == "bf16x3" else 1e-2
+    assert rel(mean.cpu(), em) <= tol, (prec, rel(mean.cpu(), em))
+    m.free()
+
+
+def test_literal_alg2_products_match_carried_products(native):
+    """Alg. 2 as printed (K v_{j-1} recomputed, f = K v + m by a product) vs K v carried
+    through the T buffer: the same iterates."""
+    X, y, Xs, _ = datagen.workload_small(n_train=300, n_test=50)
+    a = gpu_fit(native, X, y, 3, max_newton=4, max_iters=10, rank=20, tol_abs=0.0, tol_rel=0.0)
+    b = gpu_fit(native, X, y, 3, max_newton=4, max_iters=10, rank=20, tol_abs=0.0, tol_rel=0.0,
+                literal_kv=True)
+    assert rel(a.arrays()["f"].cpu(), b.arrays()["f"].cpu()) <= 1e-4
+    assert rel(a.predict(t32(Xs))[0].cpu(), b.predict(t32(Xs))[0].cpu()) <= 1e-4
+
+
+def test_no_recycling_matches_oracle(native):
+    X, y, Xs, _ = datagen.workload_small(n_train=200, n_test=40)
+    kern = O.Kernel(O.RBF, 1.0, 1.0)
+    ref = oracle_fit(X, y, 3, kern, max_newton=4, max_iters=10, recycle=False, tol_abs=0, tol_rel=0)
+    m = gpu_fit(native, X, y, 3, max_newton=4, max_iters=10, recycle=False, tol_abs=0.0, tol_rel=0.0)
+    assert rel(m.arrays()["f"].cpu(), ref.f) <= 1e-4
+
+
+def test_unit_vector_policy_reproduces_exact_newton_step(native):
+    """NC unit-vector actions in one Newton step give the exact pseudo-target solve
+    (Sec. 3.2: unit vectors = Cholesky / SoD)."""
+    X, y, _ = datagen.blobs(20, 2, 3, 17)
+    kern = O.Kernel(O.RBF, 0.6, 1.0)
+    m = native.fit(t32(X), torch.as_tensor(y, device=DEV), 3, kind="rbf", lengthscale=0.6,
+                   outputscale=1.0, policy="unit", max_newton=1, max_iters=60, rank=-1,
+                   tol_abs=0.0, tol_rel=0.0)
+    v_exact, f_exact = O.exact_newton_step(X.astype(np.float32).astype(np.float64), O.Softmax(y, 3),
+                                           np.zeros((20, 3)), np.zeros((20, 3)), kern, shift=0.0)
+    arr = m.arrays()
+    assert m.report.iters[0] == 60
+    assert rel(arr["f"].cpu(), f_exact) <= 1e-4
+
+
+def test_outer_tolerance_stops_like_the_oracle(native):
+    X, y, _, _ = datagen.workload_small()
+    kern = O.Kernel(O.RBF, 1.0, 1.0)
+    ref = oracle_fit(X, y, 3, kern, max_newton=10, max_iters=50, R=50, tol_newton=1e-2)
+    m = gpu_fit(native, X, y, 3, max_newton=10, max_iters=50, rank=50, tol_newton=1e-2)
+    assert m.report.newton_steps == ref.newton_steps
+    for i in range(1, ref.newton_steps):
+        assert abs(m.report.rel_change[i] - ref.rel_changes[i - 1]) <= 1e-3 * max(1.0, ref.rel_changes[i - 1])
+
+
+def test_fit_reports_bad_labels(native):
+    X, y, _, _ = datagen.workload_small(n_train=100, n_test=10)
+    y = y.copy()
+    y[5] = 9
+    with pytest.raises(native.ItergpError) as ei:
+        gpu_fit(native, X, y, 3, max_newton=1, max_iters=2)
+    assert ei.value.code == native.EINVAL
+
+
+def test_full_size_fit_consistency_on_sampled_rows(native):
+    """Kernel-bench data at full size (N = 60000, D = 784, C = 10), 5 Newton steps x 5
+    iterations, R = 200: f = K v holds on sampled rows (the oracle's product against the
+    GPU's v), the objective increases, and the predictive is a distribution."""
+    X, y, Xs, ys, _ = datagen.workload_kernel_bench()
+    m = native.fit(t32(X), torch.as_tensor(y, device=DEV), 10, kind="matern32", lengthscale=28.0,
+                   outputscale=1.0, precision="bf16x3", max_newton=5, max_iters=5, rank=200)
+    rep = m.report
+    assert rep.newton_steps == 5 and rep.total_iters == 25
+    arr = m.arrays()
+    v = arr["v"].cpu().numpy().astype(np.float64)
+    f = arr["f"].cpu().numpy().astype(np.float64)
+    rows = np.random.default_rng(1).choice(X.shape[0], 24, replace=False)
+    kern = O.Kernel(O.MATERN32, 28.0, 1.0)
+    fk = O.kmatvec(X[rows].astype(np.float64), X.astype(np.float64), v, kern)
+    assert rel(f[rows], fk) <= 1e-3
+    obj = [rep.objective[i] for i in range(5)]
+    assert all(b > a for a, b in zip(obj, obj[1:])), obj
+    mean, var, probs = m.predict(t32(Xs[:2000]))
+    p = probs.cpu().numpy()
+    assert np.allclose(p.sum(1), 1.0, atol=1e-5)
+    assert (p.argmax(1) == ys[:2000]).mean() > 0.9
+    m.free()
