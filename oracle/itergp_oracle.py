@@ -277,7 +277,7 @@ class SolveInfo:
 
 def itergp(kmv, winv, b, S, T, policy: int = CG, max_iters: int = 50,
            R: int | None = None, tol_abs: float = 1e-5, tol_rel: float = 1e-5,
-           on_iterate=None):
+           on_iterate=None, project=None):
     """Alg. 2: IterGP with a virtual solver run.
 
     kmv(w)  -- product with K for an NC-vector (flat, CN order)
@@ -285,7 +285,9 @@ def itergp(kmv, winv, b, S, T, policy: int = CG, max_iters: int = 50,
     b       -- right-hand side y_hat - m (flat)
     S, T    -- action buffer and its K products (NC x B), recycled from earlier steps.
     Returns (v, Q, S, T, info); C_j = Q Q^T.  ``on_iterate(j, v, Q)`` is called after
-    every completed iteration (used by tests of the per-iteration invariants)."""
+    every completed iteration (used by tests of the per-iteration invariants).
+    ``project`` (optional) is applied to each residual; the CUDA path projects onto the
+    class-contrast subspace, which is the identity on residuals in exact arithmetic."""
     NC = b.shape[0]
 
     def winv_cols(Mat):
@@ -299,6 +301,8 @@ def itergp(kmv, winv, b, S, T, policy: int = CG, max_iters: int = 50,
     thresh = max(tol_abs, tol_rel * bnorm)
     for j in range(1, max_iters + 1):
         r = b - kmv(v) - winv(v)                            # r_{j-1}
+        if project is not None:
+            r = project(r)
         rn = float(np.linalg.norm(r))
         info.rnorm.append(rn)
         if rn < thresh:
@@ -349,10 +353,14 @@ class FitResult:
 
 def iterncgp_fit(X, lik, C: int, kern: Kernel, max_newton: int = 10, max_iters: int = 50,
                  R: int | None = None, policy: int = CG, tol_newton: float | None = None,
-                 tol_abs: float = 1e-5, tol_rel: float = 1e-5, recycle: bool = True):
+                 tol_abs: float = 1e-5, tol_rel: float = 1e-5, recycle: bool = True,
+                 project_contrasts: bool = False):
     """Alg. 1: Newton's method as a sequence of GP regression problems, each solved by
     IterGP (Alg. 2) with recycled actions (Alg. 3).  Prior mean m = 0 (App. C.3),
-    f_0 = m, empty buffers.  tol_newton=None runs exactly ``max_newton`` steps."""
+    f_0 = m, empty buffers.  tol_newton=None runs exactly ``max_newton`` steps.
+    project_contrasts=True removes the per-point class mean from y_hat - m and from every
+    residual under the residual (CG) policy (the CUDA path's stabilisation; the identity
+    in exact arithmetic, where those vectors already lie in range(I kron P))."""
     X = np.asarray(X, dtype=np.float64)
     N = X.shape[0]
     m = np.zeros((N, C))
@@ -381,11 +389,15 @@ def iterncgp_fit(X, lik, C: int, kern: Kernel, max_newton: int = 10, max_iters: 
         winv = (lambda w, f=f: lik.Winv_apply(f, w.reshape(N, C)).reshape(-1))
         yhat = pseudo_targets(lik, f)
         b = (yhat - m).reshape(-1)
+        proj = None
+        if project_contrasts and policy == CG:
+            proj = (lambda w: (w.reshape(N, C) - w.reshape(N, C).mean(axis=1, keepdims=True)).reshape(-1))
+            b = proj(b)
         if not recycle:
             S = np.zeros((N * C, 0))
             T = np.zeros((N * C, 0))
         vflat, Q, S, T, info = itergp(kmv, winv, b, S, T, policy, max_iters, R,
-                                      tol_abs, tol_rel)
+                                      tol_abs, tol_rel, project=proj)
         v = vflat.reshape(N, C)
         f = (kx @ v) + m                                    # f_{i+1} = K v + m
         res.fs.append(f.copy())

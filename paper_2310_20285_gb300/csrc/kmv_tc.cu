@@ -13,6 +13,11 @@
 // evaluation and the output stores.  TMEM columns: G0 [0,128), G1 [128,256) (double
 // buffer, P aliases the G it came from), O [256, 256 + p_tile).
 //
+// The tensor core accumulates in FP32 with truncation, which biases long sums; O is
+// therefore accumulated over sub-runs of at most kFlushChunks chunks and each sub-run
+// is added into the running sum O2 [384, 384 + p_tile) by the epilogue with ordinary
+// FP32 adds.
+//
 // Work partition: U = row_tiles x column_chunks units, CTA g owns the contiguous range
 // [g U / G, (g+1) U / G).  A CTA accumulates O over a run of chunks of one row tile; a
 // run covering a whole row tile is stored directly, partial runs (at most the first and
@@ -33,6 +38,8 @@ constexpr int BK = 64;    // D slice per stage (one 128-byte swizzle row of BF16
 constexpr int kThreads = 256;
 constexpr uint32_t kTmemCols = 512;
 constexpr uint32_t kOCol = 256;
+constexpr uint32_t kO2Col = 384;   // FP32 running sum of flushed O (IEEE round-to-nearest adds)
+constexpr int kFlushChunks = 4;    // O is flushed into O2 at least every 4 chunks (512 rows)
 constexpr uint64_t kWaitLimitNs = 4000000000ull;   // 4 s per wait
 
 struct TcArgs {
@@ -178,16 +185,16 @@ kmv_tc_kernel(const __grid_constant__ CUtensorMap mAh, const __grid_constant__ C
       const uint32_t idesc2 = idesc_bf16_f32(BM, static_cast<uint32_t>(args.p_pad));
       int stage = 0;
       uint32_t phase = 0;
-      int64_t seg = -1;
+      int64_t sub = -1;
       bool ok = true;
       auto gemm2 = [&](int64_t t) -> bool {
         const int64_t u = u_begin + t;
         const int c = static_cast<int>(u % J);
-        const bool first = (t == 0) || (c == 0);
-        const bool last = (t == T - 1) || (c == J - 1);
+        const bool first = (t == 0) || (c == 0) || (c % kFlushChunks == 0);
+        const bool last = (t == T - 1) || (c == J - 1) || ((c + 1) % kFlushChunks == 0);
         if (first) {
-          ++seg;
-          if (seg >= 1 && !mbar_wait(&oempty, static_cast<uint32_t>((seg - 1) & 1), ab, kWaitLimitNs))
+          ++sub;
+          if (sub >= 1 && !mbar_wait(&oempty, static_cast<uint32_t>((sub - 1) & 1), ab, kWaitLimitNs))
             return false;
         }
         const int gb = static_cast<int>(t & 1);
@@ -258,8 +265,8 @@ kmv_tc_kernel(const __grid_constant__ CUtensorMap mAh, const __grid_constant__ C
     const int q = warp - 4;
     const int row = 32 * q + lane;
     const uint32_t lane_base = static_cast<uint32_t>(32 * q) << 16;
-    int64_t seg = -1;
-    int seg_c0 = 0;
+    int64_t seg = -1, sub = -1;
+    int seg_c0 = 0, sub_in_seg = 0;
     float na_r = 0.f;
     int64_t grow = 0;
     const KParams kp = args.kp;
@@ -269,9 +276,11 @@ kmv_tc_kernel(const __grid_constant__ CUtensorMap mAh, const __grid_constant__ C
       const int c = static_cast<int>(u % J);
       const bool first = (t == 0) || (c == 0);
       const bool last = (t == T - 1) || (c == J - 1);
+      const bool sub_last = last || ((c + 1) % kFlushChunks == 0);
       if (first) {
         ++seg;
         seg_c0 = c;
+        sub_in_seg = 0;
         grow = r * BM + row;
         na_r = args.na[grow];
       }
@@ -309,37 +318,49 @@ kmv_tc_kernel(const __grid_constant__ CUtensorMap mAh, const __grid_constant__ C
       tmem_st_wait();
       tc_fence_before();
       mbar_arrive(&pfull[gb]);
-      if (last) {
-        if (!mbar_wait_warp(&ofull, static_cast<uint32_t>(seg & 1), ab, kWaitLimitNs)) break;
+      if (sub_last) {
+        ++sub;
+        if (!mbar_wait_warp(&ofull, static_cast<uint32_t>(sub & 1), ab, kWaitLimitNs)) break;
         tc_fence_after();
         const bool full_row = (seg_c0 == 0) && (c == J - 1);
-        float* dst;
-        int64_t ld;
-        bool valid;
-        if (full_row) {
-          dst = args.Y + grow * args.ldY;
-          ld = args.ldY;
-          valid = grow < args.m;
-        } else {
-          const int64_t slot = 2 * g + (seg == 0 ? 0 : 1);
-          dst = args.partial + (slot * BM + row) * args.p_pad;
-          ld = args.p_pad;
-          valid = true;
+        float* dst = nullptr;
+        bool valid = true;
+        if (last) {
+          if (full_row) {
+            dst = args.Y + grow * args.ldY;
+            valid = grow < args.m;
+          } else {
+            const int64_t slot = 2 * g + (seg == 0 ? 0 : 1);
+            dst = args.partial + (slot * BM + row) * args.p_pad;
+          }
         }
-        (void)ld;
+        const int lim = full_row ? args.p_valid : args.p_pad;
         for (int c16 = 0; c16 < args.p_pad / 16; ++c16) {
           uint32_t o[16];
           tmem_ld16(tb + lane_base + kOCol + 16 * c16, o);
-          tmem_ld_wait();
-          if (valid) {
-            const int lim = full_row ? args.p_valid : args.p_pad;
+          if (sub_in_seg > 0) {
+            uint32_t o2[16];
+            tmem_ld16(tb + lane_base + kO2Col + 16 * c16, o2);
+            tmem_ld_wait();
 #pragma unroll
-            for (int i = 0; i < 16; ++i)
-              if (16 * c16 + i < lim) dst[16 * c16 + i] = __uint_as_float(o[i]);
+            for (int i = 0; i < 16; ++i) o[i] = __float_as_uint(__uint_as_float(o[i]) + __uint_as_float(o2[i]));
+          } else {
+            tmem_ld_wait();
+          }
+          if (last) {
+            if (valid) {
+#pragma unroll
+              for (int i = 0; i < 16; ++i)
+                if (16 * c16 + i < lim) dst[16 * c16 + i] = __uint_as_float(o[i]);
+            }
+          } else {
+            tmem_st16(tb + lane_base + kO2Col + 16 * c16, o);
           }
         }
+        tmem_st_wait();
         tc_fence_before();
         mbar_arrive(&oempty);
+        ++sub_in_seg;
       }
     }
   }

@@ -90,7 +90,7 @@ __global__ void newton_prologue_kernel(const FitState* __restrict__ st, int64_t 
                                        const float* __restrict__ f, const int32_t* __restrict__ y,
                                        const float* __restrict__ v, float* __restrict__ g_prev,
                                        float* __restrict__ inv_pi, float* __restrict__ b,
-                                       double* __restrict__ part, int* status) {
+                                       double* __restrict__ part, int* status, int project) {
   if (!st->newton_active) return;
   __shared__ double sh[32];
   double s_b2 = 0, s_ll = 0, s_vf = 0, s_dg = 0, s_g2 = 0;
@@ -125,8 +125,17 @@ __global__ void newton_prologue_kernel(const FitState* __restrict__ st, int64_t 
     float* bi = b + i * C;
     float* gp = g_prev + i * C;
     const float* vi = v + i * C;
+    // With residual (CG) actions b lies in the class-contrast subspace range(I kron P) in
+    // exact arithmetic (f = K v with v there, W^+ maps into it); removing the per-point
+    // mean keeps rounding out of the class-sum directions, where K_hat reduces to the
+    // near-singular k(X, X).  Unit-vector actions leave that subspace: no projection.
+    float bmean = 0.f;
+    if (project) {
+      for (int c = 0; c < C; ++c) bmean += fi[c] + ((grad[c] - m1) * ipi[c] - m2);
+      bmean /= C;
+    }
     for (int c = 0; c < C; ++c) {
-      const float bc = fi[c] + ((grad[c] - m1) * ipi[c] - m2);
+      const float bc = fi[c] + ((grad[c] - m1) * ipi[c] - m2) - bmean;
       bi[c] = bc;
       s_b2 += static_cast<double>(bc) * bc;
       s_vf += static_cast<double>(vi[c]) * fi[c];
@@ -518,11 +527,11 @@ __global__ void combine_kernel(const FitState* __restrict__ st, const float* __r
 }
 
 // -------------------------------------------------------------------- inner iteration
-// r = b - u - W^+ v   (u = K v); partial |r|^2
+// r = P(b - u - W^+ v)   (u = K v, P removes the per-point class mean); partial |r|^2
 __global__ void resid_kernel(const FitState* __restrict__ st, int64_t n, int C,
                              const float* __restrict__ b, const float* __restrict__ u,
                              const float* __restrict__ v, const float* __restrict__ inv_pi,
-                             float* __restrict__ r, double* __restrict__ part) {
+                             float* __restrict__ r, double* __restrict__ part, int project) {
   if (!st->newton_active || !st->active) return;
   __shared__ double sh[32];
   double acc = 0.0;
@@ -530,8 +539,15 @@ __global__ void resid_kernel(const FitState* __restrict__ st, int64_t n, int C,
        i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
     float w[kMaxC];
     winv_point(v + i * C, inv_pi + i * C, C, w);
+    // with residual actions r is projected onto the class-contrast subspace, where it lies
+    // in exact arithmetic
+    float rm = 0.f;
+    if (project) {
+      for (int c = 0; c < C; ++c) rm += b[i * C + c] - u[i * C + c] - w[c];
+      rm /= C;
+    }
     for (int c = 0; c < C; ++c) {
-      const float rv = b[i * C + c] - u[i * C + c] - w[c];
+      const float rv = b[i * C + c] - u[i * C + c] - w[c] - rm;
       r[i * C + c] = rv;
       acc += static_cast<double>(rv) * rv;
     }
@@ -786,6 +802,7 @@ int fit_run(DeviceContext* ctx, const itergp_fit_params& prm, const KParams& kp,
   const int eb = static_cast<int>(std::min<int64_t>(ceil_div(nc, 256), 8LL * ctx->num_sms));
   const int nb_pts = static_cast<int>(std::min<int64_t>(ceil_div(n, 256), 8LL * ctx->num_sms));
   const int track_kd = prm.literal_kv ? 0 : 1;
+  const int project = prm.policy == ITERGP_POLICY_CG ? 1 : 0;
 
   // ---- workspace
   const size_t vec = align_up(sizeof(float) * nc, 256);
@@ -841,7 +858,7 @@ int fit_run(DeviceContext* ctx, const itergp_fit_params& prm, const KParams& kp,
   const int eig_threads = 512;
 
   for (int step = 0; step < prm.max_newton; ++step) {
-    newton_prologue_kernel<<<nblk, kRedThreads, 0, stream>>>(st, n, C, f, y, v, gp, ip, b, ps, ctx->status), ::itergp::note_launch();
+    newton_prologue_kernel<<<nblk, kRedThreads, 0, stream>>>(st, n, C, f, y, v, gp, ip, b, ps, ctx->status, project), ::itergp::note_launch();
     newton_finalize_kernel<<<1, 32, 0, stream>>>(st, ps, nblk, step, prm.tol_newton, prm.tol_abs, prm.tol_rel, prm.recycle), ::itergp::note_launch();
     // ---- Alg. 3: virtual solver run with compression
     if (prm.recycle && step > 0) {
@@ -864,7 +881,7 @@ int fit_run(DeviceContext* ctx, const itergp_fit_params& prm, const KParams& kp,
         int rc = kmv_execute(ctx, kp, Xop, Xop, v, C, C, u, C, stream, active);
         if (rc != ITERGP_OK) return rc;
       }
-      resid_kernel<<<nblk, kRedThreads, 0, stream>>>(st, n, C, b, u, v, ip, r, ps), ::itergp::note_launch();
+      resid_kernel<<<nblk, kRedThreads, 0, stream>>>(st, n, C, b, u, v, ip, r, ps, project), ::itergp::note_launch();
       resid_finalize_kernel<<<1, 32, 0, stream>>>(st, ps, nblk, r, nc, prm.policy, step), ::itergp::note_launch();
       action_kernel<<<eb, 256, 0, stream>>>(st, nc, prm.policy, r, s_cur, S), ::itergp::note_launch();
       int rc = kmv_execute(ctx, kp, Xop, Xop, s_cur, C, C, t_cur, C, stream, active);

@@ -241,7 +241,7 @@ class _CudaArray:
 
     def __init__(self, ptr: int, shape):
         self.__cuda_array_interface__ = {"shape": tuple(int(x) for x in shape), "typestr": "<f4",
-                                         "data": (int(ptr), True), "version": 3, "strides": None}
+                                         "data": (int(ptr), False), "version": 3, "strides": None}
 
 
 def fit(X, y, c, kind="rbf", lengthscale=1.0, outputscale=1.0, precision="fp32",

@@ -464,3 +464,18 @@ def test_probit_reduces_to_softmax_at_zero_variance():
     mean, var, probs = O.predict(Xs, X, v, np.zeros((18, 0)), kern, 3)
     assert np.allclose(var, kern.outputscale)
     assert np.allclose(probs, O.softmax(mean / math.sqrt(1 + math.pi / 8 * kern.outputscale)))
+
+
+def test_class_contrast_projection_is_the_identity_in_exact_arithmetic():
+    """The CUDA path removes the per-point class mean from y_hat - m and from each residual.
+    Both lie in range(I kron P) in exact arithmetic (f = K v with v there; W^+ maps into it,
+    Lemma A.6), so in FP64 the projected and the literal runs coincide."""
+    X, y, _ = datagen.blobs(60, 2, 3, 21)
+    kern = O.Kernel(O.RBF, 1.0, 1.0)
+    lik = O.Softmax(y, 3)
+    kw = dict(max_newton=6, max_iters=10, R=15, tol_abs=0, tol_rel=0)
+    a = O.iterncgp_fit(X, lik, 3, kern, **kw)
+    b = O.iterncgp_fit(X, lik, 3, kern, project_contrasts=True, **kw)
+    for fa, fb in zip(a.fs, b.fs):
+        assert np.allclose(fa, fb, rtol=1e-8, atol=1e-9)
+    assert np.allclose(a.v.sum(axis=1), 0.0, atol=1e-8)
