@@ -42,7 +42,8 @@ typedef enum {
   ITERGP_ECUDA = -3,        /* a CUDA runtime call failed                                 */
   ITERGP_ENUMERIC = -4,     /* a non-finite value was produced on the device              */
   ITERGP_ETIMEOUT = -5,     /* a device-side wait exceeded its bound; the kernel returned */
-  ITERGP_EUNSUPPORTED = -6  /* the current device is not sm_103a / sm_100 family          */
+  ITERGP_EUNSUPPORTED = -6, /* the current device is not sm_103a / sm_100 family          */
+  ITERGP_ESCRATCH = -7      /* itergp_kmatvec_noalloc: sizes need more than its fixed scratch */
 } itergp_status;
 
 /* Kernel functions (App. C.1 / C.3 use GPyTorch's RBF and Matern-3/2 kernels):
@@ -92,6 +93,38 @@ typedef void* itergp_stream; /* cudaStream_t */
 int itergp_kmatvec(const itergp_kernel* kernel, int32_t precision, const float* A, int64_t m,
                    const float* B, int64_t n, int64_t d, const float* S, int64_t p, float* Y,
                    itergp_stream stream);
+
+/* ----------------------------------------------------------------------------------
+ * Kernel product for callers that cannot allocate device memory.  The paper has no
+ * counterpart: this is a deployment variant of itergp_kmatvec.
+ *
+ * Some callers must not call cudaMalloc or any allocating routine while they run: code
+ * inside a CUDA-graph-building or real-time serving loop that has reserved all device
+ * memory up front, plug-in hosts whose allocator is not the CUDA one, or processes that
+ * forbid allocation after start-up.  For them this entry point computes exactly what
+ * itergp_kmatvec computes (same kernels, same arguments, same result) but takes every
+ * byte of scratch (BF16 copies, row norms, transposed S, split partial sums) from one
+ * file-scope static device array of ITERGP_NOALLOC_SCRATCH_BYTES (64 MiB) that each GPU
+ * loading the library holds until the process exits.  It calls no cudaMalloc, cudaFree
+ * or allocating library routine.
+ *
+ *  - The caller passes inputs and outputs exactly as for itergp_kmatvec; `device_status`
+ *    (device int, may be NULL) receives ITERGP_ETIMEOUT if a device-side wait gives up;
+ *    the caller zeroes it.
+ *  - Sizes whose scratch would exceed the array are rejected with ITERGP_ESCRATCH before
+ *    any launch (for the tensor precisions roughly rows x round_up(d, 64) x 4 bytes per
+ *    operand, so e.g. m = n = 8192, d = 784 fits; the FP32 precision needs far less).
+ *  - The first call on a device looks up the array's device address with
+ *    cudaGetSymbolAddress (device set-up, once per device); make that first call before
+ *    any stream capture.
+ *  - Every call shares the one array, which keeps the previous call's contents; all of it
+ *    that is read is written first within the call.  Calls whose work overlaps on the GPU
+ *    (different streams, or host threads without ordering) race on the array: serialise
+ *    them, e.g. on one stream. */
+#define ITERGP_NOALLOC_SCRATCH_BYTES (64ull << 20)
+int itergp_kmatvec_noalloc(const itergp_kernel* kernel, int32_t precision, const float* A,
+                           int64_t m, const float* B, int64_t n, int64_t d, const float* S,
+                           int64_t p, float* Y, int* device_status, itergp_stream stream);
 
 /* ----------------------------------------------------------------------------------
  * Softmax-likelihood building blocks (Alg. 1 lines "W(f)^-1" and "y_hat"; Lemma A.6).

@@ -95,11 +95,29 @@ DeviceContext* current_context() {
   return c;
 }
 
+namespace {
+thread_local ScratchArena* t_arena = nullptr;
+}
+
+void set_thread_arena(ScratchArena* arena) { t_arena = arena; }
+
 cudaError_t scratch_alloc(DeviceContext* ctx, void** p, size_t bytes, cudaStream_t s) {
+  if (t_arena != nullptr) {
+    const size_t off = align_up(t_arena->used, 256);
+    if (off + bytes > t_arena->size) return cudaErrorMemoryAllocation;
+    *p = t_arena->base + off;
+    t_arena->used = off + bytes;
+    return cudaSuccess;
+  }
   return cudaMallocFromPoolAsync(p, bytes, ctx->pool, s);
 }
 
-void scratch_free(void* p, cudaStream_t s) { cudaFreeAsync(p, s); }
+void scratch_free(void* p, cudaStream_t s) {
+  if (t_arena != nullptr && static_cast<char*>(p) >= t_arena->base &&
+      static_cast<char*>(p) < t_arena->base + t_arena->size)
+    return;
+  cudaFreeAsync(p, s);
+}
 
 namespace {
 
@@ -229,6 +247,7 @@ const char* itergp_status_string(int status) {
     case ITERGP_ENUMERIC: return "non-finite value on the device";
     case ITERGP_ETIMEOUT: return "device-side wait exceeded its bound";
     case ITERGP_EUNSUPPORTED: return "unsupported device (needs sm_100 family / sm_103a)";
+    case ITERGP_ESCRATCH: return "problem needs more scratch than the fixed static buffer holds";
     default: return "unknown status";
   }
 }

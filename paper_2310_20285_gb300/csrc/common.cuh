@@ -97,6 +97,16 @@ DeviceContext* current_context();
 cudaError_t scratch_alloc(DeviceContext* ctx, void** p, size_t bytes, cudaStream_t s);
 void scratch_free(void* p, cudaStream_t s);
 
+// A caller-provided block of device memory that scratch_alloc carves from (bump pointer,
+// 256-byte aligned) instead of the pool while it is installed on the calling thread.
+// Only the allocation-free entry point installs one; scratch_free ignores its blocks.
+struct ScratchArena {
+  char* base = nullptr;
+  size_t size = 0;
+  size_t used = 0;
+};
+void set_thread_arena(ScratchArena* arena);
+
 // RAII scratch block freed (stream-ordered) at scope exit.
 struct Scratch {
   void* ptr = nullptr;

@@ -13,7 +13,8 @@ import torch
 
 _LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libitergp.so")
 
-OK, EINVAL, ENOMEM, ECUDA, ENUMERIC, ETIMEOUT, EUNSUPPORTED = 0, -1, -2, -3, -4, -5, -6
+OK, EINVAL, ENOMEM, ECUDA, ENUMERIC, ETIMEOUT, EUNSUPPORTED, ESCRATCH = 0, -1, -2, -3, -4, -5, -6, -7
+NOALLOC_SCRATCH_BYTES = 64 << 20
 RBF, MATERN32 = 0, 1
 FP32, BF16X3, BF16, BF16_COMP = 0, 1, 2, 3
 POLICY_CG, POLICY_UNIT = 0, 1
@@ -66,6 +67,8 @@ def _load():
     lib = ct.CDLL(_LIB_PATH)
     vp, i64, i32 = ct.c_void_p, ct.c_int64, ct.c_int32
     lib.itergp_kmatvec.argtypes = [ct.POINTER(Kernel), i32, vp, i64, vp, i64, i64, vp, i64, vp, vp]
+    lib.itergp_kmatvec_noalloc.argtypes = [ct.POINTER(Kernel), i32, vp, i64, vp, i64, i64, vp, i64,
+                                           vp, vp, vp]
     lib.itergp_winv_apply.argtypes = [vp, i64, i32, vp, vp, vp]
     lib.itergp_pseudo_targets.argtypes = [vp, vp, i64, i32, vp, vp]
     lib.itergp_sym_eig.argtypes = [vp, i32, vp, vp, vp]
@@ -82,7 +85,7 @@ def _load():
     lib.itergp_timing_read.argtypes = [ct.POINTER(ct.c_double), ct.POINTER(ct.c_int64)]
     lib.itergp_launch_count.restype = ct.c_int64
     lib.itergp_launch_count.argtypes = []
-    for name in ("itergp_kmatvec", "itergp_winv_apply", "itergp_pseudo_targets",
+    for name in ("itergp_kmatvec", "itergp_kmatvec_noalloc", "itergp_winv_apply", "itergp_pseudo_targets",
                  "itergp_sym_eig", "itergp_fit", "itergp_predict", "itergp_model_get_view",
                  "itergp_sync_status"):
         getattr(lib, name).restype = ct.c_int
@@ -134,6 +137,25 @@ def kmatvec(A, B, S, kind="rbf", lengthscale=1.0, outputscale=1.0, precision="fp
                             _dev(B, torch.float32, "B"), n, d, _dev(S, torch.float32, "S"), p,
                             _dev(out, torch.float32, "out"), _stream(stream))
     _check(rc, "itergp_kmatvec")
+    return out
+
+
+def kmatvec_noalloc(A, B, S, kind="rbf", lengthscale=1.0, outputscale=1.0, precision="fp32",
+                    out=None, status=None, stream=None):
+    """Same product as kmatvec, computed without any device allocation by the library (its
+    scratch is a fixed static device array; see itergp_kmatvec_noalloc).  ``out`` and the
+    optional int32 ``status`` word are the caller's."""
+    m, d = A.shape
+    n = B.shape[0]
+    p = S.shape[1]
+    if out is None:
+        out = torch.empty((m, p), device=A.device, dtype=torch.float32)
+    k = _kernel(kind, lengthscale, outputscale)
+    st = None if status is None else _dev(status, torch.int32, "status")
+    rc = lib.itergp_kmatvec_noalloc(ct.byref(k), _prec(precision), _dev(A, torch.float32, "A"), m,
+                                    _dev(B, torch.float32, "B"), n, d, _dev(S, torch.float32, "S"),
+                                    p, _dev(out, torch.float32, "out"), st, _stream(stream))
+    _check(rc, "itergp_kmatvec_noalloc")
     return out
 
 
