@@ -299,8 +299,12 @@ def main():
         for prec in ("bf16x3", "bf16", "fp32"):
             torch.cuda.synchronize()
             t0 = time.perf_counter()
-            m = native.fit(tX, ty, 10, kind="matern32", lengthscale=ELL, outputscale=OUT,
-                           precision=prec, max_newton=5, max_iters=5, rank=200)
+            try:
+                m = native.fit(tX, ty, 10, kind="matern32", lengthscale=ELL, outputscale=OUT,
+                               precision=prec, max_newton=5, max_iters=5, rank=200)
+            except native.ItergpError as e:
+                fits[prec] = {"error": str(e)}
+                continue
             torch.cuda.synchronize()
             dt = time.perf_counter() - t0
             mean, var, probs = m.predict(torch.as_tensor(Xs, device=dev))

@@ -18,11 +18,14 @@
 // is added into the running sum O2 [384, 384 + p_tile) by the epilogue with ordinary
 // FP32 adds.
 //
-// Work partition: U = row_tiles x column_chunks units, CTA g owns the contiguous range
-// [g U / G, (g+1) U / G).  A CTA accumulates O over a run of chunks of one row tile; a
-// run covering a whole row tile is stored directly, partial runs (at most the first and
-// last of a CTA) go to scratch and a fix-up kernel adds them in CTA order, so results
-// are deterministic.
+// Work partition (G persistent CTAs, R row tiles, J column chunks): the first
+// floor(R / G) * G row tiles are processed whole, one wave at a time, and every CTA sweeps
+// the column chunks in the same order 0 .. J-1, so at any moment all CTAs read the same
+// tile of B and the L2 serves it to all of them (B is larger than the L2 at the large
+// sizes).  The remaining R mod G row tiles form Ut = (R mod G) * J units split into equal
+// contiguous ranges over the G CTAs; partial runs there (at most the first and last of a
+// CTA) go to scratch and a fix-up kernel adds them in CTA order, so results are
+// deterministic.
 #include <algorithm>
 
 #include "internal.h"
@@ -46,7 +49,7 @@ struct TcArgs {
   const float* na;        // [A.rows_pad] row norms of A
   const float* nb;        // [B.rows_pad] row norms of B
   int64_t m;              // valid rows of A
-  int64_t units;          // row_tiles * chunks
+  int64_t row_tiles;      // R
   int chunks;             // J
   int nk;                 // D slices (d_pad / 64)
   int p_pad;              // MMA N of the product (multiple of 16, <= 128)
@@ -69,6 +72,30 @@ __host__ __device__ constexpr uint32_t s_buf_bytes(int nt2, int p_pad) {
 }
 constexpr uint32_t kSmemExtra = 1024 /*alignment*/ + 2048 /*per-warp nb staging*/;
 
+// Per-CTA sequence of (row tile, chunk) steps of the partition described above.
+struct Schedule {
+  int64_t G, g, J, fw, rt0, ut, tb, T;
+  __host__ __device__ void init(int64_t R, int64_t J_, int64_t G_, int64_t g_) {
+    G = G_;
+    g = g_;
+    J = J_;
+    fw = R / G;                      // whole-row waves
+    rt0 = fw * G;                    // first tail row tile
+    ut = (R - rt0) * J;              // tail units
+    tb = part_start(g, ut, G);
+    const int64_t te = part_start(g + 1, ut, G);
+    T = fw * J + (te - tb);
+  }
+  __host__ __device__ int64_t row(int64_t t) const {
+    return t < fw * J ? (t / J) * G + g : rt0 + (tb + (t - fw * J)) / J;
+  }
+  __host__ __device__ int col(int64_t t) const {
+    return static_cast<int>(t < fw * J ? t % J : (tb + (t - fw * J)) % J);
+  }
+  __host__ __device__ bool first(int64_t t) const { return t == 0 || row(t - 1) != row(t); }
+  __host__ __device__ bool last(int64_t t) const { return t == T - 1 || row(t + 1) != row(t); }
+};
+
 template <int KIND, int NT1, int NT2, int NSTAGE>
 __global__ void __launch_bounds__(kThreads, 1)
 kmv_tc_kernel(const __grid_constant__ CUtensorMap mAh, const __grid_constant__ CUtensorMap mAl,
@@ -77,10 +104,10 @@ kmv_tc_kernel(const __grid_constant__ CUtensorMap mAh, const __grid_constant__ C
               const TcArgs args) {
   if (args.active != nullptr && *args.active == 0) return;
   const int64_t G = gridDim.x, g = blockIdx.x;
-  const int64_t u_begin = part_start(g, args.units, G), u_end = part_start(g + 1, args.units, G);
-  if (u_begin >= u_end) return;
-  const int64_t T = u_end - u_begin;
-  const int J = args.chunks;
+  Schedule sch;
+  sch.init(args.row_tiles, args.chunks, G, g);
+  if (sch.T <= 0) return;
+  const int64_t T = sch.T;
 
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
@@ -136,9 +163,8 @@ kmv_tc_kernel(const __grid_constant__ CUtensorMap mAh, const __grid_constant__ C
       uint32_t armed = 0, armed_par = 0;      // bit i: stage i armed / parity of last arm
       uint32_t s_armed = 0, s_par = 0;
       for (int64_t t = 0; t < T && !*ab; ++t) {
-        const int64_t u = u_begin + t;
-        const int32_t a_y = static_cast<int32_t>((u / J) * BM);
-        const int32_t c = static_cast<int32_t>(u % J);
+        const int32_t a_y = static_cast<int32_t>(sch.row(t) * BM);
+        const int32_t c = sch.col(t);
         const int32_t b_y = c * BN;
         for (int ks = 0; ks < args.nk; ++ks) {
           if (!mbar_wait(&empty_bar[stage], phase ^ 1u, ab, kWaitLimitNs)) break;
@@ -188,10 +214,9 @@ kmv_tc_kernel(const __grid_constant__ CUtensorMap mAh, const __grid_constant__ C
       int64_t sub = -1;
       bool ok = true;
       auto gemm2 = [&](int64_t t) -> bool {
-        const int64_t u = u_begin + t;
-        const int c = static_cast<int>(u % J);
-        const bool first = (t == 0) || (c == 0) || (c % kFlushChunks == 0);
-        const bool last = (t == T - 1) || (c == J - 1) || ((c + 1) % kFlushChunks == 0);
+        const int c = sch.col(t);
+        const bool first = sch.first(t) || (c % kFlushChunks == 0);
+        const bool last = sch.last(t) || ((c + 1) % kFlushChunks == 0);
         if (first) {
           ++sub;
           if (sub >= 1 && !mbar_wait(&oempty, static_cast<uint32_t>((sub - 1) & 1), ab, kWaitLimitNs))
@@ -270,12 +295,12 @@ kmv_tc_kernel(const __grid_constant__ CUtensorMap mAh, const __grid_constant__ C
     float na_r = 0.f;
     int64_t grow = 0;
     const KParams kp = args.kp;
+    const int J = args.chunks;
     for (int64_t t = 0; t < T; ++t) {
-      const int64_t u = u_begin + t;
-      const int64_t r = u / J;
-      const int c = static_cast<int>(u % J);
-      const bool first = (t == 0) || (c == 0);
-      const bool last = (t == T - 1) || (c == J - 1);
+      const int64_t r = sch.row(t);
+      const int c = sch.col(t);
+      const bool first = sch.first(t);
+      const bool last = sch.last(t);
       const bool sub_last = last || ((c + 1) % kFlushChunks == 0);
       if (first) {
         ++seg;
@@ -330,7 +355,8 @@ kmv_tc_kernel(const __grid_constant__ CUtensorMap mAh, const __grid_constant__ C
             dst = args.Y + grow * args.ldY;
             valid = grow < args.m;
           } else {
-            const int64_t slot = 2 * g + (seg == 0 ? 0 : 1);
+            // partial runs only occur in the tail phase; segment index there -> slot
+            const int64_t slot = 2 * g + (seg - sch.fw == 0 ? 0 : 1);
             dst = args.partial + (slot * BM + row) * args.p_pad;
           }
         }
@@ -374,22 +400,26 @@ kmv_tc_kernel(const __grid_constant__ CUtensorMap mAh, const __grid_constant__ C
   if (threadIdx.x == 0 && abort_s) atomicExch(args.status, ITERGP_ETIMEOUT);
 }
 
-// Adds the partial runs of row tiles shared by several CTAs, in CTA order.
-__global__ void tc_fixup_kernel(const float* __restrict__ partial, int64_t units, int64_t G, int J,
+// Adds the partial runs of tail row tiles shared by several CTAs, in CTA order.
+__global__ void tc_fixup_kernel(const float* __restrict__ partial, int64_t R, int64_t G, int J,
                                 int64_t m, int p_pad, int p_valid, float* __restrict__ Y,
                                 int64_t ldY, const int* __restrict__ active) {
   if (active != nullptr && *active == 0) return;
-  const int64_t r = blockIdx.x;
-  const int64_t u0 = r * J, u1 = u0 + J - 1;
-  const int64_t g_lo = part_owner(u0, units, G), g_hi = part_owner(u1, units, G);
-  if (g_lo == g_hi) return;
+  const int64_t rt0 = (R / G) * G, ut = (R - rt0) * J;
+  const int64_t r = rt0 + blockIdx.x;
+  if (r >= R) return;
+  const int64_t u0 = (r - rt0) * J, u1 = u0 + J - 1;
+  const int64_t g_lo = part_owner(u0, ut, G), g_hi = part_owner(u1, ut, G);
+  if (g_lo == g_hi) return;   // one CTA covered the whole row tile and stored it
   for (int e = threadIdx.x; e < BM * p_valid; e += blockDim.x) {
     const int row = e / p_valid, col = e % p_valid;
     const int64_t grow = r * BM + row;
     if (grow >= m) continue;
     float acc = 0.f;
     for (int64_t gg = g_lo; gg <= g_hi; ++gg) {
-      const int64_t slot = 2 * gg + (part_start(gg, units, G) < u0 ? 1 : 0);
+      const int64_t s0 = part_start(gg, ut, G);
+      if (s0 == part_start(gg + 1, ut, G)) continue;   // CTA without tail units
+      const int64_t slot = 2 * gg + (s0 < u0 ? 1 : 0);
       acc += partial[(slot * BM + row) * p_pad + col];
     }
     Y[grow * ldY + col] = acc;
@@ -462,14 +492,18 @@ int kmv_tc(DeviceContext* ctx, const KParams& kp, const RowOperand& A, const Row
   const int nt2 = precision_splits_weights(prec) ? 3 : 1;
   const size_t smem_cap = std::min<size_t>(ctx->smem_optin, 232448) - 2048;
 
-  // P tile: the largest multiple of 16 (<= 128) that leaves room for >= 2 stages.
+  // P tile: the largest multiple of 16 (<= 128) that leaves room for >= 2 stages; then the
+  // deepest instantiated stage count (2, 3, 4) that fits.  (The split distance GEMM is
+  // bounded by shared-memory bandwidth, not by stage depth: deeper rings of narrower
+  // slices measured slower.)
   const int64_t p16 = (p + 15) / 16 * 16;
   int p_tile = static_cast<int>(std::min<int64_t>(p16, 128));
   int nstage = 0;
   for (; p_tile >= 16; p_tile -= 16) {
     const size_t fixed = 2 * s_buf_bytes(nt2, p_tile) + kSmemExtra;
     const size_t room = smem_cap > fixed ? smem_cap - fixed : 0;
-    nstage = static_cast<int>(std::min<size_t>(room / stage_bytes(nt1), 4));
+    const int fit = static_cast<int>(room / stage_bytes(nt1));
+    nstage = fit >= 4 ? 4 : fit >= 3 ? 3 : fit >= 2 ? 2 : 0;
     if (nstage >= 2) break;
   }
   if (nstage < 2) return ITERGP_EUNSUPPORTED;
@@ -502,6 +536,7 @@ int kmv_tc(DeviceContext* ctx, const KParams& kp, const RowOperand& A, const Row
   const int64_t chunks = ceil_div(B.rows, BN);
   const int64_t units = row_tiles * chunks;
   const int64_t G = std::min<int64_t>(ctx->num_sms, units);
+  const int64_t tail_rows = row_tiles - (row_tiles / G) * G;
   Scratch part;
   ITERGP_CUDA_TRY(part.alloc(ctx, sizeof(float) * 2 * G * BM * p_tile, stream));
 
@@ -515,7 +550,7 @@ int kmv_tc(DeviceContext* ctx, const KParams& kp, const RowOperand& A, const Row
     a.na = A.norms;
     a.nb = B.norms;
     a.m = A.rows;
-    a.units = units;
+    a.row_tiles = row_tiles;
     a.chunks = static_cast<int>(chunks);
     a.nk = A.d_pad / BK;
     a.p_pad = pp;
@@ -533,9 +568,11 @@ int kmv_tc(DeviceContext* ctx, const KParams& kp, const RowOperand& A, const Row
                         ? launch_prec<ITERGP_RBF>(prec, nstage, (int)G, smem_t, stream, maps, a)
                         : launch_prec<ITERGP_MATERN32>(prec, nstage, (int)G, smem_t, stream, maps, a);
     ITERGP_CUDA_TRY(e);
-    tc_fixup_kernel<<<static_cast<unsigned>(row_tiles), 256, 0, stream>>>(
-        part.as<float>(), units, G, (int)chunks, A.rows, pp, pw, Y + p0, ldY, active), ::itergp::note_launch();
-    ITERGP_CUDA_TRY(cudaGetLastError());
+    if (tail_rows > 0) {
+      tc_fixup_kernel<<<static_cast<unsigned>(tail_rows), 256, 0, stream>>>(
+          part.as<float>(), row_tiles, G, (int)chunks, A.rows, pp, pw, Y + p0, ldY, active), ::itergp::note_launch();
+      ITERGP_CUDA_TRY(cudaGetLastError());
+    }
   }
   return ITERGP_OK;
 }
