@@ -527,7 +527,10 @@ __global__ void combine_kernel(const FitState* __restrict__ st, const float* __r
 }
 
 // -------------------------------------------------------------------- inner iteration
-// r = P(b - u - W^+ v)   (u = K v, P removes the per-point class mean); partial |r|^2
+// r = P(b - u - W^+ v)   (u = K v, P removes the per-point class mean); partial |r|^2.
+// The residual is the small difference of large terms (u carries K's largest eigenvalues),
+// so it is formed in FP64 arithmetic from the FP32 operands and rounded once; it is the
+// quantity the inner convergence test reduces.
 __global__ void resid_kernel(const FitState* __restrict__ st, int64_t n, int C,
                              const float* __restrict__ b, const float* __restrict__ u,
                              const float* __restrict__ v, const float* __restrict__ inv_pi,
@@ -537,19 +540,24 @@ __global__ void resid_kernel(const FitState* __restrict__ st, int64_t n, int C,
   double acc = 0.0;
   for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
        i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
-    float w[kMaxC];
-    winv_point(v + i * C, inv_pi + i * C, C, w);
-    // with residual actions r is projected onto the class-contrast subspace, where it lies
-    // in exact arithmetic
-    float rm = 0.f;
+    const float* vi = v + i * C;
+    const float* ipi = inv_pi + i * C;
+    double m1 = 0.0;
+    for (int c = 0; c < C; ++c) m1 += vi[c];
+    m1 /= C;
+    double m2 = 0.0;
+    for (int c = 0; c < C; ++c) m2 += (vi[c] - m1) * static_cast<double>(ipi[c]);
+    m2 /= C;
+    double rm = 0.0;
     if (project) {
-      for (int c = 0; c < C; ++c) rm += b[i * C + c] - u[i * C + c] - w[c];
+      for (int c = 0; c < C; ++c)
+        rm += static_cast<double>(b[i * C + c]) - u[i * C + c] - ((vi[c] - m1) * ipi[c] - m2);
       rm /= C;
     }
     for (int c = 0; c < C; ++c) {
-      const float rv = b[i * C + c] - u[i * C + c] - w[c] - rm;
-      r[i * C + c] = rv;
-      acc += static_cast<double>(rv) * rv;
+      const double rv = static_cast<double>(b[i * C + c]) - u[i * C + c] - ((vi[c] - m1) * ipi[c] - m2) - rm;
+      r[i * C + c] = static_cast<float>(rv);
+      acc += rv * rv;
     }
   }
   acc = block_reduce_sum(acc, sh);
