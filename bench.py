@@ -42,6 +42,7 @@ def parse():
     ap.add_argument("--n", type=int, default=N_DEFAULT)
     ap.add_argument("--no-extras", action="store_true", help="skip other precisions and fit timings")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--batch-count", type=int, default=256, help="problems of the batched-fit extra")
     return ap.parse_args()
 
 
@@ -157,6 +158,61 @@ def reference_arm(args):
            "e2e": {"value": value, "unit": "kernel-pairs/s", "h2d_bytes_per_step": 0,
                    "d2h_bytes_per_step": 0}}
     print(json.dumps(out))
+
+
+BATCH_SCHED = dict(max_newton=5, max_iters=10, rank=50, tol_abs=1e-5, tol_rel=1e-5)
+
+
+def bench_batched(native, datagen, torch, dev, count):
+    """Batched fits: `count` independent blob problems (N log-uniform in [200, 20000],
+    D in {8, 16, 32, 64}, C in {2..10}, RBF lengthscale log-uniform in [0.3, 3]), one
+    schedule of 5 Newton steps x <= 10 iterations, R = 50, tolerance 1e-5.  Each batched
+    fit is one itergp_fit_batch call (graph captured and launched inside); the plain
+    path fits the same problems one by one in FP32 without a graph."""
+    probs = datagen.batch_problems(count=count)
+    dp = [(torch.as_tensor(p.X, device=dev), torch.as_tensor(p.y, device=dev), p.c,
+           p.lengthscale, 1.0) for p in probs]
+    n = [p.X.shape[0] for p in probs]
+    res = {"workload": f"{count} blob problems, N log-U[200,20000] (sum {sum(n)}), D in {{8,16,32,64}}, "
+                       "C in {2..10}, RBF l log-U[0.3,3]; 5 Newton x <=10 iters, R=50, tol 1e-5",
+           "sum_n2": float(sum(x * x for x in n))}
+
+    def timed(fn):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        models = fn()
+        torch.cuda.synchronize()
+        return time.perf_counter() - t0, models
+
+    for prec in ("fp32", "bf16x3", "bf16_comp"):
+        try:
+            for m in native.fit_batch(dp, precision=prec, graph=True, **BATCH_SCHED):   # warm-up
+                m.free()
+            l0 = native.launch_count()
+            dt, models = timed(lambda: native.fit_batch(dp, precision=prec, graph=True, **BATCH_SCHED))
+            launches = native.launch_count() - l0
+        except native.ItergpError as e:
+            res[prec] = {"error": str(e)}
+            continue
+        iters = [m.report.total_iters for m in models]
+        pairs = float(sum(it * x * x for it, x in zip(iters, n)))
+        res[prec] = {"fit_s": dt, "fits_per_s": count / dt, "total_iters": int(sum(iters)),
+                     "kernel_pairs_per_s": pairs / dt, "launches": int(launches)}
+        for m in models:
+            m.free()
+    l0 = native.launch_count()
+    t0 = time.perf_counter()
+    it_plain = 0
+    for X_, y_, c_, ell_, s_ in dp:
+        m = native.fit(X_, y_, c_, kind="rbf", lengthscale=ell_, outputscale=s_, precision="fp32",
+                       graph=False, **BATCH_SCHED)
+        it_plain += m.report.total_iters
+        m.free()
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    res["fp32_one_by_one"] = {"fit_s": dt, "fits_per_s": count / dt, "total_iters": int(it_plain),
+                              "launches": int(native.launch_count() - l0)}
+    return res
 
 
 def main():
@@ -314,6 +370,8 @@ def main():
             m.free()
         out["fit"] = {"workload": "IterNCGP fit, same data, C=10, 5 Newton steps x 5 iterations, R=200",
                       **fits}
+    if rank == 0 and not args.no_extras:
+        out["batched"] = bench_batched(native, datagen, torch, dev, args.batch_count)
     if rank == 0 and world == 1:
         out["cpu_baseline"] = cpu_baseline(X, S, args.cpu_seconds)
     if rank == 0:

@@ -179,6 +179,8 @@ typedef struct {
   double tol_newton;      /* outer stop on |g_i - g_{i-1}| / |g_i| <= tol (<= 0: off)*/
   double tol_abs;         /* inner stop, absolute (paper default 1e-5)             */
   double tol_rel;         /* inner stop, relative to |y_hat - m| (default 1e-5)     */
+  int32_t graph;          /* 1: capture the whole fit into one CUDA graph and launch
+                             it (fewer launch overheads); 0: launch kernels directly */
 } itergp_fit_params;
 
 #define ITERGP_MAX_REPORT_STEPS 64
@@ -204,6 +206,17 @@ typedef struct itergp_model itergp_model;
  * Returns ITERGP_ENUMERIC if a non-finite value appeared during the fit. */
 int itergp_fit(const itergp_fit_params* params, itergp_model** out, itergp_fit_report* report,
                itergp_stream stream);
+
+/* Batched fit of `count` independent problems (different n, d, c, X, y, lengthscale and
+ * outputscale) with one schedule: every phase of Alg. 1-3 runs as one launch over all
+ * problems (per-problem flags mask finished solves) and the kernel products run as one
+ * persistent launch over the row tiles of all problems.  Fields that must agree across
+ * params[0 .. count-1]: kernel.kind, precision, policy, max_newton, max_iters, rank,
+ * recycle, tol_newton, tol_abs, tol_rel, graph; literal_kv must be 0.  models[i] and
+ * reports[i] (reports may be NULL) receive each problem's result.  On failure no model
+ * is returned.  Waits for the stream like itergp_fit. */
+int itergp_fit_batch(const itergp_fit_params* params, int32_t count, itergp_model** models,
+                     itergp_fit_report* reports, itergp_stream stream);
 
 /* Posterior predictive of the fitted model (Eqs. 9-10 with C_j = Q Q^T) and the probit
  * approximation of App. C.3:
@@ -247,6 +260,12 @@ int64_t itergp_launch_count(void);
 int itergp_sync_status(itergp_stream stream);
 
 const char* itergp_status_string(int status);
+
+/* The CUDA call behind the calling thread's most recent ITERGP_ECUDA: "<call>: <CUDA
+ * error string> (<file>:<line>)", or "" if there was none.  The pointer is owned by the
+ * library and stays valid until the thread's next failing call.  (Library plumbing; the
+ * paper has no counterpart.) */
+const char* itergp_last_error(void);
 
 /* Library version "major.minor.patch". */
 const char* itergp_version(void);

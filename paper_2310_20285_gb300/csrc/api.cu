@@ -5,6 +5,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <atomic>
+#include <memory>
 #include <mutex>
 #include <vector>
 
@@ -12,9 +13,17 @@
 
 namespace itergp {
 
-int fit_run(DeviceContext* ctx, const itergp_fit_params& prm, const KParams& kp,
-            const RowOperand& Xop, const int32_t* y, float* v, float* f, float* Q, int bcap,
-            cudaStream_t stream, itergp_fit_report* rep, int* final_B);
+struct FitProblem {
+  const itergp_fit_params* prm;
+  KParams kp;
+  const RowOperand* xop;
+  float *v, *f, *Q;
+  int bcap;
+  itergp_fit_report* rep;
+  int* final_B;
+};
+int fit_run_batch(DeviceContext* ctx, const std::vector<FitProblem>& probs, cudaStream_t stream,
+                  bool use_graph);
 int winv_apply_launch(DeviceContext* ctx, const float* f, int64_t n, int c, const float* x,
                       float* out, cudaStream_t s);
 int pseudo_targets_launch(DeviceContext* ctx, const float* f, const int32_t* y, int64_t n, int c,
@@ -22,10 +31,16 @@ int pseudo_targets_launch(DeviceContext* ctx, const float* f, const int32_t* y, 
 int sym_eig_launch(DeviceContext* ctx, const double* M, int b, double* lam, double* U,
                    cudaStream_t s);
 
+namespace {
+thread_local char t_last_error[512] = "";
+}
+
 void record_cuda_error(cudaError_t err, const char* expr, const char* file, int line) {
   static const bool verbose = std::getenv("ITERGP_DEBUG") != nullptr;
-  if (verbose)
-    std::fprintf(stderr, "[itergp] %s failed: %s (%s:%d)\n", expr, cudaGetErrorString(err), file, line);
+  const char* base = std::strrchr(file, '/');
+  std::snprintf(t_last_error, sizeof(t_last_error), "%s: %s (%s:%d)", expr, cudaGetErrorString(err),
+                base ? base + 1 : file, line);
+  if (verbose) std::fprintf(stderr, "[itergp] %s\n", t_last_error);
 }
 
 namespace {
@@ -41,8 +56,15 @@ thread_local cudaEvent_t t_begin = nullptr;
 
 void note_launch(int64_t n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 
+// Kernel timing records plain events; inside a stream capture an event record only
+// orders the capture, so captured launches are not timed.
+bool stream_capturing(cudaStream_t s) {
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  return cudaStreamIsCapturing(s, &cs) == cudaSuccess && cs != cudaStreamCaptureStatusNone;
+}
+
 void timing_begin(cudaStream_t s) {
-  if (!g_timing.load(std::memory_order_relaxed)) return;
+  if (!g_timing.load(std::memory_order_relaxed) || stream_capturing(s)) return;
   cudaEvent_t e;
   if (cudaEventCreate(&e) != cudaSuccess) return;
   cudaEventRecord(e, s);
@@ -209,6 +231,8 @@ extern "C" {
 
 const char* itergp_version(void) { return "0.1.0"; }
 
+const char* itergp_last_error(void) { return t_last_error; }
+
 int itergp_timing_enable(int enable) {
   g_timing.store(enable != 0);
   return ITERGP_OK;
@@ -318,76 +342,146 @@ int itergp_sym_eig(const double* M, int32_t b, double* lam, double* U, itergp_st
   return sym_eig_launch(ctx, M, b, lam, U, static_cast<cudaStream_t>(stream));
 }
 
-int itergp_fit(const itergp_fit_params* prm, itergp_model** out, itergp_fit_report* report,
-               itergp_stream stream) {
-  if (!prm || !out) return ITERGP_EINVAL;
-  *out = nullptr;
+namespace {
+
+int validate_fit_params(const itergp_fit_params* prm) {
+  if (!prm) return ITERGP_EINVAL;
   if (prm->n < 1 || prm->d < 1 || prm->d > 4096 || prm->c < 2 || prm->c > 64 || !prm->X || !prm->y)
     return ITERGP_EINVAL;
   if (!kernel_ok(&prm->kernel) || !precision_ok(prm->precision)) return ITERGP_EINVAL;
   if (prm->policy != ITERGP_POLICY_CG && prm->policy != ITERGP_POLICY_UNIT) return ITERGP_EINVAL;
   if (prm->max_newton < 1 || prm->max_iters < 0 || prm->max_newton > 100000) return ITERGP_EINVAL;
   if (!(prm->tol_abs >= 0) || !(prm->tol_rel >= 0)) return ITERGP_EINVAL;
+  return ITERGP_OK;
+}
+
+int64_t buffer_capacity(const itergp_fit_params& p) {
+  const int64_t nc = p.n * p.c;
+  int64_t bcap = static_cast<int64_t>(p.max_newton) * p.max_iters;
+  if (p.recycle && p.rank >= 0) bcap = std::min<int64_t>(bcap, static_cast<int64_t>(p.rank) + p.max_iters);
+  if (!p.recycle) bcap = std::min<int64_t>(bcap, p.max_iters);
+  bcap = std::min<int64_t>(bcap, nc);
+  return std::max<int64_t>(bcap, 1);
+}
+
+void free_models(std::vector<itergp_model*>& ms) {
+  for (auto* m : ms) {
+    if (m) {
+      cudaFree(m->mem);
+      delete m;
+    }
+  }
+  ms.clear();
+}
+
+// Fits params[0..count) with one schedule; on success fills models/reports.
+int fit_many(const itergp_fit_params* params, int count, itergp_model** out,
+             itergp_fit_report* reports, cudaStream_t s) {
   DeviceContext* ctx = current_context();
   if (!ctx) return ITERGP_ECUDA;
-  if (precision_is_tensor(prm->precision) && !ctx->tcgen05) return ITERGP_EUNSUPPORTED;
-  cudaStream_t s = static_cast<cudaStream_t>(stream);
-
-  const int64_t n = prm->n, nc = n * prm->c;
-  int64_t bcap = static_cast<int64_t>(prm->max_newton) * prm->max_iters;
-  if (prm->recycle && prm->rank >= 0) bcap = std::min<int64_t>(bcap, static_cast<int64_t>(prm->rank) + prm->max_iters);
-  if (!prm->recycle) bcap = std::min<int64_t>(bcap, prm->max_iters);
-  bcap = std::min<int64_t>(bcap, nc);
-  bcap = std::max<int64_t>(bcap, 1);
-  if (bcap > 512) return ITERGP_EINVAL;
-
-  auto* mdl = new itergp_model();
-  mdl->device = ctx->device;
-  mdl->n = n;
-  mdl->d = prm->d;
-  mdl->c = prm->c;
-  mdl->bcap = static_cast<int>(bcap);
-  mdl->kernel = prm->kernel;
-  mdl->precision = prm->precision;
-  const size_t xb = align_up(sizeof(float) * n * prm->d, 256);
-  const size_t rb = rows_workspace_bytes(prm->precision, n, static_cast<int>(prm->d));
-  const size_t vb = align_up(sizeof(float) * nc, 256);
-  const size_t qb = align_up(sizeof(float) * nc * bcap, 256);
-  mdl->bytes = static_cast<int64_t>(xb + rb + 2 * vb + qb);
-  if (cudaMalloc(&mdl->mem, mdl->bytes) != cudaSuccess) {
-    delete mdl;
-    return ITERGP_ENOMEM;
+  if (precision_is_tensor(params[0].precision) && !ctx->tcgen05) return ITERGP_EUNSUPPORTED;
+  std::vector<itergp_model*> models(count, nullptr);
+  std::vector<itergp_fit_report> reps(count);
+  std::vector<int> finalB(count, 0);
+  std::vector<FitProblem> probs(count);
+  for (int i = 0; i < count; ++i) {
+    const itergp_fit_params& prm = params[i];
+    const int64_t n = prm.n, nc = n * prm.c;
+    const int64_t bcap = buffer_capacity(prm);
+    if (bcap > 512) {
+      free_models(models);
+      return ITERGP_EINVAL;
+    }
+    auto* mdl = new itergp_model();
+    models[i] = mdl;
+    mdl->device = ctx->device;
+    mdl->n = n;
+    mdl->d = prm.d;
+    mdl->c = prm.c;
+    mdl->bcap = static_cast<int>(bcap);
+    mdl->kernel = prm.kernel;
+    mdl->precision = prm.precision;
+    const size_t xb = align_up(sizeof(float) * n * prm.d, 256);
+    const size_t rb = rows_workspace_bytes(prm.precision, n, static_cast<int>(prm.d));
+    const size_t vb = align_up(sizeof(float) * nc, 256);
+    const size_t qb = align_up(sizeof(float) * nc * bcap, 256);
+    mdl->bytes = static_cast<int64_t>(xb + rb + 2 * vb + qb);
+    if (cudaMalloc(&mdl->mem, mdl->bytes) != cudaSuccess) {
+      mdl->mem = nullptr;
+      free_models(models);
+      return ITERGP_ENOMEM;
+    }
+    char* base = static_cast<char*>(mdl->mem);
+    mdl->X = reinterpret_cast<float*>(base);
+    mdl->v = reinterpret_cast<float*>(base + xb + rb);
+    mdl->f = reinterpret_cast<float*>(base + xb + rb + vb);
+    mdl->Q = reinterpret_cast<float*>(base + xb + rb + 2 * vb);
+    int rc = ITERGP_OK;
+    if (cudaMemcpyAsync(mdl->X, prm.X, sizeof(float) * n * prm.d, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+      rc = ITERGP_ECUDA;
+    if (rc == ITERGP_OK)
+      rc = prepare_rows(prm.precision, mdl->X, n, static_cast<int>(prm.d), prm.d, base + xb, &mdl->xop, s);
+    if (rc != ITERGP_OK) {
+      free_models(models);
+      return rc;
+    }
+    FitProblem& fp = probs[i];
+    fp.prm = &prm;
+    fp.kp = make_kparams(prm.kernel);
+    fp.xop = &mdl->xop;
+    fp.v = mdl->v;
+    fp.f = mdl->f;
+    fp.Q = mdl->Q;
+    fp.bcap = static_cast<int>(bcap);
+    fp.rep = &reps[i];
+    fp.final_B = &finalB[i];
   }
-  char* base = static_cast<char*>(mdl->mem);
-  mdl->X = reinterpret_cast<float*>(base);
-  mdl->v = reinterpret_cast<float*>(base + xb + rb);
-  mdl->f = reinterpret_cast<float*>(base + xb + rb + vb);
-  mdl->Q = reinterpret_cast<float*>(base + xb + rb + 2 * vb);
-  int rc = ITERGP_OK;
-  if (cudaMemcpyAsync(mdl->X, prm->X, sizeof(float) * n * prm->d, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
-    rc = ITERGP_ECUDA;
-  if (rc == ITERGP_OK)
-    rc = prepare_rows(prm->precision, mdl->X, n, static_cast<int>(prm->d), prm->d, base + xb, &mdl->xop, s);
-  itergp_fit_report rep{};
-  int finalB = 0;
-  if (rc == ITERGP_OK)
-    rc = fit_run(ctx, *prm, make_kparams(prm->kernel), mdl->xop, prm->y, mdl->v, mdl->f, mdl->Q,
-                 static_cast<int>(bcap), s, &rep, &finalB);
+  int rc = fit_run_batch(ctx, probs, s, params[0].graph != 0);
   if (rc == ITERGP_OK) {
-    const int st = itergp_sync_status(stream);
+    const int st = itergp_sync_status(s);
     if (st != ITERGP_OK) rc = st;
   }
   if (rc != ITERGP_OK) {
     cudaStreamSynchronize(s);
-    cudaFree(mdl->mem);
-    delete mdl;
+    free_models(models);
     return rc;
   }
-  mdl->B = finalB;
-  rep.device_bytes = mdl->bytes;
-  if (report) *report = rep;
-  *out = mdl;
+  for (int i = 0; i < count; ++i) {
+    models[i]->B = finalB[i];
+    reps[i].device_bytes = models[i]->bytes;
+    if (reports) reports[i] = reps[i];
+    out[i] = models[i];
+  }
   return ITERGP_OK;
+}
+
+}  // namespace
+
+int itergp_fit(const itergp_fit_params* prm, itergp_model** out, itergp_fit_report* report,
+               itergp_stream stream) {
+  if (!prm || !out) return ITERGP_EINVAL;
+  *out = nullptr;
+  const int rc = validate_fit_params(prm);
+  if (rc != ITERGP_OK) return rc;
+  return fit_many(prm, 1, out, report, static_cast<cudaStream_t>(stream));
+}
+
+int itergp_fit_batch(const itergp_fit_params* params, int32_t count, itergp_model** models,
+                     itergp_fit_report* reports, itergp_stream stream) {
+  if (!params || !models || count < 1 || count > 65535) return ITERGP_EINVAL;
+  for (int i = 0; i < count; ++i) models[i] = nullptr;
+  const itergp_fit_params& a = params[0];
+  for (int i = 0; i < count; ++i) {
+    const int rc = validate_fit_params(&params[i]);
+    if (rc != ITERGP_OK) return rc;
+    const itergp_fit_params& b = params[i];
+    if (b.kernel.kind != a.kernel.kind || b.precision != a.precision || b.policy != a.policy ||
+        b.max_newton != a.max_newton || b.max_iters != a.max_iters || b.rank != a.rank ||
+        b.recycle != a.recycle || b.literal_kv != 0 || b.tol_newton != a.tol_newton ||
+        b.tol_abs != a.tol_abs || b.tol_rel != a.tol_rel || b.graph != a.graph)
+      return ITERGP_EINVAL;
+  }
+  return fit_many(params, count, models, reports, static_cast<cudaStream_t>(stream));
 }
 
 int itergp_predict(const itergp_model* mdl, const float* Xs, int64_t m, float* mean, float* var,

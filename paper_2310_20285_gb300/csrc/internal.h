@@ -60,4 +60,47 @@ __host__ __device__ inline int64_t part_owner(int64_t u, int64_t U, int64_t G) {
   return ((u + 1) * G - 1) / U;
 }
 
+
+// ---------------------------------------------------------------- batched products
+// One row tile of one problem of a batched product, processed over all column chunks.
+struct WorkItem {
+  int32_t prob;      // index into the problem table
+  int32_t a_row;     // arena row of the tile's first row (multiple of 128)
+  int32_t tile_row;  // first output row of the tile within its problem
+  int32_t b_row0;    // arena row (= transposed-S column) of the problem's first row
+  int32_t chunks;    // 128-row column chunks of the problem
+  int32_t n_rows;    // rows of the problem
+  int32_t pad0, pad1;
+};
+
+// Per-problem output and kernel of a batched product launch.
+struct TcProb {
+  float* Y;          // output rows (already offset to the P tile's first column)
+  int64_t ldY;
+  int64_t m;         // valid rows
+  int32_t p_valid;   // valid output columns
+  int32_t pad;
+  KParams kp;
+  const int* active; // the problem's solver flag (nullptr: always active)
+};
+
+// Device-side tables of a batched product.
+struct KmvItemTables {
+  const WorkItem* items = nullptr;      // [n_items], grouped per CTA
+  const int32_t* item_begin = nullptr;  // [G + 1] (tensor-core path)
+  const TcProb* probs = nullptr;        // [nprob]
+  int G = 0;
+  int n_items = 0;
+};
+
+// Tensor-core product in item mode over an arena of rows (A = B = arena); s_hi/s_lo:
+// transposed split weights [p16][arena.rows_pad].  All problems share `kind`.
+int kmv_tc_items(DeviceContext* ctx, int kind, const RowOperand& arena, const KmvItemTables& tab,
+                 int p16, const __nv_bfloat16* s_hi, const __nv_bfloat16* s_lo, cudaStream_t stream);
+
+// FP32 SIMT product in item mode: one CTA per item; FP32 arena rows (ld = arena.d_pad),
+// S = FP32 arena [rows_pad][p_max].  All problems share `kind`.
+int kmv_simt_items(DeviceContext* ctx, int kind, const RowOperand& arena, const KmvItemTables& tab,
+                   const float* S, int p_max, cudaStream_t stream);
+
 }  // namespace itergp

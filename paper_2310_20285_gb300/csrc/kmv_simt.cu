@@ -32,14 +32,34 @@ kmv_simt_kernel(const float* __restrict__ A, int64_t ldA, const float* __restric
                 const float* __restrict__ B, int64_t ldB, const float* __restrict__ nb, int64_t n,
                 int d, const float* __restrict__ S, int64_t ldS, int64_t p, float* __restrict__ out,
                 int64_t ldo, int64_t split_stride, int chunks_per_split, KParams kp,
-                const int* __restrict__ active) {
+                const int* __restrict__ active, const WorkItem* __restrict__ items,
+                const TcProb* __restrict__ probs) {
   if (active != nullptr && *active == 0) return;
   constexpr int PT = 16 * PJ;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   SimtSmem<PJ>& sm = *reinterpret_cast<SimtSmem<PJ>*>(smem_raw);
 
   const int tid = threadIdx.x, tx = tid % 16, ty = tid / 16;
-  const int64_t m0 = static_cast<int64_t>(blockIdx.x) * BM;
+  int64_t m0 = static_cast<int64_t>(blockIdx.x) * BM;
+  if (items != nullptr) {
+    // item mode: one whole row tile of one problem of a batch (A = B = the row arena)
+    const WorkItem it = items[blockIdx.x];
+    const TcProb pr = probs[it.prob];
+    if (pr.active != nullptr && *pr.active == 0) return;
+    A += static_cast<int64_t>(it.a_row) * ldA;
+    na += it.a_row;
+    m = pr.m - it.tile_row < BM ? pr.m - it.tile_row : BM;
+    m0 = 0;
+    B += static_cast<int64_t>(it.b_row0) * ldB;
+    nb += it.b_row0;
+    n = it.n_rows;
+    S += static_cast<int64_t>(it.b_row0) * ldS;
+    p = pr.p_valid;
+    out = pr.Y + static_cast<int64_t>(it.tile_row) * pr.ldY;
+    ldo = pr.ldY;
+    kp = pr.kp;
+    chunks_per_split = static_cast<int>((n + BN - 1) / BN);
+  }
   const int64_t p0 = static_cast<int64_t>(blockIdx.z) * PT;
   const int64_t n_chunks = (n + BN - 1) / BN;
   const int64_t c_begin = static_cast<int64_t>(blockIdx.y) * chunks_per_split;
@@ -201,14 +221,15 @@ __global__ void reduce_splits_kernel(const float* __restrict__ part, int splits,
 template <int KIND, int PJ>
 cudaError_t launch_simt(dim3 grid, cudaStream_t st, const RowOperand& A, const RowOperand& B,
                         const float* S, int64_t ldS, int64_t p, float* out, int64_t ldo,
-                        int64_t split_stride, int cps, const KParams& kp, const int* active) {
+                        int64_t split_stride, int cps, const KParams& kp, const int* active,
+                        const WorkItem* items = nullptr, const TcProb* probs = nullptr) {
   const size_t smem = sizeof(SimtSmem<PJ>);
   auto fn = kmv_simt_kernel<KIND, PJ>;
   cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   timing_begin(st);
   fn<<<grid, 256, smem, st>>>(A.X, A.ldX, A.norms, A.rows, B.X, B.ldX, B.norms, B.rows, A.d, S, ldS,
-                              p, out, ldo, split_stride, cps, kp, active), ::itergp::note_launch();
+                              p, out, ldo, split_stride, cps, kp, active, items, probs), ::itergp::note_launch();
   timing_end(st);
   return cudaGetLastError();
 }
@@ -226,7 +247,31 @@ cudaError_t dispatch_pj(int pj, dim3 grid, cudaStream_t st, const RowOperand& A,
   }
 }
 
+template <int KIND>
+cudaError_t dispatch_items(int pj, dim3 grid, cudaStream_t st, const RowOperand& arena,
+                           const float* S, int p_max, const KParams& kp, const KmvItemTables& tab) {
+  switch (pj) {
+    case 1: return launch_simt<KIND, 1>(grid, st, arena, arena, S, p_max, p_max, nullptr, 0, 0, 0, kp, nullptr, tab.items, tab.probs);
+    case 2: return launch_simt<KIND, 2>(grid, st, arena, arena, S, p_max, p_max, nullptr, 0, 0, 0, kp, nullptr, tab.items, tab.probs);
+    case 4: return launch_simt<KIND, 4>(grid, st, arena, arena, S, p_max, p_max, nullptr, 0, 0, 0, kp, nullptr, tab.items, tab.probs);
+    default: return launch_simt<KIND, 8>(grid, st, arena, arena, S, p_max, p_max, nullptr, 0, 0, 0, kp, nullptr, tab.items, tab.probs);
+  }
+}
+
 }  // namespace
+
+int kmv_simt_items(DeviceContext* ctx, int kind, const RowOperand& arena, const KmvItemTables& tab,
+                   const float* S, int p_max, cudaStream_t stream) {
+  (void)ctx;
+  if (p_max > 128 || tab.n_items <= 0) return tab.n_items == 0 ? ITERGP_OK : ITERGP_EINVAL;
+  const int pj = p_max <= 16 ? 1 : p_max <= 32 ? 2 : p_max <= 64 ? 4 : 8;
+  dim3 grid(static_cast<unsigned>(tab.n_items), 1, 1);
+  const KParams kp = make_kparams(itergp_kernel{kind, 1.f, 1.f});   // per-item values from the table
+  cudaError_t e = kind == ITERGP_RBF ? dispatch_items<ITERGP_RBF>(pj, grid, stream, arena, S, p_max, kp, tab)
+                                     : dispatch_items<ITERGP_MATERN32>(pj, grid, stream, arena, S, p_max, kp, tab);
+  ITERGP_CUDA_TRY(e);
+  return ITERGP_OK;
+}
 
 int kmv_simt(DeviceContext* ctx, const KParams& kp, const RowOperand& A, const RowOperand& B,
              const float* S, int64_t ldS, int64_t p, float* Y, int64_t ldY, cudaStream_t stream,

@@ -27,6 +27,7 @@
 // CTA) go to scratch and a fix-up kernel adds them in CTA order, so results are
 // deterministic.
 #include <algorithm>
+#include <cstring>
 
 #include "internal.h"
 #include "tc_ptx.cuh"
@@ -61,6 +62,10 @@ struct TcArgs {
   KParams kp;
   int* status;
   const int* active;
+  // item mode (batched problems): per-CTA lists of whole row tiles
+  const WorkItem* items;            // nullptr: single-problem schedule
+  const int32_t* item_begin;        // [G + 1]
+  const TcProb* probs;
 };
 
 __host__ __device__ constexpr uint32_t stage_bytes(int nt1) {
@@ -96,6 +101,81 @@ struct Schedule {
   __host__ __device__ bool last(int64_t t) const { return t == T - 1 || row(t + 1) != row(t); }
 };
 
+struct StepInfo {
+  int32_t a_row;   // A-arena row of the current tile
+  int32_t b_row;   // B-arena row (transposed-S column) of the current chunk
+  int32_t c;       // chunk index within the row tile (flush boundaries)
+  int32_t item;    // item index (item mode) or -1
+  bool first, last;// first / last chunk of the CTA's run on this row tile
+};
+
+// Walks a CTA's steps in order; every role owns one and advances it in lockstep with the
+// step counter t.  Single mode follows Schedule; item mode walks the CTA's items, skipping
+// problems whose solver has stopped.
+struct Walker {
+  Schedule sch;
+  int64_t t = 0;
+  const WorkItem* items = nullptr;
+  const TcProb* probs = nullptr;
+  int32_t k = 0, k_end = 0, c = 0;
+
+  __device__ bool item_active(int32_t kk) const {
+    const int* a = probs[items[kk].prob].active;
+    return a == nullptr || *a != 0;
+  }
+  __device__ void skip_inactive() {
+    while (k < k_end && !item_active(k)) ++k;
+    c = 0;
+  }
+  __device__ void init(const TcArgs& a, int64_t G, int64_t g) {
+    items = a.items;
+    probs = a.probs;
+    t = 0;
+    if (items == nullptr) {
+      sch.init(a.row_tiles, a.chunks, G, g);
+    } else {
+      k = a.item_begin[g];
+      k_end = a.item_begin[g + 1];
+      skip_inactive();
+    }
+  }
+  __device__ int64_t total() const {   // number of steps
+    if (items == nullptr) return sch.T;
+    int64_t n = 0;
+    for (int32_t kk = k; kk < k_end; ++kk)
+      if (item_active(kk)) n += items[kk].chunks;
+    return n;
+  }
+  __device__ StepInfo cur() const {
+    StepInfo s;
+    if (items == nullptr) {
+      const int cc = sch.col(t);
+      s.a_row = static_cast<int32_t>(sch.row(t) * BM);
+      s.b_row = cc * BN;
+      s.c = cc;
+      s.first = sch.first(t);
+      s.last = sch.last(t);
+      s.item = -1;
+    } else {
+      const WorkItem& it = items[k];
+      s.a_row = it.a_row;
+      s.b_row = it.b_row0 + c * BN;
+      s.c = c;
+      s.first = (c == 0);
+      s.last = (c == it.chunks - 1);
+      s.item = k;
+    }
+    return s;
+  }
+  __device__ void next() {
+    ++t;
+    if (items != nullptr && ++c >= items[k].chunks) {
+      ++k;
+      skip_inactive();
+    }
+  }
+};
+
 template <int KIND, int NT1, int NT2, int NSTAGE>
 __global__ void __launch_bounds__(kThreads, 1)
 kmv_tc_kernel(const __grid_constant__ CUtensorMap mAh, const __grid_constant__ CUtensorMap mAl,
@@ -104,10 +184,11 @@ kmv_tc_kernel(const __grid_constant__ CUtensorMap mAh, const __grid_constant__ C
               const TcArgs args) {
   if (args.active != nullptr && *args.active == 0) return;
   const int64_t G = gridDim.x, g = blockIdx.x;
-  Schedule sch;
-  sch.init(args.row_tiles, args.chunks, G, g);
-  if (sch.T <= 0) return;
-  const int64_t T = sch.T;
+  Walker walk0;
+  walk0.init(args, G, g);
+  const int64_t T = walk0.total();
+  if (T <= 0) return;
+  const Schedule& sch = walk0.sch;
 
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
@@ -162,10 +243,11 @@ kmv_tc_kernel(const __grid_constant__ CUtensorMap mAh, const __grid_constant__ C
       uint32_t phase = 0;
       uint32_t armed = 0, armed_par = 0;      // bit i: stage i armed / parity of last arm
       uint32_t s_armed = 0, s_par = 0;
-      for (int64_t t = 0; t < T && !*ab; ++t) {
-        const int32_t a_y = static_cast<int32_t>(sch.row(t) * BM);
-        const int32_t c = sch.col(t);
-        const int32_t b_y = c * BN;
+      Walker wk = walk0;
+      for (int64_t t = 0; t < T && !*ab; ++t, wk.next()) {
+        const StepInfo st = wk.cur();
+        const int32_t a_y = st.a_row;
+        const int32_t b_y = st.b_row;
         for (int ks = 0; ks < args.nk; ++ks) {
           if (!mbar_wait(&empty_bar[stage], phase ^ 1u, ab, kWaitLimitNs)) break;
           mbar_arrive_expect_tx(&full_bar[stage], SB);
@@ -213,10 +295,13 @@ kmv_tc_kernel(const __grid_constant__ CUtensorMap mAh, const __grid_constant__ C
       uint32_t phase = 0;
       int64_t sub = -1;
       bool ok = true;
+      Walker wk2 = walk0;   // lags the GEMM1 loop by one step
       auto gemm2 = [&](int64_t t) -> bool {
-        const int c = sch.col(t);
-        const bool first = sch.first(t) || (c % kFlushChunks == 0);
-        const bool last = sch.last(t) || ((c + 1) % kFlushChunks == 0);
+        const StepInfo st = wk2.cur();
+        wk2.next();
+        const int c = st.c;
+        const bool first = st.first || (c % kFlushChunks == 0);
+        const bool last = st.last || ((c + 1) % kFlushChunks == 0);
         if (first) {
           ++sub;
           if (sub >= 1 && !mbar_wait(&oempty, static_cast<uint32_t>((sub - 1) & 1), ab, kWaitLimitNs))
@@ -294,25 +379,38 @@ kmv_tc_kernel(const __grid_constant__ CUtensorMap mAh, const __grid_constant__ C
     int seg_c0 = 0, sub_in_seg = 0;
     float na_r = 0.f;
     int64_t grow = 0;
-    const KParams kp = args.kp;
+    KParams kp = args.kp;
     const int J = args.chunks;
-    for (int64_t t = 0; t < T; ++t) {
-      const int64_t r = sch.row(t);
-      const int c = sch.col(t);
-      const bool first = sch.first(t);
-      const bool last = sch.last(t);
+    float* out_row = nullptr;       // item mode: this row's output
+    bool out_valid = false;
+    int out_lim = 0;
+    Walker wk = walk0;
+    for (int64_t t = 0; t < T; ++t, wk.next()) {
+      const StepInfo st = wk.cur();
+      const int c = st.c;
+      const bool first = st.first;
+      const bool last = st.last;
       const bool sub_last = last || ((c + 1) % kFlushChunks == 0);
       if (first) {
         ++seg;
         seg_c0 = c;
         sub_in_seg = 0;
-        grow = r * BM + row;
+        grow = static_cast<int64_t>(st.a_row) + row;
         na_r = args.na[grow];
+        if (st.item >= 0) {
+          const WorkItem& it = args.items[st.item];
+          const TcProb& pr = args.probs[it.prob];
+          kp = pr.kp;
+          const int64_t prow = static_cast<int64_t>(it.tile_row) + row;
+          out_valid = prow < pr.m;
+          out_row = pr.Y + prow * pr.ldY;
+          out_lim = pr.p_valid;
+        }
       }
       float* nb_s = nb_all + q * BN;
       __syncwarp();
 #pragma unroll
-      for (int k = 0; k < BN / 32; ++k) nb_s[lane + 32 * k] = args.nb[static_cast<int64_t>(c) * BN + lane + 32 * k];
+      for (int k = 0; k < BN / 32; ++k) nb_s[lane + 32 * k] = args.nb[static_cast<int64_t>(st.b_row) + lane + 32 * k];
       __syncwarp();
       const int gb = static_cast<int>(t & 1);
       if (!mbar_wait_warp(&gfull[gb], static_cast<uint32_t>((t >> 1) & 1), ab, kWaitLimitNs)) break;
@@ -347,11 +445,14 @@ kmv_tc_kernel(const __grid_constant__ CUtensorMap mAh, const __grid_constant__ C
         ++sub;
         if (!mbar_wait_warp(&ofull, static_cast<uint32_t>(sub & 1), ab, kWaitLimitNs)) break;
         tc_fence_after();
-        const bool full_row = (seg_c0 == 0) && (c == J - 1);
+        const bool full_row = st.item >= 0 || ((seg_c0 == 0) && (c == J - 1));
         float* dst = nullptr;
         bool valid = true;
         if (last) {
-          if (full_row) {
+          if (st.item >= 0) {
+            dst = out_row;
+            valid = out_valid;
+          } else if (full_row) {
             dst = args.Y + grow * args.ldY;
             valid = grow < args.m;
           } else {
@@ -360,7 +461,7 @@ kmv_tc_kernel(const __grid_constant__ CUtensorMap mAh, const __grid_constant__ C
             dst = args.partial + (slot * BM + row) * args.p_pad;
           }
         }
-        const int lim = full_row ? args.p_valid : args.p_pad;
+        const int lim = st.item >= 0 ? out_lim : (full_row ? args.p_valid : args.p_pad);
         for (int c16 = 0; c16 < args.p_pad / 16; ++c16) {
           uint32_t o[16];
           tmem_ld16(tb + lane_base + kOCol + 16 * c16, o);
@@ -484,6 +585,47 @@ cudaError_t launch_prec(int prec, int nstage, int grid, size_t smem, cudaStream_
 
 }  // namespace
 
+int kmv_tc_items(DeviceContext* ctx, int kind, const RowOperand& arena, const KmvItemTables& tab,
+                 int p16, const __nv_bfloat16* s_hi, const __nv_bfloat16* s_lo, cudaStream_t stream) {
+  const int prec = arena.precision;
+  const int nt1 = precision_splits_rows(prec) ? 3 : 1;
+  const int nt2 = precision_splits_weights(prec) ? 3 : 1;
+  if (p16 > 128 || p16 % 16 != 0 || tab.G <= 0) return ITERGP_EINVAL;
+  const size_t smem_cap = std::min<size_t>(ctx->smem_optin, 232448) - 2048;
+  const size_t fixed = 2 * s_buf_bytes(nt2, p16) + kSmemExtra;
+  const int fit = static_cast<int>((smem_cap > fixed ? smem_cap - fixed : 0) / stage_bytes(nt1));
+  const int nstage = fit >= 4 ? 4 : fit >= 3 ? 3 : fit >= 2 ? 2 : 0;
+  if (nstage < 2) return ITERGP_EUNSUPPORTED;
+  const size_t smem = nstage * stage_bytes(nt1) + 2 * s_buf_bytes(nt2, p16) + kSmemExtra;
+  CUtensorMap maps[6];
+  const bool ok =
+      encode_bf16_sw128(&maps[0], arena.hi, arena.rows_pad, arena.d_pad, arena.d_pad, BM) &&
+      encode_bf16_sw128(&maps[1], nt1 == 3 ? arena.lo : arena.hi, arena.rows_pad, arena.d_pad, arena.d_pad, BM) &&
+      encode_bf16_sw128(&maps[2], arena.hi, arena.rows_pad, arena.d_pad, arena.d_pad, BN) &&
+      encode_bf16_sw128(&maps[3], nt1 == 3 ? arena.lo : arena.hi, arena.rows_pad, arena.d_pad, arena.d_pad, BN) &&
+      encode_bf16_sw128(&maps[4], s_hi, p16, arena.rows_pad, arena.rows_pad, p16) &&
+      encode_bf16_sw128(&maps[5], nt2 == 3 ? s_lo : s_hi, p16, arena.rows_pad, arena.rows_pad, p16);
+  if (!ok) return ITERGP_ECUDA;
+  TcArgs a{};
+  a.na = arena.norms;
+  a.nb = arena.norms;
+  a.nk = arena.d_pad / BK;
+  a.p_pad = p16;
+  a.p_valid = p16;
+  a.s_row0 = 0;
+  a.status = ctx->status;
+  a.active = nullptr;
+  a.items = tab.items;
+  a.item_begin = tab.item_begin;
+  a.probs = tab.probs;
+  a.kp = make_kparams(itergp_kernel{kind, 1.f, 1.f});   // per-item values come from the table
+  cudaError_t e = kind == ITERGP_RBF
+                      ? launch_prec<ITERGP_RBF>(prec, nstage, tab.G, smem, stream, maps, a)
+                      : launch_prec<ITERGP_MATERN32>(prec, nstage, tab.G, smem, stream, maps, a);
+  ITERGP_CUDA_TRY(e);
+  return ITERGP_OK;
+}
+
 int kmv_tc(DeviceContext* ctx, const KParams& kp, const RowOperand& A, const RowOperand& B,
            const float* S, int64_t ldS, int64_t p, float* Y, int64_t ldY, cudaStream_t stream,
            const int* active) {
@@ -546,7 +688,7 @@ int kmv_tc(DeviceContext* ctx, const KParams& kp, const RowOperand& A, const Row
     ok = encode_bf16_sw128(&maps[4], s_hi, p16, n_pad, n_pad, pp) &&
          encode_bf16_sw128(&maps[5], nt2 == 3 ? s_lo : s_hi, p16, n_pad, n_pad, pp);
     if (!ok) return ITERGP_ECUDA;
-    TcArgs a;
+    TcArgs a{};   // items/item_begin/probs stay null: single-problem schedule
     a.na = A.norms;
     a.nb = B.norms;
     a.m = A.rows;
@@ -562,6 +704,9 @@ int kmv_tc(DeviceContext* ctx, const KParams& kp, const RowOperand& A, const Row
     a.kp = kp;
     a.status = ctx->status;
     a.active = active;
+    a.items = nullptr;
+    a.item_begin = nullptr;
+    a.probs = nullptr;
     const size_t smem_t = nstage * stage_bytes(nt1) + 2 * s_buf_bytes(nt2, pp) + kSmemExtra;
     (void)smem;
     cudaError_t e = kp.kind == ITERGP_RBF

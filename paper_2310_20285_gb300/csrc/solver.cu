@@ -39,17 +39,20 @@ struct FitState {
   double rel_change[ITERGP_MAX_REPORT_STEPS];
 };
 
-struct FitConfig {
-  int64_t n;
-  int c;
-  int64_t nc;
-  int bcap;            // buffer capacity (columns)
-  int policy;
-  int rank;            // R (< 0: no limit)
-  int max_iters;
-  int literal_kv;
-  int recycle;
-  double tol_newton, tol_abs, tol_rel;
+// Per-problem device descriptor of a (batched) fit: sizes, state and every array.  Kernels
+// receive the table and select their problem with blockIdx.y (per-problem kernels with
+// blockIdx.x).
+struct ProbDev {
+  FitState* st;
+  int64_t n, nc;
+  int c, bcap;
+  const int32_t* y;
+  float *f, *v, *Q;                  // model arrays
+  float *S, *T, *KQ;                 // buffers [bcap][nc]
+  float *u, *b, *r, *z, *gp, *ip, *s_cur, *t_cur;
+  float *w, *sq, *W;
+  double *Am, *Vm, *pg, *pv, *ps;
+  int* bold;
 };
 
 namespace {
@@ -86,11 +89,18 @@ __device__ __forceinline__ void set_status(int* status, int code) { atomicCAS(st
 // For every point: pi = softmax(f_n), 1/pi = exp(lse - f), grad = e_y - pi,
 // b = y_hat - m = f + W^+ grad (m = 0).  Partial sums: |b|^2, log p(y|f), v.(f - m),
 // |g - g_prev|^2, |g|^2 with g = f - m; g_prev <- g.
-__global__ void newton_prologue_kernel(const FitState* __restrict__ st, int64_t n, int C,
-                                       const float* __restrict__ f, const int32_t* __restrict__ y,
-                                       const float* __restrict__ v, float* __restrict__ g_prev,
-                                       float* __restrict__ inv_pi, float* __restrict__ b,
-                                       double* __restrict__ part, int* status, int project) {
+__global__ void newton_prologue_kernel(const ProbDev* __restrict__ probs, int* status, int project) {
+  const ProbDev& P = probs[blockIdx.y];
+  const FitState* st = P.st;
+  const int64_t n = P.n;
+  const int C = P.c;
+  const float* __restrict__ f = P.f;
+  const int32_t* __restrict__ y = P.y;
+  const float* __restrict__ v = P.v;
+  float* __restrict__ g_prev = P.gp;
+  float* __restrict__ inv_pi = P.ip;
+  float* __restrict__ b = P.b;
+  double* __restrict__ part = P.ps;
   if (!st->newton_active) return;
   __shared__ double sh[32];
   double s_b2 = 0, s_ll = 0, s_vf = 0, s_dg = 0, s_g2 = 0;
@@ -154,9 +164,12 @@ __global__ void newton_prologue_kernel(const FitState* __restrict__ st, int64_t 
   r = block_reduce_sum(s_g2, sh); if (threadIdx.x == 0) part[blockIdx.x * 5 + 4] = r;
 }
 
-__global__ void newton_finalize_kernel(FitState* st, const double* __restrict__ part, int nblk,
-                                       int step, double tol_newton, double tol_abs,
-                                       double tol_rel, int recycle) {
+__global__ void newton_finalize_kernel(const ProbDev* __restrict__ probs, int nblk, int step,
+                                       double tol_newton, double tol_abs, double tol_rel,
+                                       int recycle) {
+  const ProbDev& P = probs[blockIdx.x];
+  FitState* st = P.st;
+  const double* __restrict__ part = P.ps;
   if (threadIdx.x != 0 || !st->newton_active) return;
   double s[5] = {0, 0, 0, 0, 0};
   for (int b = 0; b < nblk; ++b)
@@ -183,9 +196,15 @@ __global__ void newton_finalize_kernel(FitState* st, const double* __restrict__ 
 
 // -------------------------------------------------------------------- Alg. 3 pieces
 // Z = T + W^+ S for the B committed columns (written into the Q buffer as scratch).
-__global__ void vsr_z_kernel(const FitState* __restrict__ st, int64_t n, int C, int64_t nc,
-                             const float* __restrict__ S, const float* __restrict__ T,
-                             const float* __restrict__ inv_pi, float* __restrict__ Z) {
+__global__ void vsr_z_kernel(const ProbDev* __restrict__ probs) {
+  const ProbDev& P = probs[blockIdx.y];
+  const FitState* st = P.st;
+  const int64_t n = P.n, nc = P.nc;
+  const int C = P.c;
+  const float* __restrict__ S = P.S;
+  const float* __restrict__ T = P.T;
+  const float* __restrict__ inv_pi = P.ip;
+  float* __restrict__ Z = P.Q;
   if (!st->newton_active) return;
   const int B = st->B;
   const int64_t total = static_cast<int64_t>(B) * n;
@@ -204,14 +223,20 @@ __global__ void vsr_z_kernel(const FitState* __restrict__ st, int64_t n, int C, 
 // Gram partials G[split][a][b] = sum_{e in split} X[a][e] Y[b][e], a, b < B (32 x 32
 // tiles, FP32 products summed in FP64).
 constexpr int kGT = 32;
-__global__ void gram_partial_kernel(const FitState* __restrict__ st, const float* __restrict__ X,
-                                    const float* __restrict__ Y, int64_t nc, int bcap,
-                                    int64_t per_split, double* __restrict__ part) {
+__global__ void gram_partial_kernel(const ProbDev* __restrict__ probs, int tiles) {
+  const ProbDev& P = probs[blockIdx.z];
+  const FitState* st = P.st;
+  const float* __restrict__ X = P.S;
+  const float* __restrict__ Y = P.Q;
+  const int64_t nc = P.nc;
+  const int bcap = P.bcap;
+  double* __restrict__ part = P.pg;
   if (!st->newton_active) return;
   const int B = st->B;
-  const int a0 = blockIdx.x * kGT, b0 = blockIdx.y * kGT;
+  const int a0 = (blockIdx.x / tiles) * kGT, b0 = (blockIdx.x % tiles) * kGT;
   if (a0 >= B || b0 >= B) return;
-  const int64_t e0 = static_cast<int64_t>(blockIdx.z) * per_split;
+  const int64_t per_split = (nc + gridDim.y - 1) / gridDim.y;
+  const int64_t e0 = static_cast<int64_t>(blockIdx.y) * per_split;
   const int64_t e1 = std::min<int64_t>(e0 + per_split, nc);
   __shared__ float xs[64][kGT + 1], ys[64][kGT + 1];
   const int tid = threadIdx.x, tx = tid % 16, ty = tid / 16;   // 2 x 2 outputs each
@@ -238,7 +263,7 @@ __global__ void gram_partial_kernel(const FitState* __restrict__ st, const float
       for (int j = 0; j < 2; ++j) acc[i][j] += loc[i][j];
     __syncthreads();
   }
-  double* out = part + static_cast<int64_t>(blockIdx.z) * bcap * bcap;
+  double* out = part + static_cast<int64_t>(blockIdx.y) * bcap * bcap;
   for (int i = 0; i < 2; ++i)
     for (int j = 0; j < 2; ++j) {
       const int a = a0 + 2 * ty + i, bb = b0 + 2 * tx + j;
@@ -369,9 +394,15 @@ __device__ void eig_order(const double* A, int n, int ld, int* order) {
 // Sum Gram partials, symmetrise, eigendecompose, drop lambda <= 1e-12 lambda_max, keep
 // the R largest (Alg. 3), write rotation W[b][k] = U[b][k] lambda_k^-1/2 (FP32) and
 // sqrt(lambda_k); set B = B0 = kept columns.
-__global__ void vsr_eig_kernel(FitState* st, const double* __restrict__ part, int splits, int bcap,
-                               int rank, double* __restrict__ Amat, double* __restrict__ Vmat,
-                               float* __restrict__ W, float* __restrict__ sq, int step) {
+__global__ void vsr_eig_kernel(const ProbDev* __restrict__ probs, int splits, int rank, int step) {
+  const ProbDev& P = probs[blockIdx.x];
+  FitState* st = P.st;
+  const double* __restrict__ part = P.pg;
+  const int bcap = P.bcap;
+  double* __restrict__ Amat = P.Am;
+  double* __restrict__ Vmat = P.Vm;
+  float* __restrict__ W = P.W;
+  float* __restrict__ sq = P.sq;
   if (!st->newton_active) return;
   const int B = st->B;
   if (B == 0) {
@@ -421,10 +452,17 @@ __global__ void vsr_eig_kernel(FitState* st, const double* __restrict__ part, in
 
 // Q[:, k] = sum_b S[:, b] W[b][k];  KQ[:, k] = sum_b T[:, b] W[b][k]   (k < B_new, b < B_old)
 // W is read with warp-uniform addresses (broadcast loads through L1).
-__global__ void vsr_rotate_kernel(const FitState* __restrict__ st, const int* __restrict__ bold_ptr,
-                                  int64_t nc, int bcap, const float* __restrict__ S,
-                                  const float* __restrict__ T, const float* __restrict__ W,
-                                  float* __restrict__ Q, float* __restrict__ KQ) {
+__global__ void vsr_rotate_kernel(const ProbDev* __restrict__ probs) {
+  const ProbDev& P = probs[blockIdx.y];
+  const FitState* st = P.st;
+  const int* __restrict__ bold_ptr = P.bold;
+  const int64_t nc = P.nc;
+  const int bcap = P.bcap;
+  const float* __restrict__ S = P.S;
+  const float* __restrict__ T = P.T;
+  const float* __restrict__ W = P.W;
+  float* __restrict__ Q = P.Q;
+  float* __restrict__ KQ = P.KQ;
   if (!st->newton_active) return;
   const int Bn = st->B, Bo = *bold_ptr;
   if (Bn == 0) return;
@@ -457,10 +495,15 @@ __global__ void vsr_rotate_kernel(const FitState* __restrict__ st, const int* __
 }
 
 // S[:, k] = Q[:, k] sqrt(lambda_k), T[:, k] = KQ[:, k] sqrt(lambda_k)  (= S U, T U)
-__global__ void vsr_rescale_kernel(const FitState* __restrict__ st, int64_t nc,
-                                   const float* __restrict__ sq, const float* __restrict__ Q,
-                                   const float* __restrict__ KQ, float* __restrict__ S,
-                                   float* __restrict__ T) {
+__global__ void vsr_rescale_kernel(const ProbDev* __restrict__ probs) {
+  const ProbDev& P = probs[blockIdx.y];
+  const FitState* st = P.st;
+  const int64_t nc = P.nc;
+  const float* __restrict__ sq = P.sq;
+  const float* __restrict__ Q = P.Q;
+  const float* __restrict__ KQ = P.KQ;
+  float* __restrict__ S = P.S;
+  float* __restrict__ T = P.T;
   if (!st->newton_active) return;
   const int Bn = st->B;
   const int64_t total = static_cast<int64_t>(Bn) * nc;
@@ -472,15 +515,20 @@ __global__ void vsr_rescale_kernel(const FitState* __restrict__ st, int64_t nc,
   }
 }
 
-__global__ void copy_int_kernel(const FitState* __restrict__ st, int* dst) {
-  if (threadIdx.x == 0 && blockIdx.x == 0) *dst = st->B;
+__global__ void copy_int_kernel(const ProbDev* __restrict__ probs) {
+  if (threadIdx.x == 0) *probs[blockIdx.x].bold = probs[blockIdx.x].st->B;
 }
 
 // -------------------------------------------------------------------- projections
 // part[blk][k] = sum_{e in blk} Q[k][e] x[e]   for k < B   (warp per column)
-__global__ void proj_partial_kernel(const FitState* __restrict__ st, int guard_inner,
-                                    const float* __restrict__ Q, const float* __restrict__ x,
-                                    int64_t nc, int bcap, double* __restrict__ part) {
+__global__ void proj_partial_kernel(const ProbDev* __restrict__ probs, int guard_inner) {
+  const ProbDev& P = probs[blockIdx.y];
+  const FitState* st = P.st;
+  const float* __restrict__ Q = P.Q;
+  const float* __restrict__ x = guard_inner ? P.z : P.b;   // Q^T z in the loop, Q0^T b after Alg. 3
+  const int64_t nc = P.nc;
+  const int bcap = P.bcap;
+  double* __restrict__ part = P.pv;
   if (!st->newton_active || (guard_inner && !st->active)) return;
   const int B = st->B;
   const int64_t per = (nc + gridDim.x - 1) / gridDim.x;
@@ -496,9 +544,12 @@ __global__ void proj_partial_kernel(const FitState* __restrict__ st, int guard_i
   }
 }
 
-__global__ void proj_finalize_kernel(const FitState* __restrict__ st, int guard_inner,
-                                     const double* __restrict__ part, int nblk, int bcap,
-                                     float* __restrict__ w) {
+__global__ void proj_finalize_kernel(const ProbDev* __restrict__ probs, int guard_inner, int nblk) {
+  const ProbDev& P = probs[blockIdx.x];
+  const FitState* st = P.st;
+  const double* __restrict__ part = P.pv;
+  const int bcap = P.bcap;
+  float* __restrict__ w = P.w;
   if (!st->newton_active || (guard_inner && !st->active)) return;
   const int B = st->B;
   for (int k = threadIdx.x; k < B; k += blockDim.x) {
@@ -509,9 +560,15 @@ __global__ void proj_finalize_kernel(const FitState* __restrict__ st, int guard_
 }
 
 // v = Q w, u = KQ w over the B0 recycled columns (v0 = C0 b, K v0)
-__global__ void combine_kernel(const FitState* __restrict__ st, const float* __restrict__ Q,
-                               const float* __restrict__ KQ, const float* __restrict__ w,
-                               int64_t nc, float* __restrict__ v, float* __restrict__ u) {
+__global__ void combine_kernel(const ProbDev* __restrict__ probs) {
+  const ProbDev& P = probs[blockIdx.y];
+  const FitState* st = P.st;
+  const float* __restrict__ Q = P.Q;
+  const float* __restrict__ KQ = P.KQ;
+  const float* __restrict__ w = P.w;
+  const int64_t nc = P.nc;
+  float* __restrict__ v = P.v;
+  float* __restrict__ u = P.u;
   if (!st->newton_active) return;
   const int B = st->B;
   for (int64_t e = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; e < nc;
@@ -531,10 +588,17 @@ __global__ void combine_kernel(const FitState* __restrict__ st, const float* __r
 // The residual is the small difference of large terms (u carries K's largest eigenvalues),
 // so it is formed in FP64 arithmetic from the FP32 operands and rounded once; it is the
 // quantity the inner convergence test reduces.
-__global__ void resid_kernel(const FitState* __restrict__ st, int64_t n, int C,
-                             const float* __restrict__ b, const float* __restrict__ u,
-                             const float* __restrict__ v, const float* __restrict__ inv_pi,
-                             float* __restrict__ r, double* __restrict__ part, int project) {
+__global__ void resid_kernel(const ProbDev* __restrict__ probs, int project) {
+  const ProbDev& P = probs[blockIdx.y];
+  const FitState* st = P.st;
+  const int64_t n = P.n;
+  const int C = P.c;
+  const float* __restrict__ b = P.b;
+  const float* __restrict__ u = P.u;
+  const float* __restrict__ v = P.v;
+  const float* __restrict__ inv_pi = P.ip;
+  float* __restrict__ r = P.r;
+  double* __restrict__ part = P.ps;
   if (!st->newton_active || !st->active) return;
   __shared__ double sh[32];
   double acc = 0.0;
@@ -565,9 +629,12 @@ __global__ void resid_kernel(const FitState* __restrict__ st, int64_t n, int C,
 }
 
 // commit the pending column; |r|; inner stopping test (App. B.2); alpha
-__global__ void resid_finalize_kernel(FitState* st, const double* __restrict__ part, int nblk,
-                                      const float* __restrict__ r, int64_t nc, int policy,
-                                      int step) {
+__global__ void resid_finalize_kernel(const ProbDev* __restrict__ probs, int nblk, int policy) {
+  const ProbDev& P = probs[blockIdx.x];
+  FitState* st = P.st;
+  const double* __restrict__ part = P.ps;
+  const float* __restrict__ r = P.r;
+  const int64_t nc = P.nc;
   if (threadIdx.x != 0 || !st->newton_active || !st->active) return;
   if (st->pending) {
     st->B += 1;
@@ -595,9 +662,13 @@ __global__ void resid_finalize_kernel(FitState* st, const double* __restrict__ p
 }
 
 // s = r (CG) or e_{B0+j} (unit vectors) into the staging vector and S[:, B]
-__global__ void action_kernel(const FitState* __restrict__ st, int64_t nc, int policy,
-                              const float* __restrict__ r, float* __restrict__ s_cur,
-                              float* __restrict__ S) {
+__global__ void action_kernel(const ProbDev* __restrict__ probs, int policy) {
+  const ProbDev& P = probs[blockIdx.y];
+  const FitState* st = P.st;
+  const int64_t nc = P.nc;
+  const float* __restrict__ r = P.r;
+  float* __restrict__ s_cur = P.s_cur;
+  float* __restrict__ S = P.S;
   if (!st->newton_active || !st->active) return;
   float* col = S + static_cast<int64_t>(st->B) * nc;
   const int64_t idx = static_cast<int64_t>(st->B0) + st->j;
@@ -610,10 +681,16 @@ __global__ void action_kernel(const FitState* __restrict__ st, int64_t nc, int p
 }
 
 // T[:, B] = t; z = t + W^+ s
-__global__ void z_kernel(const FitState* __restrict__ st, int64_t n, int C,
-                         const float* __restrict__ s_cur, const float* __restrict__ t_cur,
-                         const float* __restrict__ inv_pi, float* __restrict__ z,
-                         float* __restrict__ T) {
+__global__ void z_kernel(const ProbDev* __restrict__ probs) {
+  const ProbDev& P = probs[blockIdx.y];
+  const FitState* st = P.st;
+  const int64_t n = P.n;
+  const int C = P.c;
+  const float* __restrict__ s_cur = P.s_cur;
+  const float* __restrict__ t_cur = P.t_cur;
+  const float* __restrict__ inv_pi = P.ip;
+  float* __restrict__ z = P.z;
+  float* __restrict__ T = P.T;
   if (!st->newton_active || !st->active) return;
   const int64_t nc = n * C;
   float* tcol = T + static_cast<int64_t>(st->B) * nc;
@@ -630,11 +707,17 @@ __global__ void z_kernel(const FitState* __restrict__ st, int64_t n, int C,
 }
 
 // d = s - Q w -> Q[:, B] (unnormalised); K d = t - KQ w -> KQ[:, B]; partial eta = z.d
-__global__ void direction_kernel(const FitState* __restrict__ st, int64_t nc,
-                                 const float* __restrict__ s_cur, const float* __restrict__ t_cur,
-                                 const float* __restrict__ z, const float* __restrict__ w,
-                                 float* __restrict__ Q, float* __restrict__ KQ, int track_kd,
-                                 double* __restrict__ part) {
+__global__ void direction_kernel(const ProbDev* __restrict__ probs, int track_kd) {
+  const ProbDev& P = probs[blockIdx.y];
+  const FitState* st = P.st;
+  const int64_t nc = P.nc;
+  const float* __restrict__ s_cur = P.s_cur;
+  const float* __restrict__ t_cur = P.t_cur;
+  const float* __restrict__ z = P.z;
+  const float* __restrict__ w = P.w;
+  float* __restrict__ Q = P.Q;
+  float* __restrict__ KQ = P.KQ;
+  double* __restrict__ part = P.ps;
   if (!st->newton_active || !st->active) return;
   __shared__ double sh[32];
   const int B = st->B;
@@ -656,7 +739,9 @@ __global__ void direction_kernel(const FitState* __restrict__ st, int64_t nc,
   if (threadIdx.x == 0) part[blockIdx.x] = acc;
 }
 
-__global__ void eta_finalize_kernel(FitState* st, const double* __restrict__ part, int nblk) {
+__global__ void eta_finalize_kernel(const ProbDev* __restrict__ probs, int nblk) {
+  FitState* st = probs[blockIdx.x].st;
+  const double* __restrict__ part = probs[blockIdx.x].ps;
   if (threadIdx.x != 0 || !st->newton_active || !st->active) return;
   double s = 0.0;
   for (int b = 0; b < nblk; ++b) s += part[b];
@@ -674,9 +759,14 @@ __global__ void eta_finalize_kernel(FitState* st, const double* __restrict__ par
 }
 
 // Q[:, B] /= sqrt(eta); KQ[:, B] /= sqrt(eta); v += (alpha/eta) d; u += (alpha/eta) K d
-__global__ void update_kernel(const FitState* __restrict__ st, int64_t nc, float* __restrict__ Q,
-                              float* __restrict__ KQ, float* __restrict__ v, float* __restrict__ u,
-                              int track_kd) {
+__global__ void update_kernel(const ProbDev* __restrict__ probs, int track_kd) {
+  const ProbDev& P = probs[blockIdx.y];
+  const FitState* st = P.st;
+  const int64_t nc = P.nc;
+  float* __restrict__ Q = P.Q;
+  float* __restrict__ KQ = P.KQ;
+  float* __restrict__ v = P.v;
+  float* __restrict__ u = P.u;
   if (!st->newton_active || !st->active) return;
   const int B = st->B;
   const float coef = static_cast<float>(st->coef), ise = static_cast<float>(st->inv_sqrt_eta);
@@ -696,7 +786,8 @@ __global__ void update_kernel(const FitState* __restrict__ st, int64_t nc, float
 }
 
 // end of a Newton step: commit the pending column, record the step
-__global__ void step_end_kernel(FitState* st, int step) {
+__global__ void step_end_kernel(const ProbDev* __restrict__ probs, int step) {
+  FitState* st = probs[blockIdx.x].st;
   if (threadIdx.x != 0 || !st->newton_active) return;
   if (st->pending) {
     st->B += 1;
@@ -712,8 +803,12 @@ __global__ void step_end_kernel(FitState* st, int step) {
 }
 
 // f_{i+1} = u + m  (u = K v, m = 0)
-__global__ void copy_f_kernel(const FitState* __restrict__ st, int64_t nc, const float* __restrict__ u,
-                              float* __restrict__ f) {
+__global__ void copy_f_kernel(const ProbDev* __restrict__ probs) {
+  const ProbDev& P = probs[blockIdx.y];
+  const FitState* st = P.st;
+  const int64_t nc = P.nc;
+  const float* __restrict__ u = P.u;
+  float* __restrict__ f = P.f;
   if (!st->newton_active) return;
   for (int64_t e = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; e < nc;
        e += static_cast<int64_t>(gridDim.x) * blockDim.x)
@@ -793,142 +888,427 @@ inline size_t eig_smem_bytes(int b) {
   return sizeof(double) * (2 * (b / 2 + 1) + 32) + sizeof(int) * (3 * (b + 1));
 }
 
+// ------------------------------------------------------------ batched product staging
+// Row arena: FP32 rows of every problem, each block padded to a multiple of 128 rows and
+// to d_max columns with zeros (zero columns leave distances unchanged).
+struct ArenaCopy {
+  const float* X;
+  int64_t rows, row0;
+  int d;
+};
+__global__ void arena_copy_kernel(const ArenaCopy* __restrict__ tab, float* __restrict__ arena,
+                                  int d_max) {
+  const ArenaCopy t = tab[blockIdx.y];
+  const int64_t rows_pad = (t.rows + 127) / 128 * 128;
+  const int64_t total = rows_pad * d_max;
+  for (int64_t e = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; e < total;
+       e += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const int64_t r = e / d_max;
+    const int col = static_cast<int>(e % d_max);
+    arena[(t.row0 + r) * d_max + col] = (r < t.rows && col < t.d) ? t.X[r * t.d + col] : 0.f;
+  }
+}
+
+// Per-problem source of the weights S_p (n_p x C_p, row-major) of a batched product.
+struct SSource {
+  const float* S;
+  int64_t rows, row0;
+  int c;
+  const int* active;
+};
+// Transposed, split BF16 weights [p16][arena rows] (tensor-core path).
+template <bool SPLIT>
+__global__ void s_stage_tc_kernel(const SSource* __restrict__ tab, int p16, int64_t arena_rows,
+                                  __nv_bfloat16* __restrict__ hi, __nv_bfloat16* __restrict__ lo) {
+  const SSource t = tab[blockIdx.y];
+  if (t.active != nullptr && *t.active == 0) return;
+  const int64_t rows_pad = (t.rows + 127) / 128 * 128;
+  const int64_t total = rows_pad * p16;
+  for (int64_t e = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; e < total;
+       e += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const int cc = static_cast<int>(e / rows_pad);
+    const int64_t r = e % rows_pad;
+    const float x = (r < t.rows && cc < t.c) ? t.S[r * t.c + cc] : 0.f;
+    const __nv_bfloat16 h = __float2bfloat16_rn(x);
+    hi[cc * arena_rows + t.row0 + r] = h;
+    if (SPLIT) lo[cc * arena_rows + t.row0 + r] = __float2bfloat16_rn(x - __bfloat162float(h));
+  }
+}
+// FP32 weights [arena rows][p_max] (SIMT path).
+__global__ void s_stage_simt_kernel(const SSource* __restrict__ tab, int p_max, float* __restrict__ out) {
+  const SSource t = tab[blockIdx.y];
+  if (t.active != nullptr && *t.active == 0) return;
+  const int64_t rows_pad = (t.rows + 127) / 128 * 128;
+  const int64_t total = rows_pad * p_max;
+  for (int64_t e = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; e < total;
+       e += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const int64_t r = e / p_max;
+    const int cc = static_cast<int>(e % p_max);
+    out[(t.row0 + r) * p_max + cc] = (r < t.rows && cc < t.c) ? t.S[r * t.c + cc] : 0.f;
+  }
+}
+
+}  // namespace
+
+// A batched kernel product over a fixed set of problems (built once per fit).
+struct BatchProduct {
+  int precision = 0, kind = 0, nprob = 0, p16 = 16, d_max = 0;
+  int64_t arena_rows = 0;
+  RowOperand arena;
+  KmvItemTables tab;
+  const SSource* src = nullptr;      // device [nprob]
+  __nv_bfloat16 *s_hi = nullptr, *s_lo = nullptr;
+  float* s32 = nullptr;
+  int64_t max_rows_pad = 0;
+};
+
+namespace {
+
+// LPT (longest processing time first) assignment of whole-row items to G CTAs.
+void plan_items(const std::vector<WorkItem>& items, int G, std::vector<WorkItem>* ordered,
+                std::vector<int32_t>* begin) {
+  std::vector<int> idx(items.size());
+  for (size_t i = 0; i < idx.size(); ++i) idx[i] = static_cast<int>(i);
+  std::stable_sort(idx.begin(), idx.end(), [&](int a, int b) { return items[a].chunks > items[b].chunks; });
+  std::vector<int64_t> load(G, 0);
+  std::vector<std::vector<int>> per(G);
+  for (int i : idx) {
+    int best = 0;
+    for (int g = 1; g < G; ++g)
+      if (load[g] < load[best]) best = g;
+    load[best] += items[i].chunks;
+    per[best].push_back(i);
+  }
+  ordered->clear();
+  begin->assign(G + 1, 0);
+  for (int g = 0; g < G; ++g) {
+    // within a CTA keep items of the same problem together (L2 reuse of its rows)
+    std::stable_sort(per[g].begin(), per[g].end(), [&](int a, int b) { return items[a].prob < items[b].prob; });
+    (*begin)[g] = static_cast<int32_t>(ordered->size());
+    for (int i : per[g]) ordered->push_back(items[i]);
+  }
+  (*begin)[G] = static_cast<int32_t>(ordered->size());
+}
+
 }  // namespace
 
 // ======================================================================= host side
 
-int fit_run(DeviceContext* ctx, const itergp_fit_params& prm, const KParams& kp,
-            const RowOperand& Xop, const int32_t* y, float* v, float* f, float* Q, int bcap,
-            cudaStream_t stream, itergp_fit_report* rep, int* final_B) {
-  const int64_t n = prm.n;
-  const int C = prm.c;
-  const int64_t nc = n * C;
-  const int nblk = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(2LL * ctx->num_sms, ceil_div(n, 256))));
-  const int nblk_e = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(2LL * ctx->num_sms, ceil_div(nc, 1024))));
-  const int gram_splits = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(64, ceil_div(nc, 4096))));
-  const int64_t gram_per_split = ceil_div(nc, gram_splits);
-  const int eb = static_cast<int>(std::min<int64_t>(ceil_div(nc, 256), 8LL * ctx->num_sms));
-  const int nb_pts = static_cast<int>(std::min<int64_t>(ceil_div(n, 256), 8LL * ctx->num_sms));
+struct FitProblem {
+  const itergp_fit_params* prm;
+  KParams kp;
+  const RowOperand* xop;   // prepared rows of the problem (model memory)
+  float *v, *f, *Q;
+  int bcap;
+  itergp_fit_report* rep;
+  int* final_B;
+};
+
+int fit_run_batch(DeviceContext* ctx, const std::vector<FitProblem>& probs, cudaStream_t stream,
+                  bool use_graph) {
+  const int np = static_cast<int>(probs.size());
+  if (np == 0) return ITERGP_OK;
+  const itergp_fit_params& prm = *probs[0].prm;    // schedule shared by the batch
   const int track_kd = prm.literal_kv ? 0 : 1;
   const int project = prm.policy == ITERGP_POLICY_CG ? 1 : 0;
+  int64_t max_n = 0, max_nc = 0;
+  int max_bcap = 1, c_max = 2, d_max = 1;
+  for (const FitProblem& fp : probs) {
+    max_n = std::max<int64_t>(max_n, fp.prm->n);
+    max_nc = std::max<int64_t>(max_nc, fp.prm->n * fp.prm->c);
+    max_bcap = std::max(max_bcap, fp.bcap);
+    c_max = std::max(c_max, static_cast<int>(fp.prm->c));
+    d_max = std::max(d_max, static_cast<int>(fp.prm->d));
+  }
+  const int nblk = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(2LL * ctx->num_sms, ceil_div(max_n, 256))));
+  const int nblk_e = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(2LL * ctx->num_sms, ceil_div(max_nc, 1024))));
+  const int gram_splits = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(64, ceil_div(max_nc, 4096))));
+  const int eb = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(ceil_div(max_nc, 256), 8LL * ctx->num_sms)));
+  const int nb_pts = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(ceil_div(max_n, 256), 8LL * ctx->num_sms)));
+  const int maxblk = std::max(nblk, nblk_e);
+  const int tiles = static_cast<int>(ceil_div(max_bcap, kGT));
 
-  // ---- workspace
-  const size_t vec = align_up(sizeof(float) * nc, 256);
-  const size_t buf = align_up(sizeof(float) * nc * bcap, 256);
+  // ---- workspace: per-problem arrays
   size_t off = 0;
-  auto take = [&](size_t bytes) { size_t o = off; off += align_up(bytes, 256); return o; };
-  const size_t o_state = take(sizeof(FitState));
-  const size_t o_S = take(buf), o_T = take(buf), o_KQ = take(buf);
-  const size_t o_u = take(vec), o_b = take(vec), o_r = take(vec), o_z = take(vec), o_gp = take(vec),
-               o_ip = take(vec), o_s = take(vec), o_t = take(vec);
-  const size_t o_w = take(sizeof(float) * bcap), o_sq = take(sizeof(float) * bcap);
-  const size_t o_W = take(sizeof(float) * bcap * bcap);
-  const size_t o_A = take(sizeof(double) * bcap * bcap), o_V = take(sizeof(double) * bcap * bcap);
-  const size_t o_pg = take(sizeof(double) * gram_splits * bcap * bcap);
-  const size_t o_pv = take(sizeof(double) * std::max(nblk_e, nblk) * bcap);
-  const size_t o_ps = take(sizeof(double) * 5 * std::max(nblk_e, nblk));
-  const size_t o_bold = take(sizeof(int));
+  auto take = [&](size_t bytes) { size_t o = off; off += align_up(std::max<size_t>(bytes, 1), 256); return o; };
+  struct Offs { size_t st, S, T, KQ, u, b, r, z, gp, ip, s, t, w, sq, W, A, V, pg, pv, ps, bold; };
+  std::vector<Offs> offs(np);
+  for (int i = 0; i < np; ++i) {
+    const int64_t nc = probs[i].prm->n * probs[i].prm->c;
+    const int bc = probs[i].bcap;
+    Offs& o = offs[i];
+    o.st = take(sizeof(FitState));
+    o.S = take(sizeof(float) * nc * bc);
+    o.T = take(sizeof(float) * nc * bc);
+    o.KQ = take(sizeof(float) * nc * bc);
+    o.u = take(sizeof(float) * nc); o.b = take(sizeof(float) * nc); o.r = take(sizeof(float) * nc);
+    o.z = take(sizeof(float) * nc); o.gp = take(sizeof(float) * nc); o.ip = take(sizeof(float) * nc);
+    o.s = take(sizeof(float) * nc); o.t = take(sizeof(float) * nc);
+    o.w = take(sizeof(float) * bc); o.sq = take(sizeof(float) * bc);
+    o.W = take(sizeof(float) * bc * bc);
+    o.A = take(sizeof(double) * bc * bc); o.V = take(sizeof(double) * bc * bc);
+    o.pg = take(sizeof(double) * gram_splits * bc * bc);
+    o.pv = take(sizeof(double) * maxblk * bc);
+    o.ps = take(sizeof(double) * 5 * maxblk);
+    o.bold = take(sizeof(int));
+  }
+  const size_t o_probs = take(sizeof(ProbDev) * np);
+
+  // ---- batched product plan (np > 1)
+  const bool batched = np > 1;
+  BatchProduct bp;
+  std::vector<WorkItem> items_host, ordered;
+  std::vector<int32_t> begin_host;
+  std::vector<TcProb> tcp_host;
+  std::vector<SSource> src_host;
+  std::vector<ArenaCopy> ac_host;
+  size_t o_arena = 0, o_rows = 0, o_items = 0, o_begin = 0, o_tcp = 0, o_src = 0, o_ac = 0, o_shi = 0,
+         o_slo = 0, o_s32 = 0;
+  if (batched) {
+    bp.precision = prm.precision;
+    bp.kind = prm.kernel.kind;
+    bp.nprob = np;
+    bp.d_max = d_max;
+    bp.p16 = (c_max + 15) / 16 * 16;
+    int64_t row = 0;
+    for (int i = 0; i < np; ++i) {
+      const int64_t n = probs[i].prm->n;
+      const int64_t rows_pad = ceil_div(n, 128) * 128;
+      ac_host.push_back(ArenaCopy{probs[i].prm->X, n, row, static_cast<int>(probs[i].prm->d)});
+      const int chunks = static_cast<int>(ceil_div(n, 128));
+      for (int r = 0; r < chunks; ++r)
+        items_host.push_back(WorkItem{i, static_cast<int32_t>(row + 128 * r), 128 * r,
+                                      static_cast<int32_t>(row), chunks, static_cast<int32_t>(n), 0, 0});
+      bp.max_rows_pad = std::max(bp.max_rows_pad, rows_pad);
+      row += rows_pad;
+    }
+    bp.arena_rows = row;
+    const int G = static_cast<int>(std::min<int64_t>(ctx->num_sms, static_cast<int64_t>(items_host.size())));
+    plan_items(items_host, G, &ordered, &begin_host);
+    bp.tab.G = G;
+    bp.tab.n_items = static_cast<int>(ordered.size());
+    o_arena = take(sizeof(float) * bp.arena_rows * d_max);
+    o_rows = take(rows_workspace_bytes(prm.precision, bp.arena_rows, d_max));
+    o_items = take(sizeof(WorkItem) * ordered.size());
+    o_begin = take(sizeof(int32_t) * begin_host.size());
+    o_tcp = take(sizeof(TcProb) * np);
+    o_src = take(sizeof(SSource) * np);
+    o_ac = take(sizeof(ArenaCopy) * np);
+    if (precision_is_tensor(prm.precision)) {
+      o_shi = take(sizeof(__nv_bfloat16) * bp.p16 * bp.arena_rows);
+      o_slo = take(sizeof(__nv_bfloat16) * bp.p16 * bp.arena_rows);
+    } else {
+      o_s32 = take(sizeof(float) * bp.arena_rows * c_max);
+    }
+  }
+
   Scratch ws;
   ITERGP_CUDA_TRY(ws.alloc(ctx, off, stream));
   char* base = ws.as<char>();
-  FitState* st = reinterpret_cast<FitState*>(base + o_state);
-  float* S = reinterpret_cast<float*>(base + o_S);
-  float* T = reinterpret_cast<float*>(base + o_T);
-  float* KQ = reinterpret_cast<float*>(base + o_KQ);
-  float* u = reinterpret_cast<float*>(base + o_u);
-  float* b = reinterpret_cast<float*>(base + o_b);
-  float* r = reinterpret_cast<float*>(base + o_r);
-  float* z = reinterpret_cast<float*>(base + o_z);
-  float* gp = reinterpret_cast<float*>(base + o_gp);
-  float* ip = reinterpret_cast<float*>(base + o_ip);
-  float* s_cur = reinterpret_cast<float*>(base + o_s);
-  float* t_cur = reinterpret_cast<float*>(base + o_t);
-  float* w = reinterpret_cast<float*>(base + o_w);
-  float* sq = reinterpret_cast<float*>(base + o_sq);
-  float* W = reinterpret_cast<float*>(base + o_W);
-  double* Am = reinterpret_cast<double*>(base + o_A);
-  double* Vm = reinterpret_cast<double*>(base + o_V);
-  double* pg = reinterpret_cast<double*>(base + o_pg);
-  double* pv = reinterpret_cast<double*>(base + o_pv);
-  double* ps = reinterpret_cast<double*>(base + o_ps);
-  int* bold = reinterpret_cast<int*>(base + o_bold);
-
+  std::vector<ProbDev> pd(np);
+  for (int i = 0; i < np; ++i) {
+    const Offs& o = offs[i];
+    ProbDev& d = pd[i];
+    d.st = reinterpret_cast<FitState*>(base + o.st);
+    d.n = probs[i].prm->n;
+    d.c = probs[i].prm->c;
+    d.nc = d.n * d.c;
+    d.bcap = probs[i].bcap;
+    d.y = probs[i].prm->y;
+    d.f = probs[i].f; d.v = probs[i].v; d.Q = probs[i].Q;
+    d.S = reinterpret_cast<float*>(base + o.S); d.T = reinterpret_cast<float*>(base + o.T);
+    d.KQ = reinterpret_cast<float*>(base + o.KQ);
+    d.u = reinterpret_cast<float*>(base + o.u); d.b = reinterpret_cast<float*>(base + o.b);
+    d.r = reinterpret_cast<float*>(base + o.r); d.z = reinterpret_cast<float*>(base + o.z);
+    d.gp = reinterpret_cast<float*>(base + o.gp); d.ip = reinterpret_cast<float*>(base + o.ip);
+    d.s_cur = reinterpret_cast<float*>(base + o.s); d.t_cur = reinterpret_cast<float*>(base + o.t);
+    d.w = reinterpret_cast<float*>(base + o.w); d.sq = reinterpret_cast<float*>(base + o.sq);
+    d.W = reinterpret_cast<float*>(base + o.W);
+    d.Am = reinterpret_cast<double*>(base + o.A); d.Vm = reinterpret_cast<double*>(base + o.V);
+    d.pg = reinterpret_cast<double*>(base + o.pg); d.pv = reinterpret_cast<double*>(base + o.pv);
+    d.ps = reinterpret_cast<double*>(base + o.ps);
+    d.bold = reinterpret_cast<int*>(base + o.bold);
+  }
+  ProbDev* pdev = reinterpret_cast<ProbDev*>(base + o_probs);
+  ITERGP_CUDA_TRY(cudaMemcpyAsync(pdev, pd.data(), sizeof(ProbDev) * np, cudaMemcpyHostToDevice, stream));
   FitState init{};
   init.newton_active = 1;
-  ITERGP_CUDA_TRY(cudaMemcpyAsync(st, &init, sizeof(FitState), cudaMemcpyHostToDevice, stream));
-  ITERGP_CUDA_TRY(cudaMemsetAsync(f, 0, sizeof(float) * nc, stream));
-  ITERGP_CUDA_TRY(cudaMemsetAsync(v, 0, sizeof(float) * nc, stream));
-  ITERGP_CUDA_TRY(cudaMemsetAsync(u, 0, sizeof(float) * nc, stream));
-  ITERGP_CUDA_TRY(cudaMemsetAsync(gp, 0, sizeof(float) * nc, stream));
+  for (int i = 0; i < np; ++i) {
+    ITERGP_CUDA_TRY(cudaMemcpyAsync(pd[i].st, &init, sizeof(FitState), cudaMemcpyHostToDevice, stream));
+    ITERGP_CUDA_TRY(cudaMemsetAsync(pd[i].f, 0, sizeof(float) * pd[i].nc, stream));
+    ITERGP_CUDA_TRY(cudaMemsetAsync(pd[i].v, 0, sizeof(float) * pd[i].nc, stream));
+    ITERGP_CUDA_TRY(cudaMemsetAsync(pd[i].u, 0, sizeof(float) * pd[i].nc, stream));
+    ITERGP_CUDA_TRY(cudaMemsetAsync(pd[i].gp, 0, sizeof(float) * pd[i].nc, stream));
+  }
 
-  const int* active = &st->active;
-  const size_t eig_smem = eig_smem_bytes(bcap);
+  // tables of the batched product, uploaded once
+  SSource* src_lit = nullptr;
+  std::vector<TcProb> tcp_lit;
+  if (batched) {
+    for (int i = 0; i < np; ++i) {
+      tcp_host.push_back(TcProb{pd[i].t_cur, pd[i].c, pd[i].n, pd[i].c, 0, probs[i].kp, &pd[i].st->active});
+      src_host.push_back(SSource{pd[i].s_cur, pd[i].n, ac_host[i].row0, pd[i].c, &pd[i].st->active});
+    }
+    bp.arena.X = nullptr;
+    float* arena = reinterpret_cast<float*>(base + o_arena);
+    ArenaCopy* ac = reinterpret_cast<ArenaCopy*>(base + o_ac);
+    ITERGP_CUDA_TRY(cudaMemcpyAsync(ac, ac_host.data(), sizeof(ArenaCopy) * np, cudaMemcpyHostToDevice, stream));
+    {
+      dim3 grid(static_cast<unsigned>(std::min<int64_t>(ceil_div(bp.max_rows_pad * d_max, 256), 1024)), np);
+      arena_copy_kernel<<<grid, 256, 0, stream>>>(ac, arena, d_max), ::itergp::note_launch();
+      ITERGP_CUDA_TRY(cudaGetLastError());
+    }
+    int rc = prepare_rows(prm.precision, arena, bp.arena_rows, d_max, d_max, base + o_rows, &bp.arena, stream);
+    if (rc != ITERGP_OK) return rc;
+    WorkItem* items_dev = reinterpret_cast<WorkItem*>(base + o_items);
+    int32_t* begin_dev = reinterpret_cast<int32_t*>(base + o_begin);
+    TcProb* tcp_dev = reinterpret_cast<TcProb*>(base + o_tcp);
+    SSource* src_dev = reinterpret_cast<SSource*>(base + o_src);
+    ITERGP_CUDA_TRY(cudaMemcpyAsync(items_dev, ordered.data(), sizeof(WorkItem) * ordered.size(), cudaMemcpyHostToDevice, stream));
+    ITERGP_CUDA_TRY(cudaMemcpyAsync(begin_dev, begin_host.data(), sizeof(int32_t) * begin_host.size(), cudaMemcpyHostToDevice, stream));
+    ITERGP_CUDA_TRY(cudaMemcpyAsync(tcp_dev, tcp_host.data(), sizeof(TcProb) * np, cudaMemcpyHostToDevice, stream));
+    ITERGP_CUDA_TRY(cudaMemcpyAsync(src_dev, src_host.data(), sizeof(SSource) * np, cudaMemcpyHostToDevice, stream));
+    bp.tab.items = items_dev;
+    bp.tab.item_begin = begin_dev;
+    bp.tab.probs = tcp_dev;
+    bp.src = src_dev;
+    if (precision_is_tensor(prm.precision)) {
+      bp.s_hi = reinterpret_cast<__nv_bfloat16*>(base + o_shi);
+      bp.s_lo = reinterpret_cast<__nv_bfloat16*>(base + o_slo);
+    } else {
+      bp.s32 = reinterpret_cast<float*>(base + o_s32);
+    }
+    if (prm.literal_kv) return ITERGP_EINVAL;   // batched fits carry K v (validated by the API)
+  }
+  (void)src_lit;
+  (void)tcp_lit;
+
+  // the kernel products of an iteration: t_cur = K s_cur for every active problem
+  auto products = [&]() -> int {
+    if (!batched) {
+      return kmv_execute(ctx, probs[0].kp, *probs[0].xop, *probs[0].xop, pd[0].s_cur, pd[0].c,
+                         pd[0].c, pd[0].t_cur, pd[0].c, stream, &pd[0].st->active);
+    }
+    dim3 grid(static_cast<unsigned>(std::min<int64_t>(ceil_div(bp.max_rows_pad * bp.p16, 256), 512)), np);
+    if (precision_is_tensor(prm.precision)) {
+      if (precision_splits_weights(prm.precision))
+        s_stage_tc_kernel<true><<<grid, 256, 0, stream>>>(bp.src, bp.p16, bp.arena_rows, bp.s_hi, bp.s_lo), ::itergp::note_launch();
+      else
+        s_stage_tc_kernel<false><<<grid, 256, 0, stream>>>(bp.src, bp.p16, bp.arena_rows, bp.s_hi, bp.s_lo), ::itergp::note_launch();
+      ITERGP_CUDA_TRY(cudaGetLastError());
+      return kmv_tc_items(ctx, bp.kind, bp.arena, bp.tab, bp.p16, bp.s_hi, bp.s_lo, stream);
+    }
+    s_stage_simt_kernel<<<grid, 256, 0, stream>>>(bp.src, c_max, bp.s32), ::itergp::note_launch();
+    ITERGP_CUDA_TRY(cudaGetLastError());
+    return kmv_simt_items(ctx, bp.kind, bp.arena, bp.tab, bp.s32, c_max, stream);
+  };
+
+  const size_t eig_smem = eig_smem_bytes(max_bcap);
   const int eig_threads = 512;
-
-  for (int step = 0; step < prm.max_newton; ++step) {
-    newton_prologue_kernel<<<nblk, kRedThreads, 0, stream>>>(st, n, C, f, y, v, gp, ip, b, ps, ctx->status, project), ::itergp::note_launch();
-    newton_finalize_kernel<<<1, 32, 0, stream>>>(st, ps, nblk, step, prm.tol_newton, prm.tol_abs, prm.tol_rel, prm.recycle), ::itergp::note_launch();
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  // The schedule is captured on a private stream (the caller's may be the legacy default
+  // stream, which cannot be captured) and the graph is launched on the caller's stream,
+  // after the set-up work enqueued above.
+  cudaStream_t caller = stream;
+  cudaStream_t cap = nullptr;
+  if (use_graph) {
+    ITERGP_CUDA_TRY(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+    const cudaError_t be = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+    if (be != cudaSuccess) {
+      cudaStreamDestroy(cap);
+      ITERGP_CUDA_TRY(be);
+    }
+    stream = cap;
+  }
+  int rc = ITERGP_OK;
+  for (int step = 0; step < prm.max_newton && rc == ITERGP_OK; ++step) {
+    newton_prologue_kernel<<<dim3(nblk, np), kRedThreads, 0, stream>>>(pdev, ctx->status, project), ::itergp::note_launch();
+    newton_finalize_kernel<<<np, 32, 0, stream>>>(pdev, nblk, step, prm.tol_newton, prm.tol_abs, prm.tol_rel, prm.recycle), ::itergp::note_launch();
     // ---- Alg. 3: virtual solver run with compression
     if (prm.recycle && step > 0) {
-      copy_int_kernel<<<1, 1, 0, stream>>>(st, bold), ::itergp::note_launch();
-      vsr_z_kernel<<<eb, 256, 0, stream>>>(st, n, C, nc, S, T, ip, Q), ::itergp::note_launch();
-      dim3 gg(ceil_div(bcap, kGT), ceil_div(bcap, kGT), gram_splits);
-      gram_partial_kernel<<<gg, 256, 0, stream>>>(st, S, Q, nc, bcap, gram_per_split, pg), ::itergp::note_launch();
-      vsr_eig_kernel<<<1, eig_threads, eig_smem, stream>>>(st, pg, gram_splits, bcap, prm.rank, Am, Vm, W, sq, step), ::itergp::note_launch();
-      vsr_rotate_kernel<<<eb, 256, 0, stream>>>(st, bold, nc, bcap, S, T, W, Q, KQ), ::itergp::note_launch();
-      vsr_rescale_kernel<<<eb, 256, 0, stream>>>(st, nc, sq, Q, KQ, S, T), ::itergp::note_launch();
+      copy_int_kernel<<<np, 32, 0, stream>>>(pdev), ::itergp::note_launch();
+      vsr_z_kernel<<<dim3(eb, np), 256, 0, stream>>>(pdev), ::itergp::note_launch();
+      gram_partial_kernel<<<dim3(tiles * tiles, gram_splits, np), 256, 0, stream>>>(pdev, tiles), ::itergp::note_launch();
+      vsr_eig_kernel<<<np, eig_threads, eig_smem, stream>>>(pdev, gram_splits, prm.rank, step), ::itergp::note_launch();
+      vsr_rotate_kernel<<<dim3(eb, np), 256, 0, stream>>>(pdev), ::itergp::note_launch();
+      vsr_rescale_kernel<<<dim3(eb, np), 256, 0, stream>>>(pdev), ::itergp::note_launch();
       // v0 = Q0 (Q0^T b), u0 = K v0 = KQ0 (Q0^T b)
-      proj_partial_kernel<<<nblk_e, 256, 0, stream>>>(st, 0, Q, b, nc, bcap, pv), ::itergp::note_launch();
-      proj_finalize_kernel<<<1, 256, 0, stream>>>(st, 0, pv, nblk_e, bcap, w), ::itergp::note_launch();
+      proj_partial_kernel<<<dim3(nblk_e, np), 256, 0, stream>>>(pdev, 0), ::itergp::note_launch();
+      proj_finalize_kernel<<<np, 256, 0, stream>>>(pdev, 0, nblk_e), ::itergp::note_launch();
     }
     // v0 = C0 (y_hat - m) and K v0; with no recycled columns (B = 0) both are zero
-    combine_kernel<<<eb, 256, 0, stream>>>(st, Q, KQ, w, nc, v, u), ::itergp::note_launch();
+    combine_kernel<<<dim3(eb, np), 256, 0, stream>>>(pdev), ::itergp::note_launch();
     // ---- Alg. 2 iterations
-    for (int j = 0; j < prm.max_iters; ++j) {
+    for (int j = 0; j < prm.max_iters && rc == ITERGP_OK; ++j) {
       if (prm.literal_kv) {
-        int rc = kmv_execute(ctx, kp, Xop, Xop, v, C, C, u, C, stream, active);
-        if (rc != ITERGP_OK) return rc;
+        rc = kmv_execute(ctx, probs[0].kp, *probs[0].xop, *probs[0].xop, pd[0].v, pd[0].c, pd[0].c,
+                         pd[0].u, pd[0].c, stream, &pd[0].st->active);
+        if (rc != ITERGP_OK) break;
       }
-      resid_kernel<<<nblk, kRedThreads, 0, stream>>>(st, n, C, b, u, v, ip, r, ps, project), ::itergp::note_launch();
-      resid_finalize_kernel<<<1, 32, 0, stream>>>(st, ps, nblk, r, nc, prm.policy, step), ::itergp::note_launch();
-      action_kernel<<<eb, 256, 0, stream>>>(st, nc, prm.policy, r, s_cur, S), ::itergp::note_launch();
-      int rc = kmv_execute(ctx, kp, Xop, Xop, s_cur, C, C, t_cur, C, stream, active);
-      if (rc != ITERGP_OK) return rc;
-      z_kernel<<<nb_pts, 256, 0, stream>>>(st, n, C, s_cur, t_cur, ip, z, T), ::itergp::note_launch();
-      proj_partial_kernel<<<nblk_e, 256, 0, stream>>>(st, 1, Q, z, nc, bcap, pv), ::itergp::note_launch();
-      proj_finalize_kernel<<<1, 256, 0, stream>>>(st, 1, pv, nblk_e, bcap, w), ::itergp::note_launch();
-      direction_kernel<<<nblk_e, kRedThreads, 0, stream>>>(st, nc, s_cur, t_cur, z, w, Q, KQ, track_kd, ps), ::itergp::note_launch();
-      eta_finalize_kernel<<<1, 32, 0, stream>>>(st, ps, nblk_e), ::itergp::note_launch();
-      update_kernel<<<eb, 256, 0, stream>>>(st, nc, Q, KQ, v, u, track_kd), ::itergp::note_launch();
+      resid_kernel<<<dim3(nblk, np), kRedThreads, 0, stream>>>(pdev, project), ::itergp::note_launch();
+      resid_finalize_kernel<<<np, 32, 0, stream>>>(pdev, nblk, prm.policy), ::itergp::note_launch();
+      action_kernel<<<dim3(eb, np), 256, 0, stream>>>(pdev, prm.policy), ::itergp::note_launch();
+      rc = products();
+      if (rc != ITERGP_OK) break;
+      z_kernel<<<dim3(nb_pts, np), 256, 0, stream>>>(pdev), ::itergp::note_launch();
+      proj_partial_kernel<<<dim3(nblk_e, np), 256, 0, stream>>>(pdev, 1), ::itergp::note_launch();
+      proj_finalize_kernel<<<np, 256, 0, stream>>>(pdev, 1, nblk_e), ::itergp::note_launch();
+      direction_kernel<<<dim3(nblk_e, np), kRedThreads, 0, stream>>>(pdev, track_kd), ::itergp::note_launch();
+      eta_finalize_kernel<<<np, 32, 0, stream>>>(pdev, nblk_e), ::itergp::note_launch();
+      update_kernel<<<dim3(eb, np), 256, 0, stream>>>(pdev, track_kd), ::itergp::note_launch();
     }
-    step_end_kernel<<<1, 32, 0, stream>>>(st, step), ::itergp::note_launch();
+    if (rc != ITERGP_OK) break;
+    step_end_kernel<<<np, 32, 0, stream>>>(pdev, step), ::itergp::note_launch();
     if (prm.literal_kv) {
       // f_{i+1} = K v + m by a fresh product
-      int rc = kmv_execute(ctx, kp, Xop, Xop, v, C, C, u, C, stream, &st->newton_active);
-      if (rc != ITERGP_OK) return rc;
+      rc = kmv_execute(ctx, probs[0].kp, *probs[0].xop, *probs[0].xop, pd[0].v, pd[0].c, pd[0].c,
+                       pd[0].u, pd[0].c, stream, &pd[0].st->newton_active);
+      if (rc != ITERGP_OK) break;
     }
-    copy_f_kernel<<<eb, 256, 0, stream>>>(st, nc, u, f), ::itergp::note_launch();
+    copy_f_kernel<<<dim3(eb, np), 256, 0, stream>>>(pdev), ::itergp::note_launch();
   }
+  if (use_graph) {
+    const cudaError_t ce = cudaStreamEndCapture(cap, &graph);
+    cudaStreamDestroy(cap);
+    stream = caller;
+    if (rc != ITERGP_OK || ce != cudaSuccess) {
+      if (graph) cudaGraphDestroy(graph);
+      if (rc != ITERGP_OK) return rc;
+      ITERGP_CUDA_TRY(ce);
+    }
+    const cudaError_t ie = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    ITERGP_CUDA_TRY(ie);
+    const cudaError_t le = cudaGraphLaunch(exec, stream);
+    cudaGraphExecDestroy(exec);
+    ITERGP_CUDA_TRY(le);
+  }
+  if (rc != ITERGP_OK) return rc;
   ITERGP_CUDA_TRY(cudaGetLastError());
 
-  FitState hs;
-  ITERGP_CUDA_TRY(cudaMemcpyAsync(&hs, st, sizeof(FitState), cudaMemcpyDeviceToHost, stream));
+  std::vector<FitState> hs(np);
+  for (int i = 0; i < np; ++i)
+    ITERGP_CUDA_TRY(cudaMemcpyAsync(&hs[i], pd[i].st, sizeof(FitState), cudaMemcpyDeviceToHost, stream));
   ITERGP_CUDA_TRY(cudaStreamSynchronize(stream));
-  if (rep) {
-    rep->newton_steps = hs.newton_steps;
-    rep->total_iters = hs.total_iters;
-    rep->buffer_cols = hs.B;
-    rep->stop_reason = hs.stop_reason;
-    for (int i = 0; i < ITERGP_MAX_REPORT_STEPS; ++i) {
-      rep->iters[i] = hs.iters[i];
-      rep->stops[i] = hs.stops[i];
-      rep->kept[i] = hs.kept[i];
-      rep->objective[i] = hs.objective[i];
-      rep->rel_change[i] = hs.rel_change[i];
+  for (int i = 0; i < np; ++i) {
+    itergp_fit_report* rep = probs[i].rep;
+    if (rep) {
+      rep->newton_steps = hs[i].newton_steps;
+      rep->total_iters = hs[i].total_iters;
+      rep->buffer_cols = hs[i].B;
+      rep->stop_reason = hs[i].stop_reason;
+      for (int k = 0; k < ITERGP_MAX_REPORT_STEPS; ++k) {
+        rep->iters[k] = hs[i].iters[k];
+        rep->stops[k] = hs[i].stops[k];
+        rep->kept[k] = hs[i].kept[k];
+        rep->objective[k] = hs[i].objective[k];
+        rep->rel_change[k] = hs[i].rel_change[k];
+      }
+      rep->resid_norm = hs[i].rnorm;
     }
-    rep->resid_norm = hs.rnorm;
+    *probs[i].final_B = hs[i].B;
   }
-  *final_B = hs.B;
   return ITERGP_OK;
 }
 

@@ -111,11 +111,13 @@ class BatchProblem:
 
 def batch_problems(count: int = 256, seed: int = 4, n_lo: int = 200, n_hi: int = 20000,
                    dims=(8, 16, 32, 64), c_lo: int = 2, c_hi: int = 10,
-                   ell_lo: float = 0.3, ell_hi: float = 3.0, n_test: int = 64):
+                   ell_lo: float = 0.3, ell_hi: float = 3.0, n_test: int = 64,
+                   ell_per_sqrt_d: bool = False):
     """Independent blob problems of uneven size (batched-fit workload).
 
     N = floor(exp U[ln n_lo, ln n_hi]); D uniform over ``dims``; C uniform in
-    {c_lo..c_hi}; RBF lengthscale exp U[ln ell_lo, ln ell_hi]."""
+    {c_lo..c_hi}; RBF lengthscale exp U[ln ell_lo, ln ell_hi], times sqrt(D) when
+    ``ell_per_sqrt_d`` (the kernel then sees distances on the scale of the blob spread)."""
     g = _rng(seed)
     out = []
     for i in range(count):
@@ -123,6 +125,8 @@ def batch_problems(count: int = 256, seed: int = 4, n_lo: int = 200, n_hi: int =
         d = int(g.choice(dims))
         c = int(g.integers(c_lo, c_hi + 1))
         ell = float(math.exp(g.uniform(math.log(ell_lo), math.log(ell_hi))))
+        if ell_per_sqrt_d:
+            ell *= math.sqrt(d)
         sub = int(g.integers(0, 2**31 - 1))
         X, y, centres = blobs(n, d, c, sub)
         Xs, _, _ = blobs(n_test, d, c, sub + 1, centres=centres)

@@ -41,7 +41,8 @@ class FitParams(ct.Structure):
                 ("precision", ct.c_int32), ("policy", ct.c_int32),
                 ("max_newton", ct.c_int32), ("max_iters", ct.c_int32), ("rank", ct.c_int32),
                 ("recycle", ct.c_int32), ("literal_kv", ct.c_int32),
-                ("tol_newton", ct.c_double), ("tol_abs", ct.c_double), ("tol_rel", ct.c_double)]
+                ("tol_newton", ct.c_double), ("tol_abs", ct.c_double), ("tol_rel", ct.c_double),
+                ("graph", ct.c_int32)]
 
 
 class FitReport(ct.Structure):
@@ -73,6 +74,7 @@ def _load():
     lib.itergp_pseudo_targets.argtypes = [vp, vp, i64, i32, vp, vp]
     lib.itergp_sym_eig.argtypes = [vp, i32, vp, vp, vp]
     lib.itergp_fit.argtypes = [ct.POINTER(FitParams), ct.POINTER(vp), ct.POINTER(FitReport), vp]
+    lib.itergp_fit_batch.argtypes = [ct.POINTER(FitParams), i32, ct.POINTER(vp), ct.POINTER(FitReport), vp]
     lib.itergp_predict.argtypes = [vp, vp, i64, vp, vp, vp, vp]
     lib.itergp_model_get_view.argtypes = [vp, ct.POINTER(ModelView)]
     lib.itergp_model_free.argtypes = [vp]
@@ -81,12 +83,15 @@ def _load():
     lib.itergp_status_string.argtypes = [i32]
     lib.itergp_status_string.restype = ct.c_char_p
     lib.itergp_version.restype = ct.c_char_p
+    lib.itergp_last_error.restype = ct.c_char_p
+    lib.itergp_last_error.argtypes = []
     lib.itergp_timing_enable.argtypes = [ct.c_int]
     lib.itergp_timing_read.argtypes = [ct.POINTER(ct.c_double), ct.POINTER(ct.c_int64)]
     lib.itergp_launch_count.restype = ct.c_int64
     lib.itergp_launch_count.argtypes = []
     for name in ("itergp_kmatvec", "itergp_kmatvec_noalloc", "itergp_winv_apply", "itergp_pseudo_targets",
-                 "itergp_sym_eig", "itergp_fit", "itergp_predict", "itergp_model_get_view",
+                 "itergp_sym_eig", "itergp_fit", "itergp_fit_batch", "itergp_predict",
+                 "itergp_model_get_view",
                  "itergp_sync_status"):
         getattr(lib, name).restype = ct.c_int
     return lib
@@ -101,7 +106,8 @@ def status_string(code: int) -> str:
 
 def _check(code: int, where: str):
     if code != OK:
-        raise ItergpError(code, where)
+        detail = lib.itergp_last_error().decode() if code == ECUDA else ""
+        raise ItergpError(code, f"{where} [{detail}]" if detail else where)
 
 
 def _stream(stream=None):
@@ -266,10 +272,8 @@ class _CudaArray:
                                          "data": (int(ptr), False), "version": 3, "strides": None}
 
 
-def fit(X, y, c, kind="rbf", lengthscale=1.0, outputscale=1.0, precision="fp32",
-        policy="cg", max_newton=10, max_iters=50, rank=-1, recycle=True, literal_kv=False,
-        tol_newton=0.0, tol_abs=1e-5, tol_rel=1e-5, stream=None) -> Model:
-    """IterNCGP fit (Alg. 1-3) of a softmax GP classifier on the GPU."""
+def _params(X, y, c, kind, lengthscale, outputscale, precision, policy, max_newton, max_iters,
+            rank, recycle, literal_kv, tol_newton, tol_abs, tol_rel, graph) -> FitParams:
     n, d = X.shape
     prm = FitParams()
     prm.n, prm.d, prm.c = n, d, int(c)
@@ -282,8 +286,34 @@ def fit(X, y, c, kind="rbf", lengthscale=1.0, outputscale=1.0, precision="fp32",
     prm.rank = -1 if rank is None else int(rank)
     prm.recycle, prm.literal_kv = int(bool(recycle)), int(bool(literal_kv))
     prm.tol_newton, prm.tol_abs, prm.tol_rel = float(tol_newton), float(tol_abs), float(tol_rel)
+    prm.graph = int(bool(graph))
+    return prm
+
+
+def fit(X, y, c, kind="rbf", lengthscale=1.0, outputscale=1.0, precision="fp32",
+        policy="cg", max_newton=10, max_iters=50, rank=-1, recycle=True, literal_kv=False,
+        tol_newton=0.0, tol_abs=1e-5, tol_rel=1e-5, graph=False, stream=None) -> Model:
+    """IterNCGP fit (Alg. 1-3) of a softmax GP classifier on the GPU."""
+    prm = _params(X, y, c, kind, lengthscale, outputscale, precision, policy, max_newton,
+                  max_iters, rank, recycle, literal_kv, tol_newton, tol_abs, tol_rel, graph)
     h = ct.c_void_p()
     rep = FitReport()
     rc = lib.itergp_fit(ct.byref(prm), ct.byref(h), ct.byref(rep), _stream(stream))
     _check(rc, "itergp_fit")
     return Model(h, rep, X.device)
+
+
+def fit_batch(problems, kind="rbf", precision="fp32", policy="cg", max_newton=5, max_iters=5,
+              rank=50, recycle=True, tol_newton=0.0, tol_abs=1e-5, tol_rel=1e-5, graph=True,
+              stream=None):
+    """Batched fit of independent problems [(X, y, c, lengthscale, outputscale), ...] with
+    one schedule (one launch per phase over all problems).  Returns a list of Models."""
+    prms = (FitParams * len(problems))()
+    for i, (X, y, c, ell, s) in enumerate(problems):
+        prms[i] = _params(X, y, c, kind, ell, s, precision, policy, max_newton, max_iters, rank,
+                          recycle, False, tol_newton, tol_abs, tol_rel, graph)
+    hs = (ct.c_void_p * len(problems))()
+    reps = (FitReport * len(problems))()
+    rc = lib.itergp_fit_batch(prms, len(problems), hs, reps, _stream(stream))
+    _check(rc, "itergp_fit_batch")
+    return [Model(ct.c_void_p(hs[i]), reps[i], problems[i][0].device) for i in range(len(problems))]
