@@ -160,13 +160,13 @@ def reference_arm(args):
     print(json.dumps(out))
 
 
-BATCH_SCHED = dict(max_newton=5, max_iters=10, rank=50, tol_abs=1e-5, tol_rel=1e-5)
+BATCH_SCHED = dict(max_newton=5, max_iters=5, rank=50, tol_abs=1e-5, tol_rel=1e-5)
 
 
 def bench_batched(native, datagen, torch, dev, count):
     """Batched fits: `count` independent blob problems (N log-uniform in [200, 20000],
     D in {8, 16, 32, 64}, C in {2..10}, RBF lengthscale log-uniform in [0.3, 3]), one
-    schedule of 5 Newton steps x <= 10 iterations, R = 50, tolerance 1e-5.  Each batched
+    schedule of 5 Newton steps x <= 5 iterations, R = 50, tolerance 1e-5.  Each batched
     fit is one itergp_fit_batch call (graph captured and launched inside); the plain
     path fits the same problems one by one in FP32 without a graph."""
     probs = datagen.batch_problems(count=count)
@@ -174,7 +174,7 @@ def bench_batched(native, datagen, torch, dev, count):
            p.lengthscale, 1.0) for p in probs]
     n = [p.X.shape[0] for p in probs]
     res = {"workload": f"{count} blob problems, N log-U[200,20000] (sum {sum(n)}), D in {{8,16,32,64}}, "
-                       "C in {2..10}, RBF l log-U[0.3,3]; 5 Newton x <=10 iters, R=50, tol 1e-5",
+                       "C in {2..10}, RBF l log-U[0.3,3]; 5 Newton x <=5 iters, R=50, tol 1e-5",
            "sum_n2": float(sum(x * x for x in n))}
 
     def timed(fn):
@@ -186,19 +186,23 @@ def bench_batched(native, datagen, torch, dev, count):
 
     for prec in ("fp32", "bf16x3", "bf16_comp"):
         try:
-            for m in native.fit_batch(dp, precision=prec, graph=True, **BATCH_SCHED):   # warm-up
-                m.free()
+            for m in native.fit_batch(dp, precision=prec, graph=True, errors="return", **BATCH_SCHED):
+                if isinstance(m, native.Model):   # warm-up
+                    m.free()
             l0 = native.launch_count()
-            dt, models = timed(lambda: native.fit_batch(dp, precision=prec, graph=True, **BATCH_SCHED))
+            dt, models = timed(lambda: native.fit_batch(dp, precision=prec, graph=True, errors="return",
+                                                        **BATCH_SCHED))
             launches = native.launch_count() - l0
         except native.ItergpError as e:
             res[prec] = {"error": str(e)}
             continue
-        iters = [m.report.total_iters for m in models]
-        pairs = float(sum(it * x * x for it, x in zip(iters, n)))
+        ok = [(m, x) for m, x in zip(models, n) if isinstance(m, native.Model)]
+        iters = [m.report.total_iters for m, _ in ok]
+        pairs = float(sum(m.report.total_iters * x * x for m, x in ok))
         res[prec] = {"fit_s": dt, "fits_per_s": count / dt, "total_iters": int(sum(iters)),
-                     "kernel_pairs_per_s": pairs / dt, "launches": int(launches)}
-        for m in models:
+                     "kernel_pairs_per_s": pairs / dt, "launches": int(launches),
+                     "failed": [str(m) for m in models if not isinstance(m, native.Model)]}
+        for m, _ in ok:
             m.free()
     l0 = native.launch_count()
     t0 = time.perf_counter()
@@ -365,10 +369,16 @@ def main():
             dt = time.perf_counter() - t0
             mean, var, probs = m.predict(torch.as_tensor(Xs, device=dev))
             acc = float((probs.argmax(1).cpu().numpy() == ys).mean())
-            fits[prec] = {"newton_step_ms": dt * 1e3 / max(m.report.newton_steps, 1),
-                          "fit_s": dt, "iters": int(m.report.total_iters), "test_acc": acc}
+            r = m.report
+            fits[prec] = {"newton_step_ms": dt * 1e3 / max(r.newton_steps, 1),
+                          "fit_s": dt, "iters": int(r.total_iters), "test_acc": acc,
+                          "objective": [round(r.objective[i], 1) for i in range(r.newton_steps)]}
             m.free()
         out["fit"] = {"workload": "IterNCGP fit, same data, C=10, 5 Newton steps x 5 iterations, R=200",
+                      "note": "the undamped Newton trajectory on this kernel (l = sqrt(D): K ~ 0.88 11^T) "
+                              "changes under product perturbations of 1e-7 relative (FP64 oracle with "
+                              "injected noise, N = 20000), so FP32/BF16 fits cannot follow it; times "
+                              "per Newton step are comparable, accuracies are not",
                       **fits}
     if rank == 0 and not args.no_extras:
         out["batched"] = bench_batched(native, datagen, torch, dev, args.batch_count)

@@ -197,6 +197,9 @@ typedef struct {
   double rel_change[ITERGP_MAX_REPORT_STEPS];   /* |g_i - g_{i-1}|/|g_i| (i >= 1)  */
   double resid_norm;      /* |r| at the last residual evaluation                   */
   int64_t device_bytes;   /* bytes held by the model and its buffers              */
+  int32_t status;         /* this problem's outcome: ITERGP_OK, ITERGP_EINVAL (a    */
+                          /* label out of range) or ITERGP_ENUMERIC (1/pi overflow)  */
+  int32_t reserved;
 } itergp_fit_report;
 
 typedef struct itergp_model itergp_model;
@@ -213,8 +216,11 @@ int itergp_fit(const itergp_fit_params* params, itergp_model** out, itergp_fit_r
  * persistent launch over the row tiles of all problems.  Fields that must agree across
  * params[0 .. count-1]: kernel.kind, precision, policy, max_newton, max_iters, rank,
  * recycle, tol_newton, tol_abs, tol_rel, graph; literal_kv must be 0.  models[i] and
- * reports[i] (reports may be NULL) receive each problem's result.  On failure no model
- * is returned.  Waits for the stream like itergp_fit. */
+ * reports[i] (reports may be NULL) receive each problem's result.  A problem that fails
+ * on the device (a label out of range, a non-finite value) stops alone: models[i] is
+ * NULL, reports[i].status holds its code and the call still returns ITERGP_OK for the
+ * others.  Errors of the call itself (arguments, memory, CUDA, a wait limit) return
+ * their code and no model.  Waits for the stream like itergp_fit. */
 int itergp_fit_batch(const itergp_fit_params* params, int32_t count, itergp_model** models,
                      itergp_fit_report* reports, itergp_stream stream);
 

@@ -13,17 +13,6 @@
 
 namespace itergp {
 
-struct FitProblem {
-  const itergp_fit_params* prm;
-  KParams kp;
-  const RowOperand* xop;
-  float *v, *f, *Q;
-  int bcap;
-  itergp_fit_report* rep;
-  int* final_B;
-};
-int fit_run_batch(DeviceContext* ctx, const std::vector<FitProblem>& probs, cudaStream_t stream,
-                  bool use_graph);
 int winv_apply_launch(DeviceContext* ctx, const float* f, int64_t n, int c, const float* x,
                       float* out, cudaStream_t s);
 int pseudo_targets_launch(DeviceContext* ctx, const float* f, const int32_t* y, int64_t n, int c,
@@ -212,20 +201,133 @@ __global__ void gather_vq_kernel(const float* __restrict__ v, const float* __res
 
 using namespace itergp;
 
-struct itergp_model {
-  int device = -1;
-  int64_t n = 0, d = 0;
-  int c = 0, bcap = 0, B = 0;
-  itergp_kernel kernel{};
-  int precision = 0;
-  void* mem = nullptr;
-  float* X = nullptr;
-  float* v = nullptr;
-  float* f = nullptr;
-  float* Q = nullptr;
-  RowOperand xop;
-  int64_t bytes = 0;
-};
+namespace itergp {
+
+
+int validate_fit_params(const itergp_fit_params* prm) {
+  if (!prm) return ITERGP_EINVAL;
+  if (prm->n < 1 || prm->d < 1 || prm->d > 4096 || prm->c < 2 || prm->c > 64 || !prm->X || !prm->y)
+    return ITERGP_EINVAL;
+  if (!kernel_ok(&prm->kernel) || !precision_ok(prm->precision)) return ITERGP_EINVAL;
+  if (prm->policy != ITERGP_POLICY_CG && prm->policy != ITERGP_POLICY_UNIT) return ITERGP_EINVAL;
+  if (prm->max_newton < 1 || prm->max_iters < 0 || prm->max_newton > 100000) return ITERGP_EINVAL;
+  if (!(prm->tol_abs >= 0) || !(prm->tol_rel >= 0)) return ITERGP_EINVAL;
+  return ITERGP_OK;
+}
+
+int64_t buffer_capacity(const itergp_fit_params& p) {
+  const int64_t nc = p.n * p.c;
+  int64_t bcap = static_cast<int64_t>(p.max_newton) * p.max_iters;
+  if (p.recycle && p.rank >= 0) bcap = std::min<int64_t>(bcap, static_cast<int64_t>(p.rank) + p.max_iters);
+  if (!p.recycle) bcap = std::min<int64_t>(bcap, p.max_iters);
+  bcap = std::min<int64_t>(bcap, nc);
+  return std::max<int64_t>(bcap, 1);
+}
+
+void model_release(itergp_model* m, cudaStream_t s) {
+  if (!m) return;
+  if (m->mem) cudaFreeAsync(m->mem, s);
+  delete m;
+}
+
+void free_models(std::vector<itergp_model*>& ms, cudaStream_t s) {
+  for (auto* m : ms) model_release(m, s);
+  ms.clear();
+}
+
+// Fits params[0..count) with one schedule; on success fills models/reports.
+int fit_many(const itergp_fit_params* params, int count, itergp_model** out,
+             itergp_fit_report* reports, cudaStream_t s, bool batch) {
+  DeviceContext* ctx = current_context();
+  if (!ctx) return ITERGP_ECUDA;
+  if (precision_is_tensor(params[0].precision) && !ctx->tcgen05) return ITERGP_EUNSUPPORTED;
+  std::vector<itergp_model*> models(count, nullptr);
+  std::vector<itergp_fit_report> reps(count);
+  std::vector<int> finalB(count, 0);
+  std::vector<int> status(count, ITERGP_OK);
+  std::vector<FitProblem> probs(count);
+  for (int i = 0; i < count; ++i) {
+    const itergp_fit_params& prm = params[i];
+    const int64_t n = prm.n, nc = n * prm.c;
+    const int64_t bcap = buffer_capacity(prm);
+    if (bcap > 512) {
+      free_models(models, s);
+      return ITERGP_EINVAL;
+    }
+    auto* mdl = new itergp_model();
+    models[i] = mdl;
+    mdl->device = ctx->device;
+    mdl->n = n;
+    mdl->d = prm.d;
+    mdl->c = prm.c;
+    mdl->bcap = static_cast<int>(bcap);
+    mdl->kernel = prm.kernel;
+    mdl->precision = prm.precision;
+    const size_t xb = align_up(sizeof(float) * n * prm.d, 256);
+    const size_t rb = rows_workspace_bytes(prm.precision, n, static_cast<int>(prm.d));
+    const size_t vb = align_up(sizeof(float) * nc, 256);
+    const size_t qb = align_up(sizeof(float) * nc * bcap, 256);
+    mdl->bytes = static_cast<int64_t>(xb + rb + 2 * vb + qb);
+    if (cudaMallocFromPoolAsync(&mdl->mem, mdl->bytes, ctx->pool, s) != cudaSuccess) {
+      mdl->mem = nullptr;
+      free_models(models, s);
+      return ITERGP_ENOMEM;
+    }
+    char* base = static_cast<char*>(mdl->mem);
+    mdl->X = reinterpret_cast<float*>(base);
+    mdl->v = reinterpret_cast<float*>(base + xb + rb);
+    mdl->f = reinterpret_cast<float*>(base + xb + rb + vb);
+    mdl->Q = reinterpret_cast<float*>(base + xb + rb + 2 * vb);
+    int rc = ITERGP_OK;
+    if (cudaMemcpyAsync(mdl->X, prm.X, sizeof(float) * n * prm.d, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+      rc = ITERGP_ECUDA;
+    if (rc == ITERGP_OK)
+      rc = prepare_rows(prm.precision, mdl->X, n, static_cast<int>(prm.d), prm.d, base + xb, &mdl->xop, s);
+    if (rc != ITERGP_OK) {
+      free_models(models, s);
+      return rc;
+    }
+    FitProblem& fp = probs[i];
+    fp.prm = &prm;
+    fp.kp = make_kparams(prm.kernel);
+    fp.xop = &mdl->xop;
+    fp.v = mdl->v;
+    fp.f = mdl->f;
+    fp.Q = mdl->Q;
+    fp.bcap = static_cast<int>(bcap);
+    fp.rep = &reps[i];
+    fp.final_B = &finalB[i];
+    fp.status = &status[i];
+  }
+  // fit_run_batch waits for the stream and reports the fit's own errors (device errors of
+  // single problems in `status`, wait limits in its return value)
+  const int rc = fit_run_batch(ctx, probs, s, params[0].graph != 0);
+  if (rc != ITERGP_OK) {
+    cudaStreamSynchronize(s);
+    free_models(models, s);
+    return rc;
+  }
+  if (!batch && status[0] != ITERGP_OK) {
+    free_models(models, s);
+    return status[0];
+  }
+  for (int i = 0; i < count; ++i) {
+    reps[i].device_bytes = status[i] == ITERGP_OK ? models[i]->bytes : 0;
+    if (reports) reports[i] = reps[i];
+    if (status[i] != ITERGP_OK) {   // this problem failed alone; the others stand
+      model_release(models[i], s);
+      out[i] = nullptr;
+      continue;
+    }
+    models[i]->B = finalB[i];
+    out[i] = models[i];
+  }
+  return ITERGP_OK;
+}
+
+
+}  // namespace itergp
+
 
 extern "C" {
 
@@ -342,120 +444,6 @@ int itergp_sym_eig(const double* M, int32_t b, double* lam, double* U, itergp_st
   return sym_eig_launch(ctx, M, b, lam, U, static_cast<cudaStream_t>(stream));
 }
 
-namespace {
-
-int validate_fit_params(const itergp_fit_params* prm) {
-  if (!prm) return ITERGP_EINVAL;
-  if (prm->n < 1 || prm->d < 1 || prm->d > 4096 || prm->c < 2 || prm->c > 64 || !prm->X || !prm->y)
-    return ITERGP_EINVAL;
-  if (!kernel_ok(&prm->kernel) || !precision_ok(prm->precision)) return ITERGP_EINVAL;
-  if (prm->policy != ITERGP_POLICY_CG && prm->policy != ITERGP_POLICY_UNIT) return ITERGP_EINVAL;
-  if (prm->max_newton < 1 || prm->max_iters < 0 || prm->max_newton > 100000) return ITERGP_EINVAL;
-  if (!(prm->tol_abs >= 0) || !(prm->tol_rel >= 0)) return ITERGP_EINVAL;
-  return ITERGP_OK;
-}
-
-int64_t buffer_capacity(const itergp_fit_params& p) {
-  const int64_t nc = p.n * p.c;
-  int64_t bcap = static_cast<int64_t>(p.max_newton) * p.max_iters;
-  if (p.recycle && p.rank >= 0) bcap = std::min<int64_t>(bcap, static_cast<int64_t>(p.rank) + p.max_iters);
-  if (!p.recycle) bcap = std::min<int64_t>(bcap, p.max_iters);
-  bcap = std::min<int64_t>(bcap, nc);
-  return std::max<int64_t>(bcap, 1);
-}
-
-void free_models(std::vector<itergp_model*>& ms) {
-  for (auto* m : ms) {
-    if (m) {
-      cudaFree(m->mem);
-      delete m;
-    }
-  }
-  ms.clear();
-}
-
-// Fits params[0..count) with one schedule; on success fills models/reports.
-int fit_many(const itergp_fit_params* params, int count, itergp_model** out,
-             itergp_fit_report* reports, cudaStream_t s) {
-  DeviceContext* ctx = current_context();
-  if (!ctx) return ITERGP_ECUDA;
-  if (precision_is_tensor(params[0].precision) && !ctx->tcgen05) return ITERGP_EUNSUPPORTED;
-  std::vector<itergp_model*> models(count, nullptr);
-  std::vector<itergp_fit_report> reps(count);
-  std::vector<int> finalB(count, 0);
-  std::vector<FitProblem> probs(count);
-  for (int i = 0; i < count; ++i) {
-    const itergp_fit_params& prm = params[i];
-    const int64_t n = prm.n, nc = n * prm.c;
-    const int64_t bcap = buffer_capacity(prm);
-    if (bcap > 512) {
-      free_models(models);
-      return ITERGP_EINVAL;
-    }
-    auto* mdl = new itergp_model();
-    models[i] = mdl;
-    mdl->device = ctx->device;
-    mdl->n = n;
-    mdl->d = prm.d;
-    mdl->c = prm.c;
-    mdl->bcap = static_cast<int>(bcap);
-    mdl->kernel = prm.kernel;
-    mdl->precision = prm.precision;
-    const size_t xb = align_up(sizeof(float) * n * prm.d, 256);
-    const size_t rb = rows_workspace_bytes(prm.precision, n, static_cast<int>(prm.d));
-    const size_t vb = align_up(sizeof(float) * nc, 256);
-    const size_t qb = align_up(sizeof(float) * nc * bcap, 256);
-    mdl->bytes = static_cast<int64_t>(xb + rb + 2 * vb + qb);
-    if (cudaMalloc(&mdl->mem, mdl->bytes) != cudaSuccess) {
-      mdl->mem = nullptr;
-      free_models(models);
-      return ITERGP_ENOMEM;
-    }
-    char* base = static_cast<char*>(mdl->mem);
-    mdl->X = reinterpret_cast<float*>(base);
-    mdl->v = reinterpret_cast<float*>(base + xb + rb);
-    mdl->f = reinterpret_cast<float*>(base + xb + rb + vb);
-    mdl->Q = reinterpret_cast<float*>(base + xb + rb + 2 * vb);
-    int rc = ITERGP_OK;
-    if (cudaMemcpyAsync(mdl->X, prm.X, sizeof(float) * n * prm.d, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
-      rc = ITERGP_ECUDA;
-    if (rc == ITERGP_OK)
-      rc = prepare_rows(prm.precision, mdl->X, n, static_cast<int>(prm.d), prm.d, base + xb, &mdl->xop, s);
-    if (rc != ITERGP_OK) {
-      free_models(models);
-      return rc;
-    }
-    FitProblem& fp = probs[i];
-    fp.prm = &prm;
-    fp.kp = make_kparams(prm.kernel);
-    fp.xop = &mdl->xop;
-    fp.v = mdl->v;
-    fp.f = mdl->f;
-    fp.Q = mdl->Q;
-    fp.bcap = static_cast<int>(bcap);
-    fp.rep = &reps[i];
-    fp.final_B = &finalB[i];
-  }
-  int rc = fit_run_batch(ctx, probs, s, params[0].graph != 0);
-  if (rc == ITERGP_OK) {
-    const int st = itergp_sync_status(s);
-    if (st != ITERGP_OK) rc = st;
-  }
-  if (rc != ITERGP_OK) {
-    cudaStreamSynchronize(s);
-    free_models(models);
-    return rc;
-  }
-  for (int i = 0; i < count; ++i) {
-    models[i]->B = finalB[i];
-    reps[i].device_bytes = models[i]->bytes;
-    if (reports) reports[i] = reps[i];
-    out[i] = models[i];
-  }
-  return ITERGP_OK;
-}
-
-}  // namespace
 
 int itergp_fit(const itergp_fit_params* prm, itergp_model** out, itergp_fit_report* report,
                itergp_stream stream) {
@@ -463,7 +451,7 @@ int itergp_fit(const itergp_fit_params* prm, itergp_model** out, itergp_fit_repo
   *out = nullptr;
   const int rc = validate_fit_params(prm);
   if (rc != ITERGP_OK) return rc;
-  return fit_many(prm, 1, out, report, static_cast<cudaStream_t>(stream));
+  return fit_many(prm, 1, out, report, static_cast<cudaStream_t>(stream), false);
 }
 
 int itergp_fit_batch(const itergp_fit_params* params, int32_t count, itergp_model** models,
@@ -481,7 +469,7 @@ int itergp_fit_batch(const itergp_fit_params* params, int32_t count, itergp_mode
         b.tol_abs != a.tol_abs || b.tol_rel != a.tol_rel || b.graph != a.graph)
       return ITERGP_EINVAL;
   }
-  return fit_many(params, count, models, reports, static_cast<cudaStream_t>(stream));
+  return fit_many(params, count, models, reports, static_cast<cudaStream_t>(stream), true);
 }
 
 int itergp_predict(const itergp_model* mdl, const float* Xs, int64_t m, float* mean, float* var,
@@ -538,8 +526,9 @@ void itergp_model_free(itergp_model* mdl) {
   int prev = -1;
   cudaGetDevice(&prev);
   if (prev != mdl->device) cudaSetDevice(mdl->device);
-  cudaDeviceSynchronize();
-  cudaFree(mdl->mem);
+  cudaDeviceSynchronize();   // no stream may still read the model
+  cudaFreeAsync(mdl->mem, cudaStreamLegacy);
+  cudaStreamSynchronize(cudaStreamLegacy);
   if (prev >= 0 && prev != mdl->device) cudaSetDevice(prev);
   delete mdl;
 }

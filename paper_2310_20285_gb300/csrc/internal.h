@@ -2,6 +2,8 @@
 #pragma once
 #include <cuda_bf16.h>
 
+#include <vector>
+
 #include "common.cuh"
 
 namespace itergp {
@@ -93,14 +95,80 @@ struct KmvItemTables {
   int n_items = 0;
 };
 
-// Tensor-core product in item mode over an arena of rows (A = B = arena); s_hi/s_lo:
-// transposed split weights [p16][arena.rows_pad].  All problems share `kind`.
-int kmv_tc_items(DeviceContext* ctx, int kind, const RowOperand& arena, const KmvItemTables& tab,
-                 int p16, const __nv_bfloat16* s_hi, const __nv_bfloat16* s_lo, cudaStream_t stream);
+// Tensor-core product in item mode: item rows a_row of A (query side) against the rows
+// b_row0 .. of B (problem side, both prepared with the same precision and d_pad).
+// s_hi/s_lo: transposed split weights [s_rows][B.rows_pad]; this launch reads weight rows
+// [s_row0, s_row0 + p_pad) (p_pad a multiple of 16, <= 128).  All problems share `kind`.
+int kmv_tc_items(DeviceContext* ctx, int kind, const RowOperand& A, const RowOperand& B,
+                 const KmvItemTables& tab, const __nv_bfloat16* s_hi, const __nv_bfloat16* s_lo,
+                 int64_t s_rows, int s_row0, int p_pad, cudaStream_t stream);
 
-// FP32 SIMT product in item mode: one CTA per item; FP32 arena rows (ld = arena.d_pad),
-// S = FP32 arena [rows_pad][p_max].  All problems share `kind`.
-int kmv_simt_items(DeviceContext* ctx, int kind, const RowOperand& arena, const KmvItemTables& tab,
-                   const float* S, int p_max, cudaStream_t stream);
+// FP32 SIMT product in item mode: one CTA per item; FP32 rows of A and B (pitch ldX, same
+// d), S = FP32 weights [B rows][ldS] with up to p_max (<= 128) columns.  All problems
+// share `kind`.
+int kmv_simt_items(DeviceContext* ctx, int kind, const RowOperand& A, const RowOperand& B,
+                   const KmvItemTables& tab, const float* S, int64_t ldS, int p_max,
+                   cudaStream_t stream);
+
+
+// ---------------------------------------------------------------- fits (solver.cu)
+// One problem of a (batched) fit: its parameters, prepared rows and the model arrays the
+// fit writes (v, f, Q), plus where its outcome goes.
+struct FitProblem {
+  const itergp_fit_params* prm;
+  KParams kp;
+  const RowOperand* xop;   // prepared rows of the problem (model memory)
+  float *v, *f, *Q;
+  int bcap;
+  itergp_fit_report* rep;
+  int* final_B;
+  int* status;             // the problem's own outcome (ITERGP_OK, ITERGP_EINVAL, ITERGP_ENUMERIC)
+};
+
+// Runs Alg. 1-3 for all problems with one schedule (params of probs[0]) on `stream`,
+// optionally captured into one CUDA graph; waits for the stream.  Returns errors of the
+// call (CUDA, memory, a wait limit); device errors of single problems go to their status.
+int fit_run_batch(DeviceContext* ctx, const std::vector<FitProblem>& probs, cudaStream_t stream,
+                  bool use_graph);
+
+// ---------------------------------------------------------------- models (api.cu)
+int validate_fit_params(const itergp_fit_params* prm);
+// Buffer columns a fit keeps at most: min(max_newton * max_iters, R + max_iters, N C).
+int64_t buffer_capacity(const itergp_fit_params& p);
+// Fits params[0..count) with one schedule (allocating the models from the library pool on
+// `s`) and waits.  batch = false: a device error of the problem is the return value;
+// batch = true: failed problems get out[i] = NULL and their report's status.
+int fit_many(const itergp_fit_params* params, int count, itergp_model** out,
+             itergp_fit_report* reports, cudaStream_t s, bool batch);
+// Stream-ordered release of a model no other stream still reads.
+void model_release(itergp_model* m, cudaStream_t s);
+
+// LPT (longest processing time first) assignment of whole-row items to G CTAs; items of
+// one problem stay together within a CTA.  begin: [G + 1] offsets into `ordered`.
+void plan_items(const std::vector<WorkItem>& items, int G, std::vector<WorkItem>* ordered,
+                std::vector<int32_t>* begin);
+
+// Prepared rows written into caller-provided planes with pitch d_pad (>= d, multiple of
+// 64 for tensor precisions): BF16 hi (and lo for split precisions) [rows_pad][d_pad] and
+// FP32 squared norms [rows_pad]; rows beyond `rows` are zero.
+int prepare_rows_into(int precision, const float* X, int64_t rows, int d, int64_t ldX,
+                      int64_t rows_pad, int d_pad, __nv_bfloat16* hi, __nv_bfloat16* lo,
+                      float* norms, cudaStream_t stream);
 
 }  // namespace itergp
+
+// A fitted model: one pool allocation with X, its prepared rows, v, f and Q.
+struct itergp_model {
+  int device = -1;
+  int64_t n = 0, d = 0;
+  int c = 0, bcap = 0, B = 0;
+  itergp_kernel kernel{};
+  int precision = 0;
+  void* mem = nullptr;
+  float* X = nullptr;
+  float* v = nullptr;
+  float* f = nullptr;
+  float* Q = nullptr;     // [bcap][n c]: buffer column b at Q + b n c
+  itergp::RowOperand xop;
+  int64_t bytes = 0;
+};

@@ -59,6 +59,28 @@ __global__ void zero_rows_kernel(float* __restrict__ Y, int64_t m, int64_t p, in
 
 }  // namespace
 
+int prepare_rows_into(int precision, const float* X, int64_t rows, int d, int64_t ldX,
+                      int64_t rows_pad, int d_pad, __nv_bfloat16* hi, __nv_bfloat16* lo,
+                      float* norms, cudaStream_t stream) {
+  if (rows_pad <= 0) return ITERGP_OK;
+  if (rows_pad < rows || d_pad < d || !norms) return ITERGP_EINVAL;
+  if (!precision_is_tensor(precision)) {
+    if (rows > 0) {
+      row_norms_kernel<<<static_cast<unsigned>(ceil_div(rows, 8)), 256, 0, stream>>>(X, ldX, rows, d, norms), ::itergp::note_launch();
+      ITERGP_CUDA_TRY(cudaGetLastError());
+    }
+    return ITERGP_OK;
+  }
+  if (!hi || d_pad % 64 != 0 || (precision_splits_rows(precision) && !lo)) return ITERGP_EINVAL;
+  const unsigned blocks = static_cast<unsigned>(ceil_div(rows_pad, 8));
+  if (precision_splits_rows(precision))
+    prep_rows_kernel<true, false><<<blocks, 256, 0, stream>>>(X, ldX, rows, d, rows_pad, d_pad, hi, lo, norms), ::itergp::note_launch();
+  else
+    prep_rows_kernel<false, true><<<blocks, 256, 0, stream>>>(X, ldX, rows, d, rows_pad, d_pad, hi, nullptr, norms), ::itergp::note_launch();
+  ITERGP_CUDA_TRY(cudaGetLastError());
+  return ITERGP_OK;
+}
+
 size_t rows_workspace_bytes(int precision, int64_t rows, int d) {
   const int64_t rows_pad = (rows + kRowTile - 1) / kRowTile * kRowTile;
   size_t bytes = align_up(sizeof(float) * std::max<int64_t>(rows_pad, 1), 256);

@@ -248,27 +248,31 @@ cudaError_t dispatch_pj(int pj, dim3 grid, cudaStream_t st, const RowOperand& A,
 }
 
 template <int KIND>
-cudaError_t dispatch_items(int pj, dim3 grid, cudaStream_t st, const RowOperand& arena,
-                           const float* S, int p_max, const KParams& kp, const KmvItemTables& tab) {
+cudaError_t dispatch_items(int pj, dim3 grid, cudaStream_t st, const RowOperand& A,
+                           const RowOperand& B, const float* S, int64_t ldS, int p_max,
+                           const KParams& kp, const KmvItemTables& tab) {
   switch (pj) {
-    case 1: return launch_simt<KIND, 1>(grid, st, arena, arena, S, p_max, p_max, nullptr, 0, 0, 0, kp, nullptr, tab.items, tab.probs);
-    case 2: return launch_simt<KIND, 2>(grid, st, arena, arena, S, p_max, p_max, nullptr, 0, 0, 0, kp, nullptr, tab.items, tab.probs);
-    case 4: return launch_simt<KIND, 4>(grid, st, arena, arena, S, p_max, p_max, nullptr, 0, 0, 0, kp, nullptr, tab.items, tab.probs);
-    default: return launch_simt<KIND, 8>(grid, st, arena, arena, S, p_max, p_max, nullptr, 0, 0, 0, kp, nullptr, tab.items, tab.probs);
+    case 1: return launch_simt<KIND, 1>(grid, st, A, B, S, ldS, p_max, nullptr, 0, 0, 0, kp, nullptr, tab.items, tab.probs);
+    case 2: return launch_simt<KIND, 2>(grid, st, A, B, S, ldS, p_max, nullptr, 0, 0, 0, kp, nullptr, tab.items, tab.probs);
+    case 4: return launch_simt<KIND, 4>(grid, st, A, B, S, ldS, p_max, nullptr, 0, 0, 0, kp, nullptr, tab.items, tab.probs);
+    default: return launch_simt<KIND, 8>(grid, st, A, B, S, ldS, p_max, nullptr, 0, 0, 0, kp, nullptr, tab.items, tab.probs);
   }
 }
 
 }  // namespace
 
-int kmv_simt_items(DeviceContext* ctx, int kind, const RowOperand& arena, const KmvItemTables& tab,
-                   const float* S, int p_max, cudaStream_t stream) {
+int kmv_simt_items(DeviceContext* ctx, int kind, const RowOperand& A, const RowOperand& B,
+                   const KmvItemTables& tab, const float* S, int64_t ldS, int p_max,
+                   cudaStream_t stream) {
   (void)ctx;
-  if (p_max > 128 || tab.n_items <= 0) return tab.n_items == 0 ? ITERGP_OK : ITERGP_EINVAL;
+  if (tab.n_items <= 0) return ITERGP_OK;
+  if (p_max < 1 || p_max > 128 || ldS < p_max || A.d != B.d || A.precision != ITERGP_FP32)
+    return ITERGP_EINVAL;
   const int pj = p_max <= 16 ? 1 : p_max <= 32 ? 2 : p_max <= 64 ? 4 : 8;
   dim3 grid(static_cast<unsigned>(tab.n_items), 1, 1);
   const KParams kp = make_kparams(itergp_kernel{kind, 1.f, 1.f});   // per-item values from the table
-  cudaError_t e = kind == ITERGP_RBF ? dispatch_items<ITERGP_RBF>(pj, grid, stream, arena, S, p_max, kp, tab)
-                                     : dispatch_items<ITERGP_MATERN32>(pj, grid, stream, arena, S, p_max, kp, tab);
+  cudaError_t e = kind == ITERGP_RBF ? dispatch_items<ITERGP_RBF>(pj, grid, stream, A, B, S, ldS, p_max, kp, tab)
+                                     : dispatch_items<ITERGP_MATERN32>(pj, grid, stream, A, B, S, ldS, p_max, kp, tab);
   ITERGP_CUDA_TRY(e);
   return ITERGP_OK;
 }

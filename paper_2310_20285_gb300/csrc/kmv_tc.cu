@@ -585,12 +585,15 @@ cudaError_t launch_prec(int prec, int nstage, int grid, size_t smem, cudaStream_
 
 }  // namespace
 
-int kmv_tc_items(DeviceContext* ctx, int kind, const RowOperand& arena, const KmvItemTables& tab,
-                 int p16, const __nv_bfloat16* s_hi, const __nv_bfloat16* s_lo, cudaStream_t stream) {
-  const int prec = arena.precision;
+int kmv_tc_items(DeviceContext* ctx, int kind, const RowOperand& A, const RowOperand& B,
+                 const KmvItemTables& tab, const __nv_bfloat16* s_hi, const __nv_bfloat16* s_lo,
+                 int64_t s_rows, int s_row0, int p16, cudaStream_t stream) {
+  const int prec = B.precision;
   const int nt1 = precision_splits_rows(prec) ? 3 : 1;
   const int nt2 = precision_splits_weights(prec) ? 3 : 1;
-  if (p16 > 128 || p16 % 16 != 0 || tab.G <= 0) return ITERGP_EINVAL;
+  if (p16 > 128 || p16 < 16 || p16 % 16 != 0 || tab.G <= 0 || A.precision != prec ||
+      A.d_pad != B.d_pad || s_row0 < 0 || s_row0 + p16 > s_rows)
+    return ITERGP_EINVAL;
   const size_t smem_cap = std::min<size_t>(ctx->smem_optin, 232448) - 2048;
   const size_t fixed = 2 * s_buf_bytes(nt2, p16) + kSmemExtra;
   const int fit = static_cast<int>((smem_cap > fixed ? smem_cap - fixed : 0) / stage_bytes(nt1));
@@ -599,20 +602,20 @@ int kmv_tc_items(DeviceContext* ctx, int kind, const RowOperand& arena, const Km
   const size_t smem = nstage * stage_bytes(nt1) + 2 * s_buf_bytes(nt2, p16) + kSmemExtra;
   CUtensorMap maps[6];
   const bool ok =
-      encode_bf16_sw128(&maps[0], arena.hi, arena.rows_pad, arena.d_pad, arena.d_pad, BM) &&
-      encode_bf16_sw128(&maps[1], nt1 == 3 ? arena.lo : arena.hi, arena.rows_pad, arena.d_pad, arena.d_pad, BM) &&
-      encode_bf16_sw128(&maps[2], arena.hi, arena.rows_pad, arena.d_pad, arena.d_pad, BN) &&
-      encode_bf16_sw128(&maps[3], nt1 == 3 ? arena.lo : arena.hi, arena.rows_pad, arena.d_pad, arena.d_pad, BN) &&
-      encode_bf16_sw128(&maps[4], s_hi, p16, arena.rows_pad, arena.rows_pad, p16) &&
-      encode_bf16_sw128(&maps[5], nt2 == 3 ? s_lo : s_hi, p16, arena.rows_pad, arena.rows_pad, p16);
+      encode_bf16_sw128(&maps[0], A.hi, A.rows_pad, A.d_pad, A.d_pad, BM) &&
+      encode_bf16_sw128(&maps[1], nt1 == 3 ? A.lo : A.hi, A.rows_pad, A.d_pad, A.d_pad, BM) &&
+      encode_bf16_sw128(&maps[2], B.hi, B.rows_pad, B.d_pad, B.d_pad, BN) &&
+      encode_bf16_sw128(&maps[3], nt1 == 3 ? B.lo : B.hi, B.rows_pad, B.d_pad, B.d_pad, BN) &&
+      encode_bf16_sw128(&maps[4], s_hi, s_rows, B.rows_pad, B.rows_pad, p16) &&
+      encode_bf16_sw128(&maps[5], nt2 == 3 ? s_lo : s_hi, s_rows, B.rows_pad, B.rows_pad, p16);
   if (!ok) return ITERGP_ECUDA;
   TcArgs a{};
-  a.na = arena.norms;
-  a.nb = arena.norms;
-  a.nk = arena.d_pad / BK;
+  a.na = A.norms;
+  a.nb = B.norms;
+  a.nk = B.d_pad / BK;
   a.p_pad = p16;
   a.p_valid = p16;
-  a.s_row0 = 0;
+  a.s_row0 = s_row0;
   a.status = ctx->status;
   a.active = nullptr;
   a.items = tab.items;

@@ -89,9 +89,10 @@ __device__ __forceinline__ void set_status(int* status, int code) { atomicCAS(st
 // For every point: pi = softmax(f_n), 1/pi = exp(lse - f), grad = e_y - pi,
 // b = y_hat - m = f + W^+ grad (m = 0).  Partial sums: |b|^2, log p(y|f), v.(f - m),
 // |g - g_prev|^2, |g|^2 with g = f - m; g_prev <- g.
-__global__ void newton_prologue_kernel(const ProbDev* __restrict__ probs, int* status, int project) {
+__global__ void newton_prologue_kernel(const ProbDev* __restrict__ probs, int project) {
   const ProbDev& P = probs[blockIdx.y];
   const FitState* st = P.st;
+  int* status = &P.st->status;   // errors stop this problem only
   const int64_t n = P.n;
   const int C = P.c;
   const float* __restrict__ f = P.f;
@@ -171,6 +172,13 @@ __global__ void newton_finalize_kernel(const ProbDev* __restrict__ probs, int nb
   FitState* st = P.st;
   const double* __restrict__ part = P.ps;
   if (threadIdx.x != 0 || !st->newton_active) return;
+  if (st->status != ITERGP_OK) {
+    // a label out of range or a non-finite 1/pi in the prologue: this problem stops here
+    // with f of the last completed step; the others continue
+    st->newton_active = 0;
+    st->active = 0;
+    return;
+  }
   double s[5] = {0, 0, 0, 0, 0};
   for (int b = 0; b < nblk; ++b)
     for (int k = 0; k < 5; ++k) s[k] += part[b * 5 + k];
@@ -962,8 +970,6 @@ struct BatchProduct {
   int64_t max_rows_pad = 0;
 };
 
-namespace {
-
 // LPT (longest processing time first) assignment of whole-row items to G CTAs.
 void plan_items(const std::vector<WorkItem>& items, int G, std::vector<WorkItem>* ordered,
                 std::vector<int32_t>* begin) {
@@ -990,19 +996,8 @@ void plan_items(const std::vector<WorkItem>& items, int G, std::vector<WorkItem>
   (*begin)[G] = static_cast<int32_t>(ordered->size());
 }
 
-}  // namespace
 
 // ======================================================================= host side
-
-struct FitProblem {
-  const itergp_fit_params* prm;
-  KParams kp;
-  const RowOperand* xop;   // prepared rows of the problem (model memory)
-  float *v, *f, *Q;
-  int bcap;
-  itergp_fit_report* rep;
-  int* final_B;
-};
 
 int fit_run_batch(DeviceContext* ctx, const std::vector<FitProblem>& probs, cudaStream_t stream,
                   bool use_graph) {
@@ -1053,6 +1048,7 @@ int fit_run_batch(DeviceContext* ctx, const std::vector<FitProblem>& probs, cuda
     o.bold = take(sizeof(int));
   }
   const size_t o_probs = take(sizeof(ProbDev) * np);
+  const size_t o_status = take(sizeof(int));
 
   // ---- batched product plan (np > 1)
   const bool batched = np > 1;
@@ -1130,6 +1126,12 @@ int fit_run_batch(DeviceContext* ctx, const std::vector<FitProblem>& probs, cuda
     d.bold = reinterpret_cast<int*>(base + o.bold);
   }
   ProbDev* pdev = reinterpret_cast<ProbDev*>(base + o_probs);
+  // Kernel-level errors of this fit (a wait that ran out) go to a word of its own, so
+  // fits and products on other streams never see them.
+  DeviceContext fit_ctx = *ctx;
+  fit_ctx.status = reinterpret_cast<int*>(base + o_status);
+  ITERGP_CUDA_TRY(cudaMemsetAsync(fit_ctx.status, 0, sizeof(int), stream));
+  ctx = &fit_ctx;
   ITERGP_CUDA_TRY(cudaMemcpyAsync(pdev, pd.data(), sizeof(ProbDev) * np, cudaMemcpyHostToDevice, stream));
   FitState init{};
   init.newton_active = 1;
@@ -1196,11 +1198,12 @@ int fit_run_batch(DeviceContext* ctx, const std::vector<FitProblem>& probs, cuda
       else
         s_stage_tc_kernel<false><<<grid, 256, 0, stream>>>(bp.src, bp.p16, bp.arena_rows, bp.s_hi, bp.s_lo), ::itergp::note_launch();
       ITERGP_CUDA_TRY(cudaGetLastError());
-      return kmv_tc_items(ctx, bp.kind, bp.arena, bp.tab, bp.p16, bp.s_hi, bp.s_lo, stream);
+      return kmv_tc_items(ctx, bp.kind, bp.arena, bp.arena, bp.tab, bp.s_hi, bp.s_lo, bp.p16, 0,
+                          bp.p16, stream);
     }
     s_stage_simt_kernel<<<grid, 256, 0, stream>>>(bp.src, c_max, bp.s32), ::itergp::note_launch();
     ITERGP_CUDA_TRY(cudaGetLastError());
-    return kmv_simt_items(ctx, bp.kind, bp.arena, bp.tab, bp.s32, c_max, stream);
+    return kmv_simt_items(ctx, bp.kind, bp.arena, bp.arena, bp.tab, bp.s32, c_max, c_max, stream);
   };
 
   const size_t eig_smem = eig_smem_bytes(max_bcap);
@@ -1223,7 +1226,7 @@ int fit_run_batch(DeviceContext* ctx, const std::vector<FitProblem>& probs, cuda
   }
   int rc = ITERGP_OK;
   for (int step = 0; step < prm.max_newton && rc == ITERGP_OK; ++step) {
-    newton_prologue_kernel<<<dim3(nblk, np), kRedThreads, 0, stream>>>(pdev, ctx->status, project), ::itergp::note_launch();
+    newton_prologue_kernel<<<dim3(nblk, np), kRedThreads, 0, stream>>>(pdev, project), ::itergp::note_launch();
     newton_finalize_kernel<<<np, 32, 0, stream>>>(pdev, nblk, step, prm.tol_newton, prm.tol_abs, prm.tol_rel, prm.recycle), ::itergp::note_launch();
     // ---- Alg. 3: virtual solver run with compression
     if (prm.recycle && step > 0) {
@@ -1288,9 +1291,12 @@ int fit_run_batch(DeviceContext* ctx, const std::vector<FitProblem>& probs, cuda
   ITERGP_CUDA_TRY(cudaGetLastError());
 
   std::vector<FitState> hs(np);
+  int fit_status = ITERGP_OK;
   for (int i = 0; i < np; ++i)
     ITERGP_CUDA_TRY(cudaMemcpyAsync(&hs[i], pd[i].st, sizeof(FitState), cudaMemcpyDeviceToHost, stream));
+  ITERGP_CUDA_TRY(cudaMemcpyAsync(&fit_status, fit_ctx.status, sizeof(int), cudaMemcpyDeviceToHost, stream));
   ITERGP_CUDA_TRY(cudaStreamSynchronize(stream));
+  if (fit_status != ITERGP_OK) return fit_status;
   for (int i = 0; i < np; ++i) {
     itergp_fit_report* rep = probs[i].rep;
     if (rep) {
@@ -1306,7 +1312,9 @@ int fit_run_batch(DeviceContext* ctx, const std::vector<FitProblem>& probs, cuda
         rep->rel_change[k] = hs[i].rel_change[k];
       }
       rep->resid_norm = hs[i].rnorm;
+      rep->status = hs[i].status;
     }
+    *probs[i].status = hs[i].status;
     *probs[i].final_B = hs[i].B;
   }
   return ITERGP_OK;

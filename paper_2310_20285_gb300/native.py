@@ -52,7 +52,8 @@ class FitReport(ct.Structure):
                 ("kept", ct.c_int32 * MAX_REPORT_STEPS),
                 ("objective", ct.c_double * MAX_REPORT_STEPS),
                 ("rel_change", ct.c_double * MAX_REPORT_STEPS),
-                ("resid_norm", ct.c_double), ("device_bytes", ct.c_int64)]
+                ("resid_norm", ct.c_double), ("device_bytes", ct.c_int64),
+                ("status", ct.c_int32), ("reserved", ct.c_int32)]
 
 
 class ModelView(ct.Structure):
@@ -305,9 +306,11 @@ def fit(X, y, c, kind="rbf", lengthscale=1.0, outputscale=1.0, precision="fp32",
 
 def fit_batch(problems, kind="rbf", precision="fp32", policy="cg", max_newton=5, max_iters=5,
               rank=50, recycle=True, tol_newton=0.0, tol_abs=1e-5, tol_rel=1e-5, graph=True,
-              stream=None):
+              stream=None, errors="raise"):
     """Batched fit of independent problems [(X, y, c, lengthscale, outputscale), ...] with
-    one schedule (one launch per phase over all problems).  Returns a list of Models."""
+    one schedule (one launch per phase over all problems).  Returns a list of Models.  A
+    problem that fails on the device fails alone: errors="raise" frees the other models
+    and raises its ItergpError; errors="return" puts the ItergpError in its slot."""
     prms = (FitParams * len(problems))()
     for i, (X, y, c, ell, s) in enumerate(problems):
         prms[i] = _params(X, y, c, kind, ell, s, precision, policy, max_newton, max_iters, rank,
@@ -316,4 +319,13 @@ def fit_batch(problems, kind="rbf", precision="fp32", policy="cg", max_newton=5,
     reps = (FitReport * len(problems))()
     rc = lib.itergp_fit_batch(prms, len(problems), hs, reps, _stream(stream))
     _check(rc, "itergp_fit_batch")
-    return [Model(ct.c_void_p(hs[i]), reps[i], problems[i][0].device) for i in range(len(problems))]
+    out = [Model(ct.c_void_p(hs[i]), reps[i], problems[i][0].device) if hs[i]
+           else ItergpError(reps[i].status, f"itergp_fit_batch (problem {i})")
+           for i in range(len(problems))]
+    failed = [o for o in out if isinstance(o, ItergpError)]
+    if failed and errors == "raise":
+        for o in out:
+            if isinstance(o, Model):
+                o.free()
+        raise failed[0]
+    return out

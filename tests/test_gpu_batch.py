@@ -174,3 +174,26 @@ def test_batch_rejects_mismatched_schedules(native):
     hs = (ct.c_void_p * 2)()
     assert native.lib.itergp_fit_batch(prms, 2, hs, None, native._stream()) == native.EINVAL
     assert not hs[0] and not hs[1]
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16x3"])
+def test_a_failing_problem_fails_alone(native, prec):
+    """A label out of range in one problem stops that problem (EINVAL in its slot); every
+    other problem's result is bitwise the one of the batch without it (each row tile is
+    computed over all its chunks in a fixed order, whatever CTA runs it)."""
+    probs = small_batch(count=5, seed=21)
+    dev = to_dev(probs)
+    bad = list(dev[2])
+    yb = bad[1].clone()
+    yb[7] = bad[2] + 3
+    bad[1] = yb
+    mixed = dev[:2] + [tuple(bad)] + dev[3:]
+    got = native.fit_batch(mixed, precision=prec, graph=True, errors="return", **SCHED)
+    assert isinstance(got[2], native.ItergpError) and got[2].code == native.EINVAL
+    ref = native.fit_batch(dev[:2] + dev[3:], precision=prec, graph=True, **SCHED)
+    for a, b in zip([g for i, g in enumerate(got) if i != 2], ref):
+        assert torch.equal(a.arrays()["f"], b.arrays()["f"])
+        a.free()
+        b.free()
+    with pytest.raises(native.ItergpError):
+        native.fit_batch(mixed, precision=prec, graph=True, **SCHED)
