@@ -43,6 +43,8 @@ def parse():
     ap.add_argument("--no-extras", action="store_true", help="skip other precisions and fit timings")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--batch-count", type=int, default=256, help="problems of the batched-fit extra")
+    ap.add_argument("--serve-seconds", type=float, default=20.0, help="arrival window of the serving extra")
+    ap.add_argument("--no-tune", action="store_true", help="skip autotuning the product's launch variants")
     return ap.parse_args()
 
 
@@ -219,6 +221,93 @@ def bench_batched(native, datagen, torch, dev, count):
     return res
 
 
+def bench_serving(native, datagen, precision, seconds, seed=5, drain_s=10.0):
+    """Serving: Poisson arrivals over `seconds` of fit requests at 50/s (N log-uniform in
+    [1e3, 5e4], D = 32, C = 5 blobs, RBF l log-uniform in [0.3, 3]; 5 Newton x <= 5
+    iterations, R = 50) and predict requests at 2000/s (M uniform in [1, 4096], D = 32)
+    against models already resident, admitted under an 80 GB model budget.  The fit
+    inputs come from a pool of 64 generated problems and the queries from a pool of 16
+    blocks (every request is still its own copy, fit and model).  Latency = completion
+    (results in the caller's host buffers) minus submission."""
+    import numpy as np
+    rng = np.random.default_rng(seed)
+    pool = datagen.batch_problems(count=64, seed=seed, n_lo=1000, n_hi=50000, dims=(32,), c_lo=5,
+                                  c_hi=5, ell_lo=0.3, ell_hi=3.0, n_test=8)
+    qpool = [datagen.normal((4096, 32), seed + 100 + k) * 3.0 for k in range(16)]
+    fit_t = np.cumsum(rng.exponential(1 / 50.0, size=int(60 * seconds) + 10))
+    pred_t = np.cumsum(rng.exponential(1 / 2000.0, size=int(2100 * seconds) + 10))
+    fit_t = fit_t[fit_t < seconds]
+    pred_t = pred_t[pred_t < seconds]
+    arrivals = sorted([(t, 0) for t in fit_t] + [(t, 1) for t in pred_t])
+    fit_pick = rng.integers(0, len(pool), size=len(fit_t))
+    pred_m = rng.integers(1, 4097, size=len(pred_t))
+    pred_q = rng.integers(0, len(qpool), size=len(pred_t))
+    pred_u = rng.random(size=len(pred_t))
+    srv = native.Server(model_bytes=80 << 30, work_bytes=24 << 30, precision=precision, d_max=32,
+                        c_max=5, max_fit_batch=64, max_predict_batch=512, max_predict_rows=1 << 18,
+                        max_newton=5, max_iters=5, rank=50, graph=True)
+    resident, lat = [], {0: [], 1: []}
+    done_fit, skipped, kinds = 0, 0, {}
+    submitted = {0: 0, 1: 0}
+
+    def take(events):
+        nonlocal done_fit
+        for (rid, model, kind, status, ts, t0, td, batch) in events:
+            if kind == 1:
+                srv.result(rid)
+            if status != 0:
+                continue
+            lat[kind].append(td - ts)
+            if kind == 0:
+                resident.append(model)
+                done_fit += 1
+
+    t_start = time.perf_counter()
+    fi = pi = 0
+    for t, kind in arrivals:
+        while True:
+            now = time.perf_counter() - t_start
+            if now >= t:
+                break
+            take(srv.poll(timeout_s=min(t - now, 0.002)))
+        if kind == 0:
+            p = pool[fit_pick[fi]]
+            fi += 1
+            srv.submit_fit(p.X, p.y, p.c, p.lengthscale, 1.0)
+            submitted[0] += 1
+        else:
+            m, q, u = int(pred_m[pi]), int(pred_q[pi]), float(pred_u[pi])
+            pi += 1
+            if not resident:
+                skipped += 1
+                continue
+            try:
+                srv.submit_predict(resident[int(u * len(resident))], qpool[q][:m])
+                submitted[1] += 1
+            except native.ItergpError:
+                skipped += 1
+    t_arr = time.perf_counter() - t_start
+    t_end = t_arr + drain_s
+    while time.perf_counter() - t_start < t_end and len(lat[0]) + len(lat[1]) < submitted[0] + submitted[1]:
+        take(srv.poll(timeout_s=0.05))
+    wall = time.perf_counter() - t_start
+    st = srv.stats()
+    srv.close()
+
+    def pct(x, q):
+        return float(np.percentile(np.asarray(x), q) * 1e3) if x else None
+
+    return {"precision": precision, "arrival_s": round(t_arr, 3), "wall_s": round(wall, 3),
+            "fits": {"submitted": submitted[0], "done": len(lat[0]), "req_per_s": len(lat[0]) / wall,
+                     "p50_ms": pct(lat[0], 50), "p99_ms": pct(lat[0], 99)},
+            "predicts": {"submitted": submitted[1], "done": len(lat[1]), "req_per_s": len(lat[1]) / wall,
+                         "p50_ms": pct(lat[1], 50), "p99_ms": pct(lat[1], 99),
+                         "skipped_no_model": skipped},
+            "backlog_at_end": {"fits": st["queued_fits"], "predicts": st["queued_predicts"]},
+            "fit_batches": st["fit_batches"], "predict_batches": st["predict_batches"],
+            "evicted": st["evicted"]}
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -253,6 +342,23 @@ def main():
         if world > 1:
             dist.barrier()
         torch.cuda.synchronize()
+
+    # autotune the launch variants of every product shape timed below (recorded in the
+    # library's table, reported in the JSON line)
+    tuning = []
+    if not args.no_tune:
+        shapes = [("kernel bench", 60000, D, P, "matern32", args.precision, False)]
+        if rank == 0 and not args.no_extras:
+            shapes += [("batched fits", 8192, 64, 16, "rbf", pr, True) for pr in ("bf16x3", "bf16_comp")]
+            shapes += [("served mean", 16384, 32, 16, "rbf", "bf16x3", True),
+                       ("served variance", 16384, 32, 128, "rbf", "bf16x3", True)]
+        for label, tn, td, tp, kind, prec, items in shapes:
+            vs, best = native.autotune(tn, td, tp, kind=kind, precision=prec, items=items,
+                                       lengthscale=ELL if kind == "matern32" else 1.0)
+            tuning.append({"shape": label, "n": tn, "d": td, "p": tp, "precision": prec,
+                           "schedule": "items" if items else "single",
+                           "variants_ms": {f"{e}w/{st}st": round(ms, 4) for e, st, ms in vs},
+                           "chosen": f"{best[0]} epilogue warps, {best[1]} stages"})
 
     for _ in range(max(args.warmup, 3)):
         step()
@@ -333,7 +439,7 @@ def main():
                                   "784-D sparse clusters (19% non-zero), S ~ N(0,1)",
                       "precision": args.precision, "l2": "inputs exceed L2 (X is 188 MB FP32, 200 MB BF16 hi+lo)",
                       "parallelism": f"{world} independent problem(s), one per GPU"},
-           "roofline": roof, "clocks": clk, "gpu_launches": int(launches),
+           "roofline": roof, "clocks": clk, "gpu_launches": int(launches), "tuning": tuning,
            "e2e": {"value": world * n * n / t_e2e, "unit": "kernel-pairs/s",
                    "h2d_bytes_per_step": int(hX.numel() * 4 + hS.numel() * 4),
                    "d2h_bytes_per_step": int(hY.numel() * 4), "ms_per_step": t_e2e * 1e3}}
@@ -382,6 +488,14 @@ def main():
                       **fits}
     if rank == 0 and not args.no_extras:
         out["batched"] = bench_batched(native, datagen, torch, dev, args.batch_count)
+    if rank == 0 and not args.no_extras and args.serve_seconds > 0:
+        out["serving"] = {
+            "workload": f"{args.serve_seconds:g} s of Poisson arrivals: fits 50/s (N log-U[1e3,5e4], D=32, C=5, "
+                        "RBF l log-U[0.3,3], 5 Newton x <=5 iters, R=50) and predicts 2000/s (M U[1,4096], "
+                        "D=32) against resident models; 80 GB model budget; latency = results in host "
+                        "buffers minus submission",
+            "forms": [bench_serving(native, datagen, prec, args.serve_seconds)
+                      for prec in ("bf16x3", "fp32")]}
     if rank == 0 and world == 1:
         out["cpu_baseline"] = cpu_baseline(X, S, args.cpu_seconds)
     if rank == 0:

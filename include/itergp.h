@@ -43,7 +43,8 @@ typedef enum {
   ITERGP_ENUMERIC = -4,     /* a non-finite value was produced on the device              */
   ITERGP_ETIMEOUT = -5,     /* a device-side wait exceeded its bound; the kernel returned */
   ITERGP_EUNSUPPORTED = -6, /* the current device is not sm_103a / sm_100 family          */
-  ITERGP_ESCRATCH = -7      /* itergp_kmatvec_noalloc: sizes need more than its fixed scratch */
+  ITERGP_ESCRATCH = -7,     /* itergp_kmatvec_noalloc: sizes need more than its fixed scratch */
+  ITERGP_EGONE = -8         /* server: the model is not resident (evicted, released, failed) */
 } itergp_status;
 
 /* Kernel functions (App. C.1 / C.3 use GPyTorch's RBF and Matern-3/2 kernels):
@@ -272,6 +273,120 @@ const char* itergp_status_string(int status);
  * library and stays valid until the thread's next failing call.  (Library plumbing; the
  * paper has no counterpart.) */
 const char* itergp_last_error(void);
+
+/* ------------------------------------------------------------------------------------
+ * Serving (a project addition; the paper has no serving layer).
+ *
+ * A server owns one GPU's share of models: it fits models from host data and answers
+ * predictive queries against them, with continuous batching on two streams driven by two
+ * host threads:
+ *  - fits: requests waiting when the fit stream frees up are admitted together (in
+ *    arrival order, while the HBM budgets allow) and run as ONE batched fit
+ *    (itergp_fit_batch semantics: every phase of Alg. 1-3 is one launch over the batch);
+ *    each fitted model is then installed in the server's model slab;
+ *  - predicts: requests waiting when the predict stream frees up are admitted together,
+ *    across models, and answered by one batched product per part (mean: K(X*,X) v;
+ *    variance: K(X*,X) Q) over all of them, then one epilogue (Eqs. 9-10, probit).
+ * Predicts run while fits are on the GPU.  Every model keeps X (prepared rows), v and the
+ * root Q of C_j = Q Q^T resident in the slab until it is released or evicted.
+ *
+ * Memory: `model_bytes` is the slab, carved into 128-row blocks.  A fit is admitted only
+ * when its rows fit in the slab; idle models (no queued or running predicts) are evicted
+ * least recently used first to make room.  `work_bytes` bounds the workspace of the fits
+ * in flight.  A request that can never fit fails with ITERGP_ENOMEM.
+ *
+ * All models of a server share kernel.kind, precision and the fit schedule.  Data passed
+ * to submit calls is copied before the call returns; predict outputs are written to the
+ * caller's host buffers, which must stay valid until the request's completion event. */
+typedef struct itergp_server itergp_server;
+
+typedef struct {
+  int64_t model_bytes;       /* HBM for resident models (the slab)                      */
+  int64_t work_bytes;        /* HBM for the workspaces of fits in flight                */
+  int32_t kind;              /* itergp_kernel_kind of every model                       */
+  int32_t precision;         /* itergp_precision of fits and predicts                   */
+  int32_t d_max;             /* largest input dimension (1..1024)                       */
+  int32_t c_max;             /* largest class count (2..16)                             */
+  int32_t max_fit_batch;     /* problems per batched fit (>= 1)                         */
+  int32_t max_predict_batch; /* requests per batched predict (>= 1)                     */
+  int64_t max_predict_rows;  /* query rows per batched predict (>= 4096)                */
+  int32_t max_newton, max_iters, rank;   /* fit schedule (Alg. 1-3); CG actions,        */
+  int32_t graph;             /* recycling on; graph != 0 captures each fit batch         */
+  double tol_abs, tol_rel;   /* inner tolerances (App. B.2)                             */
+} itergp_server_config;
+
+typedef enum { ITERGP_REQ_FIT = 0, ITERGP_REQ_PREDICT = 1 } itergp_request_kind;
+
+typedef struct {
+  int64_t id;                /* model id (fit) or request id (predict)                 */
+  int64_t model;             /* the model the request belongs to                       */
+  int32_t kind;              /* itergp_request_kind                                     */
+  int32_t status;            /* ITERGP_OK or the request's error                        */
+  double submit_s, start_s, done_s;   /* server clock (s): submitted, launched, results ready */
+  int32_t batch;             /* requests in the launch batch it ran in                 */
+  int32_t reserved;
+} itergp_server_event;
+
+typedef struct {
+  int64_t resident_models, resident_rows, slab_rows;
+  int64_t fits_done, predicts_done, fit_batches, predict_batches, evicted;
+  int64_t queued_fits, queued_predicts;
+} itergp_server_stats;
+
+/* Creates the server on the current device (allocates the slab, starts its threads).
+ * c_max * (1 + buffer capacity of the schedule) must be <= 144 (one mean tile of 16 and
+ * one variance tile of 128 weight columns per model). */
+int itergp_server_create(const itergp_server_config* config, itergp_server** out);
+/* Stops accepting requests, drops those still queued (no events for them), waits for the
+ * batches on the GPU, joins the threads and frees the slab. */
+int itergp_server_destroy(itergp_server* server);
+/* Queues a fit of host X (n x d) with host labels y (n, values in [0, c)).  *model_id
+ * identifies the model in predicts and events. */
+int itergp_server_submit_fit(itergp_server* server, const float* X, const int32_t* y,
+                             int64_t n, int64_t d, int32_t c, float lengthscale,
+                             float outputscale, int64_t* model_id);
+/* Queues a predict of host Xs (m x d of the model) against a model that is resident or
+ * still being fitted.  mean (m x c) is required; var and probs (m x c) may be NULL. */
+int itergp_server_submit_predict(itergp_server* server, int64_t model_id, const float* Xs,
+                                 int64_t m, float* mean, float* var, float* probs,
+                                 int64_t* request_id);
+/* Moves up to `capacity` completion events (oldest first) to `events`; waits up to
+ * timeout_us (< 0: forever) for the first one.  *count may be 0 after a timeout. */
+int itergp_server_poll(itergp_server* server, itergp_server_event* events, int32_t capacity,
+                       int32_t* count, int64_t timeout_us);
+/* Releases a model's slab rows once its queued predicts are done (later predicts on it
+ * fail with ITERGP_EGONE). */
+int itergp_server_release(itergp_server* server, int64_t model_id);
+int itergp_server_get_stats(itergp_server* server, itergp_server_stats* stats);
+
+/* ------------------------------------------------------------------------------------
+ * Autotuning of the tensor-core product (a project addition; the paper has no such part).
+ * A launch variant is the number of epilogue warps (4, or 8 with two warps per TMEM lane
+ * quadrant splitting the columns) and the depth of the TMA stage ring (2-4).  The library
+ * keeps a process-wide table keyed by (precision, kernel kind, D padded to 64, P tile,
+ * schedule); launches not in the table use 4 warps and the deepest ring that fits.
+ *
+ * itergp_autotune times every variant that fits on synthetic operands of the given shape
+ * (n rows of dimension d, p weight columns; items = 0: the single-problem schedule of
+ * itergp_kmatvec and fits, items = 1: the batched/served item schedule, p <= 128), records
+ * the fastest in the table and reports all timings (ms per launch).  It waits for the
+ * stream.  Tensor-core precisions only.
+ * itergp_tune_save / _load write / merge the table as text lines
+ * "precision kind d_pad p_tile items epilogue_warps stages"; _clear empties it. */
+#define ITERGP_TUNE_MAX 6
+typedef struct {
+  int32_t epilogue_warps, stages;
+  double ms;
+} itergp_tune_variant;
+typedef struct {
+  int32_t count, best;
+  itergp_tune_variant variants[ITERGP_TUNE_MAX];
+} itergp_tune_result;
+int itergp_autotune(const itergp_kernel* kernel, int32_t precision, int64_t n, int64_t d, int64_t p,
+                    int32_t items, itergp_tune_result* result, itergp_stream stream);
+int itergp_tune_save(const char* path);
+int itergp_tune_load(const char* path);
+int itergp_tune_clear(void);
 
 /* Library version "major.minor.patch". */
 const char* itergp_version(void);

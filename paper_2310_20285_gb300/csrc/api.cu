@@ -177,6 +177,20 @@ __global__ void predict_epilogue_kernel(const float* __restrict__ Y, int64_t m, 
 }
 
 // S_view[n][col]: col < C -> v[n][col]; col = C + b C + c -> Q[b][n][c]
+// Deterministic pseudo-random fill (integer hash of the index; timing inputs only).
+__global__ void fill_hash_kernel(float* __restrict__ x, int64_t n, uint32_t seed, float lo, float hi) {
+  for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
+       i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    uint32_t h = static_cast<uint32_t>(i) * 0x9E3779B1u ^ seed ^ static_cast<uint32_t>(i >> 32);
+    h ^= h >> 16;
+    h *= 0x7FEB352Du;
+    h ^= h >> 15;
+    h *= 0x846CA68Bu;
+    h ^= h >> 16;
+    x[i] = lo + (hi - lo) * static_cast<float>(h >> 8) * (1.f / 16777216.f);
+  }
+}
+
 __global__ void gather_vq_kernel(const float* __restrict__ v, const float* __restrict__ Q,
                                  int64_t n, int C, int B, float* __restrict__ out) {
   const int64_t P = static_cast<int64_t>(C) * (1 + B);
@@ -374,6 +388,7 @@ const char* itergp_status_string(int status) {
     case ITERGP_ETIMEOUT: return "device-side wait exceeded its bound";
     case ITERGP_EUNSUPPORTED: return "unsupported device (needs sm_100 family / sm_103a)";
     case ITERGP_ESCRATCH: return "problem needs more scratch than the fixed static buffer holds";
+    case ITERGP_EGONE: return "model not resident (evicted, released or failed)";
     default: return "unknown status";
   }
 }
@@ -504,6 +519,44 @@ int itergp_predict(const itergp_model* mdl, const float* Xs, int64_t m, float* m
   const unsigned blocks = static_cast<unsigned>(std::min<int64_t>(ceil_div(m, 256), 8LL * ctx->num_sms));
   predict_epilogue_kernel<<<blocks, 256, 0, s>>>(Y, m, C, B, P, mdl->kernel.outputscale, mean, var, probs), ::itergp::note_launch();
   ITERGP_CUDA_TRY(cudaGetLastError());
+  return ITERGP_OK;
+}
+
+int itergp_autotune(const itergp_kernel* kernel, int32_t precision, int64_t n, int64_t d, int64_t p,
+                    int32_t items, itergp_tune_result* result, itergp_stream stream) {
+  if (!kernel_ok(kernel) || !result || !precision_is_tensor(precision) || n < 128 || n > (int64_t(1) << 26) ||
+      d < 1 || d > 4096 || p < 1 || p > (items ? 128 : 4096))
+    return ITERGP_EINVAL;
+  DeviceContext* ctx = current_context();
+  if (!ctx) return ITERGP_ECUDA;
+  if (!ctx->tcgen05) return ITERGP_EUNSUPPORTED;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const size_t bx = align_up(sizeof(float) * n * d, 256), bs = align_up(sizeof(float) * n * p, 256);
+  const size_t br = rows_workspace_bytes(precision, n, static_cast<int>(d));
+  Scratch ws;
+  ITERGP_CUDA_TRY(ws.alloc(ctx, bx + 2 * bs + br, s));
+  float* X = ws.as<float>();
+  float* S = ws.as<float>(bx);
+  float* Y = ws.as<float>(bx + bs);
+  const unsigned blocks = static_cast<unsigned>(8 * ctx->num_sms);
+  fill_hash_kernel<<<blocks, 256, 0, s>>>(X, n * d, 0x1234u, 0.f, 1.f), ::itergp::note_launch();
+  fill_hash_kernel<<<blocks, 256, 0, s>>>(S, n * p, 0x9876u, -1.f, 1.f), ::itergp::note_launch();
+  ITERGP_CUDA_TRY(cudaGetLastError());
+  RowOperand op;
+  int rc = prepare_rows(precision, X, n, static_cast<int>(d), d, ws.as<char>(bx + 2 * bs), &op, s);
+  if (rc != ITERGP_OK) return rc;
+  int count = 0, best = -1, epi[ITERGP_TUNE_MAX], ns[ITERGP_TUNE_MAX];
+  double ms[ITERGP_TUNE_MAX];
+  rc = kmv_tc_tune(ctx, make_kparams(*kernel), op, S, p, Y, items ? 1 : 0, ITERGP_TUNE_MAX, &count, epi,
+                   ns, ms, &best, s);
+  if (rc != ITERGP_OK) return rc;
+  result->count = count;
+  result->best = best;
+  for (int i = 0; i < count; ++i) {
+    result->variants[i].epilogue_warps = epi[i];
+    result->variants[i].stages = ns[i];
+    result->variants[i].ms = ms[i];
+  }
   return ITERGP_OK;
 }
 

@@ -148,6 +148,14 @@ void model_release(itergp_model* m, cudaStream_t s);
 void plan_items(const std::vector<WorkItem>& items, int G, std::vector<WorkItem>* ordered,
                 std::vector<int32_t>* begin);
 
+// Times every launch variant of the tensor-core product (epilogue warps x stages) on X
+// (A = B = X, weights S: rows x p, output Y) in the single (items = 0) or item-mode
+// schedule, records the fastest for (precision, kind, d_pad, P tile, schedule) and
+// returns the timings (up to cap variants).
+int kmv_tc_tune(DeviceContext* ctx, const KParams& kp, const RowOperand& X, const float* S,
+                int64_t p, float* Y, int items, int cap, int* count, int* epi_out, int* ns_out,
+                double* ms_out, int* best, cudaStream_t stream);
+
 // Prepared rows written into caller-provided planes with pitch d_pad (>= d, multiple of
 // 64 for tensor precisions): BF16 hi (and lo for split precisions) [rows_pad][d_pad] and
 // FP32 squared norms [rows_pad]; rows beyond `rows` are zero.

@@ -27,6 +27,9 @@
 // CTA) go to scratch and a fix-up kernel adds them in CTA order, so results are
 // deterministic.
 #include <algorithm>
+#include <map>
+#include <mutex>
+#include <tuple>
 #include <cstring>
 
 #include "internal.h"
@@ -39,7 +42,9 @@ namespace {
 constexpr int BM = 128;   // rows of A per tile (MMA M)
 constexpr int BN = 128;   // rows of B per chunk (MMA N of the distance GEMM, K of the product)
 constexpr int BK = 64;    // D slice per stage (one 128-byte swizzle row of BF16)
-constexpr int kThreads = 256;
+// Threads: warps 0-3 (TMA, MMA, TMEM owner, idle) plus EPI epilogue warps (4 or 8; with 8,
+// two warps share each TMEM lane quadrant and split the columns).
+__host__ __device__ constexpr int tc_threads(int epi) { return (4 + epi) * 32; }
 constexpr uint32_t kTmemCols = 512;
 constexpr uint32_t kOCol = 256;
 constexpr uint32_t kO2Col = 384;   // FP32 running sum of flushed O (IEEE round-to-nearest adds)
@@ -56,6 +61,7 @@ struct TcArgs {
   int p_pad;              // MMA N of the product (multiple of 16, <= 128)
   int p_valid;            // valid output columns of this P tile
   int s_row0;             // first row of this P tile in the transposed S
+  int p_col0;             // item mode: first output column of this P tile
   float* Y;               // output, already offset to the tile's first column
   int64_t ldY;
   float* partial;         // [2 G][BM][p_pad]
@@ -75,7 +81,8 @@ __host__ __device__ constexpr uint32_t s_box_bytes(int p_pad) { return static_ca
 __host__ __device__ constexpr uint32_t s_buf_bytes(int nt2, int p_pad) {
   return 2u * s_box_bytes(p_pad) * (nt2 == 3 ? 2u : 1u);
 }
-constexpr uint32_t kSmemExtra = 1024 /*alignment*/ + 2048 /*per-warp nb staging*/;
+// alignment slack + per-epilogue-warp staging of 128 column norms
+__host__ __device__ constexpr uint32_t smem_extra(int epi) { return 1024u + static_cast<uint32_t>(epi) * 512u; }
 
 // Per-CTA sequence of (row tile, chunk) steps of the partition described above.
 struct Schedule {
@@ -176,8 +183,8 @@ struct Walker {
   }
 };
 
-template <int KIND, int NT1, int NT2, int NSTAGE>
-__global__ void __launch_bounds__(kThreads, 1)
+template <int KIND, int NT1, int NT2, int NSTAGE, int EPI>
+__global__ void __launch_bounds__(tc_threads(EPI), 1)
 kmv_tc_kernel(const __grid_constant__ CUtensorMap mAh, const __grid_constant__ CUtensorMap mAl,
               const __grid_constant__ CUtensorMap mBh, const __grid_constant__ CUtensorMap mBl,
               const __grid_constant__ CUtensorMap mSh, const __grid_constant__ CUtensorMap mSl,
@@ -198,7 +205,7 @@ kmv_tc_kernel(const __grid_constant__ CUtensorMap mAh, const __grid_constant__ C
   const uint32_t SBOX = s_box_bytes(args.p_pad);
   const uint32_t SBUF = s_buf_bytes(NT2, args.p_pad);
   uint8_t* s_region = smem + NSTAGE * SB;
-  float* nb_all = reinterpret_cast<float*>(s_region + 2 * SBUF);   // [4 warps][128]
+  float* nb_all = reinterpret_cast<float*>(s_region + 2 * SBUF);   // [EPI warps][128]
 
   __shared__ __align__(8) uint64_t full_bar[NSTAGE], empty_bar[NSTAGE];
   __shared__ __align__(8) uint64_t gfull[2], pfull[2], sfull[2], sempty[2], ofull, oempty, drain;
@@ -214,12 +221,12 @@ kmv_tc_kernel(const __grid_constant__ CUtensorMap mAh, const __grid_constant__ C
     }
     for (int i = 0; i < 2; ++i) {
       mbar_init(&gfull[i], 1);
-      mbar_init(&pfull[i], 128);
+      mbar_init(&pfull[i], 32 * EPI);
       mbar_init(&sfull[i], 1);
       mbar_init(&sempty[i], 1);
     }
     mbar_init(&ofull, 1);
-    mbar_init(&oempty, 128);
+    mbar_init(&oempty, 32 * EPI);
     mbar_init(&drain, 1);
     fence_mbar_init();
   }
@@ -372,7 +379,10 @@ kmv_tc_kernel(const __grid_constant__ CUtensorMap mAh, const __grid_constant__ C
     }
   } else if (warp >= 4) {
     // ------------------------------------------------------------------ epilogue
-    const int q = warp - 4;
+    constexpr int NH = EPI / 4;     // epilogue warps per TMEM lane quadrant
+    const int e = warp - 4;
+    const int q = e & 3;            // lane quadrant (= warp % 4, the warp's TMEM lanes)
+    const int h = e >> 2;           // this warp's share of the columns
     const int row = 32 * q + lane;
     const uint32_t lane_base = static_cast<uint32_t>(32 * q) << 16;
     int64_t seg = -1, sub = -1;
@@ -403,11 +413,11 @@ kmv_tc_kernel(const __grid_constant__ CUtensorMap mAh, const __grid_constant__ C
           kp = pr.kp;
           const int64_t prow = static_cast<int64_t>(it.tile_row) + row;
           out_valid = prow < pr.m;
-          out_row = pr.Y + prow * pr.ldY;
-          out_lim = pr.p_valid;
+          out_row = pr.Y + prow * pr.ldY + args.p_col0;
+          out_lim = pr.p_valid - args.p_col0;   // <= 0: nothing of this tile to write
         }
       }
-      float* nb_s = nb_all + q * BN;
+      float* nb_s = nb_all + e * BN;
       __syncwarp();
 #pragma unroll
       for (int k = 0; k < BN / 32; ++k) nb_s[lane + 32 * k] = args.nb[static_cast<int64_t>(st.b_row) + lane + 32 * k];
@@ -417,7 +427,7 @@ kmv_tc_kernel(const __grid_constant__ CUtensorMap mAh, const __grid_constant__ C
       tc_fence_after();
       const uint32_t gcol = tb + lane_base + gb * BN;
 #pragma unroll 1
-      for (int grp = 0; grp < BN / 32; ++grp) {
+      for (int grp = h * (BN / 32 / NH); grp < (h + 1) * (BN / 32 / NH); ++grp) {
         uint32_t v[32];
         tmem_ld32(gcol + 32 * grp, v);
         tmem_ld_wait();
@@ -462,7 +472,7 @@ kmv_tc_kernel(const __grid_constant__ CUtensorMap mAh, const __grid_constant__ C
           }
         }
         const int lim = st.item >= 0 ? out_lim : (full_row ? args.p_valid : args.p_pad);
-        for (int c16 = 0; c16 < args.p_pad / 16; ++c16) {
+        for (int c16 = h; c16 < args.p_pad / 16; c16 += NH) {
           uint32_t o[16];
           tmem_ld16(tb + lane_base + kOCol + 16 * c16, o);
           if (sub_in_seg > 0) {
@@ -551,36 +561,73 @@ __global__ void prep_s_kernel(const float* __restrict__ S, int64_t ldS, int64_t 
   }
 }
 
-template <int KIND, int NT1, int NT2, int NSTAGE>
+template <int KIND, int NT1, int NT2, int NSTAGE, int EPI>
 cudaError_t launch_tc(int grid, size_t smem, cudaStream_t st, const CUtensorMap* maps,
                       const TcArgs& a) {
-  auto fn = kmv_tc_kernel<KIND, NT1, NT2, NSTAGE>;
+  auto fn = kmv_tc_kernel<KIND, NT1, NT2, NSTAGE, EPI>;
   cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   timing_begin(st);
-  fn<<<grid, kThreads, smem, st>>>(maps[0], maps[1], maps[2], maps[3], maps[4], maps[5], a), ::itergp::note_launch();
+  fn<<<grid, tc_threads(EPI), smem, st>>>(maps[0], maps[1], maps[2], maps[3], maps[4], maps[5], a), ::itergp::note_launch();
   timing_end(st);
   return cudaGetLastError();
 }
 
-template <int KIND, int NT1, int NT2>
+template <int KIND, int NT1, int NT2, int EPI>
 cudaError_t launch_stages(int nstage, int grid, size_t smem, cudaStream_t st,
                           const CUtensorMap* maps, const TcArgs& a) {
   switch (nstage) {
-    case 2: return launch_tc<KIND, NT1, NT2, 2>(grid, smem, st, maps, a);
-    case 3: return launch_tc<KIND, NT1, NT2, 3>(grid, smem, st, maps, a);
-    default: return launch_tc<KIND, NT1, NT2, 4>(grid, smem, st, maps, a);
+    case 2: return launch_tc<KIND, NT1, NT2, 2, EPI>(grid, smem, st, maps, a);
+    case 3: return launch_tc<KIND, NT1, NT2, 3, EPI>(grid, smem, st, maps, a);
+    default: return launch_tc<KIND, NT1, NT2, 4, EPI>(grid, smem, st, maps, a);
+  }
+}
+
+template <int KIND, int EPI>
+cudaError_t launch_prec_epi(int prec, int nstage, int grid, size_t smem, cudaStream_t st,
+                            const CUtensorMap* maps, const TcArgs& a) {
+  switch (prec) {
+    case ITERGP_BF16X3: return launch_stages<KIND, 3, 3, EPI>(nstage, grid, smem, st, maps, a);
+    case ITERGP_BF16_COMP: return launch_stages<KIND, 3, 1, EPI>(nstage, grid, smem, st, maps, a);
+    default: return launch_stages<KIND, 1, 1, EPI>(nstage, grid, smem, st, maps, a);
   }
 }
 
 template <int KIND>
-cudaError_t launch_prec(int prec, int nstage, int grid, size_t smem, cudaStream_t st,
+cudaError_t launch_prec(int prec, int nstage, int epi, int grid, size_t smem, cudaStream_t st,
                         const CUtensorMap* maps, const TcArgs& a) {
-  switch (prec) {
-    case ITERGP_BF16X3: return launch_stages<KIND, 3, 3>(nstage, grid, smem, st, maps, a);
-    case ITERGP_BF16_COMP: return launch_stages<KIND, 3, 1>(nstage, grid, smem, st, maps, a);
-    default: return launch_stages<KIND, 1, 1>(nstage, grid, smem, st, maps, a);
-  }
+  return epi == 8 ? launch_prec_epi<KIND, 8>(prec, nstage, grid, smem, st, maps, a)
+                  : launch_prec_epi<KIND, 4>(prec, nstage, grid, smem, st, maps, a);
+}
+
+// ---------------------------------------------------------------- launch variants
+// A variant: epilogue warps (4 or 8) and pipeline stages (0: the deepest that fits).
+// The table holds what the autotuner measured per (precision, kind, d_pad, P tile,
+// schedule); a thread may force a variant while it times candidates.
+struct TcVariant {
+  int epi = 4;
+  int nstage = 0;
+};
+
+std::mutex g_tune_mu;
+std::map<std::tuple<int, int, int, int, int>, TcVariant> g_tune;
+thread_local const TcVariant* t_forced = nullptr;
+
+TcVariant tc_variant(int prec, int kind, int d_pad, int p_pad, int items) {
+  if (t_forced) return *t_forced;
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  auto it = g_tune.find(std::make_tuple(prec, kind, d_pad, std::min(p_pad, 128), items));
+  return it == g_tune.end() ? TcVariant{} : it->second;
+}
+
+// Deepest stage count (<= want, 0 = no limit) that fits with P tile p_tile; 0 if < 2.
+int stages_that_fit(const DeviceContext* ctx, int nt1, int nt2, int p_tile, int epi, int want) {
+  const size_t smem_cap = std::min<size_t>(ctx->smem_optin, 232448) - 2048;
+  const size_t fixed = 2 * s_buf_bytes(nt2, p_tile) + smem_extra(epi);
+  const int fit = static_cast<int>((smem_cap > fixed ? smem_cap - fixed : 0) / stage_bytes(nt1));
+  int ns = fit >= 4 ? 4 : fit >= 3 ? 3 : fit >= 2 ? 2 : 0;
+  if (want >= 2 && ns > want) ns = want;
+  return ns;
 }
 
 }  // namespace
@@ -594,38 +641,45 @@ int kmv_tc_items(DeviceContext* ctx, int kind, const RowOperand& A, const RowOpe
   if (p16 > 128 || p16 < 16 || p16 % 16 != 0 || tab.G <= 0 || A.precision != prec ||
       A.d_pad != B.d_pad || s_row0 < 0 || s_row0 + p16 > s_rows)
     return ITERGP_EINVAL;
-  const size_t smem_cap = std::min<size_t>(ctx->smem_optin, 232448) - 2048;
-  const size_t fixed = 2 * s_buf_bytes(nt2, p16) + kSmemExtra;
-  const int fit = static_cast<int>((smem_cap > fixed ? smem_cap - fixed : 0) / stage_bytes(nt1));
-  const int nstage = fit >= 4 ? 4 : fit >= 3 ? 3 : fit >= 2 ? 2 : 0;
+  // P tile: the widest multiple of 16 (<= p16) that leaves room for >= 2 stages
+  const TcVariant var = tc_variant(prec, kind, B.d_pad, p16, 1);
+  int p_tile = p16, nstage = 0;
+  for (; p_tile >= 16; p_tile -= 16) {
+    nstage = stages_that_fit(ctx, nt1, nt2, p_tile, var.epi, var.nstage);
+    if (nstage >= 2) break;
+  }
   if (nstage < 2) return ITERGP_EUNSUPPORTED;
-  const size_t smem = nstage * stage_bytes(nt1) + 2 * s_buf_bytes(nt2, p16) + kSmemExtra;
   CUtensorMap maps[6];
-  const bool ok =
-      encode_bf16_sw128(&maps[0], A.hi, A.rows_pad, A.d_pad, A.d_pad, BM) &&
-      encode_bf16_sw128(&maps[1], nt1 == 3 ? A.lo : A.hi, A.rows_pad, A.d_pad, A.d_pad, BM) &&
-      encode_bf16_sw128(&maps[2], B.hi, B.rows_pad, B.d_pad, B.d_pad, BN) &&
-      encode_bf16_sw128(&maps[3], nt1 == 3 ? B.lo : B.hi, B.rows_pad, B.d_pad, B.d_pad, BN) &&
-      encode_bf16_sw128(&maps[4], s_hi, s_rows, B.rows_pad, B.rows_pad, p16) &&
-      encode_bf16_sw128(&maps[5], nt2 == 3 ? s_lo : s_hi, s_rows, B.rows_pad, B.rows_pad, p16);
+  bool ok = encode_bf16_sw128(&maps[0], A.hi, A.rows_pad, A.d_pad, A.d_pad, BM) &&
+            encode_bf16_sw128(&maps[1], nt1 == 3 ? A.lo : A.hi, A.rows_pad, A.d_pad, A.d_pad, BM) &&
+            encode_bf16_sw128(&maps[2], B.hi, B.rows_pad, B.d_pad, B.d_pad, BN) &&
+            encode_bf16_sw128(&maps[3], nt1 == 3 ? B.lo : B.hi, B.rows_pad, B.d_pad, B.d_pad, BN);
   if (!ok) return ITERGP_ECUDA;
-  TcArgs a{};
-  a.na = A.norms;
-  a.nb = B.norms;
-  a.nk = B.d_pad / BK;
-  a.p_pad = p16;
-  a.p_valid = p16;
-  a.s_row0 = s_row0;
-  a.status = ctx->status;
-  a.active = nullptr;
-  a.items = tab.items;
-  a.item_begin = tab.item_begin;
-  a.probs = tab.probs;
-  a.kp = make_kparams(itergp_kernel{kind, 1.f, 1.f});   // per-item values come from the table
-  cudaError_t e = kind == ITERGP_RBF
-                      ? launch_prec<ITERGP_RBF>(prec, nstage, tab.G, smem, stream, maps, a)
-                      : launch_prec<ITERGP_MATERN32>(prec, nstage, tab.G, smem, stream, maps, a);
-  ITERGP_CUDA_TRY(e);
+  for (int p0 = 0; p0 < p16; p0 += p_tile) {
+    const int pp = std::min(p_tile, p16 - p0);   // multiple of 16
+    ok = encode_bf16_sw128(&maps[4], s_hi, s_rows, B.rows_pad, B.rows_pad, pp) &&
+         encode_bf16_sw128(&maps[5], nt2 == 3 ? s_lo : s_hi, s_rows, B.rows_pad, B.rows_pad, pp);
+    if (!ok) return ITERGP_ECUDA;
+    TcArgs a{};
+    a.na = A.norms;
+    a.nb = B.norms;
+    a.nk = B.d_pad / BK;
+    a.p_pad = pp;
+    a.p_valid = pp;
+    a.s_row0 = s_row0 + p0;
+    a.p_col0 = p0;
+    a.status = ctx->status;
+    a.active = nullptr;
+    a.items = tab.items;
+    a.item_begin = tab.item_begin;
+    a.probs = tab.probs;
+    a.kp = make_kparams(itergp_kernel{kind, 1.f, 1.f});   // per-item values come from the table
+    const size_t smem = nstage * stage_bytes(nt1) + 2 * s_buf_bytes(nt2, pp) + smem_extra(var.epi);
+    cudaError_t e = kind == ITERGP_RBF
+                        ? launch_prec<ITERGP_RBF>(prec, nstage, var.epi, tab.G, smem, stream, maps, a)
+                        : launch_prec<ITERGP_MATERN32>(prec, nstage, var.epi, tab.G, smem, stream, maps, a);
+    ITERGP_CUDA_TRY(e);
+  }
   return ITERGP_OK;
 }
 
@@ -635,24 +689,20 @@ int kmv_tc(DeviceContext* ctx, const KParams& kp, const RowOperand& A, const Row
   const int prec = A.precision;
   const int nt1 = precision_splits_rows(prec) ? 3 : 1;
   const int nt2 = precision_splits_weights(prec) ? 3 : 1;
-  const size_t smem_cap = std::min<size_t>(ctx->smem_optin, 232448) - 2048;
 
   // P tile: the largest multiple of 16 (<= 128) that leaves room for >= 2 stages; then the
   // deepest instantiated stage count (2, 3, 4) that fits.  (The split distance GEMM is
   // bounded by shared-memory bandwidth, not by stage depth: deeper rings of narrower
   // slices measured slower.)
   const int64_t p16 = (p + 15) / 16 * 16;
+  const TcVariant var = tc_variant(prec, kp.kind, A.d_pad, static_cast<int>(std::min<int64_t>(p16, 128)), 0);
   int p_tile = static_cast<int>(std::min<int64_t>(p16, 128));
   int nstage = 0;
   for (; p_tile >= 16; p_tile -= 16) {
-    const size_t fixed = 2 * s_buf_bytes(nt2, p_tile) + kSmemExtra;
-    const size_t room = smem_cap > fixed ? smem_cap - fixed : 0;
-    const int fit = static_cast<int>(room / stage_bytes(nt1));
-    nstage = fit >= 4 ? 4 : fit >= 3 ? 3 : fit >= 2 ? 2 : 0;
+    nstage = stages_that_fit(ctx, nt1, nt2, p_tile, var.epi, var.nstage);
     if (nstage >= 2) break;
   }
   if (nstage < 2) return ITERGP_EUNSUPPORTED;
-  const size_t smem = nstage * stage_bytes(nt1) + 2 * s_buf_bytes(nt2, p_tile) + kSmemExtra;
 
   // transposed, split S
   const int64_t n_pad = B.rows_pad;
@@ -710,11 +760,10 @@ int kmv_tc(DeviceContext* ctx, const KParams& kp, const RowOperand& A, const Row
     a.items = nullptr;
     a.item_begin = nullptr;
     a.probs = nullptr;
-    const size_t smem_t = nstage * stage_bytes(nt1) + 2 * s_buf_bytes(nt2, pp) + kSmemExtra;
-    (void)smem;
+    const size_t smem_t = nstage * stage_bytes(nt1) + 2 * s_buf_bytes(nt2, pp) + smem_extra(var.epi);
     cudaError_t e = kp.kind == ITERGP_RBF
-                        ? launch_prec<ITERGP_RBF>(prec, nstage, (int)G, smem_t, stream, maps, a)
-                        : launch_prec<ITERGP_MATERN32>(prec, nstage, (int)G, smem_t, stream, maps, a);
+                        ? launch_prec<ITERGP_RBF>(prec, nstage, var.epi, (int)G, smem_t, stream, maps, a)
+                        : launch_prec<ITERGP_MATERN32>(prec, nstage, var.epi, (int)G, smem_t, stream, maps, a);
     ITERGP_CUDA_TRY(e);
     if (tail_rows > 0) {
       tc_fixup_kernel<<<static_cast<unsigned>(tail_rows), 256, 0, stream>>>(
@@ -726,3 +775,135 @@ int kmv_tc(DeviceContext* ctx, const KParams& kp, const RowOperand& A, const Row
 }
 
 }  // namespace itergp
+
+// ---------------------------------------------------------------- autotuning
+namespace itergp {
+
+int kmv_tc_tune(DeviceContext* ctx, const KParams& kp, const RowOperand& X, const float* S,
+                int64_t p, float* Y, int items, int cap, int* count, int* epi_out, int* ns_out,
+                double* ms_out, int* best, cudaStream_t stream) {
+  const int prec = X.precision;
+  const int nt1 = precision_splits_rows(prec) ? 3 : 1;
+  const int nt2 = precision_splits_weights(prec) ? 3 : 1;
+  const int p16 = static_cast<int>(std::min<int64_t>((p + 15) / 16 * 16, 128));
+  // item mode: one problem covering all rows, weights staged as the batched fit stages them
+  Scratch tabs, sbuf;
+  KmvItemTables tab;
+  __nv_bfloat16 *s_hi = nullptr, *s_lo = nullptr;
+  if (items) {
+    if (p > 128) return ITERGP_EINVAL;
+    const int chunks = static_cast<int>(ceil_div(X.rows, BM));
+    std::vector<WorkItem> its;
+    for (int r = 0; r < chunks; ++r)
+      its.push_back(WorkItem{0, 128 * r, 128 * r, 0, chunks, static_cast<int32_t>(X.rows), 0, 0});
+    const int G = static_cast<int>(std::min<int64_t>(ctx->num_sms, chunks));
+    std::vector<WorkItem> ord;
+    std::vector<int32_t> beg;
+    plan_items(its, G, &ord, &beg);
+    TcProb pr{Y, p, X.rows, static_cast<int32_t>(p), 0, kp, nullptr};
+    const size_t b_items = align_up(sizeof(WorkItem) * ord.size(), 256);
+    const size_t b_beg = align_up(sizeof(int32_t) * beg.size(), 256);
+    ITERGP_CUDA_TRY(tabs.alloc(ctx, b_items + b_beg + sizeof(TcProb), stream));
+    ITERGP_CUDA_TRY(cudaMemcpyAsync(tabs.as<char>(), ord.data(), sizeof(WorkItem) * ord.size(), cudaMemcpyHostToDevice, stream));
+    ITERGP_CUDA_TRY(cudaMemcpyAsync(tabs.as<char>(b_items), beg.data(), sizeof(int32_t) * beg.size(), cudaMemcpyHostToDevice, stream));
+    ITERGP_CUDA_TRY(cudaMemcpyAsync(tabs.as<char>(b_items + b_beg), &pr, sizeof(TcProb), cudaMemcpyHostToDevice, stream));
+    tab.items = tabs.as<WorkItem>();
+    tab.item_begin = reinterpret_cast<const int32_t*>(tabs.as<char>(b_items));
+    tab.probs = reinterpret_cast<const TcProb*>(tabs.as<char>(b_items + b_beg));
+    tab.G = G;
+    tab.n_items = static_cast<int>(ord.size());
+    const size_t s_elems = static_cast<size_t>(p16) * X.rows_pad;
+    ITERGP_CUDA_TRY(sbuf.alloc(ctx, s_elems * 2 * 2, stream));
+    s_hi = sbuf.as<__nv_bfloat16>();
+    s_lo = s_hi + s_elems;
+    dim3 grid(static_cast<unsigned>(X.rows_pad / 32), static_cast<unsigned>(ceil_div(p16, 32)));
+    prep_s_kernel<true><<<grid, dim3(32, 8), 0, stream>>>(S, p, X.rows, p, X.rows_pad, p16, s_hi, s_lo, nullptr), ::itergp::note_launch();
+    ITERGP_CUDA_TRY(cudaGetLastError());
+  }
+  cudaEvent_t e0, e1;
+  ITERGP_CUDA_TRY(cudaEventCreate(&e0));
+  ITERGP_CUDA_TRY(cudaEventCreate(&e1));
+  int n = 0, rc = ITERGP_OK;
+  *best = -1;
+  for (int epi : {4, 8}) {
+    for (int ns : {2, 3, 4}) {
+      if (n >= cap) break;
+      if (stages_that_fit(ctx, nt1, nt2, std::min(p16, 128), epi, ns) != ns) continue;
+      const TcVariant v{epi, ns};
+      t_forced = &v;
+      auto run = [&] {
+        return items ? kmv_tc_items(ctx, kp.kind, X, X, tab, s_hi, s_lo, p16, 0, p16, stream)
+                     : kmv_tc(ctx, kp, X, X, S, p, p, Y, p, stream, nullptr);
+      };
+      rc = run();   // warm-up
+      int reps = 0;
+      float ms = 0.f;
+      if (rc == ITERGP_OK && cudaEventRecord(e0, stream) == cudaSuccess) {
+        for (reps = 0; reps < 5 && rc == ITERGP_OK; ++reps) rc = run();
+        if (cudaEventRecord(e1, stream) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+            cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess)
+          rc = ITERGP_ECUDA;
+      }
+      t_forced = nullptr;
+      if (rc != ITERGP_OK) break;
+      epi_out[n] = epi;
+      ns_out[n] = ns;
+      ms_out[n] = ms / reps;
+      if (*best < 0 || ms_out[n] < ms_out[*best]) *best = n;
+      ++n;
+    }
+    if (rc != ITERGP_OK) break;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  *count = n;
+  if (rc != ITERGP_OK) return rc;
+  if (*best >= 0) {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune[std::make_tuple(prec, kp.kind, X.d_pad, p16, items ? 1 : 0)] = TcVariant{epi_out[*best], ns_out[*best]};
+  }
+  return ITERGP_OK;
+}
+
+}  // namespace itergp
+
+extern "C" int itergp_tune_save(const char* path) {
+  if (!path) return ITERGP_EINVAL;
+  FILE* f = std::fopen(path, "w");
+  if (!f) return ITERGP_EINVAL;
+  std::lock_guard<std::mutex> lk(itergp::g_tune_mu);
+  std::fprintf(f, "# precision kind d_pad p_tile items epilogue_warps stages\n");
+  for (const auto& kv : itergp::g_tune)
+    std::fprintf(f, "%d %d %d %d %d %d %d\n", std::get<0>(kv.first), std::get<1>(kv.first),
+                 std::get<2>(kv.first), std::get<3>(kv.first), std::get<4>(kv.first), kv.second.epi,
+                 kv.second.nstage);
+  std::fclose(f);
+  return ITERGP_OK;
+}
+
+extern "C" int itergp_tune_load(const char* path) {
+  if (!path) return ITERGP_EINVAL;
+  FILE* f = std::fopen(path, "r");
+  if (!f) return ITERGP_EINVAL;
+  char line[256];
+  int rc = ITERGP_OK;
+  std::lock_guard<std::mutex> lk(itergp::g_tune_mu);
+  while (std::fgets(line, sizeof(line), f)) {
+    if (line[0] == '#') continue;
+    int a[7];
+    if (std::sscanf(line, "%d %d %d %d %d %d %d", &a[0], &a[1], &a[2], &a[3], &a[4], &a[5], &a[6]) != 7 ||
+        (a[5] != 4 && a[5] != 8) || a[6] < 0 || a[6] > 4) {
+      rc = ITERGP_EINVAL;
+      continue;
+    }
+    itergp::g_tune[std::make_tuple(a[0], a[1], a[2], a[3], a[4])] = itergp::TcVariant{a[5], a[6]};
+  }
+  std::fclose(f);
+  return rc;
+}
+
+extern "C" int itergp_tune_clear(void) {
+  std::lock_guard<std::mutex> lk(itergp::g_tune_mu);
+  itergp::g_tune.clear();
+  return ITERGP_OK;
+}

@@ -13,7 +13,7 @@ import torch
 
 _LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libitergp.so")
 
-OK, EINVAL, ENOMEM, ECUDA, ENUMERIC, ETIMEOUT, EUNSUPPORTED, ESCRATCH = 0, -1, -2, -3, -4, -5, -6, -7
+OK, EINVAL, ENOMEM, ECUDA, ENUMERIC, ETIMEOUT, EUNSUPPORTED, ESCRATCH, EGONE = 0, -1, -2, -3, -4, -5, -6, -7, -8
 NOALLOC_SCRATCH_BYTES = 64 << 20
 RBF, MATERN32 = 0, 1
 FP32, BF16X3, BF16, BF16_COMP = 0, 1, 2, 3
@@ -62,6 +62,40 @@ class ModelView(ct.Structure):
                 ("X", ct.c_void_p), ("v", ct.c_void_p), ("f", ct.c_void_p), ("Q", ct.c_void_p)]
 
 
+class ServerConfig(ct.Structure):
+    _fields_ = [("model_bytes", ct.c_int64), ("work_bytes", ct.c_int64), ("kind", ct.c_int32),
+                ("precision", ct.c_int32), ("d_max", ct.c_int32), ("c_max", ct.c_int32),
+                ("max_fit_batch", ct.c_int32), ("max_predict_batch", ct.c_int32),
+                ("max_predict_rows", ct.c_int64), ("max_newton", ct.c_int32),
+                ("max_iters", ct.c_int32), ("rank", ct.c_int32), ("graph", ct.c_int32),
+                ("tol_abs", ct.c_double), ("tol_rel", ct.c_double)]
+
+
+class ServerEvent(ct.Structure):
+    _fields_ = [("id", ct.c_int64), ("model", ct.c_int64), ("kind", ct.c_int32),
+                ("status", ct.c_int32), ("submit_s", ct.c_double), ("start_s", ct.c_double),
+                ("done_s", ct.c_double), ("batch", ct.c_int32), ("reserved", ct.c_int32)]
+
+
+class ServerStats(ct.Structure):
+    _fields_ = [(n, ct.c_int64) for n in ("resident_models", "resident_rows", "slab_rows",
+                                          "fits_done", "predicts_done", "fit_batches",
+                                          "predict_batches", "evicted", "queued_fits",
+                                          "queued_predicts")]
+
+
+REQ_FIT, REQ_PREDICT = 0, 1
+TUNE_MAX = 6
+
+
+class TuneVariant(ct.Structure):
+    _fields_ = [("epilogue_warps", ct.c_int32), ("stages", ct.c_int32), ("ms", ct.c_double)]
+
+
+class TuneResult(ct.Structure):
+    _fields_ = [("count", ct.c_int32), ("best", ct.c_int32), ("variants", TuneVariant * TUNE_MAX)]
+
+
 def _load():
     if not os.path.exists(_LIB_PATH):
         raise ImportError(f"libitergp.so not built ({_LIB_PATH}); run "
@@ -90,10 +124,24 @@ def _load():
     lib.itergp_timing_read.argtypes = [ct.POINTER(ct.c_double), ct.POINTER(ct.c_int64)]
     lib.itergp_launch_count.restype = ct.c_int64
     lib.itergp_launch_count.argtypes = []
-    for name in ("itergp_kmatvec", "itergp_kmatvec_noalloc", "itergp_winv_apply", "itergp_pseudo_targets",
+    lib.itergp_server_create.argtypes = [ct.POINTER(ServerConfig), ct.POINTER(vp)]
+    lib.itergp_server_destroy.argtypes = [vp]
+    lib.itergp_server_submit_fit.argtypes = [vp, vp, vp, i64, i64, i32, ct.c_float, ct.c_float,
+                                             ct.POINTER(i64)]
+    lib.itergp_server_submit_predict.argtypes = [vp, i64, vp, i64, vp, vp, vp, ct.POINTER(i64)]
+    lib.itergp_server_poll.argtypes = [vp, ct.POINTER(ServerEvent), i32, ct.POINTER(i32), i64]
+    lib.itergp_server_release.argtypes = [vp, i64]
+    lib.itergp_server_get_stats.argtypes = [vp, ct.POINTER(ServerStats)]
+    lib.itergp_autotune.argtypes = [ct.POINTER(Kernel), i32, i64, i64, i64, i32, ct.POINTER(TuneResult), vp]
+    lib.itergp_tune_save.argtypes = [ct.c_char_p]
+    lib.itergp_tune_load.argtypes = [ct.c_char_p]
+    lib.itergp_tune_clear.argtypes = []
+    for name in ("itergp_autotune", "itergp_tune_save", "itergp_tune_load", "itergp_tune_clear",
+                 "itergp_kmatvec", "itergp_kmatvec_noalloc", "itergp_winv_apply", "itergp_pseudo_targets",
                  "itergp_sym_eig", "itergp_fit", "itergp_fit_batch", "itergp_predict",
-                 "itergp_model_get_view",
-                 "itergp_sync_status"):
+                 "itergp_model_get_view", "itergp_sync_status", "itergp_server_create",
+                 "itergp_server_destroy", "itergp_server_submit_fit", "itergp_server_submit_predict",
+                 "itergp_server_poll", "itergp_server_release", "itergp_server_get_stats"):
         getattr(lib, name).restype = ct.c_int
     return lib
 
@@ -329,3 +377,114 @@ def fit_batch(problems, kind="rbf", precision="fp32", policy="cg", max_newton=5,
                 o.free()
         raise failed[0]
     return out
+
+
+def autotune(n, d, p, kind="rbf", precision="bf16x3", items=False, lengthscale=1.0, stream=None):
+    """Times every launch variant of the tensor-core product for this shape, records the
+    fastest in the library's table; returns [(epilogue_warps, stages, ms)] and the best."""
+    res = TuneResult()
+    _check(lib.itergp_autotune(ct.byref(_kernel(kind, lengthscale, 1.0)), _prec(precision), int(n), int(d),
+                               int(p), 1 if items else 0, ct.byref(res), _stream(stream)),
+           "itergp_autotune")
+    vs = [(v.epilogue_warps, v.stages, v.ms) for v in res.variants[:res.count]]
+    return vs, (vs[res.best] if res.best >= 0 else None)
+
+
+def tune_save(path):
+    _check(lib.itergp_tune_save(str(path).encode()), "itergp_tune_save")
+
+
+def tune_load(path):
+    _check(lib.itergp_tune_load(str(path).encode()), "itergp_tune_load")
+
+
+def tune_clear():
+    _check(lib.itergp_tune_clear(), "itergp_tune_clear")
+
+
+class Server:
+    """Request loop over resident models (itergp_server_*): fits and predicts are queued
+    from host arrays, run in batches on the GPU by the library's own threads, and report
+    completion events.  Predict results land in NumPy arrays owned by this object until
+    the request completes (``result(request_id)``)."""
+
+    def __init__(self, model_bytes, work_bytes, precision="bf16x3", kind="rbf", d_max=32,
+                 c_max=5, max_fit_batch=64, max_predict_batch=256, max_predict_rows=1 << 16,
+                 max_newton=5, max_iters=5, rank=50, graph=True, tol_abs=1e-5, tol_rel=1e-5):
+        import numpy as np
+        self._np = np
+        cfg = ServerConfig(int(model_bytes), int(work_bytes), KERNELS[kind], _prec(precision),
+                           int(d_max), int(c_max), int(max_fit_batch), int(max_predict_batch),
+                           int(max_predict_rows), int(max_newton), int(max_iters), int(rank),
+                           1 if graph else 0, float(tol_abs), float(tol_rel))
+        h = ct.c_void_p()
+        _check(lib.itergp_server_create(ct.byref(cfg), ct.byref(h)), "itergp_server_create")
+        self._h = h
+        self._c = {}          # model id -> classes
+        self._out = {}        # request id -> (mean, var, probs, inputs kept alive)
+
+    def submit_fit(self, X, y, c, lengthscale=1.0, outputscale=1.0) -> int:
+        np = self._np
+        X = np.ascontiguousarray(X, dtype=np.float32)
+        y = np.ascontiguousarray(y, dtype=np.int32)
+        mid = ct.c_int64()
+        _check(lib.itergp_server_submit_fit(self._h, X.ctypes.data, y.ctypes.data, X.shape[0],
+                                            X.shape[1], int(c), float(lengthscale),
+                                            float(outputscale), ct.byref(mid)),
+               "itergp_server_submit_fit")
+        self._c[mid.value] = int(c)
+        return mid.value
+
+    def submit_predict(self, model_id, Xs, var=True, probs=True) -> int:
+        np = self._np
+        Xs = np.ascontiguousarray(Xs, dtype=np.float32)
+        c = self._c[model_id]
+        mean = np.empty((Xs.shape[0], c), dtype=np.float32)
+        v = np.empty_like(mean) if var else None
+        p = np.empty_like(mean) if probs else None
+        rid = ct.c_int64()
+        _check(lib.itergp_server_submit_predict(self._h, int(model_id), Xs.ctypes.data, Xs.shape[0],
+                                                mean.ctypes.data, v.ctypes.data if var else None,
+                                                p.ctypes.data if probs else None, ct.byref(rid)),
+               "itergp_server_submit_predict")
+        self._out[rid.value] = (mean, v, p)
+        return rid.value
+
+    def poll(self, timeout_s=0.0, capacity=4096):
+        """Completion events [(id, model, kind, status, submit_s, start_s, done_s, batch)]."""
+        evs = (ServerEvent * capacity)()
+        n = ct.c_int32()
+        _check(lib.itergp_server_poll(self._h, evs, capacity, ct.byref(n),
+                                      -1 if timeout_s is None else int(timeout_s * 1e6)),
+               "itergp_server_poll")
+        return [(e.id, e.model, e.kind, e.status, e.submit_s, e.start_s, e.done_s, e.batch)
+                for e in evs[:n.value]]
+
+    def result(self, request_id):
+        """(mean, var, probs) of a completed predict (and forgets it)."""
+        return self._out.pop(request_id)
+
+    def release(self, model_id):
+        _check(lib.itergp_server_release(self._h, int(model_id)), "itergp_server_release")
+
+    def stats(self) -> dict:
+        st = ServerStats()
+        _check(lib.itergp_server_get_stats(self._h, ct.byref(st)), "itergp_server_get_stats")
+        return {n: getattr(st, n) for n, _ in ServerStats._fields_}
+
+    def close(self):
+        if self._h:
+            _check(lib.itergp_server_destroy(self._h), "itergp_server_destroy")
+            self._h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

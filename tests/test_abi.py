@@ -107,3 +107,52 @@ def test_model_free_accepts_null(lib):
     lib.itergp_model_free.argtypes = [ct.c_void_p]
     lib.itergp_model_free.restype = None
     lib.itergp_model_free(None)
+
+
+class ServerConfig(ct.Structure):
+    _fields_ = [("model_bytes", ct.c_int64), ("work_bytes", ct.c_int64), ("kind", ct.c_int32),
+                ("precision", ct.c_int32), ("d_max", ct.c_int32), ("c_max", ct.c_int32),
+                ("max_fit_batch", ct.c_int32), ("max_predict_batch", ct.c_int32),
+                ("max_predict_rows", ct.c_int64), ("max_newton", ct.c_int32),
+                ("max_iters", ct.c_int32), ("rank", ct.c_int32), ("graph", ct.c_int32),
+                ("tol_abs", ct.c_double), ("tol_rel", ct.c_double)]
+
+
+def test_server_config_is_validated_on_the_host(lib):
+    """Invalid server configurations fail with EINVAL before any CUDA call (no GPU here)."""
+    lib.itergp_server_create.argtypes = [ct.POINTER(ServerConfig), ct.POINTER(ct.c_void_p)]
+    lib.itergp_server_create.restype = ct.c_int
+
+    def cfg(**kw):
+        base = dict(model_bytes=1 << 30, work_bytes=1 << 30, kind=0, precision=0, d_max=32, c_max=5,
+                    max_fit_batch=8, max_predict_batch=8, max_predict_rows=1 << 16, max_newton=5,
+                    max_iters=5, rank=50, graph=1, tol_abs=1e-5, tol_rel=1e-5)
+        base.update(kw)
+        return ServerConfig(**base)
+
+    h = ct.c_void_p()
+    for bad in (dict(model_bytes=0), dict(d_max=0), dict(c_max=1), dict(c_max=17), dict(kind=7),
+                dict(precision=9), dict(max_fit_batch=0), dict(max_predict_rows=100),
+                dict(max_iters=0), dict(tol_abs=-1.0),
+                dict(c_max=6)):   # 6 classes x 25 buffer columns > 128 variance weight rows
+        assert lib.itergp_server_create(ct.byref(cfg(**bad)), ct.byref(h)) == -1, bad
+        assert not h.value
+
+
+def test_tune_cache_round_trip(lib, tmp_path):
+    """The variant table's text cache loads, merges and saves without a GPU; malformed
+    lines are rejected."""
+    lib.itergp_tune_load.argtypes = [ct.c_char_p]
+    lib.itergp_tune_save.argtypes = [ct.c_char_p]
+    src = tmp_path / "in.txt"
+    src.write_text("# comment\n1 0 64 16 1 8 2\n3 1 832 80 0 4 0\n")
+    assert lib.itergp_tune_clear() == 0
+    assert lib.itergp_tune_load(str(src).encode()) == 0
+    out = tmp_path / "out.txt"
+    assert lib.itergp_tune_save(str(out).encode()) == 0
+    rows = [l for l in out.read_text().splitlines() if not l.startswith("#")]
+    assert sorted(rows) == sorted(["1 0 64 16 1 8 2", "3 1 832 80 0 4 0"])
+    bad = tmp_path / "bad.txt"
+    bad.write_text("1 0 64 16 1 6 2\n")          # 6 epilogue warps is not a variant
+    assert lib.itergp_tune_load(str(bad).encode()) == -1
+    assert lib.itergp_tune_clear() == 0

@@ -1,0 +1,149 @@
+"""Serving loop: fits and predicts over resident models with continuous batching
+(itergp_server_*).  Each served result is checked against the same request served alone,
+against the library's standalone fit + predict, and (on a sample) against the oracle."""
+import time
+
+import numpy as np
+import pytest
+import torch
+
+import oracle.itergp_oracle as O
+from paper_2310_20285_gb300 import datagen
+
+pytestmark = pytest.mark.gpu
+DEV = torch.device("cuda:0")
+SCHED = dict(max_newton=5, max_iters=5, rank=50, tol_abs=1e-5, tol_rel=1e-5)
+GB = 1 << 30
+
+
+def problems(count, seed, n_lo=300, n_hi=1500):
+    return datagen.batch_problems(count=count, seed=seed, n_lo=n_lo, n_hi=n_hi, dims=(8, 16),
+                                  c_lo=2, c_hi=5, ell_lo=0.8, ell_hi=3.0, n_test=300,
+                                  ell_per_sqrt_d=True)
+
+
+def rel(a, b, floor=1e-6):
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), floor * np.sqrt(b.size)))
+
+
+def drain(srv, want, timeout=120.0):
+    """Collect events until `want` request ids completed."""
+    got = {}
+    t_end = time.time() + timeout
+    while len(got) < want and time.time() < t_end:
+        for e in srv.poll(timeout_s=0.5):
+            got[e[0]] = e
+    assert len(got) == want, (len(got), want)
+    return got
+
+
+def serve(native, probs, prec, mix=True, **kw):
+    """Submit every fit, then a few predicts per model (some before their fit is done);
+    returns {problem index: (mean, var, probs)} and the events."""
+    srv = native.Server(model_bytes=kw.pop("model_bytes", 2 * GB), work_bytes=kw.pop("work_bytes", 4 * GB),
+                        precision=prec, d_max=16, c_max=5, **SCHED, **kw)
+    ids, reqs = [], []
+    for p in probs:
+        ids.append(srv.submit_fit(p.X, p.y, p.c, p.lengthscale, 1.0))
+        if mix:
+            reqs.append((len(ids) - 1, srv.submit_predict(ids[-1], p.Xs[:100])))
+    for i, p in enumerate(probs):
+        reqs.append((i, srv.submit_predict(ids[i], p.Xs)))
+    ev = drain(srv, len(ids) + len(reqs))
+    out = {}
+    for i, rid in reqs:
+        assert ev[rid][3] == native.OK, ev[rid]
+        r = srv.result(rid)
+        if r[0].shape[0] == probs[i].Xs.shape[0]:
+            out[i] = r
+    stats = srv.stats()
+    srv.close()
+    return out, ev, ids, reqs, stats
+
+
+@pytest.mark.parametrize("prec,tol", [("fp32", 1e-4), ("bf16x3", 1e-4)])
+def test_each_result_is_the_same_alone_and_in_the_mix(native, prec, tol):
+    probs = problems(6, seed=5)
+    mixed, ev, ids, reqs, stats = serve(native, probs, prec)
+    assert stats["fits_done"] == 6 and stats["predicts_done"] == 12
+    for i, p in enumerate(probs):
+        alone, *_ = serve(native, [p], prec, mix=False)
+        for a, b in zip(mixed[i], alone[0]):
+            assert rel(a, b) <= tol, (prec, i, rel(a, b))
+
+
+@pytest.mark.parametrize("prec,tol", [("fp32", 1e-4), ("bf16x3", 1e-4)])
+def test_served_results_match_the_standalone_api_and_the_oracle(native, prec, tol):
+    probs = problems(4, seed=8)
+    served, *_ = serve(native, probs, prec)
+    for i, p in enumerate(probs):
+        m = native.fit(torch.as_tensor(p.X, device=DEV), torch.as_tensor(p.y, device=DEV), p.c,
+                       kind="rbf", lengthscale=p.lengthscale, precision=prec, **SCHED)
+        mean, var, pr = m.predict(torch.as_tensor(p.Xs, device=DEV))
+        assert rel(served[i][0], mean.cpu()) <= tol
+        assert np.max(np.abs(served[i][1] - var.cpu().numpy())) <= 1e-3
+        assert np.max(np.abs(served[i][2] - pr.cpu().numpy())) <= 1e-3
+        m.free()
+    # the oracle, on the first problem (App. B.2 tolerances, 5 x 5, R = 50)
+    p = probs[0]
+    kern = O.Kernel(O.RBF, p.lengthscale, 1.0)
+    ref = O.iterncgp_fit(p.X.astype(np.float64), O.Softmax(p.y, p.c), p.c, kern, max_newton=5,
+                         max_iters=5, R=50, tol_abs=1e-5, tol_rel=1e-5)
+    em, ev_, ep = O.predict(p.Xs.astype(np.float64), p.X.astype(np.float64), ref.v, ref.Q, kern, p.c)
+    assert rel(served[0][0], em) <= tol
+    assert np.max(np.abs(served[0][1] - ev_)) <= 1e-3
+
+
+def test_predicts_wait_for_their_fit(native):
+    probs = problems(2, seed=3)
+    _, ev, ids, reqs, _ = serve(native, probs, "bf16x3")
+    for i, rid in reqs:
+        assert ev[rid][6] >= ev[ids[i]][6]          # done after the model's fit completed
+        assert ev[rid][5] >= ev[ids[i]][6] - 1e-6   # started after it too
+
+
+def test_lru_eviction_release_and_requests_that_cannot_fit(native):
+    probs = problems(6, seed=11, n_lo=1000, n_hi=1200)
+    # a slab of about 4 models' rows (bf16x3: 2 * 64 * 2 B rows + 4 B norm + 2 * 144 * 2 B weights)
+    per_row = 2 * 64 * 2 + 4 + 2 * 144 * 2
+    srv = native.Server(model_bytes=4 * 1280 * per_row + 4096, work_bytes=4 * GB, precision="bf16x3",
+                        d_max=16, c_max=5, max_fit_batch=1, **SCHED)
+    ids = []
+    for p in probs:
+        ids.append(srv.submit_fit(p.X, p.y, p.c, p.lengthscale, 1.0))
+        drain(srv, 1)
+    st = srv.stats()
+    assert st["evicted"] >= 2 and st["resident_models"] <= 4
+    with pytest.raises(native.ItergpError) as e:
+        srv.submit_predict(ids[0], probs[0].Xs)      # least recently used: evicted
+    assert e.value.code == native.EGONE
+    rid = srv.submit_predict(ids[-1], probs[-1].Xs)
+    assert drain(srv, 1)[rid][3] == native.OK
+    srv.release(ids[-1])
+    with pytest.raises(native.ItergpError) as e:
+        srv.submit_predict(ids[-1], probs[-1].Xs)
+    assert e.value.code == native.EGONE
+    # a model larger than the whole slab fails with ENOMEM
+    big = datagen.batch_problems(count=1, seed=2, n_lo=9000, n_hi=9001, dims=(8,), c_lo=3, c_hi=3)[0]
+    mid = srv.submit_fit(big.X, big.y, big.c, big.lengthscale, 1.0)
+    assert drain(srv, 1)[mid][3] == native.ENOMEM
+    srv.close()
+
+
+def test_a_bad_fit_fails_alone(native):
+    probs = problems(3, seed=13)
+    srv = native.Server(model_bytes=GB, work_bytes=4 * GB, precision="fp32", d_max=16, c_max=5, **SCHED)
+    y_bad = probs[1].y.copy()
+    y_bad[5] = probs[1].c + 2
+    ids = [srv.submit_fit(probs[0].X, probs[0].y, probs[0].c, probs[0].lengthscale),
+           srv.submit_fit(probs[1].X, y_bad, probs[1].c, probs[1].lengthscale),
+           srv.submit_fit(probs[2].X, probs[2].y, probs[2].c, probs[2].lengthscale)]
+    ev = drain(srv, 3)
+    assert [ev[i][3] for i in ids] == [native.OK, native.EINVAL, native.OK]
+    with pytest.raises(native.ItergpError):
+        srv.submit_predict(ids[1], probs[1].Xs)
+    rid = srv.submit_predict(ids[2], probs[2].Xs)
+    assert drain(srv, 1)[rid][3] == native.OK
+    srv.close()
