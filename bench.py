@@ -358,7 +358,7 @@ def main():
             tuning.append({"shape": label, "n": tn, "d": td, "p": tp, "precision": prec,
                            "schedule": "items" if items else "single",
                            "variants_ms": {f"{e}w/{st}st": round(ms, 4) for e, st, ms in vs},
-                           "chosen": f"{best[0]} epilogue warps, {best[1]} stages"})
+                           "chosen": f"{best[0]} epilogue warps, {best[1]} stages" if best else None})
 
     for _ in range(max(args.warmup, 3)):
         step()

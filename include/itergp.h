@@ -182,6 +182,8 @@ typedef struct {
   double tol_rel;         /* inner stop, relative to |y_hat - m| (default 1e-5)     */
   int32_t graph;          /* 1: capture the whole fit into one CUDA graph and launch
                              it (fewer launch overheads); 0: launch kernels directly */
+  const float* f0;        /* device, n x c starting iterate, or NULL for f_0 = m = 0
+                             (Alg. 1); with a start, Psi(f_0) is reported with v = 0  */
 } itergp_fit_params;
 
 #define ITERGP_MAX_REPORT_STEPS 64

@@ -354,17 +354,19 @@ class FitResult:
 def iterncgp_fit(X, lik, C: int, kern: Kernel, max_newton: int = 10, max_iters: int = 50,
                  R: int | None = None, policy: int = CG, tol_newton: float | None = None,
                  tol_abs: float = 1e-5, tol_rel: float = 1e-5, recycle: bool = True,
-                 project_contrasts: bool = False):
+                 project_contrasts: bool = False, f0=None):
     """Alg. 1: Newton's method as a sequence of GP regression problems, each solved by
     IterGP (Alg. 2) with recycled actions (Alg. 3).  Prior mean m = 0 (App. C.3),
     f_0 = m, empty buffers.  tol_newton=None runs exactly ``max_newton`` steps.
     project_contrasts=True removes the per-point class mean from y_hat - m and from every
     residual under the residual (CG) policy (the CUDA path's stabilisation; the identity
-    in exact arithmetic, where those vectors already lie in range(I kron P))."""
+    in exact arithmetic, where those vectors already lie in range(I kron P)).
+    f0 (N x C) replaces the starting iterate f_0 = m (used to start a step from a given
+    iterate); the objective of step 0 is then reported with v = 0 as for f_0 = m."""
     X = np.asarray(X, dtype=np.float64)
     N = X.shape[0]
     m = np.zeros((N, C))
-    f = m.copy()
+    f = m.copy() if f0 is None else np.array(f0, dtype=np.float64).reshape(N, C)
     S = np.zeros((N * C, 0))
     T = np.zeros((N * C, 0))
     v = np.zeros((N, C))

@@ -826,9 +826,12 @@ int kmv_tc_tune(DeviceContext* ctx, const KParams& kp, const RowOperand& X, cons
   int n = 0, rc = ITERGP_OK;
   *best = -1;
   for (int epi : {4, 8}) {
+    // the P tile the launchers use with this epilogue width: the widest that fits 2 stages
+    int p_tile = p16;
+    while (p_tile > 16 && stages_that_fit(ctx, nt1, nt2, p_tile, epi, 0) < 2) p_tile -= 16;
     for (int ns : {2, 3, 4}) {
       if (n >= cap) break;
-      if (stages_that_fit(ctx, nt1, nt2, std::min(p16, 128), epi, ns) != ns) continue;
+      if (stages_that_fit(ctx, nt1, nt2, p_tile, epi, ns) != ns) continue;
       const TcVariant v{epi, ns};
       t_forced = &v;
       auto run = [&] {

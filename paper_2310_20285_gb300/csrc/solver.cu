@@ -1137,7 +1137,11 @@ int fit_run_batch(DeviceContext* ctx, const std::vector<FitProblem>& probs, cuda
   init.newton_active = 1;
   for (int i = 0; i < np; ++i) {
     ITERGP_CUDA_TRY(cudaMemcpyAsync(pd[i].st, &init, sizeof(FitState), cudaMemcpyHostToDevice, stream));
-    ITERGP_CUDA_TRY(cudaMemsetAsync(pd[i].f, 0, sizeof(float) * pd[i].nc, stream));
+    if (probs[i].prm->f0)   // a given starting iterate (teacher forcing), else f_0 = m = 0
+      ITERGP_CUDA_TRY(cudaMemcpyAsync(pd[i].f, probs[i].prm->f0, sizeof(float) * pd[i].nc,
+                                      cudaMemcpyDeviceToDevice, stream));
+    else
+      ITERGP_CUDA_TRY(cudaMemsetAsync(pd[i].f, 0, sizeof(float) * pd[i].nc, stream));
     ITERGP_CUDA_TRY(cudaMemsetAsync(pd[i].v, 0, sizeof(float) * pd[i].nc, stream));
     ITERGP_CUDA_TRY(cudaMemsetAsync(pd[i].u, 0, sizeof(float) * pd[i].nc, stream));
     ITERGP_CUDA_TRY(cudaMemsetAsync(pd[i].gp, 0, sizeof(float) * pd[i].nc, stream));

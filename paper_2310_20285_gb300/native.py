@@ -42,7 +42,7 @@ class FitParams(ct.Structure):
                 ("max_newton", ct.c_int32), ("max_iters", ct.c_int32), ("rank", ct.c_int32),
                 ("recycle", ct.c_int32), ("literal_kv", ct.c_int32),
                 ("tol_newton", ct.c_double), ("tol_abs", ct.c_double), ("tol_rel", ct.c_double),
-                ("graph", ct.c_int32)]
+                ("graph", ct.c_int32), ("f0", ct.c_void_p)]
 
 
 class FitReport(ct.Structure):
@@ -322,7 +322,7 @@ class _CudaArray:
 
 
 def _params(X, y, c, kind, lengthscale, outputscale, precision, policy, max_newton, max_iters,
-            rank, recycle, literal_kv, tol_newton, tol_abs, tol_rel, graph) -> FitParams:
+            rank, recycle, literal_kv, tol_newton, tol_abs, tol_rel, graph, f0=None) -> FitParams:
     n, d = X.shape
     prm = FitParams()
     prm.n, prm.d, prm.c = n, d, int(c)
@@ -336,15 +336,20 @@ def _params(X, y, c, kind, lengthscale, outputscale, precision, policy, max_newt
     prm.recycle, prm.literal_kv = int(bool(recycle)), int(bool(literal_kv))
     prm.tol_newton, prm.tol_abs, prm.tol_rel = float(tol_newton), float(tol_abs), float(tol_rel)
     prm.graph = int(bool(graph))
+    if f0 is not None:
+        if tuple(f0.shape) != (n, int(c)):
+            raise ValueError("f0 must be n x c")
+        prm.f0 = _dev(f0, torch.float32, "f0").value
     return prm
 
 
 def fit(X, y, c, kind="rbf", lengthscale=1.0, outputscale=1.0, precision="fp32",
         policy="cg", max_newton=10, max_iters=50, rank=-1, recycle=True, literal_kv=False,
-        tol_newton=0.0, tol_abs=1e-5, tol_rel=1e-5, graph=False, stream=None) -> Model:
-    """IterNCGP fit (Alg. 1-3) of a softmax GP classifier on the GPU."""
+        tol_newton=0.0, tol_abs=1e-5, tol_rel=1e-5, graph=False, stream=None, f0=None) -> Model:
+    """IterNCGP fit (Alg. 1-3) of a softmax GP classifier on the GPU; f0 (n x c, device)
+    starts Newton's method at that iterate instead of m = 0."""
     prm = _params(X, y, c, kind, lengthscale, outputscale, precision, policy, max_newton,
-                  max_iters, rank, recycle, literal_kv, tol_newton, tol_abs, tol_rel, graph)
+                  max_iters, rank, recycle, literal_kv, tol_newton, tol_abs, tol_rel, graph, f0)
     h = ct.c_void_p()
     rep = FitReport()
     rc = lib.itergp_fit(ct.byref(prm), ct.byref(h), ct.byref(rep), _stream(stream))

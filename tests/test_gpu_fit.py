@@ -255,3 +255,24 @@ def test_full_size_fit_consistency_on_sampled_rows(native):
     assert (p.argmax(1) == ys[:2000]).mean() > 0.9
     assert np.all(var.cpu().numpy() <= 1.0 + 1e-5)
     m.free()
+
+
+@pytest.mark.parametrize("data", ["small", "kernel_bench2000"])
+def test_teacher_forced_newton_steps(native, data):
+    """Each Newton step started on the GPU (FP32) from the oracle's own iterate f_i lands
+    on the oracle's f_{i+1}: without recycling a step depends only on f_i (Alg. 1)."""
+    if data == "small":
+        X, y, _, _ = datagen.workload_small()
+        c, kern, kind, steps, iters = 3, O.Kernel(O.RBF, 1.0, 1.0), "rbf", 10, 12
+    else:
+        X, y, _, _, _ = datagen.workload_kernel_bench(n=2000, n_test=10)
+        c, kern, kind, steps, iters = 10, O.Kernel(O.MATERN32, 28.0, 1.0), "matern32", 5, 5
+    ref = oracle_fit(X, y, c, kern, max_newton=steps, max_iters=iters, recycle=False, tol_abs=0,
+                     tol_rel=0)
+    for i in range(steps):
+        m = native.fit(t32(X), torch.as_tensor(y, dtype=torch.int32, device=DEV), c, kind=kind,
+                       lengthscale=kern.lengthscale, max_newton=1, max_iters=iters, recycle=False,
+                       tol_abs=0.0, tol_rel=0.0, f0=t32(ref.fs[i]))
+        assert m.report.iters[0] == ref.infos[i].iters, (i, m.report.iters[0], ref.infos[i].iters)
+        assert rel(m.arrays()["f"].cpu(), ref.fs[i + 1]) <= 1e-4, (data, i, rel(m.arrays()["f"].cpu(), ref.fs[i + 1]))
+        m.free()

@@ -22,9 +22,10 @@ def force(native, tmp_path, prec, kind, d, p16, items, epi, stages):
 
 
 @pytest.mark.parametrize("prec", ["bf16x3", "bf16_comp", "bf16"])
-@pytest.mark.parametrize("items", [False, True])
-def test_autotune_times_every_variant(native, prec, items):
-    vs, best = native.autotune(4096, 32, 16, precision=prec, items=items)
+@pytest.mark.parametrize("items,p", [(False, 16), (True, 16), (True, 128), (False, 80)])
+def test_autotune_times_every_variant(native, prec, items, p):
+    """Includes widths where the launchers tile P (128 split weights do not fit 2 stages)."""
+    vs, best = native.autotune(4096, 32, p, precision=prec, items=items)
     assert len(vs) >= 4 and best in vs
     assert {v[0] for v in vs} == {4, 8}
     assert all(v[2] > 0 for v in vs)

@@ -479,3 +479,17 @@ def test_class_contrast_projection_is_the_identity_in_exact_arithmetic():
     for fa, fb in zip(a.fs, b.fs):
         assert np.allclose(fa, fb, rtol=1e-8, atol=1e-9)
     assert np.allclose(a.v.sum(axis=1), 0.0, atol=1e-8)
+
+
+def test_restart_from_an_iterate_reproduces_the_next_step():
+    """Without recycling a Newton step depends only on f_i (Alg. 1), so restarting the fit
+    at its own iterate f_i reproduces f_{i+1}; pins the starting-iterate option that the
+    teacher-forced GPU tests use."""
+    X, y, _, _ = datagen.workload_small(n_train=120, n_test=2)
+    kern = O.Kernel(O.RBF, 1.0, 1.0)
+    full = O.iterncgp_fit(X, O.Softmax(y, 3), 3, kern, max_newton=4, max_iters=8, recycle=False,
+                          tol_abs=0, tol_rel=0)
+    for i in range(3):
+        step = O.iterncgp_fit(X, O.Softmax(y, 3), 3, kern, max_newton=1, max_iters=8,
+                              recycle=False, tol_abs=0, tol_rel=0, f0=full.fs[i])
+        assert np.allclose(step.f, full.fs[i + 1], rtol=0, atol=1e-12 * np.abs(full.fs[i + 1]).max())
