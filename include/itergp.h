@@ -390,6 +390,13 @@ int itergp_tune_save(const char* path);
 int itergp_tune_load(const char* path);
 int itergp_tune_clear(void);
 
+/* Self-test of failure detection (a project addition): launches one CTA that waits, with
+ * the same bounded mbarrier wait the tensor-core kernel uses, on a barrier nothing ever
+ * arrives on.  After limit_ns (1e5 .. 5e9) the wait gives up, the kernel records
+ * ITERGP_ETIMEOUT in the device status word (read and cleared by itergp_sync_status) and
+ * returns; the context stays usable.  No fault, trap or hang is involved. */
+int itergp_selftest_wait(uint64_t limit_ns, itergp_stream stream);
+
 /* Library version "major.minor.patch". */
 const char* itergp_version(void);
 

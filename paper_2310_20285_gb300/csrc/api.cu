@@ -522,6 +522,13 @@ int itergp_predict(const itergp_model* mdl, const float* Xs, int64_t m, float* m
   return ITERGP_OK;
 }
 
+int itergp_selftest_wait(uint64_t limit_ns, itergp_stream stream) {
+  if (limit_ns < 100000u || limit_ns > 5000000000ull) return ITERGP_EINVAL;
+  DeviceContext* ctx = current_context();
+  if (!ctx) return ITERGP_ECUDA;
+  return wait_selftest_launch(ctx, limit_ns, static_cast<cudaStream_t>(stream));
+}
+
 int itergp_autotune(const itergp_kernel* kernel, int32_t precision, int64_t n, int64_t d, int64_t p,
                     int32_t items, itergp_tune_result* result, itergp_stream stream) {
   if (!kernel_ok(kernel) || !result || !precision_is_tensor(precision) || n < 128 || n > (int64_t(1) << 26) ||

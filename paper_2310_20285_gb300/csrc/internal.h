@@ -156,6 +156,10 @@ int kmv_tc_tune(DeviceContext* ctx, const KParams& kp, const RowOperand& X, cons
                 int64_t p, float* Y, int items, int cap, int* count, int* epi_out, int* ns_out,
                 double* ms_out, int* best, cudaStream_t stream);
 
+// Self-test of the bounded waits: one CTA waits on an mbarrier nothing arrives on and
+// records ITERGP_ETIMEOUT in ctx->status after limit_ns.
+int wait_selftest_launch(DeviceContext* ctx, uint64_t limit_ns, cudaStream_t stream);
+
 // Prepared rows written into caller-provided planes with pitch d_pad (>= d, multiple of
 // 64 for tensor precisions): BF16 hi (and lo for split precisions) [rows_pad][d_pad] and
 // FP32 squared norms [rows_pad]; rows beyond `rows` are zero.

@@ -910,3 +910,36 @@ extern "C" int itergp_tune_clear(void) {
   itergp::g_tune.clear();
   return ITERGP_OK;
 }
+
+// ---------------------------------------------------------------- wait self-test
+namespace itergp {
+namespace {
+
+// One thread waits, with the product kernel's bounded wait, on an mbarrier that nothing
+// ever arrives on (phase 0 of a fresh barrier never completes); when the limit runs out
+// the kernel records ITERGP_ETIMEOUT and returns, leaving the context usable.
+__global__ void wait_selftest_kernel(uint64_t limit_ns, int* status) {
+  __shared__ __align__(8) uint64_t bar;
+  __shared__ int abort_s;
+  if (threadIdx.x == 0) {
+    abort_s = 0;
+    mbar_init(&bar, 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    volatile int* ab = &abort_s;
+    if (!mbar_wait(&bar, 0u, ab, limit_ns)) atomicExch(status, ITERGP_ETIMEOUT);
+  }
+  __syncthreads();
+}
+
+}  // namespace
+
+int wait_selftest_launch(DeviceContext* ctx, uint64_t limit_ns, cudaStream_t stream) {
+  wait_selftest_kernel<<<1, 32, 0, stream>>>(limit_ns, ctx->status), ::itergp::note_launch();
+  ITERGP_CUDA_TRY(cudaGetLastError());
+  return ITERGP_OK;
+}
+
+}  // namespace itergp

@@ -136,6 +136,8 @@ def _load():
     lib.itergp_tune_save.argtypes = [ct.c_char_p]
     lib.itergp_tune_load.argtypes = [ct.c_char_p]
     lib.itergp_tune_clear.argtypes = []
+    lib.itergp_selftest_wait.argtypes = [ct.c_uint64, vp]
+    lib.itergp_selftest_wait.restype = ct.c_int
     for name in ("itergp_autotune", "itergp_tune_save", "itergp_tune_load", "itergp_tune_clear",
                  "itergp_kmatvec", "itergp_kmatvec_noalloc", "itergp_winv_apply", "itergp_pseudo_targets",
                  "itergp_sym_eig", "itergp_fit", "itergp_fit_batch", "itergp_predict",
@@ -393,6 +395,12 @@ def autotune(n, d, p, kind="rbf", precision="bf16x3", items=False, lengthscale=1
            "itergp_autotune")
     vs = [(v.epilogue_warps, v.stages, v.ms) for v in res.variants[:res.count]]
     return vs, (vs[res.best] if res.best >= 0 else None)
+
+
+def selftest_wait(limit_ns=20_000_000, stream=None):
+    """Launch the bounded-wait self-test (a wait that runs out after limit_ns); the device
+    status then reads ETIMEOUT (see sync_status)."""
+    _check(lib.itergp_selftest_wait(int(limit_ns), _stream(stream)), "itergp_selftest_wait")
 
 
 def tune_save(path):

@@ -257,10 +257,25 @@ def test_full_size_fit_consistency_on_sampled_rows(native):
     m.free()
 
 
+def fp32_step_tolerance(X, y, c, kern, f):
+    """1e-4, or the FP32 error of one Newton step where that is larger.  A product sums N
+    terms with rounding of about sqrt(N) u |K||s| (u = 2^-24) and the step solves with
+    K_hat = K + W^+, whose condition on range(I kron P) is at most
+    kappa = (lambda_max(k) + max 1/pi) / min 1/pi (Weyl; W_n^+ = P diag(1/pi_n) P has its
+    eigenvalues there between min and max 1/pi_n); the step's relative error is about
+    sqrt(N) u kappa, gated with a factor 4."""
+    lam = float(np.linalg.eigvalsh(O.kernel_matrix(X, X, kern))[-1])
+    ip = O.Softmax(y, c).inv_pi(np.asarray(f, dtype=np.float64))
+    kappa = (lam + ip.max()) / ip.min()
+    return max(1e-4, 4.0 * np.sqrt(X.shape[0]) * 2.0 ** -24 * kappa)
+
+
 @pytest.mark.parametrize("data", ["small", "kernel_bench2000"])
 def test_teacher_forced_newton_steps(native, data):
     """Each Newton step started on the GPU (FP32) from the oracle's own iterate f_i lands
-    on the oracle's f_{i+1}: without recycling a step depends only on f_i (Alg. 1)."""
+    on the oracle's f_{i+1}: without recycling a step depends only on f_i (Alg. 1).  The
+    784-D kernel-bench rows (l = sqrt(D): K ~ 0.88 11^T, kappa ~ 180 at step 0) exceed
+    1e-4 by the FP32 rounding of the products alone; they are gated at the derived bound."""
     if data == "small":
         X, y, _, _ = datagen.workload_small()
         c, kern, kind, steps, iters = 3, O.Kernel(O.RBF, 1.0, 1.0), "rbf", 10, 12
@@ -274,5 +289,7 @@ def test_teacher_forced_newton_steps(native, data):
                        lengthscale=kern.lengthscale, max_newton=1, max_iters=iters, recycle=False,
                        tol_abs=0.0, tol_rel=0.0, f0=t32(ref.fs[i]))
         assert m.report.iters[0] == ref.infos[i].iters, (i, m.report.iters[0], ref.infos[i].iters)
-        assert rel(m.arrays()["f"].cpu(), ref.fs[i + 1]) <= 1e-4, (data, i, rel(m.arrays()["f"].cpu(), ref.fs[i + 1]))
+        tol = fp32_step_tolerance(X.astype(np.float32).astype(np.float64), y, c, kern, ref.fs[i])
+        err = rel(m.arrays()["f"].cpu(), ref.fs[i + 1])
+        assert err <= tol, (data, i, err, tol)
         m.free()
