@@ -357,8 +357,10 @@ def main():
                                        lengthscale=ELL if kind == "matern32" else 1.0)
             tuning.append({"shape": label, "n": tn, "d": td, "p": tp, "precision": prec,
                            "schedule": "items" if items else "single",
-                           "variants_ms": {f"{e}w/{st}st": round(ms, 4) for e, st, ms in vs},
-                           "chosen": f"{best[0]} epilogue warps, {best[1]} stages" if best else None})
+                           "variants_ms": {f"{e}w/{abs(st)}st{'/residentA' if st < 0 else ''}": round(ms, 4)
+                                           for e, st, ms in vs},
+                           "chosen": (f"{best[0]} epilogue warps, {abs(best[1])} stages"
+                                      f"{', resident A' if best[1] < 0 else ''}") if best else None})
 
     for _ in range(max(args.warmup, 3)):
         step()

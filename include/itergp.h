@@ -364,17 +364,20 @@ int itergp_server_get_stats(itergp_server* server, itergp_server_stats* stats);
 /* ------------------------------------------------------------------------------------
  * Autotuning of the tensor-core product (a project addition; the paper has no such part).
  * A launch variant is the number of epilogue warps (4, or 8 with two warps per TMEM lane
- * quadrant splitting the columns) and the depth of the TMA stage ring (2-4).  The library
+ * quadrant splitting the columns), the depth of the TMA stage ring (2-4 stages of A and B
+ * tiles) and, where D fits one 64-wide slice, a resident-A ring (the row tile's A stays in
+ * shared memory; 3 or 5 stages of B tiles).  The library
  * keeps a process-wide table keyed by (precision, kernel kind, D padded to 64, P tile,
  * schedule); launches not in the table use 4 warps and the deepest ring that fits.
  *
  * itergp_autotune times every variant that fits on synthetic operands of the given shape
  * (n rows of dimension d, p weight columns; items = 0: the single-problem schedule of
  * itergp_kmatvec and fits, items = 1: the batched/served item schedule, p <= 128), records
- * the fastest in the table and reports all timings (ms per launch).  It waits for the
- * stream.  Tensor-core precisions only.
+ * the fastest in the table and reports all timings (ms per launch; stages < 0 mark the
+ * resident-A ring).  It waits for the stream.  Tensor-core precisions only.
  * itergp_tune_save / _load write / merge the table as text lines
- * "precision kind d_pad p_tile items epilogue_warps stages"; _clear empties it. */
+ * "precision kind d_pad p_tile items epilogue_warps stages resident_a" (resident_a: 1, 0,
+ * or -1 = where possible; a missing last column reads as -1); _clear empties it. */
 #define ITERGP_TUNE_MAX 6
 typedef struct {
   int32_t epilogue_warps, stages;

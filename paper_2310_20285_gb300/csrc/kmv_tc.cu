@@ -183,7 +183,9 @@ struct Walker {
   }
 };
 
-template <int KIND, int NT1, int NT2, int NSTAGE, int EPI>
+// ARES (D <= 64, one K slice): the A tile of a row segment stays resident in shared
+// memory for all of its chunks and only B streams through the ring.
+template <int KIND, int NT1, int NT2, int NSTAGE, int EPI, bool ARES>
 __global__ void __launch_bounds__(tc_threads(EPI), 1)
 kmv_tc_kernel(const __grid_constant__ CUtensorMap mAh, const __grid_constant__ CUtensorMap mAl,
               const __grid_constant__ CUtensorMap mBh, const __grid_constant__ CUtensorMap mBl,
@@ -200,15 +202,18 @@ kmv_tc_kernel(const __grid_constant__ CUtensorMap mAh, const __grid_constant__ C
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
                                              ~static_cast<uintptr_t>(1023));
-  constexpr uint32_t SB = stage_bytes(NT1);
   constexpr uint32_t A_PART = BM * BK * 2, B_PART = BN * BK * 2;
+  constexpr uint32_t A_BYTES = (NT1 == 3 ? 2u : 1u) * A_PART;   // resident A (ARES)
+  constexpr uint32_t SB = ARES ? (NT1 == 3 ? 2u : 1u) * B_PART : stage_bytes(NT1);
   const uint32_t SBOX = s_box_bytes(args.p_pad);
   const uint32_t SBUF = s_buf_bytes(NT2, args.p_pad);
-  uint8_t* s_region = smem + NSTAGE * SB;
+  uint8_t* a_region = smem + NSTAGE * SB;                        // ARES only
+  uint8_t* s_region = a_region + (ARES ? A_BYTES : 0u);
   float* nb_all = reinterpret_cast<float*>(s_region + 2 * SBUF);   // [EPI warps][128]
 
   __shared__ __align__(8) uint64_t full_bar[NSTAGE], empty_bar[NSTAGE];
   __shared__ __align__(8) uint64_t gfull[2], pfull[2], sfull[2], sempty[2], ofull, oempty, drain;
+  __shared__ __align__(8) uint64_t afull, aempty;               // resident A (ARES)
   __shared__ uint32_t tmem_base_s;
   __shared__ int abort_s;
 
@@ -228,6 +233,8 @@ kmv_tc_kernel(const __grid_constant__ CUtensorMap mAh, const __grid_constant__ C
     mbar_init(&ofull, 1);
     mbar_init(&oempty, 32 * EPI);
     mbar_init(&drain, 1);
+    mbar_init(&afull, 1);
+    mbar_init(&aempty, 1);
     fence_mbar_init();
   }
   if (warp == 2) {
@@ -250,12 +257,38 @@ kmv_tc_kernel(const __grid_constant__ CUtensorMap mAh, const __grid_constant__ C
       uint32_t phase = 0;
       uint32_t armed = 0, armed_par = 0;      // bit i: stage i armed / parity of last arm
       uint32_t s_armed = 0, s_par = 0;
+      bool a_armed = false;
+      uint32_t a_par = 0;
+      int64_t seg = -1;
       Walker wk = walk0;
       for (int64_t t = 0; t < T && !*ab; ++t, wk.next()) {
         const StepInfo st = wk.cur();
         const int32_t a_y = st.a_row;
         const int32_t b_y = st.b_row;
-        for (int ks = 0; ks < args.nk; ++ks) {
+        if (ARES) {
+          if (st.first) {
+            // a new row segment: reload A once the previous segment's MMAs are done with it
+            ++seg;
+            if (seg >= 1 && !mbar_wait(&aempty, static_cast<uint32_t>((seg - 1) & 1), ab, kWaitLimitNs)) break;
+            mbar_arrive_expect_tx(&afull, A_BYTES);
+            a_armed = true;
+            a_par = static_cast<uint32_t>(seg & 1);
+            tma_load_2d(a_region, &mAh, &afull, 0, a_y);
+            if (NT1 == 3) tma_load_2d(a_region + A_PART, &mAl, &afull, 0, a_y);
+          }
+          if (!mbar_wait(&empty_bar[stage], phase ^ 1u, ab, kWaitLimitNs)) break;
+          mbar_arrive_expect_tx(&full_bar[stage], SB);
+          armed |= 1u << stage;
+          armed_par = (armed_par & ~(1u << stage)) | (phase << stage);
+          uint8_t* bbase = smem + stage * SB;
+          tma_load_2d(bbase, &mBh, &full_bar[stage], 0, b_y);
+          if (NT1 == 3) tma_load_2d(bbase + B_PART, &mBl, &full_bar[stage], 0, b_y);
+          if (++stage == NSTAGE) {
+            stage = 0;
+            phase ^= 1u;
+          }
+        }
+        for (int ks = 0; !ARES && ks < args.nk; ++ks) {
           if (!mbar_wait(&empty_bar[stage], phase ^ 1u, ab, kWaitLimitNs)) break;
           mbar_arrive_expect_tx(&full_bar[stage], SB);
           armed |= 1u << stage;
@@ -291,6 +324,7 @@ kmv_tc_kernel(const __grid_constant__ CUtensorMap mAh, const __grid_constant__ C
           if (armed & (1u << i)) mbar_wait_drain(&full_bar[i], (armed_par >> i) & 1u, kWaitLimitNs);
         for (int i = 0; i < 2; ++i)
           if (s_armed & (1u << i)) mbar_wait_drain(&sfull[i], (s_par >> i) & 1u, kWaitLimitNs);
+        if (a_armed) mbar_wait_drain(&afull, a_par, kWaitLimitNs);
       }
     }
   } else if (warp == 1) {
@@ -338,9 +372,23 @@ kmv_tc_kernel(const __grid_constant__ CUtensorMap mAh, const __grid_constant__ C
         if (last) mma_commit(&ofull);
         return true;
       };
-      for (int64_t t = 0; t < T && ok; ++t) {
+      Walker wk1 = walk0;    // GEMM1 steps (segment boundaries for the resident A)
+      int64_t aseg = -1;
+      for (int64_t t = 0; t < T && ok; ++t, wk1.next()) {
         const int gb = static_cast<int>(t & 1);
         const uint32_t gt = tb + gb * BN;
+        bool seg_last = false;
+        if (ARES) {
+          const StepInfo st1 = wk1.cur();
+          seg_last = st1.last;
+          if (st1.first) {
+            ++aseg;
+            if (!mbar_wait(&afull, static_cast<uint32_t>(aseg & 1), ab, kWaitLimitNs)) {
+              ok = false;
+              break;
+            }
+          }
+        }
         for (int ks = 0; ks < args.nk; ++ks) {
           if (!mbar_wait(&full_bar[stage], phase, ab, kWaitLimitNs)) {
             ok = false;
@@ -348,15 +396,16 @@ kmv_tc_kernel(const __grid_constant__ CUtensorMap mAh, const __grid_constant__ C
           }
           tc_fence_after();
           const uint32_t base = smem_u32(smem + stage * SB);
-          const uint32_t bbase = base + (NT1 == 3 ? 2 : 1) * A_PART;
-          const uint64_t dAh = sdesc_kmajor_sw128(base);
+          const uint32_t abase = ARES ? smem_u32(a_region) : base;
+          const uint32_t bbase = ARES ? base : base + (NT1 == 3 ? 2 : 1) * A_PART;
+          const uint64_t dAh = sdesc_kmajor_sw128(abase);
           const uint64_t dBh = sdesc_kmajor_sw128(bbase);
 #pragma unroll
           for (int kk = 0; kk < BK / 16; ++kk) {
             const uint32_t acc = (ks | kk) != 0 ? 1u : 0u;
             mma_ss(gt, dAh + 2 * kk, dBh + 2 * kk, idesc1, acc);
             if (NT1 == 3) {
-              const uint64_t dAl = sdesc_kmajor_sw128(base + A_PART);
+              const uint64_t dAl = sdesc_kmajor_sw128(abase + A_PART);
               const uint64_t dBl = sdesc_kmajor_sw128(bbase + B_PART);
               mma_ss(gt, dAh + 2 * kk, dBl + 2 * kk, idesc1, 1u);
               mma_ss(gt, dAl + 2 * kk, dBh + 2 * kk, idesc1, 1u);
@@ -369,6 +418,7 @@ kmv_tc_kernel(const __grid_constant__ CUtensorMap mAh, const __grid_constant__ C
           }
         }
         if (!ok) break;
+        if (ARES && seg_last) mma_commit(&aempty);   // the segment's A is no longer read
         mma_commit(&gfull[gb]);
         if (t >= 1 && !gemm2(t - 1)) ok = false;
       }
@@ -561,10 +611,10 @@ __global__ void prep_s_kernel(const float* __restrict__ S, int64_t ldS, int64_t 
   }
 }
 
-template <int KIND, int NT1, int NT2, int NSTAGE, int EPI>
+template <int KIND, int NT1, int NT2, int NSTAGE, int EPI, bool ARES>
 cudaError_t launch_tc(int grid, size_t smem, cudaStream_t st, const CUtensorMap* maps,
                       const TcArgs& a) {
-  auto fn = kmv_tc_kernel<KIND, NT1, NT2, NSTAGE, EPI>;
+  auto fn = kmv_tc_kernel<KIND, NT1, NT2, NSTAGE, EPI, ARES>;
   cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   timing_begin(st);
@@ -573,31 +623,35 @@ cudaError_t launch_tc(int grid, size_t smem, cudaStream_t st, const CUtensorMap*
   return cudaGetLastError();
 }
 
+// Instantiated rings: streamed A+B 2, 3, 4 stages; resident A (B-only stages) 3, 5.
 template <int KIND, int NT1, int NT2, int EPI>
-cudaError_t launch_stages(int nstage, int grid, size_t smem, cudaStream_t st,
+cudaError_t launch_stages(int nstage, bool ares, int grid, size_t smem, cudaStream_t st,
                           const CUtensorMap* maps, const TcArgs& a) {
+  if (ares)
+    return nstage == 5 ? launch_tc<KIND, NT1, NT2, 5, EPI, true>(grid, smem, st, maps, a)
+                       : launch_tc<KIND, NT1, NT2, 3, EPI, true>(grid, smem, st, maps, a);
   switch (nstage) {
-    case 2: return launch_tc<KIND, NT1, NT2, 2, EPI>(grid, smem, st, maps, a);
-    case 3: return launch_tc<KIND, NT1, NT2, 3, EPI>(grid, smem, st, maps, a);
-    default: return launch_tc<KIND, NT1, NT2, 4, EPI>(grid, smem, st, maps, a);
+    case 2: return launch_tc<KIND, NT1, NT2, 2, EPI, false>(grid, smem, st, maps, a);
+    case 3: return launch_tc<KIND, NT1, NT2, 3, EPI, false>(grid, smem, st, maps, a);
+    default: return launch_tc<KIND, NT1, NT2, 4, EPI, false>(grid, smem, st, maps, a);
   }
 }
 
 template <int KIND, int EPI>
-cudaError_t launch_prec_epi(int prec, int nstage, int grid, size_t smem, cudaStream_t st,
+cudaError_t launch_prec_epi(int prec, int nstage, bool ares, int grid, size_t smem, cudaStream_t st,
                             const CUtensorMap* maps, const TcArgs& a) {
   switch (prec) {
-    case ITERGP_BF16X3: return launch_stages<KIND, 3, 3, EPI>(nstage, grid, smem, st, maps, a);
-    case ITERGP_BF16_COMP: return launch_stages<KIND, 3, 1, EPI>(nstage, grid, smem, st, maps, a);
-    default: return launch_stages<KIND, 1, 1, EPI>(nstage, grid, smem, st, maps, a);
+    case ITERGP_BF16X3: return launch_stages<KIND, 3, 3, EPI>(nstage, ares, grid, smem, st, maps, a);
+    case ITERGP_BF16_COMP: return launch_stages<KIND, 3, 1, EPI>(nstage, ares, grid, smem, st, maps, a);
+    default: return launch_stages<KIND, 1, 1, EPI>(nstage, ares, grid, smem, st, maps, a);
   }
 }
 
 template <int KIND>
-cudaError_t launch_prec(int prec, int nstage, int epi, int grid, size_t smem, cudaStream_t st,
-                        const CUtensorMap* maps, const TcArgs& a) {
-  return epi == 8 ? launch_prec_epi<KIND, 8>(prec, nstage, grid, smem, st, maps, a)
-                  : launch_prec_epi<KIND, 4>(prec, nstage, grid, smem, st, maps, a);
+cudaError_t launch_prec(int prec, int nstage, bool ares, int epi, int grid, size_t smem,
+                        cudaStream_t st, const CUtensorMap* maps, const TcArgs& a) {
+  return epi == 8 ? launch_prec_epi<KIND, 8>(prec, nstage, ares, grid, smem, st, maps, a)
+                  : launch_prec_epi<KIND, 4>(prec, nstage, ares, grid, smem, st, maps, a);
 }
 
 // ---------------------------------------------------------------- launch variants
@@ -607,6 +661,7 @@ cudaError_t launch_prec(int prec, int nstage, int epi, int grid, size_t smem, cu
 struct TcVariant {
   int epi = 4;
   int nstage = 0;
+  int ares = -1;   // resident A (one K slice only): 1 on, 0 off, -1 on where possible
 };
 
 std::mutex g_tune_mu;
@@ -620,14 +675,24 @@ TcVariant tc_variant(int prec, int kind, int d_pad, int p_pad, int items) {
   return it == g_tune.end() ? TcVariant{} : it->second;
 }
 
-// Deepest stage count (<= want, 0 = no limit) that fits with P tile p_tile; 0 if < 2.
-int stages_that_fit(const DeviceContext* ctx, int nt1, int nt2, int p_tile, int epi, int want) {
+// Deepest instantiated stage count (<= want, 0 = no limit) that fits with P tile p_tile;
+// 0 if none.  Streamed rings: 2, 3, 4 stages of A+B; resident A: 3 or 5 B-only stages.
+int stages_that_fit(const DeviceContext* ctx, int nt1, int nt2, int p_tile, int epi, int want,
+                    bool ares = false) {
   const size_t smem_cap = std::min<size_t>(ctx->smem_optin, 232448) - 2048;
-  const size_t fixed = 2 * s_buf_bytes(nt2, p_tile) + smem_extra(epi);
-  const int fit = static_cast<int>((smem_cap > fixed ? smem_cap - fixed : 0) / stage_bytes(nt1));
-  int ns = fit >= 4 ? 4 : fit >= 3 ? 3 : fit >= 2 ? 2 : 0;
-  if (want >= 2 && ns > want) ns = want;
+  const size_t a_bytes = ares ? static_cast<size_t>(nt1 == 3 ? 2 : 1) * BM * BK * 2 : 0;
+  const size_t stage = ares ? static_cast<size_t>(nt1 == 3 ? 2 : 1) * BN * BK * 2 : stage_bytes(nt1);
+  const size_t fixed = 2 * s_buf_bytes(nt2, p_tile) + smem_extra(epi) + a_bytes;
+  const int fit = static_cast<int>((smem_cap > fixed ? smem_cap - fixed : 0) / stage);
+  int ns = ares ? (fit >= 5 ? 5 : fit >= 3 ? 3 : 0) : (fit >= 4 ? 4 : fit >= 3 ? 3 : fit >= 2 ? 2 : 0);
+  if (want >= 2 && ns > want) ns = ares ? (want >= 5 ? 5 : want >= 3 ? 3 : 0) : want;
   return ns;
+}
+
+size_t tc_smem_bytes(int nt1, int nt2, int p_pad, int epi, int nstage, bool ares) {
+  const size_t a_bytes = ares ? static_cast<size_t>(nt1 == 3 ? 2 : 1) * BM * BK * 2 : 0;
+  const size_t stage = ares ? static_cast<size_t>(nt1 == 3 ? 2 : 1) * BN * BK * 2 : stage_bytes(nt1);
+  return nstage * stage + a_bytes + 2 * s_buf_bytes(nt2, p_pad) + smem_extra(epi);
 }
 
 }  // namespace
@@ -643,8 +708,14 @@ int kmv_tc_items(DeviceContext* ctx, int kind, const RowOperand& A, const RowOpe
     return ITERGP_EINVAL;
   // P tile: the widest multiple of 16 (<= p16) that leaves room for >= 2 stages
   const TcVariant var = tc_variant(prec, kind, B.d_pad, p16, 1);
+  const bool can_ares = B.d_pad == BK && var.ares != 0;   // one K slice: A can stay resident
   int p_tile = p16, nstage = 0;
+  bool ares = false;
   for (; p_tile >= 16; p_tile -= 16) {
+    if (can_ares && (nstage = stages_that_fit(ctx, nt1, nt2, p_tile, var.epi, var.nstage, true)) >= 3) {
+      ares = true;
+      break;
+    }
     nstage = stages_that_fit(ctx, nt1, nt2, p_tile, var.epi, var.nstage);
     if (nstage >= 2) break;
   }
@@ -674,10 +745,10 @@ int kmv_tc_items(DeviceContext* ctx, int kind, const RowOperand& A, const RowOpe
     a.item_begin = tab.item_begin;
     a.probs = tab.probs;
     a.kp = make_kparams(itergp_kernel{kind, 1.f, 1.f});   // per-item values come from the table
-    const size_t smem = nstage * stage_bytes(nt1) + 2 * s_buf_bytes(nt2, pp) + smem_extra(var.epi);
+    const size_t smem = tc_smem_bytes(nt1, nt2, pp, var.epi, nstage, ares);
     cudaError_t e = kind == ITERGP_RBF
-                        ? launch_prec<ITERGP_RBF>(prec, nstage, var.epi, tab.G, smem, stream, maps, a)
-                        : launch_prec<ITERGP_MATERN32>(prec, nstage, var.epi, tab.G, smem, stream, maps, a);
+                        ? launch_prec<ITERGP_RBF>(prec, nstage, ares, var.epi, tab.G, smem, stream, maps, a)
+                        : launch_prec<ITERGP_MATERN32>(prec, nstage, ares, var.epi, tab.G, smem, stream, maps, a);
     ITERGP_CUDA_TRY(e);
   }
   return ITERGP_OK;
@@ -696,9 +767,15 @@ int kmv_tc(DeviceContext* ctx, const KParams& kp, const RowOperand& A, const Row
   // slices measured slower.)
   const int64_t p16 = (p + 15) / 16 * 16;
   const TcVariant var = tc_variant(prec, kp.kind, A.d_pad, static_cast<int>(std::min<int64_t>(p16, 128)), 0);
+  const bool can_ares = A.d_pad == BK && var.ares != 0;   // one K slice: A can stay resident
   int p_tile = static_cast<int>(std::min<int64_t>(p16, 128));
   int nstage = 0;
+  bool ares = false;
   for (; p_tile >= 16; p_tile -= 16) {
+    if (can_ares && (nstage = stages_that_fit(ctx, nt1, nt2, p_tile, var.epi, var.nstage, true)) >= 3) {
+      ares = true;
+      break;
+    }
     nstage = stages_that_fit(ctx, nt1, nt2, p_tile, var.epi, var.nstage);
     if (nstage >= 2) break;
   }
@@ -760,10 +837,10 @@ int kmv_tc(DeviceContext* ctx, const KParams& kp, const RowOperand& A, const Row
     a.items = nullptr;
     a.item_begin = nullptr;
     a.probs = nullptr;
-    const size_t smem_t = nstage * stage_bytes(nt1) + 2 * s_buf_bytes(nt2, pp) + smem_extra(var.epi);
+    const size_t smem_t = tc_smem_bytes(nt1, nt2, pp, var.epi, nstage, ares);
     cudaError_t e = kp.kind == ITERGP_RBF
-                        ? launch_prec<ITERGP_RBF>(prec, nstage, var.epi, (int)G, smem_t, stream, maps, a)
-                        : launch_prec<ITERGP_MATERN32>(prec, nstage, var.epi, (int)G, smem_t, stream, maps, a);
+                        ? launch_prec<ITERGP_RBF>(prec, nstage, ares, var.epi, (int)G, smem_t, stream, maps, a)
+                        : launch_prec<ITERGP_MATERN32>(prec, nstage, ares, var.epi, (int)G, smem_t, stream, maps, a);
     ITERGP_CUDA_TRY(e);
     if (tail_rows > 0) {
       tc_fixup_kernel<<<static_cast<unsigned>(tail_rows), 256, 0, stream>>>(
@@ -825,14 +902,16 @@ int kmv_tc_tune(DeviceContext* ctx, const KParams& kp, const RowOperand& X, cons
   ITERGP_CUDA_TRY(cudaEventCreate(&e1));
   int n = 0, rc = ITERGP_OK;
   *best = -1;
-  for (int epi : {4, 8}) {
-    // the P tile the launchers use with this epilogue width: the widest that fits 2 stages
+  for (int ares : {0, 1}) for (int epi : {4, 8}) {
+    if (ares && X.d_pad != BK) continue;
+    // the P tile the launchers use with this variant: the widest that fits its ring
     int p_tile = p16;
-    while (p_tile > 16 && stages_that_fit(ctx, nt1, nt2, p_tile, epi, 0) < 2) p_tile -= 16;
-    for (int ns : {2, 3, 4}) {
+    const int min_ns = ares ? 3 : 2;
+    while (p_tile > 16 && stages_that_fit(ctx, nt1, nt2, p_tile, epi, 0, ares != 0) < min_ns) p_tile -= 16;
+    for (int ns : {2, 3, 4, 5}) {
       if (n >= cap) break;
-      if (stages_that_fit(ctx, nt1, nt2, p_tile, epi, ns) != ns) continue;
-      const TcVariant v{epi, ns};
+      if (stages_that_fit(ctx, nt1, nt2, p_tile, epi, ns, ares != 0) != ns) continue;
+      const TcVariant v{epi, ns, ares};
       t_forced = &v;
       auto run = [&] {
         return items ? kmv_tc_items(ctx, kp.kind, X, X, tab, s_hi, s_lo, p16, 0, p16, stream)
@@ -850,7 +929,7 @@ int kmv_tc_tune(DeviceContext* ctx, const KParams& kp, const RowOperand& X, cons
       t_forced = nullptr;
       if (rc != ITERGP_OK) break;
       epi_out[n] = epi;
-      ns_out[n] = ns;
+      ns_out[n] = ares ? -ns : ns;   // negative: resident-A ring
       ms_out[n] = ms / reps;
       if (*best < 0 || ms_out[n] < ms_out[*best]) *best = n;
       ++n;
@@ -863,7 +942,9 @@ int kmv_tc_tune(DeviceContext* ctx, const KParams& kp, const RowOperand& X, cons
   if (rc != ITERGP_OK) return rc;
   if (*best >= 0) {
     std::lock_guard<std::mutex> lk(g_tune_mu);
-    g_tune[std::make_tuple(prec, kp.kind, X.d_pad, p16, items ? 1 : 0)] = TcVariant{epi_out[*best], ns_out[*best]};
+    const int bns = ns_out[*best];
+    g_tune[std::make_tuple(prec, kp.kind, X.d_pad, p16, items ? 1 : 0)] =
+        TcVariant{epi_out[*best], bns < 0 ? -bns : bns, bns < 0 ? 1 : 0};
   }
   return ITERGP_OK;
 }
@@ -875,11 +956,11 @@ extern "C" int itergp_tune_save(const char* path) {
   FILE* f = std::fopen(path, "w");
   if (!f) return ITERGP_EINVAL;
   std::lock_guard<std::mutex> lk(itergp::g_tune_mu);
-  std::fprintf(f, "# precision kind d_pad p_tile items epilogue_warps stages\n");
+  std::fprintf(f, "# precision kind d_pad p_tile items epilogue_warps stages resident_a\n");
   for (const auto& kv : itergp::g_tune)
-    std::fprintf(f, "%d %d %d %d %d %d %d\n", std::get<0>(kv.first), std::get<1>(kv.first),
+    std::fprintf(f, "%d %d %d %d %d %d %d %d\n", std::get<0>(kv.first), std::get<1>(kv.first),
                  std::get<2>(kv.first), std::get<3>(kv.first), std::get<4>(kv.first), kv.second.epi,
-                 kv.second.nstage);
+                 kv.second.nstage, kv.second.ares);
   std::fclose(f);
   return ITERGP_OK;
 }
@@ -893,13 +974,15 @@ extern "C" int itergp_tune_load(const char* path) {
   std::lock_guard<std::mutex> lk(itergp::g_tune_mu);
   while (std::fgets(line, sizeof(line), f)) {
     if (line[0] == '#') continue;
-    int a[7];
-    if (std::sscanf(line, "%d %d %d %d %d %d %d", &a[0], &a[1], &a[2], &a[3], &a[4], &a[5], &a[6]) != 7 ||
-        (a[5] != 4 && a[5] != 8) || a[6] < 0 || a[6] > 4) {
+    int a[8];
+    a[7] = -1;   // resident A: automatic when the column is absent
+    const int got = std::sscanf(line, "%d %d %d %d %d %d %d %d", &a[0], &a[1], &a[2], &a[3], &a[4],
+                                &a[5], &a[6], &a[7]);
+    if (got < 7 || (a[5] != 4 && a[5] != 8) || a[6] < 0 || a[6] > 5 || a[7] < -1 || a[7] > 1) {
       rc = ITERGP_EINVAL;
       continue;
     }
-    itergp::g_tune[std::make_tuple(a[0], a[1], a[2], a[3], a[4])] = itergp::TcVariant{a[5], a[6]};
+    itergp::g_tune[std::make_tuple(a[0], a[1], a[2], a[3], a[4])] = itergp::TcVariant{a[5], a[6], a[7]};
   }
   std::fclose(f);
   return rc;

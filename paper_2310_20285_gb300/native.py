@@ -393,7 +393,7 @@ def autotune(n, d, p, kind="rbf", precision="bf16x3", items=False, lengthscale=1
     _check(lib.itergp_autotune(ct.byref(_kernel(kind, lengthscale, 1.0)), _prec(precision), int(n), int(d),
                                int(p), 1 if items else 0, ct.byref(res), _stream(stream)),
            "itergp_autotune")
-    vs = [(v.epilogue_warps, v.stages, v.ms) for v in res.variants[:res.count]]
+    vs = [(v.epilogue_warps, v.stages, v.ms) for v in res.variants[:res.count]]   # stages < 0: resident A
     return vs, (vs[res.best] if res.best >= 0 else None)
 
 

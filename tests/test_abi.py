@@ -145,13 +145,13 @@ def test_tune_cache_round_trip(lib, tmp_path):
     lib.itergp_tune_load.argtypes = [ct.c_char_p]
     lib.itergp_tune_save.argtypes = [ct.c_char_p]
     src = tmp_path / "in.txt"
-    src.write_text("# comment\n1 0 64 16 1 8 2\n3 1 832 80 0 4 0\n")
+    src.write_text("# comment\n1 0 64 16 1 8 2\n3 1 832 80 0 4 0 0\n2 0 64 16 1 4 5 1\n")
     assert lib.itergp_tune_clear() == 0
     assert lib.itergp_tune_load(str(src).encode()) == 0
     out = tmp_path / "out.txt"
     assert lib.itergp_tune_save(str(out).encode()) == 0
     rows = [l for l in out.read_text().splitlines() if not l.startswith("#")]
-    assert sorted(rows) == sorted(["1 0 64 16 1 8 2", "3 1 832 80 0 4 0"])
+    assert sorted(rows) == sorted(["1 0 64 16 1 8 2 -1", "3 1 832 80 0 4 0 0", "2 0 64 16 1 4 5 1"])
     bad = tmp_path / "bad.txt"
     bad.write_text("1 0 64 16 1 6 2\n")          # 6 epilogue warps is not a variant
     assert lib.itergp_tune_load(str(bad).encode()) == -1

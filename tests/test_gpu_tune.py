@@ -12,11 +12,12 @@ DEV = torch.device("cuda:0")
 PREC_CODE = {"bf16x3": 1, "bf16": 2, "bf16_comp": 3}
 
 
-def force(native, tmp_path, prec, kind, d, p16, items, epi, stages):
-    """Install one table entry through the text cache."""
+def force(native, tmp_path, prec, kind, d, p16, items, epi, stages, ares=-1):
+    """Install one table entry through the text cache (ares: resident-A ring, one K slice
+    only; -1 automatic)."""
     path = tmp_path / "tune.txt"
     d_pad = (d + 63) // 64 * 64
-    path.write_text(f"{PREC_CODE[prec]} {kind} {d_pad} {p16} {items} {epi} {stages}\n")
+    path.write_text(f"{PREC_CODE[prec]} {kind} {d_pad} {p16} {items} {epi} {stages} {ares}\n")
     native.tune_clear()
     native.tune_load(path)
 
@@ -33,28 +34,30 @@ def test_autotune_times_every_variant(native, prec, items, p):
 
 
 @pytest.mark.parametrize("prec", ["bf16x3", "bf16"])
-@pytest.mark.parametrize("epi,stages", [(8, 2), (8, 4), (4, 3)])
-def test_variants_compute_the_same_product(native, tmp_path, prec, epi, stages):
+@pytest.mark.parametrize("epi,stages,ares", [(8, 2, 0), (8, 4, 0), (4, 3, 0), (4, 3, 1), (8, 5, 1)])
+def test_variants_compute_the_same_product(native, tmp_path, prec, epi, stages, ares):
+    """D = 40 (one 64-wide K slice), so both the streamed and the resident-A rings apply;
+    the reference is the streamed 4-warp ring."""
     X = torch.as_tensor(datagen.normal((3000, 40), 3), device=DEV)
     S = torch.as_tensor(datagen.normal((3000, 24), 4), device=DEV)
-    native.tune_clear()
+    force(native, tmp_path, prec, 1, 40, 32, 0, 4, 2, 0)
     ref = native.kmatvec(X, X, S, kind="matern32", lengthscale=3.0, precision=prec).clone()
-    force(native, tmp_path, prec, 1, 40, 32, 0, epi, stages)
+    force(native, tmp_path, prec, 1, 40, 32, 0, epi, stages, ares)
     got = native.kmatvec(X, X, S, kind="matern32", lengthscale=3.0, precision=prec)
     native.tune_clear()
     assert torch.equal(got, ref)
 
 
-@pytest.mark.parametrize("epi,stages", [(8, 2), (8, 3)])
-def test_variants_give_the_same_batched_fit(native, tmp_path, epi, stages):
+@pytest.mark.parametrize("epi,stages,ares", [(8, 2, 0), (8, 3, 0), (4, 5, 1), (8, 3, 1)])
+def test_variants_give_the_same_batched_fit(native, tmp_path, epi, stages, ares):
     probs = datagen.batch_problems(count=5, seed=17, n_lo=200, n_hi=1500, dims=(8, 16), c_lo=2,
                                    c_hi=7, ell_lo=0.8, ell_hi=3.0, n_test=16, ell_per_sqrt_d=True)
     dev = [(torch.as_tensor(p.X, device=DEV), torch.as_tensor(p.y, device=DEV), p.c, p.lengthscale, 1.0)
            for p in probs]
     sched = dict(max_newton=3, max_iters=6, rank=10, tol_abs=0.0, tol_rel=0.0)
-    native.tune_clear()
+    force(native, tmp_path, "bf16x3", 0, 16, 16, 1, 4, 2, 0)
     ref = native.fit_batch(dev, precision="bf16x3", **sched)
-    force(native, tmp_path, "bf16x3", 0, 16, 16, 1, epi, stages)
+    force(native, tmp_path, "bf16x3", 0, 16, 16, 1, epi, stages, ares)
     got = native.fit_batch(dev, precision="bf16x3", **sched)
     native.tune_clear()
     for a, b in zip(got, ref):
