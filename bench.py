@@ -221,6 +221,62 @@ def bench_batched(native, datagen, torch, dev, count):
     return res
 
 
+def calibration_metrics(probs, y, n_bins=15):
+    """Accuracy, NLL (negative mean log-probability of the true class) and expected
+    calibration error of the top-class confidence over n_bins equal-width bins."""
+    import numpy as np
+    probs = np.asarray(probs, dtype=np.float64)
+    pred = probs.argmax(1)
+    conf = probs.max(1)
+    correct = (pred == y).astype(np.float64)
+    nll = float(-np.mean(np.log(np.maximum(probs[np.arange(len(y)), y], 1e-300))))
+    edges = np.linspace(0.0, 1.0, n_bins + 1)
+    ece = 0.0
+    for lo, hi in zip(edges[:-1], edges[1:]):
+        m = (conf > lo) & (conf <= hi)
+        if m.any():
+            ece += m.mean() * abs(correct[m].mean() - conf[m].mean())
+    return float(correct.mean()), nll, float(ece)
+
+
+def bench_gmm(native, datagen, torch, dev):
+    """The paper's large-scale synthetic problem (App. C.3): 10 classes of 3-D Gaussians,
+    10^4 training points per class (N = 10^5), 10^3 test points per class, Matern-3/2
+    l = 0.05, s = 0.05, CG actions with recycling, j <= 5, R = infinity and R = 10.  Each
+    row is a fit stopped after k Newton steps (timed), then test accuracy, NLL and ECE
+    (15 bins) of the probit predictive, computed outside the timed region."""
+    import numpy as np
+    X, y = datagen.gmm3d(10000, seed_model=1, seed_draw=2)
+    Xs, ys = datagen.gmm3d(1000, seed_model=1, seed_draw=3)
+    tX = torch.as_tensor(X.astype(np.float32), device=dev)
+    ty = torch.as_tensor(y, device=dev)
+    tXs = torch.as_tensor(Xs.astype(np.float32), device=dev)
+    out = {"workload": "GMM, C=10, D=3, N=1e5 train / 1e4 test, Matern-3/2 l=0.05 s=0.05, "
+                       "CG actions, recycling, j<=5; fits stopped after k Newton steps",
+           "runs": []}
+    for prec, rank in (("bf16x3", None), ("bf16x3", 10), ("fp32", 10)):
+        rows = []
+        for k in (1, 2, 3, 5, 8):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            try:
+                m = native.fit(tX, ty, 10, kind="matern32", lengthscale=0.05, outputscale=0.05,
+                               precision=prec, max_newton=k, max_iters=5, rank=rank)
+            except native.ItergpError as e:
+                rows.append({"newton_steps": k, "error": str(e)})
+                break
+            torch.cuda.synchronize()
+            dt = time.perf_counter() - t0
+            _, _, probs = m.predict(tXs)
+            acc, nll, ece = calibration_metrics(probs.cpu().numpy(), ys)
+            rows.append({"newton_steps": k, "fit_s": round(dt, 4), "test_acc": round(acc, 4),
+                         "test_nll": round(nll, 4), "test_ece": round(ece, 4),
+                         "iters": int(m.report.total_iters)})
+            m.free()
+        out["runs"].append({"precision": prec, "R": "inf" if rank is None else rank, "by_steps": rows})
+    return out
+
+
 def bench_serving(native, datagen, precision, seconds, seed=5, drain_s=10.0):
     """Serving: Poisson arrivals over `seconds` of fit requests at 50/s (N log-uniform in
     [1e3, 5e4], D = 32, C = 5 blobs, RBF l log-uniform in [0.3, 3]; 5 Newton x <= 5
@@ -350,8 +406,7 @@ def main():
         shapes = [("kernel bench", 60000, D, P, "matern32", args.precision, False)]
         if rank == 0 and not args.no_extras:
             shapes += [("batched fits", 8192, 64, 16, "rbf", pr, True) for pr in ("bf16x3", "bf16_comp")]
-            shapes += [("served mean", 16384, 32, 16, "rbf", "bf16x3", True),
-                       ("served variance", 16384, 32, 128, "rbf", "bf16x3", True)]
+            shapes += [("served mean + variance", 16384, 32, 128, "rbf", "bf16x3", True)]
         for label, tn, td, tp, kind, prec, items in shapes:
             vs, best = native.autotune(tn, td, tp, kind=kind, precision=prec, items=items,
                                        lengthscale=ELL if kind == "matern32" else 1.0)
@@ -499,6 +554,8 @@ def main():
                       **fits}
     if rank == 0 and not args.no_extras:
         out["batched"] = bench_batched(native, datagen, torch, dev, args.batch_count)
+    if rank == 0 and not args.no_extras:
+        out["gmm_large"] = bench_gmm(native, datagen, torch, dev)
     if rank == 0 and not args.no_extras and args.serve_seconds > 0:
         out["serving"] = {
             "workload": f"{args.serve_seconds:g} s of Poisson arrivals: fits 50/s (N log-U[1e3,5e4], D=32, C=5, "

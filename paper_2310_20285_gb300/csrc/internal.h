@@ -97,8 +97,9 @@ struct KmvItemTables {
 
 // Tensor-core product in item mode: item rows a_row of A (query side) against the rows
 // b_row0 .. of B (problem side, both prepared with the same precision and d_pad).
-// s_hi/s_lo: transposed split weights [s_rows][B.rows_pad]; this launch reads weight rows
-// [s_row0, s_row0 + p_pad) (p_pad a multiple of 16, <= 128).  All problems share `kind`.
+// s_hi/s_lo: transposed split weights [s_rows][B.rows_pad]; this call reads weight rows
+// [s_row0, s_row0 + p_pad) (p_pad a multiple of 16, <= 256; launched in P tiles of at
+// most 128 that fit the shared memory).  All problems share `kind`.
 int kmv_tc_items(DeviceContext* ctx, int kind, const RowOperand& A, const RowOperand& B,
                  const KmvItemTables& tab, const __nv_bfloat16* s_hi, const __nv_bfloat16* s_lo,
                  int64_t s_rows, int s_row0, int p_pad, cudaStream_t stream);

@@ -703,13 +703,13 @@ int kmv_tc_items(DeviceContext* ctx, int kind, const RowOperand& A, const RowOpe
   const int prec = B.precision;
   const int nt1 = precision_splits_rows(prec) ? 3 : 1;
   const int nt2 = precision_splits_weights(prec) ? 3 : 1;
-  if (p16 > 128 || p16 < 16 || p16 % 16 != 0 || tab.G <= 0 || A.precision != prec ||
+  if (p16 > 256 || p16 < 16 || p16 % 16 != 0 || tab.G <= 0 || A.precision != prec ||
       A.d_pad != B.d_pad || s_row0 < 0 || s_row0 + p16 > s_rows)
     return ITERGP_EINVAL;
   // P tile: the widest multiple of 16 (<= p16) that leaves room for >= 2 stages
   const TcVariant var = tc_variant(prec, kind, B.d_pad, p16, 1);
   const bool can_ares = B.d_pad == BK && var.ares != 0;   // one K slice: A can stay resident
-  int p_tile = p16, nstage = 0;
+  int p_tile = std::min(p16, 128), nstage = 0;
   bool ares = false;
   for (; p_tile >= 16; p_tile -= 16) {
     if (can_ares && (nstage = stages_that_fit(ctx, nt1, nt2, p_tile, var.epi, var.nstage, true)) >= 3) {

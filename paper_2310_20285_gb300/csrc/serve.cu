@@ -93,8 +93,7 @@ __global__ void slab_weights32_kernel(const float* __restrict__ v, const float* 
 
 // ------------------------------------------------------------------ predict epilogue
 struct PredDesc {
-  const float* ym;   // [m][16]  K(X*, X) v
-  const float* yv;   // [m][128] K(X*, X) Q (columns b C + c)
+  const float* y;    // [m][144]: columns 0..C-1 K(X*, X) v, columns 16 + b C + c K(X*, X) Q_b
   float* out;        // [3][m][C]: mean, variance, probabilities
   int64_t m;
   int32_t c, b;
@@ -114,10 +113,10 @@ __global__ void serve_epilogue_kernel(const PredDesc* __restrict__ descs) {
     float* probs = q.out + 2 * q.m * C + i * C;
     float mx = -INFINITY;
     for (int c = 0; c < C; ++c) {
-      const float mu = q.ym[i * kMeanRows + c];
+      const float mu = q.y[i * kWeightRows + c];
       float acc = 0.f;
       for (int b = 0; b < q.b; ++b) {
-        const float t = q.yv[i * kVarRows + b * C + c];
+        const float t = q.y[i * kWeightRows + kMeanRows + b * C + c];
         acc = fmaf(t, t, acc);
       }
       const float vc = q.s - acc;
@@ -598,10 +597,7 @@ void itergp_server::run_predicts(std::vector<PredReq*>& batch, const std::vector
   if (tc) {
     g_mean = static_cast<int>(std::min<int64_t>(ctx->num_sms, static_cast<int64_t>(items_mean.size())));
     plan_items(items_mean, g_mean, &ord_mean, &beg_mean);
-    if (!items_var.empty()) {
-      g_var = static_cast<int>(std::min<int64_t>(ctx->num_sms, static_cast<int64_t>(items_var.size())));
-      plan_items(items_var, g_var, &ord_var, &beg_var);
-    }
+    // the variance columns ride in the same launch as the mean (weight rows [0, 16 + C B))
   } else {
     ord_mean = items_mean;
     ord_var = items_var;
@@ -611,8 +607,7 @@ void itergp_server::run_predicts(std::vector<PredReq*>& batch, const std::vector
   auto take = [&](size_t b) { const size_t o = off; off += align_up(std::max<size_t>(b, 1), 256); return o; };
   const size_t o_q = take(sizeof(float) * q_rows * dm);
   const size_t o_rows = take(rows_workspace_bytes(cfg.precision, q_rows, dm));
-  const size_t o_ym = take(sizeof(float) * m_total * kMeanRows);
-  const size_t o_yv = take(sizeof(float) * (max_cb > 0 ? m_total : 1) * kVarRows);
+  const size_t o_y = take(sizeof(float) * m_total * kWeightRows);
   const size_t o_out = take(sizeof(float) * out_total);
   const size_t o_tab = off;   // tables: items, begins, probs, descs (staged with the queries)
   size_t toff = 0;
@@ -634,8 +629,7 @@ void itergp_server::run_predicts(std::vector<PredReq*>& batch, const std::vector
   }
   char* base = dev.as<char>();
   float* qX = reinterpret_cast<float*>(base + o_q);
-  float* ym = reinterpret_cast<float*>(base + o_ym);
-  float* yv = reinterpret_cast<float*>(base + o_yv);
+  float* ybuf = reinterpret_cast<float*>(base + o_y);
   float* out = reinterpret_cast<float*>(base + o_out);
   char* tab = base + o_tab;
   // ---- stage queries (rows padded with zeros to 128 and to d_max) and tables
@@ -655,10 +649,14 @@ void itergp_server::run_predicts(std::vector<PredReq*>& batch, const std::vector
   std::vector<PredDesc> ds(count);
   for (int i = 0; i < count; ++i) {
     const Resident& r = models[i];
-    pm[i] = TcProb{ym + o0[i] * kMeanRows, kMeanRows, batch[i]->m, r.c, 0, r.kp, nullptr};
-    pv[i] = TcProb{yv + o0[i] * kVarRows, kVarRows, batch[i]->m, r.c * r.B, 0, r.kp, nullptr};
-    ds[i] = PredDesc{ym + o0[i] * kMeanRows, yv + o0[i] * kVarRows, out + oo[i], batch[i]->m, r.c, r.B,
-                     r.outputscale, 0};
+    float* yi = ybuf + o0[i] * kWeightRows;
+    if (tc) {   // one pass over weight rows [0, 16 + C B): mean and variance columns together
+      pm[i] = TcProb{yi, kWeightRows, batch[i]->m, kMeanRows + r.c * r.B, 0, r.kp, nullptr};
+    } else {    // FP32: a mean pass (columns 0..C-1) and a variance pass (columns 16..)
+      pm[i] = TcProb{yi, kWeightRows, batch[i]->m, r.c, 0, r.kp, nullptr};
+      pv[i] = TcProb{yi + kMeanRows, kWeightRows, batch[i]->m, r.c * r.B, 0, r.kp, nullptr};
+    }
+    ds[i] = PredDesc{yi, out + oo[i], batch[i]->m, r.c, r.B, r.outputscale, 0};
   }
   std::memcpy(ht + t_im, ord_mean.data(), sizeof(WorkItem) * ord_mean.size());
   std::memcpy(ht + t_iv, ord_var.data(), sizeof(WorkItem) * ord_var.size());
@@ -686,10 +684,8 @@ void itergp_server::run_predicts(std::vector<PredReq*>& batch, const std::vector
   tv.n_items = static_cast<int>(ord_var.size());
   if (rc == ITERGP_OK) {
     if (tc) {
-      rc = kmv_tc_items(ctx, cfg.kind, qop, rows_op, tm, w_hi, w_lo, kWeightRows, 0, kMeanRows, s);
-      if (rc == ITERGP_OK && tv.n_items > 0)
-        rc = kmv_tc_items(ctx, cfg.kind, qop, rows_op, tv, w_hi, w_lo, kWeightRows, kMeanRows,
-                          static_cast<int>((max_cb + 15) / 16 * 16), s);
+      rc = kmv_tc_items(ctx, cfg.kind, qop, rows_op, tm, w_hi, w_lo, kWeightRows, 0,
+                        kMeanRows + static_cast<int>((max_cb + 15) / 16 * 16), s);
     } else {
       rc = kmv_simt_items(ctx, cfg.kind, qop, rows_op, tm, w32, kWeightRows, max_c, s);
       if (rc == ITERGP_OK && tv.n_items > 0)

@@ -1,0 +1,57 @@
+"""The paper's large-scale synthetic problem (App. C.3: 10 classes of 3-D Gaussians,
+Matern-3/2 l = 0.05, s = 0.05) on the same code path: sampled rows of the N = 10^5
+product against the oracle, and a fit on a subsample against the oracle's fit."""
+import numpy as np
+import pytest
+import torch
+
+import oracle.itergp_oracle as O
+from paper_2310_20285_gb300 import datagen
+
+pytestmark = pytest.mark.gpu
+DEV = torch.device("cuda:0")
+KERN = O.Kernel(O.MATERN32, 0.05, 0.05)
+
+
+def rel(a, b):
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+@pytest.mark.parametrize("prec,tol", [("fp32", 1e-4), ("bf16x3", 1e-2)])
+def test_full_size_product_rows(native, prec, tol):
+    """l = 0.05 against |x| ~ 2: the |a|^2 + |b|^2 - 2 a.b form loses digits to
+    cancellation (CPU emulation of the FP32 form: 3e-5; of the BF16X3 split: 2.6e-3)."""
+    X, _ = datagen.gmm3d(10000, seed_model=1, seed_draw=2)
+    X = X.astype(np.float32)
+    S = datagen.normal((X.shape[0], 10), 5)
+    Y = native.kmatvec(torch.as_tensor(X, device=DEV), torch.as_tensor(X, device=DEV),
+                       torch.as_tensor(S, device=DEV), kind="matern32", lengthscale=0.05,
+                       outputscale=0.05, precision=prec).cpu().numpy()
+    rows = np.random.default_rng(0).choice(X.shape[0], 48, replace=False)
+    ref = O.kmatvec(X[rows].astype(np.float64), X.astype(np.float64), S.astype(np.float64), KERN)
+    assert rel(Y[rows], ref) <= tol, (prec, rel(Y[rows], ref))
+
+
+def test_subsample_fit_matches_the_oracle(native):
+    """2000 training points (200 per class), R = 10, j <= 5, 5 Newton steps, FP32."""
+    X, y = datagen.gmm3d(200, seed_model=1, seed_draw=7)
+    Xs, ys = datagen.gmm3d(100, seed_model=1, seed_draw=8)
+    X = X.astype(np.float32)
+    X64 = X.astype(np.float64)
+    ref = O.iterncgp_fit(X64, O.Softmax(y, 10), 10, KERN, max_newton=5, max_iters=5, R=10)
+    m = native.fit(torch.as_tensor(X, device=DEV), torch.as_tensor(y, device=DEV), 10,
+                   kind="matern32", lengthscale=0.05, outputscale=0.05, precision="fp32",
+                   max_newton=5, max_iters=5, rank=10)
+    got = [m.report.iters[i] for i in range(5)]
+    want = [inf.iters for inf in ref.infos]
+    # the solves converge in 2-3 iterations; a stopping check whose FP64 residual lies
+    # within FP32 resolution of the 1e-5 threshold may fall either way
+    assert all(abs(a - b) <= 1 for a, b in zip(got, want)), (got, want)
+    assert rel(m.arrays()["f"].cpu(), ref.f) <= 1e-4
+    mean, var, probs = m.predict(torch.as_tensor(Xs.astype(np.float32), device=DEV))
+    em, ev, ep = O.predict(Xs.astype(np.float32).astype(np.float64), X64, ref.v, ref.Q, KERN, 10)
+    assert rel(mean.cpu(), em) <= 1e-4
+    assert np.max(np.abs(var.cpu().numpy() - ev)) <= 1e-3 * 0.05
+    m.free()
