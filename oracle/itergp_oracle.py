@@ -180,6 +180,61 @@ class Gaussian:
         return self.noise * np.eye(self.y.size)
 
 
+class Bernoulli:
+    """Binary classification with one latent function and the logistic inverse link
+    pi = 1 / (1 + e^-f) (App. C, binary classification with one latent function):
+    y in {0, 1}, log p(y|f) = sum_n y_n f_n - log(1 + e^f_n), grad = y - pi,
+    W = diag(pi (1 - pi)), so W^-1 = diag(1 / (pi (1 - pi))) = diag(2 + e^f + e^-f)."""
+
+    def __init__(self, y: np.ndarray):
+        self.y = np.asarray(y, dtype=np.float64).reshape(-1, 1)
+        self.C = 1
+
+    def loglik(self, f):
+        f = np.asarray(f, dtype=np.float64).reshape(-1, 1)
+        return float(np.sum(self.y * f - np.logaddexp(0.0, f)))
+
+    def grad(self, f):
+        f = np.asarray(f, dtype=np.float64).reshape(-1, 1)
+        return self.y - 1.0 / (1.0 + np.exp(-f))
+
+    def winv_diag(self, f):
+        f = np.asarray(f, dtype=np.float64).reshape(-1, 1)
+        return 2.0 + np.exp(f) + np.exp(-f)
+
+    def Winv_apply(self, f, x):
+        return self.winv_diag(f) * np.asarray(x, dtype=np.float64).reshape(-1, 1)
+
+    def Winv_dense(self, f):
+        return np.diag(self.winv_diag(f).reshape(-1))
+
+
+class Poisson:
+    """Count regression with the log link (App. A, derivatives of the Poisson log
+    likelihood): rate lambda = e^f, log p(y|f) = sum_n y_n f_n - e^f_n (the constant
+    -log y_n! is dropped), grad = y - e^f, W = diag(e^f), W^-1 = diag(e^-f)."""
+
+    def __init__(self, y: np.ndarray):
+        self.y = np.asarray(y, dtype=np.float64).reshape(-1, 1)
+        self.C = 1
+
+    def loglik(self, f):
+        f = np.asarray(f, dtype=np.float64).reshape(-1, 1)
+        return float(np.sum(self.y * f - np.exp(f)))
+
+    def grad(self, f):
+        return self.y - np.exp(np.asarray(f, dtype=np.float64).reshape(-1, 1))
+
+    def winv_diag(self, f):
+        return np.exp(-np.asarray(f, dtype=np.float64).reshape(-1, 1))
+
+    def Winv_apply(self, f, x):
+        return self.winv_diag(f) * np.asarray(x, dtype=np.float64).reshape(-1, 1)
+
+    def Winv_dense(self, f):
+        return np.diag(self.winv_diag(f).reshape(-1))
+
+
 # ---------------------------------------------------------------------------------------
 # Exact Newton (the plain definition, Eqs. 3 and 6-7 / Prop. A.1)
 # ---------------------------------------------------------------------------------------

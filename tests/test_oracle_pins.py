@@ -493,3 +493,85 @@ def test_restart_from_an_iterate_reproduces_the_next_step():
         step = O.iterncgp_fit(X, O.Softmax(y, 3), 3, kern, max_newton=1, max_iters=8,
                               recycle=False, tol_abs=0, tol_rel=0, f0=full.fs[i])
         assert np.allclose(step.f, full.fs[i + 1], rtol=0, atol=1e-12 * np.abs(full.fs[i + 1]).max())
+
+
+# ------------------------------------------------------ one-latent likelihoods (App. A, C)
+
+def one_latent_problem(kind, n=12, seed=3):
+    g = np.random.default_rng(seed)
+    X = g.uniform(-2, 2, size=(n, 2))
+    ftrue = np.sin(X[:, 0]) + 0.5 * X[:, 1]
+    if kind == "bernoulli":
+        y = (g.random(n) < 1 / (1 + np.exp(-2 * ftrue))).astype(np.int64)
+        lik = O.Bernoulli(y)
+    else:
+        y = g.poisson(np.exp(ftrue))
+        lik = O.Poisson(y)
+    return X, y, lik
+
+
+@pytest.mark.parametrize("kind", ["bernoulli", "poisson"])
+def test_one_latent_loglik_against_scipy_pmfs(kind):
+    X, y, lik = one_latent_problem(kind)
+    f = np.random.default_rng(4).standard_normal((len(y), 1))
+    if kind == "bernoulli":
+        ref = scipy.stats.bernoulli.logpmf(y, scipy.special.expit(f[:, 0])).sum()
+    else:   # the oracle drops the constant -log y!
+        ref = scipy.stats.poisson.logpmf(y, np.exp(f[:, 0])).sum() + scipy.special.gammaln(y + 1.0).sum()
+    assert np.isclose(lik.loglik(f), ref, rtol=1e-12, atol=1e-12)
+
+
+@pytest.mark.parametrize("kind", ["bernoulli", "poisson"])
+def test_one_latent_gradient_and_hessian_by_finite_differences(kind):
+    X, y, lik = one_latent_problem(kind)
+    f = np.random.default_rng(5).standard_normal((len(y), 1))
+    h = 1e-5
+    for i in range(len(y)):
+        e = np.zeros_like(f)
+        e[i] = h
+        g_fd = (lik.loglik(f + e) - lik.loglik(f - e)) / (2 * h)
+        assert np.isclose(lik.grad(f)[i, 0], g_fd, rtol=1e-6, atol=1e-8)
+        hess_fd = (lik.grad(f + e)[i, 0] - lik.grad(f - e)[i, 0]) / (2 * h)
+        assert np.isclose(lik.winv_diag(f)[i, 0], -1.0 / hess_fd, rtol=1e-6)
+
+
+def textbook_newton_diag(K, w, grad, f, m):
+    """Eq. 3 with a diagonal W = diag(w): f + (W + K^-1)^-1 (grad - K^-1 (f - m))."""
+    Kinv = np.linalg.inv(K)
+    g = grad.reshape(-1) - Kinv @ (f - m).reshape(-1)
+    return f + np.linalg.solve(np.diag(w) + Kinv, g).reshape(f.shape)
+
+
+@pytest.mark.parametrize("kind", ["bernoulli", "poisson"])
+def test_one_latent_newton_via_pseudo_targets_equals_textbook_newton(kind):
+    """Alg. 1's GP-regression form of the step (pseudo targets, noise W^-1; shift 0 for a
+    single latent) equals Eq. 3 with W from a finite-difference Hessian."""
+    X, y, lik = one_latent_problem(kind)
+    kern = O.Kernel(O.RBF, 0.8, 1.0)
+    K = O.kernel_matrix(X, X, kern)
+    m = np.zeros((len(y), 1))
+    f = m.copy()
+    h = 1e-5
+    for _ in range(4):
+        _, f_next = O.exact_newton_step(X, lik, f, m, kern, shift=0.0)
+        w = np.array([-(lik.grad(f + h * np.eye(len(y))[:, [i]])[i, 0]
+                        - lik.grad(f - h * np.eye(len(y))[:, [i]])[i, 0]) / (2 * h)
+                      for i in range(len(y))])
+        ref = textbook_newton_diag(K, w, lik.grad(f), f, m)
+        assert np.allclose(f_next, ref, rtol=1e-6, atol=1e-7)
+        f = f_next
+    # at the mode grad log p = K^-1 (f - m) = v (Eq. 3)
+    fs, vs = O.exact_newton(X, lik, 1, kern, steps=15, shift=0.0)
+    assert np.allclose(lik.grad(fs[-1]), vs[-1], atol=1e-8)
+
+
+@pytest.mark.parametrize("kind", ["bernoulli", "poisson"])
+def test_one_latent_unit_actions_reproduce_the_exact_step(kind):
+    """N unit-vector actions (C = 1) reproduce the exact Newton step (Alg. 2 / Sec. 3)."""
+    X, y, lik = one_latent_problem(kind, n=10)
+    kern = O.Kernel(O.RBF, 0.8, 1.0)
+    ref = O.exact_newton(X, lik, 1, kern, steps=3, shift=0.0)[0]
+    res = O.iterncgp_fit(X, lik, 1, kern, max_newton=3, max_iters=len(y), policy=O.UNIT,
+                         recycle=False, tol_abs=0, tol_rel=0)
+    for a, b in zip(res.fs, ref):
+        assert np.allclose(a, b, atol=1e-9)
