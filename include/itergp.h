@@ -161,12 +161,23 @@ typedef enum {
   ITERGP_STOP_ETA = 2       /* eta_j <= 0: action not kept                        */
 } itergp_stop_reason;
 
+/* Likelihoods p(y | f).  Softmax is the paper's multi-class model; the others are its
+ * one-latent specialisations and the conjugate case, all solved by the same Alg. 1-3
+ * (only W^-1 and the pointwise terms change).  Objectives drop terms constant in f. */
+typedef enum {
+  ITERGP_LIK_SOFTMAX = 0,    /* c >= 2 classes, y labels in [0, c): W^+ of Lemma A.6     */
+  ITERGP_LIK_BERNOULLI = 1,  /* c = 1, y in {0, 1}, logistic link: W^-1 = 1/(pi (1-pi)) (App. C) */
+  ITERGP_LIK_POISSON = 2,    /* c = 1, counts y >= 0, log link: W^-1 = e^-f (App. A)     */
+  ITERGP_LIK_GAUSSIAN = 3    /* c >= 1 outputs, real targets y_real, W^-1 = noise I (Thm. A.2) */
+} itergp_likelihood;
+
 typedef struct {
   int64_t n;              /* number of training points, >= 1                       */
   int64_t d;              /* input dimension, 1 .. 4096                            */
-  int32_t c;              /* number of classes, 2 .. 64                            */
+  int32_t c;              /* classes (softmax: 2 .. 64), outputs (Gaussian: 1 .. 64),
+                             1 for Bernoulli and Poisson                            */
   const float* X;         /* device, n x d FP32 (copied into the model)           */
-  const int32_t* y;       /* device, n labels in [0, c)                           */
+  const int32_t* y;       /* device, n labels in [0, c) / {0,1} / counts (not Gaussian) */
   itergp_kernel kernel;
   int32_t precision;      /* itergp_precision of every kernel product             */
   int32_t policy;         /* itergp_policy: residual actions (CG) or unit vectors */
@@ -184,6 +195,9 @@ typedef struct {
                              it (fewer launch overheads); 0: launch kernels directly */
   const float* f0;        /* device, n x c starting iterate, or NULL for f_0 = m = 0
                              (Alg. 1); with a start, Psi(f_0) is reported with v = 0  */
+  int32_t likelihood;     /* itergp_likelihood (0 = softmax)                        */
+  float noise;            /* Gaussian likelihood: noise variance sigma^2 > 0          */
+  const float* y_real;    /* Gaussian likelihood: device, n x c real targets (y unused) */
 } itergp_fit_params;
 
 #define ITERGP_MAX_REPORT_STEPS 64

@@ -140,9 +140,13 @@ bool kernel_ok(const itergp_kernel* k) {
 bool precision_ok(int p) { return p >= ITERGP_FP32 && p <= ITERGP_BF16_COMP; }
 
 // mean = Y[:, :C]; var_c = s - sum_b Y[:, C + b C + c]^2; probs = softmax(mean / sqrt(1 + pi/8 var))
+// probs: softmax -- probit-approximated class probabilities (App. C.3); Bernoulli --
+// P(y = 1) by the same probit approximation; Poisson -- predictive mean count
+// E[e^f] = e^(mean + var / 2); Gaussian -- the predictive mean of y.
 __global__ void predict_epilogue_kernel(const float* __restrict__ Y, int64_t m, int C, int B,
                                         int64_t P, float s, float* __restrict__ mean,
-                                        float* __restrict__ var, float* __restrict__ probs) {
+                                        float* __restrict__ var, float* __restrict__ probs,
+                                        int lik) {
   for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < m;
        i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
     const float* yi = Y + i * P;
@@ -163,6 +167,23 @@ __global__ void predict_epilogue_kernel(const float* __restrict__ Y, int64_t m, 
           mx = fmaxf(mx, a);
         }
       }
+    }
+    if (probs && lik != ITERGP_LIK_SOFTMAX) {
+      for (int c = 0; c < C; ++c) {
+        float acc = 0.f;
+        for (int b = 0; b < B; ++b) {
+          const float q = yi[C + b * C + c];
+          acc = fmaf(q, q, acc);
+        }
+        const float vc = s - acc;
+        if (lik == ITERGP_LIK_BERNOULLI)
+          probs[i * C + c] = 1.f / (1.f + expf(-yi[c] / sqrtf(1.f + 0.39269908169872414f * vc)));
+        else if (lik == ITERGP_LIK_POISSON)
+          probs[i * C + c] = expf(yi[c] + 0.5f * vc);
+        else
+          probs[i * C + c] = yi[c];
+      }
+      continue;
     }
     if (probs) {
       float se = 0.f;
@@ -220,8 +241,22 @@ namespace itergp {
 
 int validate_fit_params(const itergp_fit_params* prm) {
   if (!prm) return ITERGP_EINVAL;
-  if (prm->n < 1 || prm->d < 1 || prm->d > 4096 || prm->c < 2 || prm->c > 64 || !prm->X || !prm->y)
+  if (prm->n < 1 || prm->d < 1 || prm->d > 4096 || prm->c < 1 || prm->c > 64 || !prm->X)
     return ITERGP_EINVAL;
+  switch (prm->likelihood) {
+    case ITERGP_LIK_SOFTMAX:
+      if (prm->c < 2 || !prm->y) return ITERGP_EINVAL;
+      break;
+    case ITERGP_LIK_BERNOULLI:
+    case ITERGP_LIK_POISSON:
+      if (prm->c != 1 || !prm->y) return ITERGP_EINVAL;
+      break;
+    case ITERGP_LIK_GAUSSIAN:
+      if (!prm->y_real || !(prm->noise > 0.f) || !std::isfinite(prm->noise)) return ITERGP_EINVAL;
+      break;
+    default:
+      return ITERGP_EINVAL;
+  }
   if (!kernel_ok(&prm->kernel) || !precision_ok(prm->precision)) return ITERGP_EINVAL;
   if (prm->policy != ITERGP_POLICY_CG && prm->policy != ITERGP_POLICY_UNIT) return ITERGP_EINVAL;
   if (prm->max_newton < 1 || prm->max_iters < 0 || prm->max_newton > 100000) return ITERGP_EINVAL;
@@ -277,6 +312,7 @@ int fit_many(const itergp_fit_params* params, int count, itergp_model** out,
     mdl->bcap = static_cast<int>(bcap);
     mdl->kernel = prm.kernel;
     mdl->precision = prm.precision;
+    mdl->likelihood = prm.likelihood;
     const size_t xb = align_up(sizeof(float) * n * prm.d, 256);
     const size_t rb = rows_workspace_bytes(prm.precision, n, static_cast<int>(prm.d));
     const size_t vb = align_up(sizeof(float) * nc, 256);
@@ -481,7 +517,8 @@ int itergp_fit_batch(const itergp_fit_params* params, int32_t count, itergp_mode
     if (b.kernel.kind != a.kernel.kind || b.precision != a.precision || b.policy != a.policy ||
         b.max_newton != a.max_newton || b.max_iters != a.max_iters || b.rank != a.rank ||
         b.recycle != a.recycle || b.literal_kv != 0 || b.tol_newton != a.tol_newton ||
-        b.tol_abs != a.tol_abs || b.tol_rel != a.tol_rel || b.graph != a.graph)
+        b.tol_abs != a.tol_abs || b.tol_rel != a.tol_rel || b.graph != a.graph ||
+        b.likelihood != a.likelihood)
       return ITERGP_EINVAL;
   }
   return fit_many(params, count, models, reports, static_cast<cudaStream_t>(stream), true);
@@ -517,7 +554,8 @@ int itergp_predict(const itergp_model* mdl, const float* Xs, int64_t m, float* m
   rc = kmv_execute(ctx, make_kparams(mdl->kernel), op, mdl->xop, Sv, P, P, Y, P, s, nullptr);
   if (rc != ITERGP_OK) return rc;
   const unsigned blocks = static_cast<unsigned>(std::min<int64_t>(ceil_div(m, 256), 8LL * ctx->num_sms));
-  predict_epilogue_kernel<<<blocks, 256, 0, s>>>(Y, m, C, B, P, mdl->kernel.outputscale, mean, var, probs), ::itergp::note_launch();
+  predict_epilogue_kernel<<<blocks, 256, 0, s>>>(Y, m, C, B, P, mdl->kernel.outputscale, mean, var, probs,
+                                                 mdl->likelihood), ::itergp::note_launch();
   ITERGP_CUDA_TRY(cudaGetLastError());
   return ITERGP_OK;
 }

@@ -177,6 +177,7 @@ struct itergp_model {
   int c = 0, bcap = 0, B = 0;
   itergp_kernel kernel{};
   int precision = 0;
+  int likelihood = ITERGP_LIK_SOFTMAX;
   void* mem = nullptr;
   float* X = nullptr;
   float* v = nullptr;

@@ -445,6 +445,14 @@ kmv_tc_kernel(const __grid_constant__ CUtensorMap mAh, const __grid_constant__ C
     bool out_valid = false;
     int out_lim = 0;
     Walker wk = walk0;
+    // column norms of the next step are loaded while the current chunk is processed
+    Walker wkn = walk0;
+    float nb_next[BN / 32];
+    {
+      const StepInfo s0 = wkn.cur();
+#pragma unroll
+      for (int k = 0; k < BN / 32; ++k) nb_next[k] = args.nb[static_cast<int64_t>(s0.b_row) + lane + 32 * k];
+    }
     for (int64_t t = 0; t < T; ++t, wk.next()) {
       const StepInfo st = wk.cur();
       const int c = st.c;
@@ -470,17 +478,28 @@ kmv_tc_kernel(const __grid_constant__ CUtensorMap mAh, const __grid_constant__ C
       float* nb_s = nb_all + e * BN;
       __syncwarp();
 #pragma unroll
-      for (int k = 0; k < BN / 32; ++k) nb_s[lane + 32 * k] = args.nb[static_cast<int64_t>(st.b_row) + lane + 32 * k];
+      for (int k = 0; k < BN / 32; ++k) nb_s[lane + 32 * k] = nb_next[k];
       __syncwarp();
+      wkn.next();
+      if (t + 1 < T) {
+        const StepInfo sn = wkn.cur();
+#pragma unroll
+        for (int k = 0; k < BN / 32; ++k) nb_next[k] = args.nb[static_cast<int64_t>(sn.b_row) + lane + 32 * k];
+      }
       const int gb = static_cast<int>(t & 1);
       if (!mbar_wait_warp(&gfull[gb], static_cast<uint32_t>((t >> 1) & 1), ab, kWaitLimitNs)) break;
       tc_fence_after();
       const uint32_t gcol = tb + lane_base + gb * BN;
+      // the TMEM load of the next 32-column group is in flight while this one is computed
+      const int grp0 = h * (BN / 32 / NH), grp1 = (h + 1) * (BN / 32 / NH);
+      uint32_t v[32];
+      tmem_ld32(gcol + 32 * grp0, v);
+      tmem_ld_wait();
 #pragma unroll 1
-      for (int grp = h * (BN / 32 / NH); grp < (h + 1) * (BN / 32 / NH); ++grp) {
-        uint32_t v[32];
-        tmem_ld32(gcol + 32 * grp, v);
-        tmem_ld_wait();
+      for (int grp = grp0; grp < grp1; ++grp) {
+        uint32_t vn[32];
+        const bool more = grp + 1 < grp1;   // warp-uniform
+        if (more) tmem_ld32(gcol + 32 * (grp + 1), vn);
         uint32_t ph[16], pl[16];
 #pragma unroll
         for (int i = 0; i < 16; ++i) {
@@ -497,6 +516,11 @@ kmv_tc_kernel(const __grid_constant__ CUtensorMap mAh, const __grid_constant__ C
         }
         tmem_st16(gcol + 32 * grp, ph);
         if (NT2 == 3) tmem_st16(gcol + 32 * grp + 16, pl);
+        if (more) {
+          tmem_ld_wait();
+#pragma unroll
+          for (int i = 0; i < 32; ++i) v[i] = vn[i];
+        }
       }
       tmem_st_wait();
       tc_fence_before();

@@ -47,6 +47,9 @@ struct ProbDev {
   int64_t n, nc;
   int c, bcap;
   const int32_t* y;
+  int lik;                           // itergp_likelihood
+  float noise;                       // Gaussian noise variance
+  const float* yr;                   // Gaussian real targets (n x c)
   float *f, *v, *Q;                  // model arrays
   float *S, *T, *KQ;                 // buffers [bcap][nc]
   float *u, *b, *r, *z, *gp, *ip, *s_cur, *t_cur;
@@ -71,15 +74,18 @@ __device__ __forceinline__ double block_reduce_sum(double v, double* sh) {
   return t;  // valid in thread 0
 }
 
-// out_n = P diag(inv_pi_n) P x_n, P = I - 11^T/C   (Lemma A.6)
+// Softmax: out_n = P diag(inv_pi_n) P x_n, P = I - 11^T/C (Lemma A.6).  Likelihoods with a
+// diagonal W (one latent per point: Bernoulli, Poisson; Gaussian): out = ip * x with ip
+// the diagonal of W^-1 -- the same formula with the class means m1, m2 set to zero.
 __device__ __forceinline__ void winv_point(const float* __restrict__ x, const float* __restrict__ ip,
-                                           int C, float* __restrict__ out) {
-  float m1 = 0.f;
-  for (int c = 0; c < C; ++c) m1 += x[c];
-  m1 /= C;
-  float m2 = 0.f;
-  for (int c = 0; c < C; ++c) m2 += (x[c] - m1) * ip[c];
-  m2 /= C;
+                                           int C, float* __restrict__ out, bool diag = false) {
+  float m1 = 0.f, m2 = 0.f;
+  if (!diag) {
+    for (int c = 0; c < C; ++c) m1 += x[c];
+    m1 /= C;
+    for (int c = 0; c < C; ++c) m2 += (x[c] - m1) * ip[c];
+    m2 /= C;
+  }
   for (int c = 0; c < C; ++c) out[c] = (x[c] - m1) * ip[c] - m2;
 }
 
@@ -105,34 +111,67 @@ __global__ void newton_prologue_kernel(const ProbDev* __restrict__ probs, int pr
   if (!st->newton_active) return;
   __shared__ double sh[32];
   double s_b2 = 0, s_ll = 0, s_vf = 0, s_dg = 0, s_g2 = 0;
+  const bool diag = P.lik != ITERGP_LIK_SOFTMAX;
   for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
        i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
     const float* fi = f + i * C;
-    float mx = fi[0];
-    for (int c = 1; c < C; ++c) mx = fmaxf(mx, fi[c]);
-    float se = 0.f;
-    for (int c = 0; c < C; ++c) se += expf(fi[c] - mx);
-    const float lse = mx + logf(se);
-    int yi = y[i];
-    if (yi < 0 || yi >= C) {
-      set_status(status, ITERGP_EINVAL);
-      yi = 0;
-    }
     float* ipi = inv_pi + i * C;
-    float gsum = 0.f;
     float grad[kMaxC];
-    for (int c = 0; c < C; ++c) {
-      const float e = expf(lse - fi[c]);
-      if (!isfinite(e)) set_status(status, ITERGP_ENUMERIC);
-      ipi[c] = e;
-      grad[c] = (c == yi ? 1.f : 0.f) - expf(fi[c] - lse);
-      gsum += grad[c];
+    float m1 = 0.f, m2 = 0.f;
+    if (P.lik == ITERGP_LIK_SOFTMAX) {
+      float mx = fi[0];
+      for (int c = 1; c < C; ++c) mx = fmaxf(mx, fi[c]);
+      float se = 0.f;
+      for (int c = 0; c < C; ++c) se += expf(fi[c] - mx);
+      const float lse = mx + logf(se);
+      int yi = y[i];
+      if (yi < 0 || yi >= C) {
+        set_status(status, ITERGP_EINVAL);
+        yi = 0;
+      }
+      float gsum = 0.f;
+      for (int c = 0; c < C; ++c) {
+        const float e = expf(lse - fi[c]);
+        if (!isfinite(e)) set_status(status, ITERGP_ENUMERIC);
+        ipi[c] = e;
+        grad[c] = (c == yi ? 1.f : 0.f) - expf(fi[c] - lse);
+        gsum += grad[c];
+      }
+      // W^+ grad with P applied on both sides
+      m1 = gsum / C;
+      for (int c = 0; c < C; ++c) m2 += (grad[c] - m1) * ipi[c];
+      m2 /= C;
+      s_ll += static_cast<double>(fi[yi]) - lse;
+    } else if (P.lik == ITERGP_LIK_BERNOULLI) {
+      // pi = 1 / (1 + e^-f), grad = y - pi, W^-1 = 2 + e^f + e^-f (App. C)
+      const int yi = y[i];
+      if (yi != 0 && yi != 1) set_status(status, ITERGP_EINVAL);
+      const float fv = fi[0];
+      const float ef = expf(fv), emf = expf(-fv);
+      const float w = 2.f + ef + emf;
+      if (!isfinite(w)) set_status(status, ITERGP_ENUMERIC);
+      ipi[0] = w;
+      grad[0] = static_cast<float>(yi == 1) - 1.f / (1.f + emf);
+      s_ll += static_cast<double>(yi == 1 ? fv : 0.f) - (fmaxf(fv, 0.f) + log1pf(expf(-fabsf(fv))));
+    } else if (P.lik == ITERGP_LIK_POISSON) {
+      // rate e^f, grad = y - e^f, W^-1 = e^-f (App. A)
+      const int yi = y[i];
+      if (yi < 0) set_status(status, ITERGP_EINVAL);
+      const float fv = fi[0];
+      const float ef = expf(fv), emf = expf(-fv);
+      if (!isfinite(ef) || !isfinite(emf)) set_status(status, ITERGP_ENUMERIC);
+      ipi[0] = emf;
+      grad[0] = static_cast<float>(yi) - ef;
+      s_ll += static_cast<double>(yi) * fv - ef;
+    } else {
+      // Gaussian: grad = (y - f) / sigma^2, W^-1 = sigma^2 I (Thm. A.2)
+      for (int c = 0; c < C; ++c) {
+        const float rr = P.yr[i * C + c] - fi[c];
+        ipi[c] = P.noise;
+        grad[c] = rr / P.noise;
+        s_ll += -0.5 * static_cast<double>(rr) * rr / P.noise;
+      }
     }
-    // W^+ grad with P applied on both sides
-    const float m1 = gsum / C;
-    float m2 = 0.f;
-    for (int c = 0; c < C; ++c) m2 += (grad[c] - m1) * ipi[c];
-    m2 /= C;
     float* bi = b + i * C;
     float* gp = g_prev + i * C;
     const float* vi = v + i * C;
@@ -141,7 +180,7 @@ __global__ void newton_prologue_kernel(const ProbDev* __restrict__ probs, int pr
     // mean keeps rounding out of the class-sum directions, where K_hat reduces to the
     // near-singular k(X, X).  Unit-vector actions leave that subspace: no projection.
     float bmean = 0.f;
-    if (project) {
+    if (project && !diag) {
       for (int c = 0; c < C; ++c) bmean += fi[c] + ((grad[c] - m1) * ipi[c] - m2);
       bmean /= C;
     }
@@ -155,7 +194,6 @@ __global__ void newton_prologue_kernel(const ProbDev* __restrict__ probs, int pr
       s_g2 += static_cast<double>(fi[c]) * fi[c];
       gp[c] = fi[c];
     }
-    s_ll += static_cast<double>(fi[yi]) - lse;
   }
   double r;
   r = block_reduce_sum(s_b2, sh); if (threadIdx.x == 0) part[blockIdx.x * 5 + 0] = r;
@@ -221,7 +259,7 @@ __global__ void vsr_z_kernel(const ProbDev* __restrict__ probs) {
     const int64_t col = e / n, i = e % n;
     const float* s = S + col * nc + i * C;
     float w[kMaxC];
-    winv_point(s, inv_pi + i * C, C, w);
+    winv_point(s, inv_pi + i * C, C, w, P.lik != ITERGP_LIK_SOFTMAX);
     const float* t = T + col * nc + i * C;
     float* z = Z + col * nc + i * C;
     for (int c = 0; c < C; ++c) z[c] = t[c] + w[c];
@@ -608,20 +646,22 @@ __global__ void resid_kernel(const ProbDev* __restrict__ probs, int project) {
   float* __restrict__ r = P.r;
   double* __restrict__ part = P.ps;
   if (!st->newton_active || !st->active) return;
+  const bool diag = P.lik != ITERGP_LIK_SOFTMAX;   // W^-1 diagonal: no class means
   __shared__ double sh[32];
   double acc = 0.0;
   for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
        i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
     const float* vi = v + i * C;
     const float* ipi = inv_pi + i * C;
-    double m1 = 0.0;
-    for (int c = 0; c < C; ++c) m1 += vi[c];
-    m1 /= C;
-    double m2 = 0.0;
-    for (int c = 0; c < C; ++c) m2 += (vi[c] - m1) * static_cast<double>(ipi[c]);
-    m2 /= C;
+    double m1 = 0.0, m2 = 0.0;
+    if (!diag) {
+      for (int c = 0; c < C; ++c) m1 += vi[c];
+      m1 /= C;
+      for (int c = 0; c < C; ++c) m2 += (vi[c] - m1) * static_cast<double>(ipi[c]);
+      m2 /= C;
+    }
     double rm = 0.0;
-    if (project) {
+    if (project && !diag) {
       for (int c = 0; c < C; ++c)
         rm += static_cast<double>(b[i * C + c]) - u[i * C + c] - ((vi[c] - m1) * ipi[c] - m2);
       rm /= C;
@@ -705,7 +745,7 @@ __global__ void z_kernel(const ProbDev* __restrict__ probs) {
   for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
        i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
     float w[kMaxC];
-    winv_point(s_cur + i * C, inv_pi + i * C, C, w);
+    winv_point(s_cur + i * C, inv_pi + i * C, C, w, P.lik != ITERGP_LIK_SOFTMAX);
     for (int c = 0; c < C; ++c) {
       const float tv = t_cur[i * C + c];
       tcol[i * C + c] = tv;
@@ -1005,7 +1045,9 @@ int fit_run_batch(DeviceContext* ctx, const std::vector<FitProblem>& probs, cuda
   if (np == 0) return ITERGP_OK;
   const itergp_fit_params& prm = *probs[0].prm;    // schedule shared by the batch
   const int track_kd = prm.literal_kv ? 0 : 1;
-  const int project = prm.policy == ITERGP_POLICY_CG ? 1 : 0;
+  // the class-contrast projection belongs to the softmax likelihood (one latent per
+  // point has no class-sum directions)
+  const int project = prm.policy == ITERGP_POLICY_CG && prm.likelihood == ITERGP_LIK_SOFTMAX ? 1 : 0;
   int64_t max_n = 0, max_nc = 0;
   int max_bcap = 1, c_max = 2, d_max = 1;
   for (const FitProblem& fp : probs) {
@@ -1111,6 +1153,9 @@ int fit_run_batch(DeviceContext* ctx, const std::vector<FitProblem>& probs, cuda
     d.nc = d.n * d.c;
     d.bcap = probs[i].bcap;
     d.y = probs[i].prm->y;
+    d.lik = probs[i].prm->likelihood;
+    d.noise = probs[i].prm->noise;
+    d.yr = probs[i].prm->y_real;
     d.f = probs[i].f; d.v = probs[i].v; d.Q = probs[i].Q;
     d.S = reinterpret_cast<float*>(base + o.S); d.T = reinterpret_cast<float*>(base + o.T);
     d.KQ = reinterpret_cast<float*>(base + o.KQ);

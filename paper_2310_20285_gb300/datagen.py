@@ -134,6 +134,23 @@ def batch_problems(count: int = 256, seed: int = 4, n_lo: int = 200, n_hi: int =
     return out
 
 
+def one_latent(kind: str, n: int, seed: int, d: int = 2, n_test: int = 100):
+    """Single-latent problems: X ~ U[-3, 3]^d, latent g(x) = sin(x_1) + x_2 / 2, and
+    y ~ Bernoulli(1 / (1 + e^(-2 g))) ("bernoulli"), y ~ Poisson(e^g) ("poisson") or
+    y = g + N(0, 0.1^2) ("gaussian").  Returns X, y, Xs (float32, labels int32)."""
+    g = _rng(seed)
+    X = g.uniform(-3.0, 3.0, size=(n + n_test, d))
+    lat = np.sin(X[:, 0]) + (0.5 * X[:, 1] if d > 1 else 0.0)
+    if kind == "bernoulli":
+        y = (g.random(n + n_test) < 1.0 / (1.0 + np.exp(-2.0 * lat))).astype(np.int32)
+    elif kind == "poisson":
+        y = g.poisson(np.exp(lat)).astype(np.int32)
+    else:
+        y = (lat + 0.1 * g.standard_normal(n + n_test)).astype(np.float32)
+    X = X.astype(np.float32)
+    return X[:n], y[:n], X[n:]
+
+
 def poisson_arrivals(rate: float, duration: float, seed: int) -> np.ndarray:
     """Arrival times (seconds) of a Poisson process of ``rate`` per second."""
     g = _rng(seed)

@@ -22,6 +22,7 @@ STOP_MAXITER, STOP_TOL, STOP_ETA = 0, 1, 2
 MAX_REPORT_STEPS = 64
 
 PRECISIONS = {"fp32": FP32, "bf16x3": BF16X3, "bf16": BF16, "bf16_comp": BF16_COMP}
+LIKELIHOODS = {"softmax": 0, "bernoulli": 1, "poisson": 2, "gaussian": 3}
 KERNELS = {"rbf": RBF, "matern32": MATERN32}
 
 
@@ -42,7 +43,8 @@ class FitParams(ct.Structure):
                 ("max_newton", ct.c_int32), ("max_iters", ct.c_int32), ("rank", ct.c_int32),
                 ("recycle", ct.c_int32), ("literal_kv", ct.c_int32),
                 ("tol_newton", ct.c_double), ("tol_abs", ct.c_double), ("tol_rel", ct.c_double),
-                ("graph", ct.c_int32), ("f0", ct.c_void_p)]
+                ("graph", ct.c_int32), ("f0", ct.c_void_p), ("likelihood", ct.c_int32),
+                ("noise", ct.c_float), ("y_real", ct.c_void_p)]
 
 
 class FitReport(ct.Structure):
@@ -324,12 +326,20 @@ class _CudaArray:
 
 
 def _params(X, y, c, kind, lengthscale, outputscale, precision, policy, max_newton, max_iters,
-            rank, recycle, literal_kv, tol_newton, tol_abs, tol_rel, graph, f0=None) -> FitParams:
+            rank, recycle, literal_kv, tol_newton, tol_abs, tol_rel, graph, f0=None,
+            likelihood="softmax", noise=1.0) -> FitParams:
     n, d = X.shape
     prm = FitParams()
     prm.n, prm.d, prm.c = n, d, int(c)
     prm.X = _dev(X, torch.float32, "X").value
-    prm.y = _dev(y, torch.int32, "y").value
+    prm.likelihood = LIKELIHOODS[likelihood]
+    if likelihood == "gaussian":   # real targets, n x c
+        if y.numel() != n * int(c):
+            raise ValueError("gaussian targets must be n x c")
+        prm.y_real = _dev(y, torch.float32, "y").value
+        prm.noise = float(noise)
+    else:
+        prm.y = _dev(y, torch.int32, "y").value
     prm.kernel = _kernel(kind, lengthscale, outputscale)
     prm.precision = _prec(precision)
     prm.policy = POLICY_CG if policy in ("cg", POLICY_CG) else POLICY_UNIT
@@ -347,11 +357,15 @@ def _params(X, y, c, kind, lengthscale, outputscale, precision, policy, max_newt
 
 def fit(X, y, c, kind="rbf", lengthscale=1.0, outputscale=1.0, precision="fp32",
         policy="cg", max_newton=10, max_iters=50, rank=-1, recycle=True, literal_kv=False,
-        tol_newton=0.0, tol_abs=1e-5, tol_rel=1e-5, graph=False, stream=None, f0=None) -> Model:
-    """IterNCGP fit (Alg. 1-3) of a softmax GP classifier on the GPU; f0 (n x c, device)
-    starts Newton's method at that iterate instead of m = 0."""
+        tol_newton=0.0, tol_abs=1e-5, tol_rel=1e-5, graph=False, stream=None, f0=None,
+        likelihood="softmax", noise=1.0) -> Model:
+    """IterNCGP fit (Alg. 1-3) on the GPU.  likelihood: "softmax" (c >= 2 classes, integer
+    labels), "bernoulli" (c = 1, labels 0/1), "poisson" (c = 1, counts) or "gaussian"
+    (real targets y of n x c, noise variance `noise`).  f0 (n x c, device) starts Newton's
+    method at that iterate instead of m = 0."""
     prm = _params(X, y, c, kind, lengthscale, outputscale, precision, policy, max_newton,
-                  max_iters, rank, recycle, literal_kv, tol_newton, tol_abs, tol_rel, graph, f0)
+                  max_iters, rank, recycle, literal_kv, tol_newton, tol_abs, tol_rel, graph, f0,
+                  likelihood, noise)
     h = ct.c_void_p()
     rep = FitReport()
     rc = lib.itergp_fit(ct.byref(prm), ct.byref(h), ct.byref(rep), _stream(stream))

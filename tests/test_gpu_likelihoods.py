@@ -1,0 +1,105 @@
+"""One-latent likelihoods (Bernoulli with the logistic link, App. C; Poisson with the log
+link, App. A) and the conjugate Gaussian case (Thm. A.2) through the same Alg. 1-3 path,
+against the oracle."""
+import ctypes as ct
+
+import numpy as np
+import pytest
+import torch
+
+import oracle.itergp_oracle as O
+from paper_2310_20285_gb300 import datagen
+
+pytestmark = pytest.mark.gpu
+DEV = torch.device("cuda:0")
+KERN = O.Kernel(O.RBF, 1.0, 1.0)
+
+
+def rel(a, b):
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def lik_of(kind, y):
+    return O.Bernoulli(y) if kind == "bernoulli" else O.Poisson(y)
+
+
+@pytest.mark.parametrize("kind", ["bernoulli", "poisson"])
+@pytest.mark.parametrize("prec", ["fp32", "bf16x3"])
+def test_one_latent_fit_matches_the_oracle(native, kind, prec):
+    X, y, Xs = datagen.one_latent(kind, 400, seed=3)
+    X64 = X.astype(np.float64)
+    # 8 iterations keep every residual above 1e-4 of its step's first (FP32 follows FP64)
+    ref = O.iterncgp_fit(X64, lik_of(kind, y), 1, KERN, max_newton=6, max_iters=8, R=20,
+                         tol_abs=0, tol_rel=0)
+    m = native.fit(torch.as_tensor(X, device=DEV), torch.as_tensor(y, device=DEV), 1, kind="rbf",
+                   lengthscale=1.0, likelihood=kind, precision=prec, max_newton=6, max_iters=8,
+                   rank=20, tol_abs=0.0, tol_rel=0.0)
+    assert [m.report.iters[i] for i in range(6)] == [inf.iters for inf in ref.infos]
+    assert rel(m.arrays()["f"].cpu(), ref.f) <= 1e-4
+    for i in range(6):
+        assert abs(m.report.objective[i] - ref.objectives[i]) <= 1e-4 * abs(ref.objectives[i])
+    mean, var, out = m.predict(torch.as_tensor(Xs, device=DEV))
+    em, ev, _ = O.predict(Xs.astype(np.float64), X64, ref.v, ref.Q, KERN, 1)
+    assert rel(mean.cpu(), em) <= 1e-4
+    assert np.max(np.abs(var.cpu().numpy() - ev)) <= 1e-3
+    if kind == "bernoulli":    # P(y = 1) by the probit approximation
+        want = 1.0 / (1.0 + np.exp(-em / np.sqrt(1.0 + np.pi / 8.0 * ev)))
+    else:                      # predictive mean count E[e^f]
+        want = np.exp(em + 0.5 * ev)
+    assert np.max(np.abs(out.cpu().numpy() - want) / np.maximum(np.abs(want), 1e-3)) <= 1e-3
+    m.free()
+
+
+@pytest.mark.parametrize("kind", ["bernoulli", "poisson"])
+def test_one_latent_unit_actions_reproduce_exact_newton(native, kind):
+    """N unit-vector actions per step reproduce the exact Newton step (Sec. 3)."""
+    X, y, _ = datagen.one_latent(kind, 60, seed=5)
+    lik = lik_of(kind, y)
+    ref = O.exact_newton(X.astype(np.float64), lik, 1, KERN, steps=3, shift=0.0)[0]
+    m = native.fit(torch.as_tensor(X, device=DEV), torch.as_tensor(y, device=DEV), 1, kind="rbf",
+                   lengthscale=1.0, likelihood=kind, policy="unit", max_newton=3, max_iters=60,
+                   rank=-1, recycle=False, tol_abs=0.0, tol_rel=0.0)
+    assert rel(m.arrays()["f"].cpu(), ref[3]) <= 1e-4
+    m.free()
+
+
+def test_gaussian_likelihood_is_gp_regression(native):
+    """Thm. A.2: with a Gaussian likelihood one Newton step (solved to convergence) gives
+    the GP regression posterior mean K (K + sigma^2 I)^-1 y, for two outputs.  The FP32
+    solve stops at a 1e-6 relative residual; cond(K + sigma^2 I) ~ 6e3 here."""
+    X, g1, Xs = datagen.one_latent("gaussian", 300, seed=7)
+    _, g2, _ = datagen.one_latent("gaussian", 300, seed=8)
+    Y = np.stack([g1, 0.5 * g2], axis=1).astype(np.float32)
+    noise = 0.05
+    K = O.kernel_matrix(X.astype(np.float64), X.astype(np.float64), KERN)
+    f_exact = K @ np.linalg.solve(K + noise * np.eye(len(X)), Y.astype(np.float64))
+    m = native.fit(torch.as_tensor(X, device=DEV), torch.as_tensor(Y, device=DEV), 2, kind="rbf",
+                   lengthscale=1.0, likelihood="gaussian", noise=noise, max_newton=1, max_iters=200,
+                   rank=-1, tol_abs=1e-6, tol_rel=1e-6)
+    assert rel(m.arrays()["f"].cpu(), f_exact) <= 1e-3
+    mean, var, yhat = m.predict(torch.as_tensor(Xs, device=DEV))
+    Ks = O.kernel_matrix(Xs.astype(np.float64), X.astype(np.float64), KERN)
+    assert rel(mean.cpu(), Ks @ np.linalg.solve(K + noise * np.eye(len(X)), Y.astype(np.float64))) <= 1e-3
+    assert torch.equal(mean, yhat)
+    m.free()
+
+
+def test_bad_labels_and_parameters(native):
+    X, y, _ = datagen.one_latent("bernoulli", 100, seed=9)
+    yb = y.copy()
+    yb[3] = 2
+    with pytest.raises(native.ItergpError) as e:
+        native.fit(torch.as_tensor(X, device=DEV), torch.as_tensor(yb, device=DEV), 1,
+                   likelihood="bernoulli", max_newton=1, max_iters=2)
+    assert e.value.code == native.EINVAL
+    Xp, yp, _ = datagen.one_latent("poisson", 100, seed=9)
+    yp = yp.copy()
+    yp[0] = -1
+    with pytest.raises(native.ItergpError):
+        native.fit(torch.as_tensor(Xp, device=DEV), torch.as_tensor(yp, device=DEV), 1,
+                   likelihood="poisson", max_newton=1, max_iters=2)
+    with pytest.raises(native.ItergpError):   # one latent only
+        native.fit(torch.as_tensor(X, device=DEV), torch.as_tensor(y, device=DEV), 2,
+                   likelihood="bernoulli", max_newton=1, max_iters=2)
