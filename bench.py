@@ -221,6 +221,36 @@ def bench_batched(native, datagen, torch, dev, count):
     return res
 
 
+def small_d_roofline(native, torch, dev, n=131072, d=32, p=16):
+    """The product at small D (the batched and served shapes) is bound by the exp per
+    kernel value, not by the tensor cores: 2 (D + P) tensor flops against one MUFU exp2
+    per pair (RBF).  Measured against this GPU's MUFU exp2 and FFMA rates, probed here."""
+    ex2 = native.probe_throughput("ex2")
+    ffma = native.probe_throughput("ffma")
+    g = torch.Generator(device=dev).manual_seed(0)
+    X = torch.rand((n, d), device=dev, generator=g) * 4.0
+    S = torch.rand((n, p), device=dev, generator=g) * 2 - 1
+    Y = torch.empty((n, p), device=dev)
+    res = {"probe_ex2_per_s": ex2, "probe_ffma_flops_per_s": ffma,
+           "shape": f"single product N={n}, D={d}, P={p}, RBF, inputs U[0,4)^D"}
+    for prec in ("bf16x3", "bf16_comp", "fp32"):
+        native.kmatvec(X, X, S, kind="rbf", lengthscale=1.0, precision=prec, out=Y)
+        torch.cuda.synchronize()
+        reps = 5
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            native.kmatvec(X, X, S, kind="rbf", lengthscale=1.0, precision=prec, out=Y)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        pairs = n * n / (ms * 1e-3)
+        res[prec] = {"ms": ms, "kernel_pairs_per_s": pairs,
+                     "roofline": {"bound": "sfu", "achieved": pairs, "peak": ex2, "unit": "exp2/s",
+                                  "frac": pairs / ex2, "peak_kind": "measured here (ex2.approx probe)"}}
+    return res
+
+
 def calibration_metrics(probs, y, n_bins=15):
     """Accuracy, NLL (negative mean log-probability of the true class) and expected
     calibration error of the top-class confidence over n_bins equal-width bins."""
@@ -553,6 +583,7 @@ def main():
                               "per Newton step are comparable, accuracies are not",
                       **fits}
     if rank == 0 and not args.no_extras:
+        out["small_d_roofline"] = small_d_roofline(native, torch, dev)
         out["batched"] = bench_batched(native, datagen, torch, dev, args.batch_count)
     if rank == 0 and not args.no_extras:
         out["gmm_large"] = bench_gmm(native, datagen, torch, dev)

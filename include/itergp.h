@@ -414,6 +414,12 @@ int itergp_tune_clear(void);
  * returns; the context stays usable.  No fault, trap or hang is involved. */
 int itergp_selftest_wait(uint64_t limit_ns, itergp_stream stream);
 
+/* Throughput probe (a project addition): what = 0 measures MUFU exp2 (ex2.approx) and
+ * what = 1 FP32 FFMA on the current device, as operations per second over the whole GPU
+ * (FFMA counted as 2 flops).  These bound the kernel product when D is small (one exp per
+ * kernel value) and are the denominators of its roofline.  Waits for the stream. */
+int itergp_probe_throughput(int32_t what, double* ops_per_s, itergp_stream stream);
+
 /* Library version "major.minor.patch". */
 const char* itergp_version(void);
 

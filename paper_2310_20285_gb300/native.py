@@ -140,6 +140,8 @@ def _load():
     lib.itergp_tune_clear.argtypes = []
     lib.itergp_selftest_wait.argtypes = [ct.c_uint64, vp]
     lib.itergp_selftest_wait.restype = ct.c_int
+    lib.itergp_probe_throughput.argtypes = [i32, ct.POINTER(ct.c_double), vp]
+    lib.itergp_probe_throughput.restype = ct.c_int
     for name in ("itergp_autotune", "itergp_tune_save", "itergp_tune_load", "itergp_tune_clear",
                  "itergp_kmatvec", "itergp_kmatvec_noalloc", "itergp_winv_apply", "itergp_pseudo_targets",
                  "itergp_sym_eig", "itergp_fit", "itergp_fit_batch", "itergp_predict",
@@ -415,6 +417,14 @@ def selftest_wait(limit_ns=20_000_000, stream=None):
     """Launch the bounded-wait self-test (a wait that runs out after limit_ns); the device
     status then reads ETIMEOUT (see sync_status)."""
     _check(lib.itergp_selftest_wait(int(limit_ns), _stream(stream)), "itergp_selftest_wait")
+
+
+def probe_throughput(what="ex2", stream=None) -> float:
+    """Measured operations per second of MUFU exp2 ("ex2") or FP32 FFMA ("ffma", flops)."""
+    out = ct.c_double()
+    _check(lib.itergp_probe_throughput({"ex2": 0, "ffma": 1}[what], ct.byref(out), _stream(stream)),
+           "itergp_probe_throughput")
+    return out.value
 
 
 def tune_save(path):
