@@ -102,6 +102,12 @@ DeviceContext* current_context() {
   }
   uint64_t threshold = UINT64_MAX;
   cudaMemPoolSetAttribute(c->pool, cudaMemPoolAttrReleaseThreshold, &threshold);
+  if (cudaStreamCreateWithFlags(&c->release, cudaStreamNonBlocking) != cudaSuccess) {
+    cudaMemPoolDestroy(c->pool);
+    cudaFree(c->status);
+    delete c;
+    return nullptr;
+  }
   g_ctx[dev] = c;
   return c;
 }
@@ -238,6 +244,10 @@ using namespace itergp;
 
 namespace itergp {
 
+// An entry point reports only its own CUDA failures: a runtime error left on this thread
+// by earlier, unrelated calls is cleared first (errors of the device are sticky and still
+// surface through the next call that touches it).
+void clear_stale_error() { (void)cudaGetLastError(); }
 
 int validate_fit_params(const itergp_fit_params* prm) {
   if (!prm) return ITERGP_EINVAL;
@@ -276,6 +286,7 @@ int64_t buffer_capacity(const itergp_fit_params& p) {
 void model_release(itergp_model* m, cudaStream_t s) {
   if (!m) return;
   if (m->mem) cudaFreeAsync(m->mem, s);
+  if (m->used) cudaEventDestroy(m->used);
   delete m;
 }
 
@@ -313,6 +324,7 @@ int fit_many(const itergp_fit_params* params, int count, itergp_model** out,
     mdl->kernel = prm.kernel;
     mdl->precision = prm.precision;
     mdl->likelihood = prm.likelihood;
+    if (cudaEventCreateWithFlags(&mdl->used, cudaEventDisableTiming) != cudaSuccess) mdl->used = nullptr;
     const size_t xb = align_up(sizeof(float) * n * prm.d, 256);
     const size_t rb = rows_workspace_bytes(prm.precision, n, static_cast<int>(prm.d));
     const size_t vb = align_up(sizeof(float) * nc, 256);
@@ -370,6 +382,7 @@ int fit_many(const itergp_fit_params* params, int count, itergp_model** out,
       continue;
     }
     models[i]->B = finalB[i];
+    if (models[i]->used) cudaEventRecord(models[i]->used, s);
     out[i] = models[i];
   }
   return ITERGP_OK;
@@ -443,6 +456,7 @@ int itergp_sync_status(itergp_stream stream) {
 int itergp_kmatvec(const itergp_kernel* kernel, int32_t precision, const float* A, int64_t m,
                    const float* B, int64_t n, int64_t d, const float* S, int64_t p, float* Y,
                    itergp_stream stream) {
+  clear_stale_error();
   if (!kernel_ok(kernel) || !precision_ok(precision)) return ITERGP_EINVAL;
   if (m < 0 || n < 0 || p < 0 || d < 1 || d > 4096 || p > 65536) return ITERGP_EINVAL;
   if (m == 0 || p == 0) return ITERGP_OK;
@@ -472,6 +486,7 @@ int itergp_kmatvec(const itergp_kernel* kernel, int32_t precision, const float* 
 
 int itergp_winv_apply(const float* f, int64_t n, int32_t c, const float* x, float* out,
                       itergp_stream stream) {
+  clear_stale_error();
   if (n < 0 || c < 2 || c > 64) return ITERGP_EINVAL;
   if (n > 0 && (!f || !x || !out)) return ITERGP_EINVAL;
   DeviceContext* ctx = current_context();
@@ -481,6 +496,7 @@ int itergp_winv_apply(const float* f, int64_t n, int32_t c, const float* x, floa
 
 int itergp_pseudo_targets(const float* f, const int32_t* y, int64_t n, int32_t c, float* out,
                           itergp_stream stream) {
+  clear_stale_error();
   if (n < 0 || c < 2 || c > 64) return ITERGP_EINVAL;
   if (n > 0 && (!f || !y || !out)) return ITERGP_EINVAL;
   DeviceContext* ctx = current_context();
@@ -489,6 +505,7 @@ int itergp_pseudo_targets(const float* f, const int32_t* y, int64_t n, int32_t c
 }
 
 int itergp_sym_eig(const double* M, int32_t b, double* lam, double* U, itergp_stream stream) {
+  clear_stale_error();
   if (b < 1 || b > 512 || !M || !lam || !U) return ITERGP_EINVAL;
   DeviceContext* ctx = current_context();
   if (!ctx) return ITERGP_ECUDA;
@@ -498,6 +515,7 @@ int itergp_sym_eig(const double* M, int32_t b, double* lam, double* U, itergp_st
 
 int itergp_fit(const itergp_fit_params* prm, itergp_model** out, itergp_fit_report* report,
                itergp_stream stream) {
+  clear_stale_error();
   if (!prm || !out) return ITERGP_EINVAL;
   *out = nullptr;
   const int rc = validate_fit_params(prm);
@@ -507,6 +525,7 @@ int itergp_fit(const itergp_fit_params* prm, itergp_model** out, itergp_fit_repo
 
 int itergp_fit_batch(const itergp_fit_params* params, int32_t count, itergp_model** models,
                      itergp_fit_report* reports, itergp_stream stream) {
+  clear_stale_error();
   if (!params || !models || count < 1 || count > 65535) return ITERGP_EINVAL;
   for (int i = 0; i < count; ++i) models[i] = nullptr;
   const itergp_fit_params& a = params[0];
@@ -526,6 +545,7 @@ int itergp_fit_batch(const itergp_fit_params* params, int32_t count, itergp_mode
 
 int itergp_predict(const itergp_model* mdl, const float* Xs, int64_t m, float* mean, float* var,
                    float* probs, itergp_stream stream) {
+  clear_stale_error();
   if (!mdl || m < 0 || (m > 0 && (!Xs || !mean))) return ITERGP_EINVAL;
   if (m == 0) return ITERGP_OK;
   DeviceContext* ctx = current_context();
@@ -557,10 +577,12 @@ int itergp_predict(const itergp_model* mdl, const float* Xs, int64_t m, float* m
   predict_epilogue_kernel<<<blocks, 256, 0, s>>>(Y, m, C, B, P, mdl->kernel.outputscale, mean, var, probs,
                                                  mdl->likelihood), ::itergp::note_launch();
   ITERGP_CUDA_TRY(cudaGetLastError());
+  if (mdl->used) ITERGP_CUDA_TRY(cudaEventRecord(mdl->used, s));   // the model's last use
   return ITERGP_OK;
 }
 
 int itergp_selftest_wait(uint64_t limit_ns, itergp_stream stream) {
+  clear_stale_error();
   if (limit_ns < 100000u || limit_ns > 5000000000ull) return ITERGP_EINVAL;
   DeviceContext* ctx = current_context();
   if (!ctx) return ITERGP_ECUDA;
@@ -569,6 +591,7 @@ int itergp_selftest_wait(uint64_t limit_ns, itergp_stream stream) {
 
 int itergp_autotune(const itergp_kernel* kernel, int32_t precision, int64_t n, int64_t d, int64_t p,
                     int32_t items, itergp_tune_result* result, itergp_stream stream) {
+  clear_stale_error();
   if (!kernel_ok(kernel) || !result || !precision_is_tensor(precision) || n < 128 || n > (int64_t(1) << 26) ||
       d < 1 || d > 4096 || p < 1 || p > (items ? 128 : 4096))
     return ITERGP_EINVAL;
@@ -624,9 +647,19 @@ void itergp_model_free(itergp_model* mdl) {
   int prev = -1;
   cudaGetDevice(&prev);
   if (prev != mdl->device) cudaSetDevice(mdl->device);
-  cudaDeviceSynchronize();   // no stream may still read the model
-  cudaFreeAsync(mdl->mem, cudaStreamLegacy);
-  cudaStreamSynchronize(cudaStreamLegacy);
+  // wait for the model's last fit or predict (an event recorded there), then free on the
+  // library's own non-blocking stream: no device-wide synchronisation, no legacy stream
+  // (either would break a stream capture that another thread has open)
+  if (mdl->used) {
+    cudaEventSynchronize(mdl->used);
+    cudaEventDestroy(mdl->used);
+  }
+  DeviceContext* ctx = current_context();
+  cudaStream_t rs = ctx ? ctx->release : nullptr;
+  if (mdl->mem) {
+    cudaFreeAsync(mdl->mem, rs);
+    cudaStreamSynchronize(rs);
+  }
   if (prev >= 0 && prev != mdl->device) cudaSetDevice(prev);
   delete mdl;
 }

@@ -87,6 +87,7 @@ struct DeviceContext {
   size_t smem_optin = 0;
   int* status = nullptr;           // device int: 0 = OK, else itergp_status
   cudaMemPool_t pool = nullptr;
+  cudaStream_t release = nullptr;  // non-blocking stream for stream-ordered frees
   bool tcgen05 = false;            // sm_100 family with tcgen05 / TMA
 };
 

@@ -134,6 +134,7 @@ int fit_run_batch(DeviceContext* ctx, const std::vector<FitProblem>& probs, cuda
 
 // ---------------------------------------------------------------- models (api.cu)
 int validate_fit_params(const itergp_fit_params* prm);
+void clear_stale_error();
 // Buffer columns a fit keeps at most: min(max_newton * max_iters, R + max_iters, N C).
 int64_t buffer_capacity(const itergp_fit_params& p);
 // Fits params[0..count) with one schedule (allocating the models from the library pool on
@@ -179,6 +180,7 @@ struct itergp_model {
   int precision = 0;
   int likelihood = ITERGP_LIK_SOFTMAX;
   void* mem = nullptr;
+  cudaEvent_t used = nullptr;   // recorded after the model's last fit / predict
   float* X = nullptr;
   float* v = nullptr;
   float* f = nullptr;

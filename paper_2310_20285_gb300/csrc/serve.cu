@@ -772,17 +772,43 @@ int itergp_server_create(const itergp_server_config* cfg, itergp_server** out) {
     o_x = take(sizeof(float) * R * cfg->d_max);
     o_w = take(sizeof(float) * R * kWeightRows);
   }
-  if (cudaMalloc(&srv->slab, off) != cudaSuccess) {
+  // every allocation and copy of the server is stream-ordered on its own non-blocking
+  // streams (a synchronising call would break stream captures that other threads have open)
+  if (cudaStreamCreateWithFlags(&srv->fit_stream, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&srv->pred_stream, cudaStreamNonBlocking) != cudaSuccess) {
+    if (srv->fit_stream) cudaStreamDestroy(srv->fit_stream);
     delete srv;
-    return ITERGP_ENOMEM;
+    return ITERGP_ECUDA;
+  }
+  auto fail = [&](int code) {
+    if (srv->slab) {
+      cudaFreeAsync(srv->slab, srv->fit_stream);
+      cudaStreamSynchronize(srv->fit_stream);
+    }
+    cudaStreamDestroy(srv->fit_stream);
+    cudaStreamDestroy(srv->pred_stream);
+    delete srv;
+    return code;
+  };
+  if (cudaMallocFromPoolAsync(&srv->slab, off, ctx->pool, srv->fit_stream) != cudaSuccess) {
+    srv->slab = nullptr;
+    return fail(ITERGP_ENOMEM);
   }
   char* b = static_cast<char*>(srv->slab);
   // zero once: rows never written by a model (free blocks) are never read, but weights
   // beyond a model's columns must read as zeros
-  if (cudaMemset(srv->slab, 0, off) != cudaSuccess) {
-    cudaFree(srv->slab);
-    delete srv;
-    return ITERGP_ECUDA;
+  if (cudaMemsetAsync(srv->slab, 0, off, srv->fit_stream) != cudaSuccess ||
+      cudaStreamSynchronize(srv->fit_stream) != cudaSuccess)
+    return fail(ITERGP_ECUDA);
+  // predict staging at its largest size now: no pinned reallocation while running
+  {
+    const int64_t rows = cfg->max_predict_rows + 128LL * cfg->max_predict_batch;
+    const size_t tabs = static_cast<size_t>(rows / 128 + cfg->max_predict_batch) * sizeof(WorkItem) * 2 +
+                        static_cast<size_t>(cfg->max_predict_batch) * (2 * sizeof(TcProb) + 64) +
+                        static_cast<size_t>(ctx->num_sms + 1) * 8 + 64 * 1024;
+    if (!srv->pred_pin.reserve(sizeof(float) * rows * cfg->d_max + tabs) ||
+        !srv->pred_out_pin.reserve(sizeof(float) * 3 * cfg->max_predict_rows * cfg->c_max))
+      return fail(ITERGP_ENOMEM);
   }
   RowOperand& op = srv->rows_op;
   op.rows = R;
@@ -805,12 +831,6 @@ int itergp_server_create(const itergp_server_config* cfg, itergp_server** out) {
   }
   srv->blocks.init(R);
   srv->stats.slab_rows = R;
-  if (cudaStreamCreateWithFlags(&srv->fit_stream, cudaStreamNonBlocking) != cudaSuccess ||
-      cudaStreamCreateWithFlags(&srv->pred_stream, cudaStreamNonBlocking) != cudaSuccess) {
-    cudaFree(srv->slab);
-    delete srv;
-    return ITERGP_ECUDA;
-  }
   srv->fit_thr = std::thread([srv] { srv->fit_loop(); });
   srv->pred_thr = std::thread([srv] { srv->pred_loop(); });
   *out = srv;
@@ -832,11 +852,11 @@ int itergp_server_destroy(itergp_server* srv) {
   srv->cv_pred.notify_all();
   if (srv->fit_thr.joinable()) srv->fit_thr.join();
   if (srv->pred_thr.joinable()) srv->pred_thr.join();
-  cudaStreamSynchronize(srv->fit_stream);
   cudaStreamSynchronize(srv->pred_stream);
+  cudaFreeAsync(srv->slab, srv->fit_stream);   // stream-ordered, after the last fit
+  cudaStreamSynchronize(srv->fit_stream);
   cudaStreamDestroy(srv->fit_stream);
   cudaStreamDestroy(srv->pred_stream);
-  cudaFree(srv->slab);
   delete srv;
   return ITERGP_OK;
 }
