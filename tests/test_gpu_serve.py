@@ -147,3 +147,26 @@ def test_a_bad_fit_fails_alone(native):
     rid = srv.submit_predict(ids[2], probs[2].Xs)
     assert drain(srv, 1)[rid][3] == native.OK
     srv.close()
+
+
+def test_library_calls_on_other_threads_do_not_disturb_server_captures(native):
+    """While the server's threads capture and launch fit graphs, the main thread keeps
+    fitting, predicting and freeing models on the legacy stream: every request on both
+    sides succeeds (model release waits on an event and frees on a library stream; no
+    call synchronises the whole device)."""
+    probs = problems(12, seed=31, n_lo=300, n_hi=900)
+    srv = native.Server(model_bytes=GB, work_bytes=4 * GB, precision="bf16x3", d_max=16, c_max=5,
+                        max_fit_batch=2, **SCHED)
+    ids = [srv.submit_fit(p.X, p.y, p.c, p.lengthscale, 1.0) for p in probs]
+    local = problems(6, seed=32, n_lo=200, n_hi=400)
+    for p in local:
+        m = native.fit(torch.as_tensor(p.X, device=DEV), torch.as_tensor(p.y, device=DEV), p.c,
+                       kind="rbf", lengthscale=p.lengthscale, precision="fp32", max_newton=2,
+                       max_iters=4, rank=8)
+        mean, _, _ = m.predict(torch.as_tensor(p.Xs, device=DEV))
+        assert torch.isfinite(mean).all()
+        m.free()
+    ev = drain(srv, len(ids))
+    assert all(ev[i][3] == native.OK for i in ids), [ev[i][3] for i in ids]
+    srv.close()
+    assert native.sync_status() == native.OK
