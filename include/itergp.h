@@ -190,7 +190,9 @@ typedef struct {
                              in Alg. 2 (two per iteration, plus f_{i+1} = K v + m)  */
   double tol_newton;      /* outer stop on |g_i - g_{i-1}| / |g_i| <= tol (<= 0: off)*/
   double tol_abs;         /* inner stop, absolute (paper default 1e-5)             */
-  double tol_rel;         /* inner stop, relative to |y_hat - m| (default 1e-5)     */
+  double tol_rel;         /* inner stop, relative to |y_hat - m| (default 1e-5); the
+                             BF16 and BF16_COMP precisions also stop at 2^-8 |y_hat - m|,
+                             the rounding level of their products                   */
   int32_t graph;          /* 1: capture the whole fit into one CUDA graph and launch
                              it (fewer launch overheads); 0: launch kernels directly */
   const float* f0;        /* device, n x c starting iterate, or NULL for f_0 = m = 0

@@ -19,6 +19,7 @@ struct KParams {
   float s;       // outputscale
   float c_exp;   // RBF: -log2(e) / (2 l^2)          Matern: unused
   float c_u;     // Matern: sqrt(3) / l               RBF: unused
+  float log2s;   // log2(s): RBF values as 2^(c_exp r^2 + log2 s) in the tensor-core epilogue
 };
 
 inline KParams make_kparams(const itergp_kernel& k) {
@@ -28,6 +29,7 @@ inline KParams make_kparams(const itergp_kernel& k) {
   const double l = k.lengthscale;
   p.c_exp = static_cast<float>(-1.4426950408889634 / (2.0 * l * l));
   p.c_u = static_cast<float>(1.7320508075688772 / l);
+  p.log2s = static_cast<float>(std::log2(static_cast<double>(k.outputscale)));
   return p;
 }
 

@@ -440,6 +440,7 @@ kmv_tc_kernel(const __grid_constant__ CUtensorMap mAh, const __grid_constant__ C
     float na_r = 0.f;
     int64_t grow = 0;
     KParams kp = args.kp;
+    float rowc = 0.f;   // RBF: c_exp |a|^2 + log2 s of this thread's row
     const int J = args.chunks;
     float* out_row = nullptr;       // item mode: this row's output
     bool out_valid = false;
@@ -474,11 +475,13 @@ kmv_tc_kernel(const __grid_constant__ CUtensorMap mAh, const __grid_constant__ C
           out_row = pr.Y + prow * pr.ldY + args.p_col0;
           out_lim = pr.p_valid - args.p_col0;   // <= 0: nothing of this tile to write
         }
+        rowc = fmaf(kp.c_exp, na_r, kp.log2s);
       }
       float* nb_s = nb_all + e * BN;
       __syncwarp();
+      // RBF stages c_exp |b|^2 (the column term of the exponent), Matern |b|^2
 #pragma unroll
-      for (int k = 0; k < BN / 32; ++k) nb_s[lane + 32 * k] = nb_next[k];
+      for (int k = 0; k < BN / 32; ++k) nb_s[lane + 32 * k] = KIND == ITERGP_RBF ? kp.c_exp * nb_next[k] : nb_next[k];
       __syncwarp();
       wkn.next();
       if (t + 1 < T) {
@@ -501,17 +504,39 @@ kmv_tc_kernel(const __grid_constant__ CUtensorMap mAh, const __grid_constant__ C
         const bool more = grp + 1 < grp1;   // warp-uniform
         if (more) tmem_ld32(gcol + 32 * (grp + 1), vn);
         uint32_t ph[16], pl[16];
+        if (KIND == ITERGP_RBF) {
+          // k = s 2^(c_exp r^2) = 2^t, t = c_exp (|a|^2 + |b|^2 - 2 a.b) + log2 s, formed two
+          // lanes at a time; r^2 >= 0 is t <= log2 s (c_exp < 0)
+          const uint64_t m2c = f2_pack(-2.f * kp.c_exp, -2.f * kp.c_exp);
+          const uint64_t rc2 = f2_pack(rowc, rowc);
+          const float* cnb = nb_s + 32 * grp;
 #pragma unroll
-        for (int i = 0; i < 16; ++i) {
-          const float r0 = fmaxf(fmaf(-2.f, __uint_as_float(v[2 * i]), na_r + nb_s[32 * grp + 2 * i]), 0.f);
-          const float r1 = fmaxf(fmaf(-2.f, __uint_as_float(v[2 * i + 1]), na_r + nb_s[32 * grp + 2 * i + 1]), 0.f);
-          const float k0 = kernel_eval_fast<KIND>(r0, kp);
-          const float k1 = kernel_eval_fast<KIND>(r1, kp);
-          ph[i] = pack_bf16x2(k0, k1);
-          if (NT2 == 3) {
-            const float h0 = __uint_as_float(ph[i] << 16);
-            const float h1 = __uint_as_float(ph[i] & 0xFFFF0000u);
-            pl[i] = pack_bf16x2(k0 - h0, k1 - h1);
+          for (int i = 0; i < 16; ++i) {
+            const float2 cb = *reinterpret_cast<const float2*>(cnb + 2 * i);
+            const uint64_t t2 = f2_fma(f2_pack(__uint_as_float(v[2 * i]), __uint_as_float(v[2 * i + 1])), m2c,
+                                       f2_add(f2_pack(cb.x, cb.y), rc2));
+            const float k0 = ex2_approx(fminf(f2_lo(t2), kp.log2s));
+            const float k1 = ex2_approx(fminf(f2_hi(t2), kp.log2s));
+            ph[i] = pack_bf16x2(k0, k1);
+            if (NT2 == 3) {
+              const uint64_t hh = f2_pack(__uint_as_float(ph[i] << 16), __uint_as_float(ph[i] & 0xFFFF0000u));
+              const uint64_t lo2 = f2_sub(f2_pack(k0, k1), hh);
+              pl[i] = pack_bf16x2(f2_lo(lo2), f2_hi(lo2));
+            }
+          }
+        } else {
+#pragma unroll
+          for (int i = 0; i < 16; ++i) {
+            const float r0 = fmaxf(fmaf(-2.f, __uint_as_float(v[2 * i]), na_r + nb_s[32 * grp + 2 * i]), 0.f);
+            const float r1 = fmaxf(fmaf(-2.f, __uint_as_float(v[2 * i + 1]), na_r + nb_s[32 * grp + 2 * i + 1]), 0.f);
+            const float k0 = kernel_eval_fast<KIND>(r0, kp);
+            const float k1 = kernel_eval_fast<KIND>(r1, kp);
+            ph[i] = pack_bf16x2(k0, k1);
+            if (NT2 == 3) {
+              const float h0 = __uint_as_float(ph[i] << 16);
+              const float h1 = __uint_as_float(ph[i] & 0xFFFF0000u);
+              pl[i] = pack_bf16x2(k0 - h0, k1 - h1);
+            }
           }
         }
         tmem_st16(gcol + 32 * grp, ph);

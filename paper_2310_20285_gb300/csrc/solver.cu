@@ -205,7 +205,7 @@ __global__ void newton_prologue_kernel(const ProbDev* __restrict__ probs, int pr
 
 __global__ void newton_finalize_kernel(const ProbDev* __restrict__ probs, int nblk, int step,
                                        double tol_newton, double tol_abs, double tol_rel,
-                                       int recycle) {
+                                       int recycle, double floor_rel) {
   const ProbDev& P = probs[blockIdx.x];
   FitState* st = P.st;
   const double* __restrict__ part = P.ps;
@@ -232,7 +232,10 @@ __global__ void newton_finalize_kernel(const ProbDev* __restrict__ probs, int nb
     }
   }
   st->bnorm = sqrt(s[0]);
-  st->thresh = fmax(tol_abs, tol_rel * st->bnorm);
+  // App. B.2: |r| < max(tol_abs, tol_rel |b|); with BF16 products (2^-9 relative) the
+  // solve also stops at their rounding level floor_rel |b|, below which the residual
+  // actions are rounding noise
+  st->thresh = fmax(fmax(tol_abs, tol_rel * st->bnorm), floor_rel * st->bnorm);
   st->j = 0;
   st->pending = 0;
   st->active = 1;
@@ -1048,6 +1051,9 @@ int fit_run_batch(DeviceContext* ctx, const std::vector<FitProblem>& probs, cuda
   // the class-contrast projection belongs to the softmax likelihood (one latent per
   // point has no class-sum directions)
   const int project = prm.policy == ITERGP_POLICY_CG && prm.likelihood == ITERGP_LIK_SOFTMAX ? 1 : 0;
+  // the BF16 forms round kernel values (and weights) to 8 bits: residuals below 2^-8 |b|
+  // are not resolved (FP32 and the BF16X3 split resolve far below the paper's 1e-5)
+  const double floor_rel = (prm.precision == ITERGP_BF16 || prm.precision == ITERGP_BF16_COMP) ? 0x1p-8 : 0.0;
   int64_t max_n = 0, max_nc = 0;
   int max_bcap = 1, c_max = 2, d_max = 1;
   for (const FitProblem& fp : probs) {
@@ -1276,7 +1282,8 @@ int fit_run_batch(DeviceContext* ctx, const std::vector<FitProblem>& probs, cuda
   int rc = ITERGP_OK;
   for (int step = 0; step < prm.max_newton && rc == ITERGP_OK; ++step) {
     newton_prologue_kernel<<<dim3(nblk, np), kRedThreads, 0, stream>>>(pdev, project), ::itergp::note_launch();
-    newton_finalize_kernel<<<np, 32, 0, stream>>>(pdev, nblk, step, prm.tol_newton, prm.tol_abs, prm.tol_rel, prm.recycle), ::itergp::note_launch();
+    newton_finalize_kernel<<<np, 32, 0, stream>>>(pdev, nblk, step, prm.tol_newton, prm.tol_abs, prm.tol_rel,
+                                                  prm.recycle, floor_rel), ::itergp::note_launch();
     // ---- Alg. 3: virtual solver run with compression
     if (prm.recycle && step > 0) {
       copy_int_kernel<<<np, 32, 0, stream>>>(pdev), ::itergp::note_launch();
