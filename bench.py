@@ -500,6 +500,20 @@ def main():
     e1.record()
     barrier()
     t_e2e = e0.elapsed_time(e1) / 1e3 / e2e_steps
+    # where an end-to-end step spends its time: one more (untimed) step with events between
+    # its host-to-device copies, the product and the device-to-host copy
+    seg = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    seg[0].record()
+    dX.copy_(hX, non_blocking=True)
+    dS.copy_(hS, non_blocking=True)
+    seg[1].record()
+    native.kmatvec(dX, dX, dS, kind="matern32", lengthscale=ELL, outputscale=OUT,
+                   precision=args.precision, out=dY)
+    seg[2].record()
+    hY.copy_(dY, non_blocking=True)
+    seg[3].record()
+    seg[3].synchronize()
+    h2d_ms, prod_ms, d2h_ms = (seg[i].elapsed_time(seg[i + 1]) for i in range(3))
     if world > 1:
         tt = torch.tensor([t_e2e], device=dev, dtype=torch.float64)
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
@@ -538,7 +552,10 @@ def main():
            "roofline": roof, "clocks": clk, "gpu_launches": int(launches), "tuning": tuning,
            "e2e": {"value": world * n * n / t_e2e, "unit": "kernel-pairs/s",
                    "h2d_bytes_per_step": int(hX.numel() * 4 + hS.numel() * 4),
-                   "d2h_bytes_per_step": int(hY.numel() * 4), "ms_per_step": t_e2e * 1e3}}
+                   "d2h_bytes_per_step": int(hY.numel() * 4), "ms_per_step": t_e2e * 1e3,
+                   "breakdown_ms": {"h2d": h2d_ms, "product": prod_ms, "d2h": d2h_ms},
+                   "h2d_gbs": (hX.numel() + hS.numel()) * 4 / (h2d_ms * 1e6),
+                   "d2h_gbs": hY.numel() * 4 / (d2h_ms * 1e6)}}
 
     if rank == 0 and not args.no_extras:
         paths = {}
