@@ -520,6 +520,9 @@ def main():
         t_e2e = float(tt.item())
 
     pk, pk_kind = peaks()
+    # what one CTA per SM gets from tcgen05.mma in the distance GEMM's shape (SS, M = N = 128,
+    # K = 16, issued back to back): the ceiling of the tile shape, probed here
+    mma_ceiling = native.probe_throughput("mma_ss_n128") / 1e12
     flops = 2.0 * n * n * (D + P)
     kernel_s = (kern_ms / max(kern_n, 1)) / 1e3
     achieved = flops / kernel_s / 1e12
@@ -538,7 +541,9 @@ def main():
             "frac_of_sustained": achieved / pk.get("bf16_tflops_sustained", pk["bf16_tflops"]),
             "kernel": "kmv_tc_kernel", "kernel_ms": kernel_s * 1e3,
             "algorithmic_flops_per_launch": flops,
-            "tensor_flops_issued_per_launch": flops * (3.0 if args.precision == "bf16x3" else 1.0)}
+            "tensor_flops_issued_per_launch": flops * (3.0 if args.precision == "bf16x3" else 1.0),
+            "mma_shape_ceiling_tflops": mma_ceiling,
+            "issued_frac_of_mma_shape_ceiling": achieved * (3.0 if args.precision == "bf16x3" else 1.0) / mma_ceiling}
 
     out = {"metric": METRIC, "value": value, "unit": "kernel-pairs/s", "n_gpus": world,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_max * 1e3,

@@ -416,10 +416,15 @@ int itergp_tune_clear(void);
  * returns; the context stays usable.  No fault, trap or hang is involved. */
 int itergp_selftest_wait(uint64_t limit_ns, itergp_stream stream);
 
-/* Throughput probe (a project addition): what = 0 measures MUFU exp2 (ex2.approx) and
- * what = 1 FP32 FFMA on the current device, as operations per second over the whole GPU
- * (FFMA counted as 2 flops).  These bound the kernel product when D is small (one exp per
- * kernel value) and are the denominators of its roofline.  Waits for the stream. */
+/* Throughput probe (a project addition): operations per second over the whole GPU on the
+ * current device.  what = 0: MUFU exp2 (ex2.approx); 1: FP32 FFMA (2 flops each); these
+ * bound the kernel product when D is small (one exp per kernel value).  what = 2..5: BF16
+ * tcgen05.mma flops (FP32 accumulate, K = 16 per instruction, one CTA per SM issuing
+ * back to back) in the shapes the product issues: 2 = SS M = 128, N = 128 (the distance
+ * GEMM); 3 = SS M = 128, N = 256; 4 = as 2 while four other warps stream tcgen05.ld (the
+ * epilogue's reads); 5 = TS (A from TMEM) M = 128, N = 80 (the weighted sum).  Returns
+ * ITERGP_EINVAL for another `what`; a probe wait that exceeds its 2 s bound is reported
+ * through itergp_sync_status.  Waits for the stream. */
 int itergp_probe_throughput(int32_t what, double* ops_per_s, itergp_stream stream);
 
 /* Library version "major.minor.patch". */

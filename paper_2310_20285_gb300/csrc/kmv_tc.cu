@@ -77,12 +77,97 @@ struct TcArgs {
 __host__ __device__ constexpr uint32_t stage_bytes(int nt1) {
   return (nt1 == 3 ? 2u : 1u) * (BM * BK * 2u) + (nt1 == 3 ? 2u : 1u) * (BN * BK * 2u);
 }
+// Split arrival: with a two-stage ring of split rows the stage's arrival is on the critical
+// path, so its hi halves are tracked by their own barrier and the hi.hi MMAs start as soon
+// as they land (measured faster there; with deeper rings the extra wait costs more than it
+// saves).
+__host__ __device__ constexpr bool split_arrival(int nt1, int nstage, bool ares) {
+  return nt1 == 3 && nstage == 2 && !ares;
+}
 __host__ __device__ constexpr uint32_t s_box_bytes(int p_pad) { return static_cast<uint32_t>(p_pad) * 128u; }
 __host__ __device__ constexpr uint32_t s_buf_bytes(int nt2, int p_pad) {
   return 2u * s_box_bytes(p_pad) * (nt2 == 3 ? 2u : 1u);
 }
 // alignment slack + per-epilogue-warp staging of 128 column norms
 __host__ __device__ constexpr uint32_t smem_extra(int epi) { return 1024u + static_cast<uint32_t>(epi) * 512u; }
+
+// Out-of-line slow path of a bounded mbarrier wait (the fast path is one try_wait).
+__device__ __noinline__ bool mbar_wait_slow(uint64_t* bar, uint32_t parity, volatile int* abort_flag,
+                                            uint64_t limit_ns) {
+  return mbar_wait(bar, parity, abort_flag, limit_ns);
+}
+
+// GEMM1 of one chunk: G = A . B^T over the nk D slices of the stage ring (12 MMAs per
+// slice for split rows: hi.hi + hi.lo + lo.hi, K = 16 each), releasing each stage to the
+// producer with a commit.  `pos` packs the ring position (stage | phase << 8); returns the
+// position after the chunk, or -1 if a wait gave up.  A small out-of-line function: the
+// issuing thread must keep up with one MMA every few dozen cycles.
+template <int NT1, int NSTAGE, bool ARES>
+__device__ __noinline__ int issue_gemm1(uint32_t gt, int nk, uint64_t dStage0, uint64_t dAres, uint64_t* full_bar,
+                                        uint64_t* full_lo, uint64_t* empty_bar, volatile int* ab, uint32_t idesc1,
+                                        int pos) {
+  constexpr uint32_t A_PART = BM * BK * 2, B_PART = BN * BK * 2;
+  constexpr uint32_t SB = ARES ? (NT1 == 3 ? 2u : 1u) * B_PART : stage_bytes(NT1);
+  constexpr bool SPLIT = split_arrival(NT1, NSTAGE, ARES);
+  int stage = pos & 0xFF;
+  uint32_t phase = static_cast<uint32_t>(pos >> 8);
+  for (int ks = 0; ks < nk; ++ks) {
+    // operands arrive by TMA with completion on the mbarrier (async proxy on both sides):
+    // no tcgen05 fence is needed here
+    if (!mbar_wait(&full_bar[stage], phase, ab, kWaitLimitNs)) return -1;
+    const uint64_t dSt = dStage0 + static_cast<uint64_t>(stage) * (SB >> 4);
+    const uint64_t dAh = ARES ? dAres : dSt;
+    const uint64_t dBh = ARES ? dSt : dSt + ((NT1 == 3 ? 2 : 1) * A_PART >> 4);
+    const uint64_t dAl = dAh + (A_PART >> 4);
+    const uint64_t dBl = dBh + (B_PART >> 4);
+    // one MMA order for every ring, so that all launch variants give bitwise the same
+    // product: the slice's hi.hi terms, then its correction terms hi.lo and lo.hi
+#pragma unroll
+    for (int kk = 0; kk < BK / 16; ++kk) mma_ss(gt, dAh + 2 * kk, dBh + 2 * kk, idesc1, (ks | kk) != 0 ? 1u : 0u);
+    if (NT1 == 3) {
+      if (SPLIT && !mbar_wait(&full_lo[stage], phase, ab, kWaitLimitNs)) return -1;
+#pragma unroll
+      for (int kk = 0; kk < BK / 16; ++kk) {
+        mma_ss(gt, dAh + 2 * kk, dBl + 2 * kk, idesc1, 1u);
+        mma_ss(gt, dAl + 2 * kk, dBh + 2 * kk, idesc1, 1u);
+      }
+    }
+    mma_commit(&empty_bar[stage]);
+    if (++stage == NSTAGE) {
+      stage = 0;
+      phase ^= 1u;
+    }
+  }
+  return stage | static_cast<int>(phase << 8);
+}
+
+// GEMM2 of one chunk: O (+)= P . S with P (the chunk's kernel values, BF16 hi/lo pairs
+// packed in the G buffer's TMEM columns) as the A operand and the chunk's transposed
+// weights from shared memory as B; 8 K steps of 16 rows, 3 MMAs each for split weights.
+// Waits for the epilogue's P (pfull) and the weight tile (sfull); releases the weight tile
+// (sempty) and, at the end of a flush group, hands O to the epilogue (ofull).
+template <int NT2>
+__device__ __noinline__ bool issue_gemm2(uint32_t tb, int gb, uint32_t par, bool first, bool last, uint64_t* pfull_b,
+                                         uint64_t* sfull_b, uint64_t* sempty_b, uint64_t* ofull_b,
+                                         volatile int* ab, uint64_t dS0, uint64_t sbox16, uint32_t idesc2) {
+  if (!mbar_try_wait(pfull_b, par) && !mbar_wait(pfull_b, par, ab, kWaitLimitNs)) return false;
+  if (!mbar_try_wait(sfull_b, par) && !mbar_wait(sfull_b, par, ab, kWaitLimitNs)) return false;
+  tc_fence_after();   // P was written by the epilogue's tcgen05.st
+#pragma unroll
+  for (int ks2 = 0; ks2 < BN / 16; ++ks2) {
+    const int grp = ks2 >> 1, h = ks2 & 1;
+    const uint32_t a_hi = tb + static_cast<uint32_t>(gb * BN + 32 * grp + 8 * h);
+    const uint64_t dSh = dS0 + static_cast<uint64_t>(ks2 >> 2) * sbox16 + static_cast<uint64_t>((ks2 & 3) * 2);
+    mma_ts(tb + kOCol, a_hi, dSh, idesc2, (first && ks2 == 0) ? 0u : 1u);
+    if (NT2 == 3) {
+      mma_ts(tb + kOCol, a_hi, dSh + 2 * sbox16, idesc2, 1u);
+      mma_ts(tb + kOCol, a_hi + 16, dSh, idesc2, 1u);
+    }
+  }
+  mma_commit(sempty_b);
+  if (last) mma_commit(ofull_b);
+  return true;
+}
 
 // Per-CTA sequence of (row tile, chunk) steps of the partition described above.
 struct Schedule {
@@ -205,13 +290,16 @@ kmv_tc_kernel(const __grid_constant__ CUtensorMap mAh, const __grid_constant__ C
   constexpr uint32_t A_PART = BM * BK * 2, B_PART = BN * BK * 2;
   constexpr uint32_t A_BYTES = (NT1 == 3 ? 2u : 1u) * A_PART;   // resident A (ARES)
   constexpr uint32_t SB = ARES ? (NT1 == 3 ? 2u : 1u) * B_PART : stage_bytes(NT1);
+  constexpr bool SPLIT = split_arrival(NT1, NSTAGE, ARES);
   const uint32_t SBOX = s_box_bytes(args.p_pad);
   const uint32_t SBUF = s_buf_bytes(NT2, args.p_pad);
   uint8_t* a_region = smem + NSTAGE * SB;                        // ARES only
   uint8_t* s_region = a_region + (ARES ? A_BYTES : 0u);
   float* nb_all = reinterpret_cast<float*>(s_region + 2 * SBUF);   // [EPI warps][128]
 
-  __shared__ __align__(8) uint64_t full_bar[NSTAGE], empty_bar[NSTAGE];
+  // full_bar: a whole stage, or with split arrival its hi halves (A_hi and B_hi, enough for
+  // the hi.hi MMAs) while full_lo tracks the lo halves
+  __shared__ __align__(8) uint64_t full_bar[NSTAGE], full_lo[NSTAGE], empty_bar[NSTAGE];
   __shared__ __align__(8) uint64_t gfull[2], pfull[2], sfull[2], sempty[2], ofull, oempty, drain;
   __shared__ __align__(8) uint64_t afull, aempty;               // resident A (ARES)
   __shared__ uint32_t tmem_base_s;
@@ -222,6 +310,7 @@ kmv_tc_kernel(const __grid_constant__ CUtensorMap mAh, const __grid_constant__ C
     abort_s = 0;
     for (int i = 0; i < NSTAGE; ++i) {
       mbar_init(&full_bar[i], 1);
+      mbar_init(&full_lo[i], 1);
       mbar_init(&empty_bar[i], 1);
     }
     for (int i = 0; i < 2; ++i) {
@@ -290,15 +379,19 @@ kmv_tc_kernel(const __grid_constant__ CUtensorMap mAh, const __grid_constant__ C
         }
         for (int ks = 0; !ARES && ks < args.nk; ++ks) {
           if (!mbar_wait(&empty_bar[stage], phase ^ 1u, ab, kWaitLimitNs)) break;
-          mbar_arrive_expect_tx(&full_bar[stage], SB);
+          uint64_t* lo_bar = SPLIT ? &full_lo[stage] : &full_bar[stage];
+          mbar_arrive_expect_tx(&full_bar[stage], SPLIT ? A_PART + B_PART : SB);
+          if (SPLIT) mbar_arrive_expect_tx(lo_bar, A_PART + B_PART);
           armed |= 1u << stage;
           armed_par = (armed_par & ~(1u << stage)) | (phase << stage);
           uint8_t* base = smem + stage * SB;
-          tma_load_2d(base, &mAh, &full_bar[stage], ks * BK, a_y);
-          if (NT1 == 3) tma_load_2d(base + A_PART, &mAl, &full_bar[stage], ks * BK, a_y);
           uint8_t* bbase = base + (NT1 == 3 ? 2 : 1) * A_PART;
+          tma_load_2d(base, &mAh, &full_bar[stage], ks * BK, a_y);
           tma_load_2d(bbase, &mBh, &full_bar[stage], ks * BK, b_y);
-          if (NT1 == 3) tma_load_2d(bbase + B_PART, &mBl, &full_bar[stage], ks * BK, b_y);
+          if (NT1 == 3) {
+            tma_load_2d(base + A_PART, &mAl, lo_bar, ks * BK, a_y);
+            tma_load_2d(bbase + B_PART, &mBl, lo_bar, ks * BK, b_y);
+          }
           if (++stage == NSTAGE) {
             stage = 0;
             phase ^= 1u;
@@ -321,7 +414,10 @@ kmv_tc_kernel(const __grid_constant__ CUtensorMap mAh, const __grid_constant__ C
       if (*ab) {
         // let every load this thread issued land before the CTA can exit
         for (int i = 0; i < NSTAGE; ++i)
-          if (armed & (1u << i)) mbar_wait_drain(&full_bar[i], (armed_par >> i) & 1u, kWaitLimitNs);
+          if (armed & (1u << i)) {
+            mbar_wait_drain(&full_bar[i], (armed_par >> i) & 1u, kWaitLimitNs);
+            if (SPLIT) mbar_wait_drain(&full_lo[i], (armed_par >> i) & 1u, kWaitLimitNs);
+          }
         for (int i = 0; i < 2; ++i)
           if (s_armed & (1u << i)) mbar_wait_drain(&sfull[i], (s_par >> i) & 1u, kWaitLimitNs);
         if (a_armed) mbar_wait_drain(&afull, a_par, kWaitLimitNs);
@@ -332,10 +428,20 @@ kmv_tc_kernel(const __grid_constant__ CUtensorMap mAh, const __grid_constant__ C
     if (lane == 0) {
       const uint32_t idesc1 = idesc_bf16_f32(BM, BN);
       const uint32_t idesc2 = idesc_bf16_f32(BM, static_cast<uint32_t>(args.p_pad));
+      // shared-memory descriptors of stage 0, the resident A and the weight buffers; the
+      // start-address field (bits 0-13, 16-byte units) takes offsets by plain addition
+      // because every operand lies below 256 KB of the shared window
+      const uint64_t dStage0 = sdesc_kmajor_sw128(smem_u32(smem));
+      const uint64_t dAres = sdesc_kmajor_sw128(smem_u32(a_region));
+      const uint64_t dS_base = sdesc_kmajor_sw128(smem_u32(s_region));
+      const uint64_t sbox16 = SBOX >> 4;
       int stage = 0;
       uint32_t phase = 0;
       int64_t sub = -1;
       bool ok = true;
+      // The issuing thread has to keep up with one MMA every few dozen cycles, so the hot
+      // loop holds only the fast path of each wait; slow waits and the weighted-sum GEMM2
+      // are out-of-line calls (inlined, they measurably slowed the issue of GEMM1).
       Walker wk2 = walk0;   // lags the GEMM1 loop by one step
       auto gemm2 = [&](int64_t t) -> bool {
         const StepInfo st = wk2.cur();
@@ -345,35 +451,17 @@ kmv_tc_kernel(const __grid_constant__ CUtensorMap mAh, const __grid_constant__ C
         const bool last = st.last || ((c + 1) % kFlushChunks == 0);
         if (first) {
           ++sub;
-          if (sub >= 1 && !mbar_wait(&oempty, static_cast<uint32_t>((sub - 1) & 1), ab, kWaitLimitNs))
+          if (sub >= 1 && !mbar_wait_slow(&oempty, static_cast<uint32_t>((sub - 1) & 1), ab, kWaitLimitNs))
             return false;
         }
         const int gb = static_cast<int>(t & 1);
-        const uint32_t par = static_cast<uint32_t>((t >> 1) & 1);
-        if (!mbar_wait(&pfull[gb], par, ab, kWaitLimitNs)) return false;
-        if (!mbar_wait(&sfull[gb], par, ab, kWaitLimitNs)) return false;
-        tc_fence_after();
-        const uint32_t sbase = smem_u32(s_region + gb * SBUF);
-#pragma unroll
-        for (int ks2 = 0; ks2 < BN / 16; ++ks2) {
-          const int grp = ks2 >> 1, h = ks2 & 1;
-          const uint32_t a_hi = tb + gb * BN + 32 * grp + 8 * h;
-          const uint32_t boff = static_cast<uint32_t>(ks2 >> 2) * SBOX;
-          const uint64_t koff = static_cast<uint64_t>((ks2 & 3) * 32) >> 4;
-          const uint64_t dSh = sdesc_kmajor_sw128(sbase + boff) + koff;
-          mma_ts(tb + kOCol, a_hi, dSh, idesc2, (first && ks2 == 0) ? 0u : 1u);
-          if (NT2 == 3) {
-            const uint64_t dSl = sdesc_kmajor_sw128(sbase + 2 * SBOX + boff) + koff;
-            mma_ts(tb + kOCol, a_hi, dSl, idesc2, 1u);
-            mma_ts(tb + kOCol, a_hi + 16, dSh, idesc2, 1u);
-          }
-        }
-        mma_commit(&sempty[gb]);
-        if (last) mma_commit(&ofull);
-        return true;
+        return issue_gemm2<NT2>(tb, gb, static_cast<uint32_t>((t >> 1) & 1), first, last, &pfull[gb], &sfull[gb],
+                                &sempty[gb], &ofull, ab, dS_base + static_cast<uint64_t>(gb) * (SBUF >> 4), sbox16,
+                                idesc2);
       };
       Walker wk1 = walk0;    // GEMM1 steps (segment boundaries for the resident A)
       int64_t aseg = -1;
+      const int nk = args.nk;
       for (int64_t t = 0; t < T && ok; ++t, wk1.next()) {
         const int gb = static_cast<int>(t & 1);
         const uint32_t gt = tb + gb * BN;
@@ -383,40 +471,20 @@ kmv_tc_kernel(const __grid_constant__ CUtensorMap mAh, const __grid_constant__ C
           seg_last = st1.last;
           if (st1.first) {
             ++aseg;
-            if (!mbar_wait(&afull, static_cast<uint32_t>(aseg & 1), ab, kWaitLimitNs)) {
+            if (!mbar_wait_slow(&afull, static_cast<uint32_t>(aseg & 1), ab, kWaitLimitNs)) {
               ok = false;
               break;
             }
           }
         }
-        for (int ks = 0; ks < args.nk; ++ks) {
-          if (!mbar_wait(&full_bar[stage], phase, ab, kWaitLimitNs)) {
-            ok = false;
-            break;
-          }
-          tc_fence_after();
-          const uint32_t base = smem_u32(smem + stage * SB);
-          const uint32_t abase = ARES ? smem_u32(a_region) : base;
-          const uint32_t bbase = ARES ? base : base + (NT1 == 3 ? 2 : 1) * A_PART;
-          const uint64_t dAh = sdesc_kmajor_sw128(abase);
-          const uint64_t dBh = sdesc_kmajor_sw128(bbase);
-#pragma unroll
-          for (int kk = 0; kk < BK / 16; ++kk) {
-            const uint32_t acc = (ks | kk) != 0 ? 1u : 0u;
-            mma_ss(gt, dAh + 2 * kk, dBh + 2 * kk, idesc1, acc);
-            if (NT1 == 3) {
-              const uint64_t dAl = sdesc_kmajor_sw128(abase + A_PART);
-              const uint64_t dBl = sdesc_kmajor_sw128(bbase + B_PART);
-              mma_ss(gt, dAh + 2 * kk, dBl + 2 * kk, idesc1, 1u);
-              mma_ss(gt, dAl + 2 * kk, dBh + 2 * kk, idesc1, 1u);
-            }
-          }
-          mma_commit(&empty_bar[stage]);
-          if (++stage == NSTAGE) {
-            stage = 0;
-            phase ^= 1u;
-          }
+        const int pos = issue_gemm1<NT1, NSTAGE, ARES>(gt, nk, dStage0, dAres, full_bar, full_lo, empty_bar, ab, idesc1,
+                                                       stage | static_cast<int>(phase << 8));
+        if (pos < 0) {
+          ok = false;
+          break;
         }
+        stage = pos & 0xFF;
+        phase = static_cast<uint32_t>(pos >> 8);
         if (!ok) break;
         if (ARES && seg_last) mma_commit(&aempty);   // the segment's A is no longer read
         mma_commit(&gfull[gb]);

@@ -419,10 +419,16 @@ def selftest_wait(limit_ns=20_000_000, stream=None):
     _check(lib.itergp_selftest_wait(int(limit_ns), _stream(stream)), "itergp_selftest_wait")
 
 
+PROBES = {"ex2": 0, "ffma": 1, "mma_ss_n128": 2, "mma_ss_n256": 3, "mma_ss_n128_tmem_ld": 4,
+          "mma_ts_n80": 5}
+
+
 def probe_throughput(what="ex2", stream=None) -> float:
-    """Measured operations per second of MUFU exp2 ("ex2") or FP32 FFMA ("ffma", flops)."""
+    """Measured operations per second over the GPU: MUFU exp2 ("ex2"), FP32 FFMA ("ffma",
+    flops) or BF16 tcgen05.mma flops in the product's shapes ("mma_ss_n128", "mma_ss_n256",
+    "mma_ss_n128_tmem_ld": N = 128 while other warps stream TMEM loads, "mma_ts_n80")."""
     out = ct.c_double()
-    _check(lib.itergp_probe_throughput({"ex2": 0, "ffma": 1}[what], ct.byref(out), _stream(stream)),
+    _check(lib.itergp_probe_throughput(PROBES[what], ct.byref(out), _stream(stream)),
            "itergp_probe_throughput")
     return out.value
 

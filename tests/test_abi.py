@@ -156,3 +156,14 @@ def test_tune_cache_round_trip(lib, tmp_path):
     bad.write_text("1 0 64 16 1 6 2\n")          # 6 epilogue warps is not a variant
     assert lib.itergp_tune_load(str(bad).encode()) == -1
     assert lib.itergp_tune_clear() == 0
+
+
+def test_throughput_probe_rejects_bad_arguments(lib):
+    """Unknown probes and a null result pointer fail with EINVAL before any CUDA call."""
+    f = lib.itergp_probe_throughput
+    f.restype = ct.c_int
+    f.argtypes = [ct.c_int32, ct.POINTER(ct.c_double), ct.c_void_p]
+    out = ct.c_double()
+    for what in (-1, 6, 99):
+        assert f(what, ct.byref(out), None) == -1
+    assert f(0, None, None) == -1
