@@ -210,14 +210,28 @@ struct Walker {
   const WorkItem* items = nullptr;
   const TcProb* probs = nullptr;
   int32_t k = 0, k_end = 0, c = 0;
+  // The position advances with compares and adds only (every role steps it once per
+  // chunk; divisions there cost the single issuing threads about a thousand cycles).
+  int64_t row = 0, lock = 0;                      // single problem: row tile, fw * J
+  int32_t it_a_row = 0, it_b_row0 = 0, it_chunks = 0;   // item mode: the current item
 
   __device__ bool item_active(int32_t kk) const {
     const int* a = probs[items[kk].prob].active;
     return a == nullptr || *a != 0;
   }
-  __device__ void skip_inactive() {
+  __device__ void load_item() {   // skip stopped problems, cache the item's fields
     while (k < k_end && !item_active(k)) ++k;
     c = 0;
+    if (k < k_end) {
+      const WorkItem it = items[k];
+      it_a_row = it.a_row;
+      it_b_row0 = it.b_row0;
+      it_chunks = it.chunks;
+    }
+  }
+  __device__ void seek() {        // single problem: position of step t (with divisions)
+    row = sch.row(t);
+    c = sch.col(t);
   }
   __device__ void init(const TcArgs& a, int64_t G, int64_t g) {
     items = a.items;
@@ -225,10 +239,12 @@ struct Walker {
     t = 0;
     if (items == nullptr) {
       sch.init(a.row_tiles, a.chunks, G, g);
+      lock = sch.fw * sch.J;
+      seek();
     } else {
       k = a.item_begin[g];
       k_end = a.item_begin[g + 1];
-      skip_inactive();
+      load_item();
     }
   }
   __device__ int64_t total() const {   // number of steps
@@ -241,29 +257,36 @@ struct Walker {
   __device__ StepInfo cur() const {
     StepInfo s;
     if (items == nullptr) {
-      const int cc = sch.col(t);
-      s.a_row = static_cast<int32_t>(sch.row(t) * BM);
-      s.b_row = cc * BN;
-      s.c = cc;
-      s.first = sch.first(t);
-      s.last = sch.last(t);
+      s.a_row = static_cast<int32_t>(row * BM);
+      s.b_row = c * BN;
+      s.c = c;
+      // a row run starts at chunk 0, at step 0 and where the tail begins; it ends at the
+      // row's last chunk and at the CTA's last step
+      s.first = t == 0 || c == 0 || t == lock;
+      s.last = t == sch.T - 1 || c == sch.J - 1;
       s.item = -1;
     } else {
-      const WorkItem& it = items[k];
-      s.a_row = it.a_row;
-      s.b_row = it.b_row0 + c * BN;
+      s.a_row = it_a_row;
+      s.b_row = it_b_row0 + c * BN;
       s.c = c;
       s.first = (c == 0);
-      s.last = (c == it.chunks - 1);
+      s.last = (c == it_chunks - 1);
       s.item = k;
     }
     return s;
   }
   __device__ void next() {
     ++t;
-    if (items != nullptr && ++c >= items[k].chunks) {
+    if (items == nullptr) {
+      if (t == lock) {
+        seek();                       // first tail step
+      } else if (++c == sch.J) {
+        c = 0;
+        row += t < lock ? sch.G : 1;  // next wave's row tile, or the next tail row
+      }
+    } else if (++c >= it_chunks) {
       ++k;
-      skip_inactive();
+      load_item();
     }
   }
 };
