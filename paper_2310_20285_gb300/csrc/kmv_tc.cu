@@ -48,6 +48,11 @@ __host__ __device__ constexpr int tc_threads(int epi) { return (4 + epi) * 32; }
 constexpr uint32_t kTmemCols = 512;
 constexpr uint32_t kOCol = 256;
 constexpr uint32_t kO2Col = 384;   // FP32 running sum of flushed O (IEEE round-to-nearest adds)
+// G buffers (and weight-tile slots): 3 for P tiles <= 48, else 2.  With three, GEMM2 of a
+// chunk is issued two chunks behind its GEMM1, so the epilogue of chunk t overlaps GEMM1
+// of t + 1 and t + 2 (at small D the epilogue is longer than one GEMM1).  TMEM then holds
+// G 3 x 128 columns, O at 384 and O2 at 384 + P.
+__host__ __device__ constexpr int g_bufs(int p_pad) { return p_pad <= 48 ? 3 : 2; }
 constexpr int kFlushChunks = 4;    // O is flushed into O2 at least every 4 chunks (512 rows)
 constexpr uint64_t kWaitLimitNs = 4000000000ull;   // 4 s per wait
 
@@ -147,8 +152,8 @@ __device__ __noinline__ int issue_gemm1(uint32_t gt, int nk, uint64_t dStage0, u
 // Waits for the epilogue's P (pfull) and the weight tile (sfull); releases the weight tile
 // (sempty) and, at the end of a flush group, hands O to the epilogue (ofull).
 template <int NT2>
-__device__ __noinline__ bool issue_gemm2(uint32_t tb, int gb, uint32_t par, bool first, bool last, uint64_t* pfull_b,
-                                         uint64_t* sfull_b, uint64_t* sempty_b, uint64_t* ofull_b,
+__device__ __noinline__ bool issue_gemm2(uint32_t tb, uint32_t a_col0, uint32_t o_col, uint32_t par, bool first, bool last,
+                                         uint64_t* pfull_b, uint64_t* sfull_b, uint64_t* sempty_b, uint64_t* ofull_b,
                                          volatile int* ab, uint64_t dS0, uint64_t sbox16, uint32_t idesc2) {
   if (!mbar_try_wait(pfull_b, par) && !mbar_wait(pfull_b, par, ab, kWaitLimitNs)) return false;
   if (!mbar_try_wait(sfull_b, par) && !mbar_wait(sfull_b, par, ab, kWaitLimitNs)) return false;
@@ -156,12 +161,12 @@ __device__ __noinline__ bool issue_gemm2(uint32_t tb, int gb, uint32_t par, bool
 #pragma unroll
   for (int ks2 = 0; ks2 < BN / 16; ++ks2) {
     const int grp = ks2 >> 1, h = ks2 & 1;
-    const uint32_t a_hi = tb + static_cast<uint32_t>(gb * BN + 32 * grp + 8 * h);
+    const uint32_t a_hi = tb + a_col0 + static_cast<uint32_t>(32 * grp + 8 * h);
     const uint64_t dSh = dS0 + static_cast<uint64_t>(ks2 >> 2) * sbox16 + static_cast<uint64_t>((ks2 & 3) * 2);
-    mma_ts(tb + kOCol, a_hi, dSh, idesc2, (first && ks2 == 0) ? 0u : 1u);
+    mma_ts(tb + o_col, a_hi, dSh, idesc2, (first && ks2 == 0) ? 0u : 1u);
     if (NT2 == 3) {
-      mma_ts(tb + kOCol, a_hi, dSh + 2 * sbox16, idesc2, 1u);
-      mma_ts(tb + kOCol, a_hi + 16, dSh, idesc2, 1u);
+      mma_ts(tb + o_col, a_hi, dSh + 2 * sbox16, idesc2, 1u);
+      mma_ts(tb + o_col, a_hi + 16, dSh, idesc2, 1u);
     }
   }
   mma_commit(sempty_b);
@@ -314,16 +319,19 @@ kmv_tc_kernel(const __grid_constant__ CUtensorMap mAh, const __grid_constant__ C
   constexpr uint32_t A_BYTES = (NT1 == 3 ? 2u : 1u) * A_PART;   // resident A (ARES)
   constexpr uint32_t SB = ARES ? (NT1 == 3 ? 2u : 1u) * B_PART : stage_bytes(NT1);
   constexpr bool SPLIT = split_arrival(NT1, NSTAGE, ARES);
+  const int ng = g_bufs(args.p_pad);                     // G buffers = weight-tile slots
+  const uint32_t ocol = ng == 3 ? 384u : kOCol;
+  const uint32_t o2col = ng == 3 ? 384u + static_cast<uint32_t>(args.p_pad) : kO2Col;
   const uint32_t SBOX = s_box_bytes(args.p_pad);
   const uint32_t SBUF = s_buf_bytes(NT2, args.p_pad);
   uint8_t* a_region = smem + NSTAGE * SB;                        // ARES only
   uint8_t* s_region = a_region + (ARES ? A_BYTES : 0u);
-  float* nb_all = reinterpret_cast<float*>(s_region + 2 * SBUF);   // [EPI warps][128]
+  float* nb_all = reinterpret_cast<float*>(s_region + ng * SBUF);   // [EPI warps][128]
 
   // full_bar: a whole stage, or with split arrival its hi halves (A_hi and B_hi, enough for
   // the hi.hi MMAs) while full_lo tracks the lo halves
   __shared__ __align__(8) uint64_t full_bar[NSTAGE], full_lo[NSTAGE], empty_bar[NSTAGE];
-  __shared__ __align__(8) uint64_t gfull[2], pfull[2], sfull[2], sempty[2], ofull, oempty, drain;
+  __shared__ __align__(8) uint64_t gfull[3], pfull[3], sfull[3], sempty[3], ofull, oempty, drain;
   __shared__ __align__(8) uint64_t afull, aempty;               // resident A (ARES)
   __shared__ uint32_t tmem_base_s;
   __shared__ int abort_s;
@@ -336,7 +344,7 @@ kmv_tc_kernel(const __grid_constant__ CUtensorMap mAh, const __grid_constant__ C
       mbar_init(&full_lo[i], 1);
       mbar_init(&empty_bar[i], 1);
     }
-    for (int i = 0; i < 2; ++i) {
+    for (int i = 0; i < 3; ++i) {
       mbar_init(&gfull[i], 1);
       mbar_init(&pfull[i], 32 * EPI);
       mbar_init(&sfull[i], 1);
@@ -369,6 +377,8 @@ kmv_tc_kernel(const __grid_constant__ CUtensorMap mAh, const __grid_constant__ C
       uint32_t phase = 0;
       uint32_t armed = 0, armed_par = 0;      // bit i: stage i armed / parity of last arm
       uint32_t s_armed = 0, s_par = 0;
+      int s_slot = 0;
+      uint32_t s_phase = 0;                   // weight-tile ring: slot t % ng, parity (t / ng) & 1
       bool a_armed = false;
       uint32_t a_par = 0;
       int64_t seg = -1;
@@ -421,11 +431,15 @@ kmv_tc_kernel(const __grid_constant__ CUtensorMap mAh, const __grid_constant__ C
           }
         }
         if (*ab) break;
-        const int sb = static_cast<int>(t & 1);
-        if (!mbar_wait(&sempty[sb], static_cast<uint32_t>((t >> 1) & 1) ^ 1u, ab, kWaitLimitNs)) break;
+        const int sb = s_slot;
+        if (!mbar_wait(&sempty[sb], s_phase ^ 1u, ab, kWaitLimitNs)) break;
         mbar_arrive_expect_tx(&sfull[sb], SBUF);
         s_armed |= 1u << sb;
-        s_par = (s_par & ~(1u << sb)) | (static_cast<uint32_t>((t >> 1) & 1) << sb);
+        s_par = (s_par & ~(1u << sb)) | (s_phase << sb);
+        if (++s_slot == ng) {
+          s_slot = 0;
+          s_phase ^= 1u;
+        }
         uint8_t* sbase = s_region + sb * SBUF;
         tma_load_2d(sbase, &mSh, &sfull[sb], b_y, args.s_row0);
         tma_load_2d(sbase + SBOX, &mSh, &sfull[sb], b_y + 64, args.s_row0);
@@ -441,7 +455,7 @@ kmv_tc_kernel(const __grid_constant__ CUtensorMap mAh, const __grid_constant__ C
             mbar_wait_drain(&full_bar[i], (armed_par >> i) & 1u, kWaitLimitNs);
             if (SPLIT) mbar_wait_drain(&full_lo[i], (armed_par >> i) & 1u, kWaitLimitNs);
           }
-        for (int i = 0; i < 2; ++i)
+        for (int i = 0; i < 3; ++i)
           if (s_armed & (1u << i)) mbar_wait_drain(&sfull[i], (s_par >> i) & 1u, kWaitLimitNs);
         if (a_armed) mbar_wait_drain(&afull, a_par, kWaitLimitNs);
       }
@@ -465,7 +479,9 @@ kmv_tc_kernel(const __grid_constant__ CUtensorMap mAh, const __grid_constant__ C
       // The issuing thread has to keep up with one MMA every few dozen cycles, so the hot
       // loop holds only the fast path of each wait; slow waits and the weighted-sum GEMM2
       // are out-of-line calls (inlined, they measurably slowed the issue of GEMM1).
-      Walker wk2 = walk0;   // lags the GEMM1 loop by one step
+      Walker wk2 = walk0;   // lags the GEMM1 loop by ng - 1 steps
+      int g2 = 0;           // GEMM2's buffer / slot (t % ng) and its parity ((t / ng) & 1)
+      uint32_t g2par = 0;
       auto gemm2 = [&](int64_t t) -> bool {
         const StepInfo st = wk2.cur();
         wk2.next();
@@ -477,17 +493,26 @@ kmv_tc_kernel(const __grid_constant__ CUtensorMap mAh, const __grid_constant__ C
           if (sub >= 1 && !mbar_wait_slow(&oempty, static_cast<uint32_t>((sub - 1) & 1), ab, kWaitLimitNs))
             return false;
         }
-        const int gb = static_cast<int>(t & 1);
-        return issue_gemm2<NT2>(tb, gb, static_cast<uint32_t>((t >> 1) & 1), first, last, &pfull[gb], &sfull[gb],
+        (void)t;
+        const int gb = g2;
+        const uint32_t par = g2par;
+        if (++g2 == ng) {
+          g2 = 0;
+          g2par ^= 1u;
+        }
+        return issue_gemm2<NT2>(tb, static_cast<uint32_t>(gb) * BN, ocol, par, first, last, &pfull[gb], &sfull[gb],
                                 &sempty[gb], &ofull, ab, dS_base + static_cast<uint64_t>(gb) * (SBUF >> 4), sbox16,
                                 idesc2);
       };
       Walker wk1 = walk0;    // GEMM1 steps (segment boundaries for the resident A)
       int64_t aseg = -1;
       const int nk = args.nk;
+      const int lag = ng - 1;
+      int g1 = 0;           // GEMM1's buffer (t % ng)
       for (int64_t t = 0; t < T && ok; ++t, wk1.next()) {
-        const int gb = static_cast<int>(t & 1);
-        const uint32_t gt = tb + gb * BN;
+        const int gb = g1;
+        if (++g1 == ng) g1 = 0;
+        const uint32_t gt = tb + static_cast<uint32_t>(gb) * BN;
         bool seg_last = false;
         if (ARES) {
           const StepInfo st1 = wk1.cur();
@@ -511,9 +536,10 @@ kmv_tc_kernel(const __grid_constant__ CUtensorMap mAh, const __grid_constant__ C
         if (!ok) break;
         if (ARES && seg_last) mma_commit(&aempty);   // the segment's A is no longer read
         mma_commit(&gfull[gb]);
-        if (t >= 1 && !gemm2(t - 1)) ok = false;
+        if (t >= lag && !gemm2(t - lag)) ok = false;
       }
-      if (ok) gemm2(T - 1);
+      for (int64_t t = T > lag ? T - lag : 0; ok && t < T; ++t)
+        if (!gemm2(t)) ok = false;
       // all issued MMAs must retire before TMEM is released
       mma_commit(&drain);
       mbar_wait_drain(&drain, 0, kWaitLimitNs);
@@ -537,6 +563,8 @@ kmv_tc_kernel(const __grid_constant__ CUtensorMap mAh, const __grid_constant__ C
     bool out_valid = false;
     int out_lim = 0;
     Walker wk = walk0;
+    int gbuf = 0;                   // G buffer of the current chunk (t % ng) and its parity
+    uint32_t gpar = 0;
     // column norms of the next step are loaded while the current chunk is processed
     Walker wkn = walk0;
     float nb_next[BN / 32];
@@ -580,8 +608,12 @@ kmv_tc_kernel(const __grid_constant__ CUtensorMap mAh, const __grid_constant__ C
 #pragma unroll
         for (int k = 0; k < BN / 32; ++k) nb_next[k] = args.nb[static_cast<int64_t>(sn.b_row) + lane + 32 * k];
       }
-      const int gb = static_cast<int>(t & 1);
-      if (!mbar_wait_warp(&gfull[gb], static_cast<uint32_t>((t >> 1) & 1), ab, kWaitLimitNs)) break;
+      const int gb = gbuf;
+      if (!mbar_wait_warp(&gfull[gb], gpar, ab, kWaitLimitNs)) break;
+      if (++gbuf == ng) {
+        gbuf = 0;
+        gpar ^= 1u;
+      }
       tc_fence_after();
       const uint32_t gcol = tb + lane_base + gb * BN;
       // the TMEM load of the next 32-column group is in flight while this one is computed
@@ -664,10 +696,10 @@ kmv_tc_kernel(const __grid_constant__ CUtensorMap mAh, const __grid_constant__ C
         const int lim = st.item >= 0 ? out_lim : (full_row ? args.p_valid : args.p_pad);
         for (int c16 = h; c16 < args.p_pad / 16; c16 += NH) {
           uint32_t o[16];
-          tmem_ld16(tb + lane_base + kOCol + 16 * c16, o);
+          tmem_ld16(tb + lane_base + ocol + 16 * c16, o);
           if (sub_in_seg > 0) {
             uint32_t o2[16];
-            tmem_ld16(tb + lane_base + kO2Col + 16 * c16, o2);
+            tmem_ld16(tb + lane_base + o2col + 16 * c16, o2);
             tmem_ld_wait();
 #pragma unroll
             for (int i = 0; i < 16; ++i) o[i] = __float_as_uint(__uint_as_float(o[i]) + __uint_as_float(o2[i]));
@@ -681,7 +713,7 @@ kmv_tc_kernel(const __grid_constant__ CUtensorMap mAh, const __grid_constant__ C
                 if (16 * c16 + i < lim) dst[16 * c16 + i] = __uint_as_float(o[i]);
             }
           } else {
-            tmem_st16(tb + lane_base + kO2Col + 16 * c16, o);
+            tmem_st16(tb + lane_base + o2col + 16 * c16, o);
           }
         }
         tmem_st_wait();
@@ -822,7 +854,7 @@ int stages_that_fit(const DeviceContext* ctx, int nt1, int nt2, int p_tile, int 
   const size_t smem_cap = std::min<size_t>(ctx->smem_optin, 232448) - 2048;
   const size_t a_bytes = ares ? static_cast<size_t>(nt1 == 3 ? 2 : 1) * BM * BK * 2 : 0;
   const size_t stage = ares ? static_cast<size_t>(nt1 == 3 ? 2 : 1) * BN * BK * 2 : stage_bytes(nt1);
-  const size_t fixed = 2 * s_buf_bytes(nt2, p_tile) + smem_extra(epi) + a_bytes;
+  const size_t fixed = g_bufs(p_tile) * s_buf_bytes(nt2, p_tile) + smem_extra(epi) + a_bytes;
   const int fit = static_cast<int>((smem_cap > fixed ? smem_cap - fixed : 0) / stage);
   int ns = ares ? (fit >= 5 ? 5 : fit >= 3 ? 3 : 0) : (fit >= 4 ? 4 : fit >= 3 ? 3 : fit >= 2 ? 2 : 0);
   if (want >= 2 && ns > want) ns = ares ? (want >= 5 ? 5 : want >= 3 ? 3 : 0) : want;
@@ -832,7 +864,7 @@ int stages_that_fit(const DeviceContext* ctx, int nt1, int nt2, int p_tile, int 
 size_t tc_smem_bytes(int nt1, int nt2, int p_pad, int epi, int nstage, bool ares) {
   const size_t a_bytes = ares ? static_cast<size_t>(nt1 == 3 ? 2 : 1) * BM * BK * 2 : 0;
   const size_t stage = ares ? static_cast<size_t>(nt1 == 3 ? 2 : 1) * BN * BK * 2 : stage_bytes(nt1);
-  return nstage * stage + a_bytes + 2 * s_buf_bytes(nt2, p_pad) + smem_extra(epi);
+  return nstage * stage + a_bytes + g_bufs(p_pad) * s_buf_bytes(nt2, p_pad) + smem_extra(epi);
 }
 
 }  // namespace
