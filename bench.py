@@ -527,11 +527,11 @@ def main():
     kernel_s = (kern_ms / max(kern_n, 1)) / 1e3
     achieved = flops / kernel_s / 1e12
     # DRAM bytes per launch from the ncu capture of this kernel version at N = 40000 (bf16x3,
-    # D = 784, P = 80: 1.5459 GB read + 16.8 MB written), scaled by the pairs processed
+    # D = 784, P = 80: 1.5492 GB read + 16.4 MB written), scaled by the pairs processed
     # (the lockstep schedule re-reads the B side once per wave, so traffic grows like N^2)
     traffic = None
     if args.precision == "bf16x3":
-        traffic = (1.5459e9 + 16.8e6) * (n / 40000.0) ** 2
+        traffic = (1.5492e9 + 16.4e6) * (n / 40000.0) ** 2
     roof = {"bound": "tensor", "achieved": achieved, "peak": pk["bf16_tflops"], "unit": "TFLOP/s",
             "frac": achieved / pk["bf16_tflops"], "traffic": traffic,
             "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of one launch at N=40000, "
