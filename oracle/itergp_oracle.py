@@ -50,6 +50,24 @@ class Kernel:
     outputscale: float = 1.0
 
 
+@dataclass(frozen=True)
+class ClassKernels:
+    """One kernel per output: the C latent GPs are independent (Sec. 5, large-scale
+    experiment; App. C.3) and each may carry its own hyperparameters (l_c, s_c).  The
+    prior covariance is then K = sum_c k_c(X, X) kron e_c e_c^T in CN ordering, i.e. the
+    block of class c acts on the class-c entries only."""
+    kernels: tuple
+
+
+def kernels_per_class(kern, C: int) -> list:
+    """The kernel of each of the C outputs (the shared one C times)."""
+    if isinstance(kern, ClassKernels):
+        if len(kern.kernels) != C:
+            raise ValueError("one kernel per class expected")
+        return list(kern.kernels)
+    return [kern] * C
+
+
 # ---------------------------------------------------------------------------------------
 # Kernel evaluation (Sec. 2.1 prior; App. C.1, C.3 kernels)
 # ---------------------------------------------------------------------------------------
@@ -86,9 +104,31 @@ def kmatvec(A: np.ndarray, B: np.ndarray, S: np.ndarray, kern: Kernel) -> np.nda
     return kernel_matrix(A, B, kern) @ np.asarray(S, dtype=np.float64)
 
 
-def dense_K(X: np.ndarray, C: int, kern: Kernel) -> np.ndarray:
-    """K = k(X, X) kron I_C in CN ordering (NC x NC), for tiny problems only."""
-    return np.kron(kernel_matrix(X, X, kern), np.eye(C))
+def dense_K(X: np.ndarray, C: int, kern) -> np.ndarray:
+    """K = k(X, X) kron I_C in CN ordering (NC x NC), for tiny problems only; with one
+    kernel per class, K = sum_c k_c(X, X) kron e_c e_c^T."""
+    return cross_K(X, X, C, kern)
+
+
+def cross_K(A: np.ndarray, B: np.ndarray, C: int, kern) -> np.ndarray:
+    """The multi-output cross covariance between A and B in CN ordering ((M C) x (N C))."""
+    out = 0.0
+    for c, kc in enumerate(kernels_per_class(kern, C)):
+        E = np.zeros((C, C))
+        E[c, c] = 1.0
+        out = out + np.kron(kernel_matrix(A, B, kc), E)
+    return out
+
+
+def kmatvec_classes(A: np.ndarray, B: np.ndarray, S: np.ndarray, kern, C: int) -> np.ndarray:
+    """Y[:, j] = k_{j mod C}(A, B) S[:, j]: the product with the multi-output prior when the
+    P columns of S are NC-vectors viewed as N x C blocks side by side (column j belongs to
+    class j mod C, the CN ordering)."""
+    S = np.asarray(S, dtype=np.float64)
+    Y = np.zeros((np.asarray(A).shape[0], S.shape[1]))
+    for c, kc in enumerate(kernels_per_class(kern, C)):
+        Y[:, c::C] = kernel_matrix(A, B, kc) @ S[:, c::C]
+    return Y
 
 
 # ---------------------------------------------------------------------------------------
@@ -256,7 +296,9 @@ def exact_newton_step(X, lik, f, m, kern: Kernel, shift: float | None = None):
     N, C = f.shape
     K = dense_K(X, C, kern)
     Khat = K + lik.Winv_dense(f)
-    gamma = kern.outputscale if shift is None else shift
+    # with one kernel per class K no longer maps the class-sum directions to themselves,
+    # so no shift is applied (K + W^+ is positive definite when every k_c is)
+    gamma = (0.0 if isinstance(kern, ClassKernels) else kern.outputscale) if shift is None else shift
     if gamma:
         Khat = Khat + gamma * np.kron(np.eye(N), np.ones((C, C)) / C)
     b = (pseudo_targets(lik, f) - m).reshape(-1)
@@ -427,10 +469,17 @@ def iterncgp_fit(X, lik, C: int, kern: Kernel, max_newton: int = 10, max_iters: 
     v = np.zeros((N, C))
     Q = np.zeros((N * C, 0))
     res = FitResult(v, Q, f, [f.copy()], [], [], [])
-    kx = kernel_matrix(X, X, kern)
+    per_class = isinstance(kern, ClassKernels)
+    kx = None if per_class else kernel_matrix(X, X, kern)
+    kxs = [kernel_matrix(X, X, kc) for kc in kernels_per_class(kern, C)] if per_class else None
+
+    def kprod(W):   # K applied to an N x C block (k kron I_C, or class c's kernel on column c)
+        if not per_class:
+            return kx @ W
+        return np.stack([kxs[c] @ W[:, c] for c in range(C)], axis=1)
 
     def kmv(w):
-        return (kx @ w.reshape(N, C)).reshape(-1)
+        return kprod(w.reshape(N, C)).reshape(-1)
 
     g_prev = None
     v_prev = np.zeros((N, C))
@@ -456,7 +505,7 @@ def iterncgp_fit(X, lik, C: int, kern: Kernel, max_newton: int = 10, max_iters: 
         vflat, Q, S, T, info = itergp(kmv, winv, b, S, T, policy, max_iters, R,
                                       tol_abs, tol_rel, project=proj)
         v = vflat.reshape(N, C)
-        f = (kx @ v) + m                                    # f_{i+1} = K v + m
+        f = kprod(v) + m                                    # f_{i+1} = K v + m
         res.fs.append(f.copy())
         res.infos.append(info)
         res.newton_steps = i + 1
@@ -470,16 +519,20 @@ def iterncgp_fit(X, lik, C: int, kern: Kernel, max_newton: int = 10, max_iters: 
 # Posterior predictive (Eqs. 9-10) and probit approximation (App. C.3)
 # ---------------------------------------------------------------------------------------
 
-def predict(Xs, X, v, Q, kern: Kernel, C: int):
+def predict(Xs, X, v, Q, kern, C: int):
     """mean m(x*) + k(x*, X) v (m = 0); marginal variance
     diag k_{i,j}(x*, x*) = s - sum_b ((k(x*, X) Q_b)_c)^2 (Eq. 10 with C_j = Q Q^T, as in
-    the proof of Prop. A.3); probit probabilities softmax(mean / sqrt(1 + pi/8 var))."""
+    the proof of Prop. A.3); probit probabilities softmax(mean / sqrt(1 + pi/8 var)).
+    With one kernel per class, column c uses k_c and s_c."""
     N = X.shape[0]
-    kx = kernel_matrix(Xs, X, kern)
-    mean = kx @ np.asarray(v, dtype=np.float64)
-    var = np.full(mean.shape, float(kern.outputscale))
+    ks = kernels_per_class(kern, C)
+    kx = [kernel_matrix(Xs, X, kc) for kc in ks]
+    v = np.asarray(v, dtype=np.float64)
+    mean = np.stack([kx[c] @ v[:, c] for c in range(C)], axis=1)
+    var = np.tile(np.array([float(kc.outputscale) for kc in ks]), (mean.shape[0], 1))
     for b in range(Q.shape[1]):
-        proj = kx @ Q[:, b].reshape(N, C)
+        Qb = Q[:, b].reshape(N, C)
+        proj = np.stack([kx[c] @ Qb[:, c] for c in range(C)], axis=1)
         var -= proj * proj
     probs = softmax(mean / np.sqrt(1.0 + (math.pi / 8.0) * var))
     return mean, var, probs
@@ -501,14 +554,16 @@ def exact_predict(Xs, X, lik, f_i, f_next, kern: Kernel, C: int,
     Returns the mean and the marginal variances (M x C)."""
     N = X.shape[0]
     K = dense_K(X, C, kern)
-    Kx = np.kron(kernel_matrix(Xs, X, kern), np.eye(C))     # (M C) x (N C)
+    Kx = cross_K(Xs, X, C, kern)                             # (M C) x (N C)
     mean = Kx @ np.linalg.solve(K, np.asarray(f_next, dtype=np.float64).reshape(-1))
     Khat = K + lik.Winv_dense(f_i)
+    ks = kernels_per_class(kern, C)
     if contrasts_only:
         Pi = np.kron(np.eye(N), np.eye(C) - np.ones((C, C)) / C)
-        Khat = Khat + kern.outputscale * np.kron(np.eye(N), np.ones((C, C)) / C)
+        Khat = Khat + ks[0].outputscale * np.kron(np.eye(N), np.ones((C, C)) / C)
         red = Kx @ Pi @ np.linalg.solve(Khat, Pi @ Kx.T)
     else:
         red = Kx @ np.linalg.solve(Khat, Kx.T)
-    var = kern.outputscale - np.diag(red)
+    prior = np.tile(np.array([float(kc.outputscale) for kc in ks]), Xs.shape[0])
+    var = prior - np.diag(red)
     return mean.reshape(-1, C), var.reshape(-1, C)

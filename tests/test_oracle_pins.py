@@ -575,3 +575,145 @@ def test_one_latent_unit_actions_reproduce_the_exact_step(kind):
                          recycle=False, tol_abs=0, tol_rel=0)
     for a, b in zip(res.fs, ref):
         assert np.allclose(a, b, atol=1e-9)
+
+
+# ---------------------------------------------------------------------- one kernel per class
+
+def class_kernels(C=3):
+    """Distinct hyperparameters (and kinds) per output GP."""
+    table = [(O.RBF, 0.5, 1.3), (O.MATERN32, 0.9, 0.7), (O.RBF, 1.6, 2.1), (O.MATERN32, 0.35, 1.0)]
+    return O.ClassKernels(tuple(O.Kernel(*table[c]) for c in range(C)))
+
+
+def test_class_kernel_product_brute_force_double_loop():
+    """Y[i, j] = sum_n k_{j mod C}(a_i, b_n) S[n, j], evaluated term by term."""
+    g = np.random.default_rng(5)
+    C = 3
+    A, B = g.standard_normal((6, 3)), g.standard_normal((9, 3))
+    S = g.standard_normal((9, 2 * C))
+    kerns = class_kernels(C)
+    Y = np.zeros((6, 2 * C))
+    for i in range(6):
+        for n in range(9):
+            r = math.sqrt(sum((A[i, d] - B[n, d]) ** 2 for d in range(3)))
+            for j in range(2 * C):
+                kc = kerns.kernels[j % C]
+                u = r / kc.lengthscale
+                if kc.kind == O.RBF:
+                    k = kc.outputscale * math.exp(-u * u / 2)
+                else:
+                    k = kc.outputscale * (1 + math.sqrt(3) * u) * math.exp(-math.sqrt(3) * u)
+                Y[i, j] += k * S[n, j]
+    assert np.allclose(O.kmatvec_classes(A, B, S, kerns, C), Y, rtol=1e-12, atol=1e-12)
+
+
+def test_class_kernel_prior_is_block_diagonal_per_class():
+    """CN ordering: entry (n C + c, m C + e) = k_c(x_n, x_m) delta_ce; the matrix-free
+    product of a stacked NC-vector equals the dense matrix times it."""
+    X, _, _ = tiny_problem(n=5)
+    C = 3
+    kerns = class_kernels(C)
+    K = O.dense_K(X, C, kerns)
+    for c, kc in enumerate(kerns.kernels):
+        kx = O.kernel_matrix(X, X, kc)
+        for n in range(5):
+            for m in range(5):
+                blk = K[n * C:(n + 1) * C, m * C:(m + 1) * C]
+                assert blk[c, c] == pytest.approx(kx[n, m], rel=1e-12)
+                assert np.count_nonzero(blk - np.diag(np.diag(blk))) == 0
+    w = np.random.default_rng(2).standard_normal((5, C))
+    assert np.allclose(O.kmatvec_classes(X, X, w, kerns, C).reshape(-1), K @ w.reshape(-1), atol=1e-12)
+
+
+def test_class_kernel_step_with_invertible_w_equals_textbook_newton():
+    """With an invertible W (Gaussian likelihood over C outputs, W^-1 = sigma^2 I) the
+    pseudo-target step of Eqs. 6-7 is Newton's step (Eq. 3) for any prior, so also for one
+    kernel per output; one step reaches the posterior mean."""
+    X, _, _ = tiny_problem(n=9, ell=0.6)
+    C = 3
+    kerns = class_kernels(C)
+    yr = np.random.default_rng(8).standard_normal((9, C))
+    lik = O.Gaussian(yr, 0.3)
+    K = O.dense_K(X, C, kerns)
+    m = np.zeros((9, C))
+    f = np.random.default_rng(9).standard_normal((9, C))
+    _, f_next = O.exact_newton_step(X, lik, f, m, kerns, shift=0.0)
+    W = np.eye(9 * C) / 0.3
+    Kinv = np.linalg.inv(K)
+    g = lik.grad(f).reshape(-1) - Kinv @ f.reshape(-1)
+    ref = f + np.linalg.solve(W + Kinv, g).reshape(9, C)
+    assert np.allclose(f_next, ref, rtol=1e-8, atol=1e-9)
+    post = (K @ np.linalg.solve(K + 0.3 * np.eye(9 * C), yr.reshape(-1))).reshape(9, C)
+    assert np.allclose(f_next, post, rtol=1e-8, atol=1e-9)
+
+
+def test_class_kernel_softmax_fixed_point_of_the_pseudo_inverse_iteration():
+    """Under softmax, W^+ (footnote to Eq. 6) vanishes on the per-point class sums.  A
+    fixed point f = K v + m of the pseudo-target step then satisfies W^+ (v - grad log p)
+    = 0: v agrees with the gradient on the class contrasts.  With one shared kernel K keeps
+    the class sums invariant and the fixed point is the mode (v = grad); with distinct
+    kernels it is not, and its objective (Eq. 2) stays below the mode's."""
+    X, y, _ = tiny_problem(n=9, ell=0.6)
+    C = 3
+    kerns = class_kernels(C)
+    lik = O.Softmax(y, C)
+    K = O.dense_K(X, C, kerns)
+    fs, vs = O.exact_newton(X, lik, C, kerns, steps=40)
+    f, v = fs[-1], vs[-1]
+    g = lik.grad(f)
+    contrast = lambda a: a - a.mean(axis=1, keepdims=True)
+    assert np.allclose(contrast(v), contrast(g), atol=1e-9)
+    assert np.allclose(f, (K @ v.reshape(-1)).reshape(9, C), atol=1e-12)
+    # the mode of Eq. 2 under the same prior (textbook Newton, Eq. 3)
+    fm = np.zeros((9, C))
+    for _ in range(40):
+        fm = textbook_newton_step(K, lik, fm, np.zeros((9, C)))
+    psi = lambda a: lik.loglik(a) - 0.5 * a.reshape(-1) @ np.linalg.solve(K, a.reshape(-1))
+    assert np.allclose(lik.grad(fm).reshape(-1), np.linalg.solve(K, fm.reshape(-1)), atol=1e-10)
+    assert psi(f) < psi(fm)
+    assert np.abs(v.sum(axis=1)).max() > 1e-3           # the class sums of v are not zero
+
+
+def test_class_kernel_unit_actions_reproduce_the_exact_step():
+    """With NC unit-vector actions IterGP is a direct solve: the fit's f_1 is the exact
+    Newton step under the per-class prior."""
+    X, y, _ = tiny_problem(n=8, ell=0.6)
+    C = 3
+    kerns = class_kernels(C)
+    lik = O.Softmax(y, C)
+    res = O.iterncgp_fit(X, lik, C, kerns, max_newton=2, max_iters=8 * C, policy=O.UNIT,
+                         tol_abs=0, tol_rel=0, recycle=False)
+    fs, _ = O.exact_newton(X, lik, C, kerns, steps=2)
+    assert np.allclose(res.fs[1], fs[1], rtol=1e-8, atol=1e-9)
+    assert np.allclose(res.fs[2], fs[2], rtol=1e-7, atol=1e-8)
+
+
+def test_class_kernel_predictive_with_unit_actions_equals_literal_eq5():
+    X, y, _ = tiny_problem(n=8, ell=0.6)
+    C = 3
+    kerns = class_kernels(C)
+    lik = O.Softmax(y, C)
+    Xs = datagen.blobs(5, 2, 3, 99)[0]
+    res = O.iterncgp_fit(X, lik, C, kerns, max_newton=1, max_iters=8 * C, policy=O.UNIT,
+                         tol_abs=0, tol_rel=0)
+    mean, var, probs = O.predict(Xs, X, res.v, res.Q, kerns, C)
+    em, ev = O.exact_predict(Xs, X, lik, res.fs[0], res.fs[1], kerns, C, contrasts_only=False)
+    assert np.allclose(mean, em, atol=1e-8)
+    assert np.allclose(var, ev, atol=1e-8)
+    # the prior variance of class c is its own outputscale
+    far = np.full((1, 2), 1e3)
+    _, vfar, _ = O.predict(far, X, res.v, res.Q, kerns, C)
+    assert np.allclose(vfar[0], [k.outputscale for k in kerns.kernels])
+
+
+def test_equal_class_kernels_reduce_to_the_shared_kernel():
+    X, y, kern = tiny_problem(n=14, ell=0.8)
+    C = 3
+    lik = O.Softmax(y, C)
+    a = O.iterncgp_fit(X, lik, C, kern, max_newton=3, max_iters=6, R=8)
+    b = O.iterncgp_fit(X, lik, C, O.ClassKernels((kern,) * C), max_newton=3, max_iters=6, R=8)
+    assert np.allclose(a.f, b.f, rtol=1e-10, atol=1e-12)
+    assert np.allclose(a.v, b.v, rtol=1e-10, atol=1e-12)
+    Xs = datagen.blobs(6, 2, 3, 4)[0]
+    for u, w in zip(O.predict(Xs, X, a.v, a.Q, kern, C), O.predict(Xs, X, b.v, b.Q, O.ClassKernels((kern,) * C), C)):
+        assert np.allclose(u, w, rtol=1e-10, atol=1e-12)
