@@ -95,6 +95,19 @@ int itergp_kmatvec(const itergp_kernel* kernel, int32_t precision, const float* 
                    const float* B, int64_t n, int64_t d, const float* S, int64_t p, float* Y,
                    itergp_stream stream);
 
+/* Kernel product with one kernel per class (the multi-output prior of independent GPs,
+ * Sec. 5 / App. C.3, each with its own hyperparameters):
+ *
+ *   Y[i, j] = sum_l k_{j mod c}(A[i, :], B[l, :]) S[l, j]        i < m, l < n, j < p
+ *
+ * i.e. the columns of S are NC-vectors viewed as n x c blocks side by side (CN ordering)
+ * and column j belongs to class j mod c.  kernels: host, c entries (1 <= c <= 64).  Runs c
+ * grouped products over each class's columns (the distance contraction is repeated per
+ * class).  Sizes, pointers, layouts and errors as itergp_kmatvec. */
+int itergp_kmatvec_classes(const itergp_kernel* kernels, int32_t c, int32_t precision, const float* A,
+                           int64_t m, const float* B, int64_t n, int64_t d, const float* S, int64_t p,
+                           float* Y, itergp_stream stream);
+
 /* ----------------------------------------------------------------------------------
  * Kernel product for callers that cannot allocate device memory.  The paper has no
  * counterpart: this is a deployment variant of itergp_kmatvec.
@@ -200,6 +213,14 @@ typedef struct {
   int32_t likelihood;     /* itergp_likelihood (0 = softmax)                        */
   float noise;            /* Gaussian likelihood: noise variance sigma^2 > 0          */
   const float* y_real;    /* Gaussian likelihood: device, n x c real targets (y unused) */
+  /* One kernel per output GP (the c latent GPs are independent, Sec. 5 / App. C.3): host,
+   * c entries, NULL for one shared `kernel`.  K is then block-diagonal over the classes in
+   * CN ordering and every product runs as c grouped products (one per class, each over
+   * its own columns).  Under the softmax likelihood the W^+ substitution (footnote to
+   * Eq. 6) is Newton's step only while all classes share a kernel; with distinct kernels
+   * Alg. 1 as printed converges to a point off the posterior mode.  Copied by the fit;
+   * batched fits with per-class kernels run their problems one after another. */
+  const itergp_kernel* class_kernels;
 } itergp_fit_params;
 
 #define ITERGP_MAX_REPORT_STEPS 64

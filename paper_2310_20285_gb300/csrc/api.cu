@@ -149,10 +149,16 @@ bool precision_ok(int p) { return p >= ITERGP_FP32 && p <= ITERGP_BF16_COMP; }
 // probs: softmax -- probit-approximated class probabilities (App. C.3); Bernoulli --
 // P(y = 1) by the same probit approximation; Poisson -- predictive mean count
 // E[e^f] = e^(mean + var / 2); Gaussian -- the predictive mean of y.
+// Prior variance per output: one outputscale per class, or the shared one (n == 0).
+struct ClassScales {
+  float s[64];
+  int n;
+};
+
 __global__ void predict_epilogue_kernel(const float* __restrict__ Y, int64_t m, int C, int B,
-                                        int64_t P, float s, float* __restrict__ mean,
-                                        float* __restrict__ var, float* __restrict__ probs,
-                                        int lik) {
+                                        int64_t P, float s_shared, const ClassScales cs,
+                                        float* __restrict__ mean, float* __restrict__ var,
+                                        float* __restrict__ probs, int lik) {
   for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < m;
        i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
     const float* yi = Y + i * P;
@@ -165,7 +171,7 @@ __global__ void predict_epilogue_kernel(const float* __restrict__ Y, int64_t m, 
           const float q = yi[C + b * C + c];
           acc = fmaf(q, q, acc);
         }
-        const float vc = s - acc;
+        const float vc = (cs.n ? cs.s[c] : s_shared) - acc;
         if (var) var[i * C + c] = vc;
         if (probs) {
           const float a = yi[c] / sqrtf(1.f + 0.39269908169872414f * vc);
@@ -181,7 +187,7 @@ __global__ void predict_epilogue_kernel(const float* __restrict__ Y, int64_t m, 
           const float q = yi[C + b * C + c];
           acc = fmaf(q, q, acc);
         }
-        const float vc = s - acc;
+        const float vc = (cs.n ? cs.s[c] : s_shared) - acc;
         if (lik == ITERGP_LIK_BERNOULLI)
           probs[i * C + c] = 1.f / (1.f + expf(-yi[c] / sqrtf(1.f + 0.39269908169872414f * vc)));
         else if (lik == ITERGP_LIK_POISSON)
@@ -268,6 +274,9 @@ int validate_fit_params(const itergp_fit_params* prm) {
       return ITERGP_EINVAL;
   }
   if (!kernel_ok(&prm->kernel) || !precision_ok(prm->precision)) return ITERGP_EINVAL;
+  if (prm->class_kernels)
+    for (int c = 0; c < prm->c; ++c)
+      if (!kernel_ok(&prm->class_kernels[c])) return ITERGP_EINVAL;
   if (prm->policy != ITERGP_POLICY_CG && prm->policy != ITERGP_POLICY_UNIT) return ITERGP_EINVAL;
   if (prm->max_newton < 1 || prm->max_iters < 0 || prm->max_newton > 100000) return ITERGP_EINVAL;
   if (!(prm->tol_abs >= 0) || !(prm->tol_rel >= 0)) return ITERGP_EINVAL;
@@ -322,6 +331,7 @@ int fit_many(const itergp_fit_params* params, int count, itergp_model** out,
     mdl->c = prm.c;
     mdl->bcap = static_cast<int>(bcap);
     mdl->kernel = prm.kernel;
+    if (prm.class_kernels) mdl->class_kernels.assign(prm.class_kernels, prm.class_kernels + prm.c);
     mdl->precision = prm.precision;
     mdl->likelihood = prm.likelihood;
     if (cudaEventCreateWithFlags(&mdl->used, cudaEventDisableTiming) != cudaSuccess) mdl->used = nullptr;
@@ -352,6 +362,7 @@ int fit_many(const itergp_fit_params* params, int count, itergp_model** out,
     FitProblem& fp = probs[i];
     fp.prm = &prm;
     fp.kp = make_kparams(prm.kernel);
+    for (const itergp_kernel& kc : mdl->class_kernels) fp.class_kp.push_back(make_kparams(kc));
     fp.xop = &mdl->xop;
     fp.v = mdl->v;
     fp.f = mdl->f;
@@ -484,6 +495,39 @@ int itergp_kmatvec(const itergp_kernel* kernel, int32_t precision, const float* 
   return kmv_execute(ctx, kp, opA, opB, S, p, p, Y, p, s, nullptr);
 }
 
+int itergp_kmatvec_classes(const itergp_kernel* kernels, int32_t c, int32_t precision, const float* A,
+                           int64_t m, const float* B, int64_t n, int64_t d, const float* S, int64_t p,
+                           float* Y, itergp_stream stream) {
+  clear_stale_error();
+  if (!kernels || c < 1 || c > 64 || !precision_ok(precision)) return ITERGP_EINVAL;
+  for (int k = 0; k < c; ++k)
+    if (!kernel_ok(&kernels[k])) return ITERGP_EINVAL;
+  if (m < 0 || n < 0 || p < 0 || d < 1 || d > 4096 || p > 65536) return ITERGP_EINVAL;
+  if (m == 0 || p == 0) return ITERGP_OK;
+  if (!Y || !A || (n > 0 && (!B || !S))) return ITERGP_EINVAL;
+  DeviceContext* ctx = current_context();
+  if (!ctx) return ITERGP_ECUDA;
+  if (precision_is_tensor(precision) && !ctx->tcgen05) return ITERGP_EUNSUPPORTED;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  std::vector<KParams> kps;
+  for (int k = 0; k < c; ++k) kps.push_back(make_kparams(kernels[k]));
+  const bool same = (A == B) && (m == n);
+  const size_t ba = rows_workspace_bytes(precision, m, static_cast<int>(d));
+  const size_t bb = same ? 0 : rows_workspace_bytes(precision, n, static_cast<int>(d));
+  Scratch ws;
+  ITERGP_CUDA_TRY(ws.alloc(ctx, ba + bb, s));
+  RowOperand opA, opB;
+  int rc = prepare_rows(precision, A, m, static_cast<int>(d), d, ws.as<void>(), &opA, s);
+  if (rc != ITERGP_OK) return rc;
+  if (same) {
+    opB = opA;
+  } else {
+    rc = prepare_rows(precision, B, n, static_cast<int>(d), d, ws.as<char>(ba), &opB, s);
+    if (rc != ITERGP_OK) return rc;
+  }
+  return kmv_classes(ctx, kps.data(), c, opA, opB, S, p, p, Y, p, s, nullptr);
+}
+
 int itergp_winv_apply(const float* f, int64_t n, int32_t c, const float* x, float* out,
                       itergp_stream stream) {
   clear_stale_error();
@@ -540,7 +584,28 @@ int itergp_fit_batch(const itergp_fit_params* params, int32_t count, itergp_mode
         b.likelihood != a.likelihood)
       return ITERGP_EINVAL;
   }
-  return fit_many(params, count, models, reports, static_cast<cudaStream_t>(stream), true);
+  bool per_class = false;
+  for (int i = 0; i < count; ++i) per_class = per_class || params[i].class_kernels != nullptr;
+  if (!per_class) return fit_many(params, count, models, reports, static_cast<cudaStream_t>(stream), true);
+  // grouped per-class products do not share a launch across problems: one fit each, with
+  // the batched call's per-problem error semantics
+  for (int i = 0; i < count; ++i) {
+    itergp_fit_report rep{};
+    const int rc = fit_many(&params[i], 1, &models[i], &rep, static_cast<cudaStream_t>(stream), false);
+    if (rc == ITERGP_ECUDA || rc == ITERGP_ENOMEM || rc == ITERGP_ETIMEOUT) {
+      for (int k = 0; k < i; ++k) {
+        itergp_model_free(models[k]);
+        models[k] = nullptr;
+      }
+      return rc;
+    }
+    if (rc != ITERGP_OK) {
+      models[i] = nullptr;
+      rep.status = rc;
+    }
+    if (reports) reports[i] = rep;
+  }
+  return ITERGP_OK;
 }
 
 int itergp_predict(const itergp_model* mdl, const float* Xs, int64_t m, float* mean, float* var,
@@ -571,10 +636,21 @@ int itergp_predict(const itergp_model* mdl, const float* Xs, int64_t m, float* m
     gather_vq_kernel<<<blocks, 256, 0, s>>>(mdl->v, mdl->Q, mdl->n, C, B, Sv), ::itergp::note_launch();
     ITERGP_CUDA_TRY(cudaGetLastError());
   }
-  rc = kmv_execute(ctx, make_kparams(mdl->kernel), op, mdl->xop, Sv, P, P, Y, P, s, nullptr);
+  // [v | Q] columns of class c are c, c + C, ... (CN ordering): with one kernel per class
+  // the product runs as C grouped products
+  ClassScales cs{};
+  if (!mdl->class_kernels.empty()) {
+    std::vector<KParams> kps;
+    for (const itergp_kernel& kc : mdl->class_kernels) kps.push_back(make_kparams(kc));
+    for (int c = 0; c < C; ++c) cs.s[c] = mdl->class_kernels[c].outputscale;
+    cs.n = C;
+    rc = kmv_classes(ctx, kps.data(), C, op, mdl->xop, Sv, P, P, Y, P, s, nullptr);
+  } else {
+    rc = kmv_execute(ctx, make_kparams(mdl->kernel), op, mdl->xop, Sv, P, P, Y, P, s, nullptr);
+  }
   if (rc != ITERGP_OK) return rc;
   const unsigned blocks = static_cast<unsigned>(std::min<int64_t>(ceil_div(m, 256), 8LL * ctx->num_sms));
-  predict_epilogue_kernel<<<blocks, 256, 0, s>>>(Y, m, C, B, P, mdl->kernel.outputscale, mean, var, probs,
+  predict_epilogue_kernel<<<blocks, 256, 0, s>>>(Y, m, C, B, P, mdl->kernel.outputscale, cs, mean, var, probs,
                                                  mdl->likelihood), ::itergp::note_launch();
   ITERGP_CUDA_TRY(cudaGetLastError());
   if (mdl->used) ITERGP_CUDA_TRY(cudaEventRecord(mdl->used, s));   // the model's last use

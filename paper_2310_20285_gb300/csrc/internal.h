@@ -44,6 +44,12 @@ int prepare_rows(int precision, const float* X, int64_t rows, int d, int64_t ldX
 int kmv_execute(DeviceContext* ctx, const KParams& kp, const RowOperand& A, const RowOperand& B,
                 const float* S, int64_t ldS, int64_t p, float* Y, int64_t ldY,
                 cudaStream_t stream, const int* active);
+// The product with one kernel per class: column j of S and Y belongs to class j mod C and
+// uses kps[j mod C].  Runs C grouped products, each over its class's columns gathered into
+// a contiguous block (scratch from the pool) and scattered back into Y.
+int kmv_classes(DeviceContext* ctx, const KParams* kps, int C, const RowOperand& A, const RowOperand& B,
+                const float* S, int64_t ldS, int64_t p, float* Y, int64_t ldY, cudaStream_t stream,
+                const int* active);
 
 // Plain FP32 path (kmv_simt.cu).
 int kmv_simt(DeviceContext* ctx, const KParams& kp, const RowOperand& A, const RowOperand& B,
@@ -118,6 +124,7 @@ int kmv_simt_items(DeviceContext* ctx, int kind, const RowOperand& A, const RowO
 struct FitProblem {
   const itergp_fit_params* prm;
   KParams kp;
+  std::vector<KParams> class_kp;   // one per class, or empty for the shared kernel
   const RowOperand* xop;   // prepared rows of the problem (model memory)
   float *v, *f, *Q;
   int bcap;
@@ -177,6 +184,7 @@ struct itergp_model {
   int64_t n = 0, d = 0;
   int c = 0, bcap = 0, B = 0;
   itergp_kernel kernel{};
+  std::vector<itergp_kernel> class_kernels;   // one per class, or empty for the shared kernel
   int precision = 0;
   int likelihood = ITERGP_LIK_SOFTMAX;
   void* mem = nullptr;

@@ -131,6 +131,60 @@ int prepare_rows(int precision, const float* X, int64_t rows, int d, int64_t ldX
   return ITERGP_OK;
 }
 
+namespace {
+// out[r, q] = S[r, c0 + C q]  (r < rows, q < pc): one class's columns of a CN-ordered block
+__global__ void gather_class_cols_kernel(const float* __restrict__ S, int64_t ldS, int64_t rows, int c0, int C,
+                                         int64_t pc, float* __restrict__ out, const int* __restrict__ active) {
+  if (active != nullptr && *active == 0) return;
+  const int64_t total = rows * pc;
+  for (int64_t e = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; e < total;
+       e += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const int64_t r = e / pc, q = e % pc;
+    out[e] = S[r * ldS + c0 + C * q];
+  }
+}
+
+// Y[r, c0 + C q] = in[r, q]
+__global__ void scatter_class_cols_kernel(const float* __restrict__ in, int64_t rows, int c0, int C, int64_t pc,
+                                          float* __restrict__ Y, int64_t ldY, const int* __restrict__ active) {
+  if (active != nullptr && *active == 0) return;
+  const int64_t total = rows * pc;
+  for (int64_t e = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; e < total;
+       e += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const int64_t r = e / pc, q = e % pc;
+    Y[r * ldY + c0 + C * q] = in[e];
+  }
+}
+}  // namespace
+
+int kmv_classes(DeviceContext* ctx, const KParams* kps, int C, const RowOperand& A, const RowOperand& B,
+                const float* S, int64_t ldS, int64_t p, float* Y, int64_t ldY, cudaStream_t stream,
+                const int* active) {
+  if (A.rows == 0 || p == 0) return ITERGP_OK;
+  if (C < 1 || C > 64) return ITERGP_EINVAL;
+  const int64_t pc_max = (p + C - 1) / C;
+  const size_t sb = align_up(sizeof(float) * std::max<int64_t>(B.rows, 1) * pc_max, 256);
+  const size_t yb = align_up(sizeof(float) * A.rows * pc_max, 256);
+  Scratch buf;
+  ITERGP_CUDA_TRY(buf.alloc(ctx, sb + yb, stream));
+  float* Sc = buf.as<float>();
+  float* Yc = buf.as<float>(sb);
+  for (int c = 0; c < C && c < p; ++c) {
+    const int64_t pc = (p - c + C - 1) / C;   // columns c, c + C, ... below p
+    if (B.rows > 0) {
+      const unsigned g = static_cast<unsigned>(std::min<int64_t>(ceil_div(B.rows * pc, 256), 8LL * ctx->num_sms));
+      gather_class_cols_kernel<<<g, 256, 0, stream>>>(S, ldS, B.rows, c, C, pc, Sc, active), ::itergp::note_launch();
+      ITERGP_CUDA_TRY(cudaGetLastError());
+    }
+    int rc = kmv_execute(ctx, kps[c], A, B, Sc, pc, pc, Yc, pc, stream, active);
+    if (rc != ITERGP_OK) return rc;
+    const unsigned g = static_cast<unsigned>(std::min<int64_t>(ceil_div(A.rows * pc, 256), 8LL * ctx->num_sms));
+    scatter_class_cols_kernel<<<g, 256, 0, stream>>>(Yc, A.rows, c, C, pc, Y, ldY, active), ::itergp::note_launch();
+    ITERGP_CUDA_TRY(cudaGetLastError());
+  }
+  return ITERGP_OK;
+}
+
 int kmv_execute(DeviceContext* ctx, const KParams& kp, const RowOperand& A, const RowOperand& B,
                 const float* S, int64_t ldS, int64_t p, float* Y, int64_t ldY,
                 cudaStream_t stream, const int* active) {

@@ -1050,7 +1050,11 @@ int fit_run_batch(DeviceContext* ctx, const std::vector<FitProblem>& probs, cuda
   const int track_kd = prm.literal_kv ? 0 : 1;
   // the class-contrast projection belongs to the softmax likelihood (one latent per
   // point has no class-sum directions)
-  const int project = prm.policy == ITERGP_POLICY_CG && prm.likelihood == ITERGP_LIK_SOFTMAX ? 1 : 0;
+  // It is the identity in exact arithmetic only while K keeps the class contrasts in
+  // place (one shared kernel, K = k kron I_C); one kernel per class mixes the per-point
+  // class sums into K s, so there it would change the algorithm and is off.
+  const int project = prm.policy == ITERGP_POLICY_CG && prm.likelihood == ITERGP_LIK_SOFTMAX &&
+                              probs[0].class_kp.empty() ? 1 : 0;
   // the BF16 forms round kernel values (and weights) to 8 bits: residuals below 2^-8 |b|
   // are not resolved (FP32 and the BF16X3 split resolve far below the paper's 1e-5)
   const double floor_rel = (prm.precision == ITERGP_BF16 || prm.precision == ITERGP_BF16_COMP) ? 0x1p-8 : 0.0;
@@ -1241,11 +1245,16 @@ int fit_run_batch(DeviceContext* ctx, const std::vector<FitProblem>& probs, cuda
   (void)tcp_lit;
 
   // the kernel products of an iteration: t_cur = K s_cur for every active problem
+  // K w for one problem's N x C block (one kernel per class: C grouped products)
+  auto kprod0 = [&](const float* w, float* out, const int* active) -> int {
+    if (!probs[0].class_kp.empty())
+      return kmv_classes(ctx, probs[0].class_kp.data(), pd[0].c, *probs[0].xop, *probs[0].xop, w, pd[0].c,
+                         pd[0].c, out, pd[0].c, stream, active);
+    return kmv_execute(ctx, probs[0].kp, *probs[0].xop, *probs[0].xop, w, pd[0].c, pd[0].c, out, pd[0].c,
+                       stream, active);
+  };
   auto products = [&]() -> int {
-    if (!batched) {
-      return kmv_execute(ctx, probs[0].kp, *probs[0].xop, *probs[0].xop, pd[0].s_cur, pd[0].c,
-                         pd[0].c, pd[0].t_cur, pd[0].c, stream, &pd[0].st->active);
-    }
+    if (!batched) return kprod0(pd[0].s_cur, pd[0].t_cur, &pd[0].st->active);
     dim3 grid(static_cast<unsigned>(std::min<int64_t>(ceil_div(bp.max_rows_pad * bp.p16, 256), 512)), np);
     if (precision_is_tensor(prm.precision)) {
       if (precision_splits_weights(prm.precision))
@@ -1301,8 +1310,7 @@ int fit_run_batch(DeviceContext* ctx, const std::vector<FitProblem>& probs, cuda
     // ---- Alg. 2 iterations
     for (int j = 0; j < prm.max_iters && rc == ITERGP_OK; ++j) {
       if (prm.literal_kv) {
-        rc = kmv_execute(ctx, probs[0].kp, *probs[0].xop, *probs[0].xop, pd[0].v, pd[0].c, pd[0].c,
-                         pd[0].u, pd[0].c, stream, &pd[0].st->active);
+        rc = kprod0(pd[0].v, pd[0].u, &pd[0].st->active);
         if (rc != ITERGP_OK) break;
       }
       resid_kernel<<<dim3(nblk, np), kRedThreads, 0, stream>>>(pdev, project), ::itergp::note_launch();
@@ -1321,8 +1329,7 @@ int fit_run_batch(DeviceContext* ctx, const std::vector<FitProblem>& probs, cuda
     step_end_kernel<<<np, 32, 0, stream>>>(pdev, step), ::itergp::note_launch();
     if (prm.literal_kv) {
       // f_{i+1} = K v + m by a fresh product
-      rc = kmv_execute(ctx, probs[0].kp, *probs[0].xop, *probs[0].xop, pd[0].v, pd[0].c, pd[0].c,
-                       pd[0].u, pd[0].c, stream, &pd[0].st->newton_active);
+      rc = kprod0(pd[0].v, pd[0].u, &pd[0].st->newton_active);
       if (rc != ITERGP_OK) break;
     }
     copy_f_kernel<<<dim3(eb, np), 256, 0, stream>>>(pdev), ::itergp::note_launch();

@@ -44,7 +44,8 @@ class FitParams(ct.Structure):
                 ("recycle", ct.c_int32), ("literal_kv", ct.c_int32),
                 ("tol_newton", ct.c_double), ("tol_abs", ct.c_double), ("tol_rel", ct.c_double),
                 ("graph", ct.c_int32), ("f0", ct.c_void_p), ("likelihood", ct.c_int32),
-                ("noise", ct.c_float), ("y_real", ct.c_void_p)]
+                ("noise", ct.c_float), ("y_real", ct.c_void_p),
+                ("class_kernels", ct.POINTER(Kernel))]
 
 
 class FitReport(ct.Structure):
@@ -105,6 +106,8 @@ def _load():
     lib = ct.CDLL(_LIB_PATH)
     vp, i64, i32 = ct.c_void_p, ct.c_int64, ct.c_int32
     lib.itergp_kmatvec.argtypes = [ct.POINTER(Kernel), i32, vp, i64, vp, i64, i64, vp, i64, vp, vp]
+    lib.itergp_kmatvec_classes.argtypes = [ct.POINTER(Kernel), i32, i32, vp, i64, vp, i64, i64, vp, i64,
+                                           vp, vp]
     lib.itergp_kmatvec_noalloc.argtypes = [ct.POINTER(Kernel), i32, vp, i64, vp, i64, i64, vp, i64,
                                            vp, vp, vp]
     lib.itergp_winv_apply.argtypes = [vp, i64, i32, vp, vp, vp]
@@ -198,6 +201,30 @@ def kmatvec(A, B, S, kind="rbf", lengthscale=1.0, outputscale=1.0, precision="fp
                             _dev(B, torch.float32, "B"), n, d, _dev(S, torch.float32, "S"), p,
                             _dev(out, torch.float32, "out"), _stream(stream))
     _check(rc, "itergp_kmatvec")
+    return out
+
+
+def _class_kernels(kernels):
+    """[(kind, lengthscale, outputscale), ...] -> a ctypes array of itergp_kernel."""
+    arr = (Kernel * len(kernels))()
+    for i, (kind, ell, s) in enumerate(kernels):
+        arr[i] = _kernel(kind, ell, s)
+    return arr
+
+
+def kmatvec_classes(A, B, S, kernels, precision="fp32", out=None, stream=None):
+    """Y[:, j] = k_{j mod c}(A, B) @ S[:, j] with one kernel per class (c = len(kernels);
+    the columns of S are n x c blocks side by side, CN ordering)."""
+    m, d = A.shape
+    n = B.shape[0]
+    p = S.shape[1]
+    if out is None:
+        out = torch.empty((m, p), device=A.device, dtype=torch.float32)
+    ks = _class_kernels(kernels)
+    rc = lib.itergp_kmatvec_classes(ks, len(kernels), _prec(precision), _dev(A, torch.float32, "A"), m,
+                                    _dev(B, torch.float32, "B"), n, d, _dev(S, torch.float32, "S"), p,
+                                    _dev(out, torch.float32, "out"), _stream(stream))
+    _check(rc, "itergp_kmatvec_classes")
     return out
 
 
@@ -329,7 +356,7 @@ class _CudaArray:
 
 def _params(X, y, c, kind, lengthscale, outputscale, precision, policy, max_newton, max_iters,
             rank, recycle, literal_kv, tol_newton, tol_abs, tol_rel, graph, f0=None,
-            likelihood="softmax", noise=1.0) -> FitParams:
+            likelihood="softmax", noise=1.0, class_kernels=None) -> FitParams:
     n, d = X.shape
     prm = FitParams()
     prm.n, prm.d, prm.c = n, d, int(c)
@@ -354,20 +381,27 @@ def _params(X, y, c, kind, lengthscale, outputscale, precision, policy, max_newt
         if tuple(f0.shape) != (n, int(c)):
             raise ValueError("f0 must be n x c")
         prm.f0 = _dev(f0, torch.float32, "f0").value
+    if class_kernels is not None:
+        if len(class_kernels) != int(c):
+            raise ValueError("one kernel per class expected")
+        prm._class_kernels = _class_kernels(class_kernels)   # kept alive with the params
+        prm.class_kernels = prm._class_kernels
     return prm
 
 
 def fit(X, y, c, kind="rbf", lengthscale=1.0, outputscale=1.0, precision="fp32",
         policy="cg", max_newton=10, max_iters=50, rank=-1, recycle=True, literal_kv=False,
         tol_newton=0.0, tol_abs=1e-5, tol_rel=1e-5, graph=False, stream=None, f0=None,
-        likelihood="softmax", noise=1.0) -> Model:
+        likelihood="softmax", noise=1.0, class_kernels=None) -> Model:
     """IterNCGP fit (Alg. 1-3) on the GPU.  likelihood: "softmax" (c >= 2 classes, integer
     labels), "bernoulli" (c = 1, labels 0/1), "poisson" (c = 1, counts) or "gaussian"
     (real targets y of n x c, noise variance `noise`).  f0 (n x c, device) starts Newton's
-    method at that iterate instead of m = 0."""
+    method at that iterate instead of m = 0.  class_kernels: [(kind, lengthscale,
+    outputscale)] * c gives each output GP its own kernel (then kind / lengthscale /
+    outputscale are unused)."""
     prm = _params(X, y, c, kind, lengthscale, outputscale, precision, policy, max_newton,
                   max_iters, rank, recycle, literal_kv, tol_newton, tol_abs, tol_rel, graph, f0,
-                  likelihood, noise)
+                  likelihood, noise, class_kernels)
     h = ct.c_void_p()
     rep = FitReport()
     rc = lib.itergp_fit(ct.byref(prm), ct.byref(h), ct.byref(rep), _stream(stream))
@@ -383,9 +417,14 @@ def fit_batch(problems, kind="rbf", precision="fp32", policy="cg", max_newton=5,
     problem that fails on the device fails alone: errors="raise" frees the other models
     and raises its ItergpError; errors="return" puts the ItergpError in its slot."""
     prms = (FitParams * len(problems))()
-    for i, (X, y, c, ell, s) in enumerate(problems):
-        prms[i] = _params(X, y, c, kind, ell, s, precision, policy, max_newton, max_iters, rank,
-                          recycle, False, tol_newton, tol_abs, tol_rel, graph)
+    keep = []
+    for i, prob in enumerate(problems):   # an optional 6th entry: [(kind, l, s)] * c per class
+        X, y, c, ell, s = prob[:5]
+        ck = prob[5] if len(prob) > 5 else None
+        pi = _params(X, y, c, kind, ell, s, precision, policy, max_newton, max_iters, rank,
+                     recycle, False, tol_newton, tol_abs, tol_rel, graph, class_kernels=ck)
+        keep.append(pi)
+        prms[i] = pi
     hs = (ct.c_void_p * len(problems))()
     reps = (FitReport * len(problems))()
     rc = lib.itergp_fit_batch(prms, len(problems), hs, reps, _stream(stream))

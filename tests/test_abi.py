@@ -167,3 +167,23 @@ def test_throughput_probe_rejects_bad_arguments(lib):
     for what in (-1, 6, 99):
         assert f(what, ct.byref(out), None) == -1
     assert f(0, None, None) == -1
+
+
+def test_class_kernel_product_rejects_bad_arguments(lib):
+    """itergp_kmatvec_classes validates its kernel list and sizes before any CUDA call."""
+    class K(ct.Structure):
+        _fields_ = [("kind", ct.c_int32), ("lengthscale", ct.c_float), ("outputscale", ct.c_float)]
+    f = lib.itergp_kmatvec_classes
+    f.restype = ct.c_int
+    f.argtypes = [ct.c_void_p, ct.c_int32, ct.c_int32, ct.c_void_p, ct.c_int64, ct.c_void_p, ct.c_int64,
+                  ct.c_int64, ct.c_void_p, ct.c_int64, ct.c_void_p, ct.c_void_p]
+    good = (K * 3)(K(0, 1.0, 1.0), K(1, 2.0, 0.5), K(0, 0.5, 2.0))
+    bad = (K * 3)(K(0, 1.0, 1.0), K(1, -2.0, 0.5), K(0, 0.5, 2.0))
+    p = ct.c_void_p(16)
+    assert f(None, 3, 0, p, 10, p, 10, 2, p, 3, p, None) == -1          # no kernels
+    assert f(good, 0, 0, p, 10, p, 10, 2, p, 3, p, None) == -1          # c < 1
+    assert f(good, 65, 0, p, 10, p, 10, 2, p, 3, p, None) == -1         # c > 64
+    assert f(bad, 3, 0, p, 10, p, 10, 2, p, 3, p, None) == -1           # a bad lengthscale
+    assert f(good, 3, 9, p, 10, p, 10, 2, p, 3, p, None) == -1          # unknown precision
+    assert f(good, 3, 0, p, 10, p, 10, 0, p, 3, p, None) == -1          # d < 1
+    assert f(good, 3, 0, p, 10, p, 10, 2, p, 3, None, None) == -1       # no output
