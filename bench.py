@@ -307,6 +307,63 @@ def bench_gmm(native, datagen, torch, dev):
     return out
 
 
+def bench_class_kernels(native, datagen, torch, dev):
+    """One kernel per output GP on the paper's Gaussian-mixture data (C = 10, D = 3,
+    N = 10^5): the product K S for an N x C block with per-class Matern-3/2 lengthscales
+    l_c = 0.05 (1 + 0.1 c) (grouped: C products of one column each) against the shared
+    kernel (one product of C columns), and a fit on 20000 training points (5 Newton x 5
+    iterations, R = 10) with per-class against shared hyperparameters, test accuracy on
+    the 10^4 test points outside the timed region."""
+    import numpy as np
+    X, y = datagen.gmm3d(10000, seed_model=1, seed_draw=2)
+    Xs, ys = datagen.gmm3d(1000, seed_model=1, seed_draw=3)
+    tX = torch.as_tensor(X.astype(np.float32), device=dev)
+    tXs = torch.as_tensor(Xs.astype(np.float32), device=dev)
+    n = tX.shape[0]
+    ks = [("matern32", 0.05 * (1 + 0.1 * c), 0.05) for c in range(10)]
+    g = torch.Generator(device=dev).manual_seed(0)
+    S = torch.randn((n, 10), device=dev, generator=g)
+    Y = torch.empty_like(S)
+    out = {"workload": "GMM C=10 D=3; product N=1e5, S N x 10; fit N=2e4 (first 2000 per class), "
+                       "5 Newton x 5 iters, R=10, bf16x3; per-class l_c = 0.05 (1 + 0.1 c), s = 0.05"}
+
+    def timed(fn, reps=5):
+        fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    t_cls = timed(lambda: native.kmatvec_classes(tX, tX, S, ks, precision="bf16x3", out=Y))
+    t_sh = timed(lambda: native.kmatvec(tX, tX, S, kind="matern32", lengthscale=0.05, outputscale=0.05,
+                                        precision="bf16x3", out=Y))
+    out["product"] = {"per_class_ms": t_cls, "shared_ms": t_sh,
+                      "per_class_kernel_values_per_s": 10 * n * n / (t_cls * 1e-3),
+                      "shared_kernel_values_per_s": n * n / (t_sh * 1e-3)}
+    sub = np.concatenate([np.where(y == c)[0][:2000] for c in range(10)])
+    tXf = torch.as_tensor(X[sub].astype(np.float32), device=dev)
+    tyf = torch.as_tensor(y[sub], device=dev)
+    fits = {}
+    for label, kw in (("per_class", dict(class_kernels=ks)),
+                      ("shared", dict(kind="matern32", lengthscale=0.05, outputscale=0.05))):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        m = native.fit(tXf, tyf, 10, precision="bf16x3", max_newton=5, max_iters=5, rank=10, **kw)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        _, _, probs = m.predict(tXs)
+        acc, nll, ece = calibration_metrics(probs.cpu().numpy(), ys)
+        fits[label] = {"fit_s": round(dt, 4), "test_acc": round(acc, 4), "test_nll": round(nll, 4),
+                       "test_ece": round(ece, 4), "iters": int(m.report.total_iters)}
+        m.free()
+    out["fit"] = fits
+    return out
+
+
 def bench_serving(native, datagen, precision, seconds, seed=5, drain_s=10.0):
     """Serving: Poisson arrivals over `seconds` of fit requests at 50/s (N log-uniform in
     [1e3, 5e4], D = 32, C = 5 blobs, RBF l log-uniform in [0.3, 3]; 5 Newton x <= 5
@@ -609,6 +666,7 @@ def main():
         out["batched"] = bench_batched(native, datagen, torch, dev, args.batch_count)
     if rank == 0 and not args.no_extras:
         out["gmm_large"] = bench_gmm(native, datagen, torch, dev)
+        out["class_kernels"] = bench_class_kernels(native, datagen, torch, dev)
     if rank == 0 and not args.no_extras and args.serve_seconds > 0:
         out["serving"] = {
             "workload": f"{args.serve_seconds:g} s of Poisson arrivals: fits 50/s (N log-U[1e3,5e4], D=32, C=5, "
