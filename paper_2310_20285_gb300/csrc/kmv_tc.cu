@@ -934,9 +934,9 @@ int kmv_tc(DeviceContext* ctx, const KParams& kp, const RowOperand& A, const Row
   const int nt2 = precision_splits_weights(prec) ? 3 : 1;
 
   // P tile: the largest multiple of 16 (<= 128) that leaves room for >= 2 stages; then the
-  // deepest instantiated stage count (2, 3, 4) that fits.  (The split distance GEMM is
-  // bounded by shared-memory bandwidth, not by stage depth: deeper rings of narrower
-  // slices measured slower.)
+  // deepest instantiated stage count (2, 3, 4) that fits.  (Deeper rings help only while a
+  // stage's arrival is on the critical path; the issue of the MMAs by one thread bounds
+  // the loop otherwise.)
   const int64_t p16 = (p + 15) / 16 * 16;
   const TcVariant var = tc_variant(prec, kp.kind, A.d_pad, static_cast<int>(std::min<int64_t>(p16, 128)), 0);
   const bool can_ares = A.d_pad == BK && var.ares != 0;   // one K slice: A can stay resident

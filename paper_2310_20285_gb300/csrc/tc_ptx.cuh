@@ -179,18 +179,6 @@ __device__ __forceinline__ uint64_t sdesc_kmajor_sw128(uint32_t saddr) {
   return d;
 }
 
-// K-major operand with 64-byte swizzle: rows of 64 bytes (32 BF16) in 8-row (512-byte)
-// atoms stacked contiguously (SBO = 512 B); atom base 512-byte aligned.
-__device__ __forceinline__ uint64_t sdesc_kmajor_sw64(uint32_t saddr) {
-  uint64_t d = 0;
-  d |= static_cast<uint64_t>((saddr & 0x3FFFFu) >> 4);
-  d |= static_cast<uint64_t>(1) << 16;            // LBO (unused for swizzled K-major)
-  d |= static_cast<uint64_t>(512 >> 4) << 32;     // SBO
-  d |= static_cast<uint64_t>(1) << 46;            // descriptor version (sm_100 family)
-  d |= static_cast<uint64_t>(4) << 61;            // SWIZZLE_64B
-  return d;
-}
-
 // 32 lanes x 32 columns of 32-bit words: register i <- column (taddr.col + i) of this
 // thread's lane.  A warp may only touch lanes 32*(warp_id % 4) .. +31.
 __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
