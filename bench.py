@@ -32,6 +32,29 @@ ELL, OUT = 28.0, 1.0
 METRIC = "K·S kernel-pairs/s"
 
 
+# ---- the N > 1 path: independent replicas (weak scaling), no data-path collective
+def replica_seed(rank: int) -> int:
+    """Each rank draws its own independent problem of the same shape."""
+    return 2 + 1000 * rank
+
+
+def max_over_ranks(x: float, dist, device) -> float:
+    """The slowest rank's value (an all-reduce MAX over the process group; the value
+    itself for a single process)."""
+    if dist is None or not dist.is_initialized() or dist.get_world_size() == 1:
+        return x
+    import torch
+    t = torch.tensor([x], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def aggregate_rate(units_per_rank: float, world: int, t_max: float) -> float:
+    """Whole-job throughput: every rank processes its own units within the slowest rank's
+    time."""
+    return world * units_per_rank / t_max
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -470,7 +493,7 @@ def main():
 
     dev = torch.device("cuda", local)
     # rank r works on its own independent problem (weak scaling)
-    X, y, Xs, ys, S = datagen.workload_kernel_bench(n=args.n, seed=2 + 1000 * rank)
+    X, y, Xs, ys, S = datagen.workload_kernel_bench(n=args.n, seed=replica_seed(rank))
     n = X.shape[0]
     tX = torch.as_tensor(X, device=dev)
     tS = torch.as_tensor(S, device=dev)
@@ -524,12 +547,8 @@ def main():
     kern_ms, kern_n = native.timing_read()
     clk = clocks.stop()
     t_step = ev0.elapsed_time(ev1) / 1e3 / args.steps
-    t_max = t_step
-    if world > 1:
-        tt = torch.tensor([t_step], device=dev, dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_max = float(tt.item())
-    value = world * n * n / t_max
+    t_max = max_over_ranks(t_step, dist, dev)
+    value = aggregate_rate(n * n, world, t_max)
     assert native.sync_status() == 0
 
     # ---- end to end through the C ABI with host buffers (copies in the timed region)
@@ -571,10 +590,7 @@ def main():
     seg[3].record()
     seg[3].synchronize()
     h2d_ms, prod_ms, d2h_ms = (seg[i].elapsed_time(seg[i + 1]) for i in range(3))
-    if world > 1:
-        tt = torch.tensor([t_e2e], device=dev, dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_e2e = float(tt.item())
+    t_e2e = max_over_ranks(t_e2e, dist, dev)
 
     pk, pk_kind = peaks()
     # what one CTA per SM gets from tcgen05.mma in the distance GEMM's shape (SS, M = N = 128,
@@ -612,7 +628,7 @@ def main():
                       "precision": args.precision, "l2": "inputs exceed L2 (X is 188 MB FP32, 200 MB BF16 hi+lo)",
                       "parallelism": f"{world} independent problem(s), one per GPU"},
            "roofline": roof, "clocks": clk, "gpu_launches": int(launches), "tuning": tuning,
-           "e2e": {"value": world * n * n / t_e2e, "unit": "kernel-pairs/s",
+           "e2e": {"value": aggregate_rate(n * n, world, t_e2e), "unit": "kernel-pairs/s",
                    "h2d_bytes_per_step": int(hX.numel() * 4 + hS.numel() * 4),
                    "d2h_bytes_per_step": int(hY.numel() * 4), "ms_per_step": t_e2e * 1e3,
                    "breakdown_ms": {"h2d": h2d_ms, "product": prod_ms, "d2h": d2h_ms},
