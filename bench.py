@@ -387,6 +387,60 @@ def bench_class_kernels(native, datagen, torch, dev):
     return out
 
 
+def bench_likelihoods(native, datagen, torch, dev, n=20000, n_test=10000):
+    """The one-latent likelihoods and the conjugate case through the same Alg. 1-3 path,
+    BF16X3, on N = 2e4 points X ~ U[-3, 3]^2 with g(x) = sin(x_1) + x_2 / 2:
+    Bernoulli with the logistic link (App. C; labels drawn with P(y = 1) = sigma(2 g)),
+    RBF l = 0.5, s = 0.2, 8 Newton steps x 5 CG iterations, R = 10; Poisson with the log
+    link (App. A; y ~ Poisson(e^g)), RBF l = 0.3, s = 0.05, started at the constant
+    f_0 = log(mean y), 8 x 5, R = 10; the Gaussian likelihood (Thm. A.2; noise variance
+    0.01), RBF l = 1, s = 1, one Newton step of 50 iterations without truncation (the FP64
+    oracle's test RMSE is 1.9 after 20 iterations and 0.063 after 50).
+    The undamped Newton iteration of Alg. 1 diverges on these data at larger kernel
+    scales (the FP64 oracle too, e.g. l = 1, s = 1, or any s >= 0.2 for Poisson at
+    N >= 1.6e4), so the scales are ones the oracle converges on at this N.  Each row:
+    fit wall time, predictive time on 1e4 test points (CUDA events, mean of 5), and the
+    test RMSE of the predictive mean against the latent the labels were drawn from."""
+    import numpy as np
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    out = {"workload": f"one latent, N={n:g} train / {n_test:g} test, D=2, X ~ U[-3,3]^2, "
+                       "g = sin(x1) + x2/2, RBF, bf16x3"}
+    setups = {"bernoulli": (0.5, 0.2, dict(max_newton=8, max_iters=5, rank=10)),
+              "poisson": (0.3, 0.05, dict(max_newton=8, max_iters=5, rank=10)),
+              "gaussian": (1.0, 1.0, dict(max_newton=1, max_iters=50, rank=-1, noise=0.01))}
+    for kind, (ell, sc, kw) in setups.items():
+        X, y, Xs = datagen.one_latent(kind, n, seed=11, n_test=n_test)
+        g_test = np.sin(Xs[:, 0].astype(np.float64)) + 0.5 * Xs[:, 1]
+        latent = 2.0 * g_test if kind == "bernoulli" else g_test
+        tX = torch.as_tensor(X, device=dev)
+        tXs = torch.as_tensor(Xs, device=dev)
+        ty = torch.as_tensor(y.reshape(-1, 1) if kind == "gaussian" else y, device=dev)
+        if kind == "poisson":
+            kw = dict(kw, f0=torch.full((n, 1), float(np.log(y.mean())), device=dev))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        m = native.fit(tX, ty, 1, kind="rbf", lengthscale=ell, outputscale=sc, likelihood=kind,
+                       precision="bf16x3", **kw)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        m.predict(tXs)
+        torch.cuda.synchronize()
+        e0.record()
+        for _ in range(5):
+            mean, _, _ = m.predict(tXs)
+        e1.record()
+        torch.cuda.synchronize()
+        mu = mean.double().cpu().numpy().reshape(-1)
+        r = m.report
+        out[kind] = {"lengthscale": ell, "outputscale": sc, "fit_s": round(dt, 4),
+                     "newton_steps": int(r.newton_steps), "iters": int(r.total_iters),
+                     "objective": [round(r.objective[i], 1) for i in range(r.newton_steps)],
+                     "predict_ms": round(e0.elapsed_time(e1) / 5, 3),
+                     "test_rmse_mean_vs_latent": round(float(np.sqrt(np.mean((mu - latent) ** 2))), 4)}
+        m.free()
+    return out
+
+
 def bench_serving(native, datagen, precision, seconds, seed=5, drain_s=10.0):
     """Serving: Poisson arrivals over `seconds` of fit requests at 50/s (N log-uniform in
     [1e3, 5e4], D = 32, C = 5 blobs, RBF l log-uniform in [0.3, 3]; 5 Newton x <= 5
@@ -683,6 +737,7 @@ def main():
     if rank == 0 and not args.no_extras:
         out["gmm_large"] = bench_gmm(native, datagen, torch, dev)
         out["class_kernels"] = bench_class_kernels(native, datagen, torch, dev)
+        out["likelihoods"] = bench_likelihoods(native, datagen, torch, dev)
     if rank == 0 and not args.no_extras and args.serve_seconds > 0:
         out["serving"] = {
             "workload": f"{args.serve_seconds:g} s of Poisson arrivals: fits 50/s (N log-U[1e3,5e4], D=32, C=5, "
