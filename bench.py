@@ -255,6 +255,11 @@ def small_d_roofline(native, torch, dev, n=131072, d=32, p=16):
     S = torch.rand((n, p), device=dev, generator=g) * 2 - 1
     Y = torch.empty((n, p), device=dev)
     res = {"probe_ex2_per_s": ex2, "probe_ffma_flops_per_s": ffma,
+           # the other units the product's forms use, probed the same way
+           "probe_rsqrt_per_s": native.probe_throughput("rsqrt"),
+           "probe_dfma_flops_per_s": native.probe_throughput("dfma"),
+           "probe_mma_tf32_flops_per_s": native.probe_throughput("mma_ss_n128_tf32"),
+           "probe_mma_bf16_flops_per_s": native.probe_throughput("mma_ss_n128"),
            "shape": f"single product N={n}, D={d}, P={p}, RBF, inputs U[0,4)^D"}
     for prec in ("bf16x3", "bf16_comp", "fp32"):
         native.kmatvec(X, X, S, kind="rbf", lengthscale=1.0, precision=prec, out=Y)
@@ -691,7 +696,7 @@ def main():
 
     if rank == 0 and not args.no_extras:
         paths = {}
-        for prec, k in (("bf16", 5), ("bf16_comp", 5), ("fp32", 2)):
+        for prec, k in (("bf16", 5), ("bf16_comp", 5), ("tf32", 5), ("fp32", 2)):
             step(prec)
             torch.cuda.synchronize()
             a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)

@@ -68,12 +68,17 @@ typedef struct {
  *   ITERGP_BF16      tensor cores; one BF16 product per contraction; the squared distance
  *                    uses the norms of the BF16-rounded rows.
  *   ITERGP_BF16_COMP tensor cores; split-precision (3-product) distance with FP32 norms,
- *                    one-product BF16 kernel-weighted sum. */
+ *                    one-product BF16 kernel-weighted sum.
+ *   ITERGP_TF32      tensor cores; the distance from TF32 operands (rows rounded once to
+ *                    10 mantissa bits, nearest-even; norms of the rounded rows; one
+ *                    product, K = 8 per instruction), the kernel-weighted sum as in
+ *                    BF16X3.  Not offered by the serving loop (ITERGP_EINVAL there). */
 typedef enum {
   ITERGP_FP32 = 0,
   ITERGP_BF16X3 = 1,
   ITERGP_BF16 = 2,
-  ITERGP_BF16_COMP = 3
+  ITERGP_BF16_COMP = 3,
+  ITERGP_TF32 = 4
 } itergp_precision;
 
 typedef void* itergp_stream; /* cudaStream_t */
@@ -334,7 +339,8 @@ const char* itergp_last_error(void);
  * least recently used first to make room.  `work_bytes` bounds the workspace of the fits
  * in flight.  A request that can never fit fails with ITERGP_ENOMEM.
  *
- * All models of a server share kernel.kind, precision and the fit schedule.  Data passed
+ * All models of a server share kernel.kind, precision (FP32, BF16X3, BF16 or BF16_COMP;
+ * TF32 is ITERGP_EINVAL here) and the fit schedule.  Data passed
  * to submit calls is copied before the call returns; predict outputs are written to the
  * caller's host buffers, which must stay valid until the request's completion event. */
 typedef struct itergp_server itergp_server;
@@ -443,9 +449,11 @@ int itergp_selftest_wait(uint64_t limit_ns, itergp_stream stream);
  * tcgen05.mma flops (FP32 accumulate, K = 16 per instruction, one CTA per SM issuing
  * back to back) in the shapes the product issues: 2 = SS M = 128, N = 128 (the distance
  * GEMM); 3 = SS M = 128, N = 256; 4 = as 2 while four other warps stream tcgen05.ld (the
- * epilogue's reads); 5 = TS (A from TMEM) M = 128, N = 80 (the weighted sum).  Returns
- * ITERGP_EINVAL for another `what`; a probe wait that exceeds its 2 s bound is reported
- * through itergp_sync_status.  Waits for the stream. */
+ * epilogue's reads); 5 = TS (A from TMEM) M = 128, N = 80 (the weighted sum); 6 = as 2
+ * with TF32 operands (kind::tf32, K = 8; the ITERGP_TF32 distance).  7: FP64 DFMA (2 flops
+ * each); 8: MUFU rsqrt (rsqrt.approx, Matern's distance).  Returns ITERGP_EINVAL for
+ * another `what`; a probe wait that exceeds its 2 s bound is reported through
+ * itergp_sync_status.  Waits for the stream. */
 int itergp_probe_throughput(int32_t what, double* ops_per_s, itergp_stream stream);
 
 /* Library version "major.minor.patch". */

@@ -143,7 +143,7 @@ bool kernel_ok(const itergp_kernel* k) {
          k->lengthscale > 0.f && std::isfinite(k->outputscale) && k->outputscale > 0.f;
 }
 
-bool precision_ok(int p) { return p >= ITERGP_FP32 && p <= ITERGP_BF16_COMP; }
+bool precision_ok(int p) { return p >= ITERGP_FP32 && p <= ITERGP_TF32; }
 
 // mean = Y[:, :C]; var_c = s - sum_b Y[:, C + b C + c]^2; probs = softmax(mean / sqrt(1 + pi/8 var))
 // probs: softmax -- probit-approximated class probabilities (App. C.3); Bernoulli --

@@ -19,16 +19,22 @@ struct RowOperand {
   int d_pad = 0;                     // multiple of 64 (tensor paths) / d (FP32 path)
   int precision = ITERGP_FP32;
   const float* norms = nullptr;      // [rows_pad] squared row norms (see prepare_rows)
-  const __nv_bfloat16* hi = nullptr; // [rows_pad][d_pad]
+  const __nv_bfloat16* hi = nullptr; // [rows_pad][d_pad] (TF32: FP32 values, see precision_tf32_rows)
   const __nv_bfloat16* lo = nullptr; // [rows_pad][d_pad] (split precisions only)
 };
 
 constexpr int kRowTile = 128;
 constexpr int kColTile = 64;
 
-inline bool precision_is_tensor(int p) { return p == ITERGP_BF16X3 || p == ITERGP_BF16 || p == ITERGP_BF16_COMP; }
+inline bool precision_is_tensor(int p) {
+  return p == ITERGP_BF16X3 || p == ITERGP_BF16 || p == ITERGP_BF16_COMP || p == ITERGP_TF32;
+}
 inline bool precision_splits_rows(int p) { return p == ITERGP_BF16X3 || p == ITERGP_BF16_COMP; }
-inline bool precision_splits_weights(int p) { return p == ITERGP_BF16X3; }
+inline bool precision_splits_weights(int p) { return p == ITERGP_BF16X3 || p == ITERGP_TF32; }
+// TF32 rows: one FP32 plane (rows_pad x d_pad, values rounded to TF32) in the bytes of two
+// BF16 planes; RowOperand::hi then points at FP32 data.
+inline bool precision_tf32_rows(int p) { return p == ITERGP_TF32; }
+inline int precision_row_planes(int p) { return precision_splits_rows(p) || precision_tf32_rows(p) ? 2 : 1; }
 
 // Bytes of device memory prepare_rows needs for `rows` x `d` at `precision`.
 size_t rows_workspace_bytes(int precision, int64_t rows, int d);

@@ -32,6 +32,36 @@ __global__ void prep_rows_kernel(const float* __restrict__ X, int64_t ldX, int64
   if (lane == 0) norms[row] = static_cast<float>(acc);
 }
 
+// TF32 rows: each value rounded to 10 mantissa bits (round to nearest, ties to even, on
+// the bit pattern; infinities and NaNs pass unchanged) and stored as FP32, zero padding;
+// squared norms of the rounded rows, so that |a|^2 + |b|^2 - 2 a.b describes one pair of
+// points.
+__device__ __forceinline__ float round_tf32(float x) {
+  uint32_t u = __float_as_uint(x);
+  if ((u & 0x7F800000u) != 0x7F800000u) {
+    u += 0xFFFu + ((u >> 13) & 1u);
+    u &= 0xFFFFE000u;
+  }
+  return __uint_as_float(u);
+}
+
+__global__ void prep_rows_tf32_kernel(const float* __restrict__ X, int64_t ldX, int64_t rows, int d,
+                                      int64_t rows_pad, int d_pad, float* __restrict__ out,
+                                      float* __restrict__ norms) {
+  const int64_t row = static_cast<int64_t>(blockIdx.x) * (blockDim.x / 32) + threadIdx.x / 32;
+  const int lane = threadIdx.x % 32;
+  if (row >= rows_pad) return;
+  double acc = 0.0;
+  for (int col = lane; col < d_pad; col += 32) {
+    const float x = round_tf32((row < rows && col < d) ? X[row * ldX + col] : 0.f);
+    out[row * d_pad + col] = x;
+    acc += static_cast<double>(x) * x;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if (lane == 0) norms[row] = static_cast<float>(acc);
+}
+
 // FP32 path: squared row norms only.
 __global__ void row_norms_kernel(const float* __restrict__ X, int64_t ldX, int64_t rows, int d,
                                  float* __restrict__ norms) {
@@ -73,7 +103,9 @@ int prepare_rows_into(int precision, const float* X, int64_t rows, int d, int64_
   }
   if (!hi || d_pad % 64 != 0 || (precision_splits_rows(precision) && !lo)) return ITERGP_EINVAL;
   const unsigned blocks = static_cast<unsigned>(ceil_div(rows_pad, 8));
-  if (precision_splits_rows(precision))
+  if (precision_tf32_rows(precision))
+    prep_rows_tf32_kernel<<<blocks, 256, 0, stream>>>(X, ldX, rows, d, rows_pad, d_pad, reinterpret_cast<float*>(hi), norms), ::itergp::note_launch();
+  else if (precision_splits_rows(precision))
     prep_rows_kernel<true, false><<<blocks, 256, 0, stream>>>(X, ldX, rows, d, rows_pad, d_pad, hi, lo, norms), ::itergp::note_launch();
   else
     prep_rows_kernel<false, true><<<blocks, 256, 0, stream>>>(X, ldX, rows, d, rows_pad, d_pad, hi, nullptr, norms), ::itergp::note_launch();
@@ -87,7 +119,7 @@ size_t rows_workspace_bytes(int precision, int64_t rows, int d) {
   if (precision_is_tensor(precision)) {
     const int64_t d_pad = (d + 63) / 64 * 64;
     const size_t plane = align_up(static_cast<size_t>(rows_pad) * d_pad * 2, 256);
-    bytes += plane * (precision_splits_rows(precision) ? 2 : 1);
+    bytes += plane * precision_row_planes(precision);
   }
   return bytes;
 }
@@ -123,7 +155,10 @@ int prepare_rows(int precision, const float* X, int64_t rows, int d, int64_t ldX
   op->lo = lo;
   if (op->rows_pad == 0) return ITERGP_OK;
   const unsigned blocks = static_cast<unsigned>(ceil_div(op->rows_pad, 8));
-  if (lo)
+  if (precision_tf32_rows(precision))   // one FP32 plane in the bytes of two BF16 planes
+    prep_rows_tf32_kernel<<<blocks, 256, 0, stream>>>(X, ldX, rows, d, op->rows_pad, op->d_pad,
+                                                      reinterpret_cast<float*>(hi), norms), ::itergp::note_launch();
+  else if (lo)
     prep_rows_kernel<true, false><<<blocks, 256, 0, stream>>>(X, ldX, rows, d, op->rows_pad, op->d_pad, hi, lo, norms), ::itergp::note_launch();
   else
     prep_rows_kernel<false, true><<<blocks, 256, 0, stream>>>(X, ldX, rows, d, op->rows_pad, op->d_pad, hi, lo, norms), ::itergp::note_launch();

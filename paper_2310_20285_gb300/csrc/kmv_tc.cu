@@ -42,6 +42,10 @@ namespace {
 constexpr int BM = 128;   // rows of A per tile (MMA M)
 constexpr int BN = 128;   // rows of B per chunk (MMA N of the distance GEMM, K of the product)
 constexpr int BK = 64;    // D slice per stage (one 128-byte swizzle row of BF16)
+// Row operand forms (NT1): 1 BF16 rows, 3 split BF16 rows (hi, lo), 2 TF32 rows (FP32
+// storage, 32 values per 128-byte swizzle row, kind::tf32 MMAs of K = 8).  A stage holds
+// one 128-byte row per tile row in every form, so the ring layout is the same.
+__host__ __device__ constexpr int slice_elems(int nt1) { return nt1 == 2 ? BK / 2 : BK; }
 // Threads: warps 0-3 (TMA, MMA, TMEM owner, idle) plus EPI epilogue warps (4 or 8; with 8,
 // two warps share each TMEM lane quadrant and split the columns).
 __host__ __device__ constexpr int tc_threads(int epi) { return (4 + epi) * 32; }
@@ -128,7 +132,12 @@ __device__ __noinline__ int issue_gemm1(uint32_t gt, int nk, uint64_t dStage0, u
     // one MMA order for every ring, so that all launch variants give bitwise the same
     // product: the slice's hi.hi terms, then its correction terms hi.lo and lo.hi
 #pragma unroll
-    for (int kk = 0; kk < BK / 16; ++kk) mma_ss(gt, dAh + 2 * kk, dBh + 2 * kk, idesc1, (ks | kk) != 0 ? 1u : 0u);
+    for (int kk = 0; kk < BK / 16; ++kk) {   // K steps of 32 bytes: 16 BF16 or 8 TF32 values
+      if constexpr (NT1 == 2)
+        mma_ss_tf32(gt, dAh + 2 * kk, dBh + 2 * kk, idesc1, (ks | kk) != 0 ? 1u : 0u);
+      else
+        mma_ss(gt, dAh + 2 * kk, dBh + 2 * kk, idesc1, (ks | kk) != 0 ? 1u : 0u);
+    }
     if (NT1 == 3) {
       if (SPLIT && !mbar_wait(&full_lo[stage], phase, ab, kWaitLimitNs)) return -1;
 #pragma unroll
@@ -419,8 +428,8 @@ kmv_tc_kernel(const __grid_constant__ CUtensorMap mAh, const __grid_constant__ C
           armed_par = (armed_par & ~(1u << stage)) | (phase << stage);
           uint8_t* base = smem + stage * SB;
           uint8_t* bbase = base + (NT1 == 3 ? 2 : 1) * A_PART;
-          tma_load_2d(base, &mAh, &full_bar[stage], ks * BK, a_y);
-          tma_load_2d(bbase, &mBh, &full_bar[stage], ks * BK, b_y);
+          tma_load_2d(base, &mAh, &full_bar[stage], ks * slice_elems(NT1), a_y);
+          tma_load_2d(bbase, &mBh, &full_bar[stage], ks * slice_elems(NT1), b_y);
           if (NT1 == 3) {
             tma_load_2d(base + A_PART, &mAl, lo_bar, ks * BK, a_y);
             tma_load_2d(bbase + B_PART, &mBl, lo_bar, ks * BK, b_y);
@@ -463,7 +472,7 @@ kmv_tc_kernel(const __grid_constant__ CUtensorMap mAh, const __grid_constant__ C
   } else if (warp == 1) {
     // ------------------------------------------------------------------ MMA issuer
     if (lane == 0) {
-      const uint32_t idesc1 = idesc_bf16_f32(BM, BN);
+      const uint32_t idesc1 = NT1 == 2 ? idesc_tf32_f32(BM, BN) : idesc_bf16_f32(BM, BN);
       const uint32_t idesc2 = idesc_bf16_f32(BM, static_cast<uint32_t>(args.p_pad));
       // shared-memory descriptors of stage 0, the resident A and the weight buffers; the
       // start-address field (bits 0-13, 16-byte units) takes offsets by plain addition
@@ -799,9 +808,13 @@ cudaError_t launch_tc(int grid, size_t smem, cudaStream_t st, const CUtensorMap*
 template <int KIND, int NT1, int NT2, int EPI>
 cudaError_t launch_stages(int nstage, bool ares, int grid, size_t smem, cudaStream_t st,
                           const CUtensorMap* maps, const TcArgs& a) {
-  if (ares)
-    return nstage == 5 ? launch_tc<KIND, NT1, NT2, 5, EPI, true>(grid, smem, st, maps, a)
-                       : launch_tc<KIND, NT1, NT2, 3, EPI, true>(grid, smem, st, maps, a);
+  if (ares) {
+    if constexpr (NT1 == 2)   // TF32 rows take two slices per 64 columns: no resident A
+      return cudaErrorInvalidValue;
+    else
+      return nstage == 5 ? launch_tc<KIND, NT1, NT2, 5, EPI, true>(grid, smem, st, maps, a)
+                         : launch_tc<KIND, NT1, NT2, 3, EPI, true>(grid, smem, st, maps, a);
+  }
   switch (nstage) {
     case 2: return launch_tc<KIND, NT1, NT2, 2, EPI, false>(grid, smem, st, maps, a);
     case 3: return launch_tc<KIND, NT1, NT2, 3, EPI, false>(grid, smem, st, maps, a);
@@ -815,6 +828,7 @@ cudaError_t launch_prec_epi(int prec, int nstage, bool ares, int grid, size_t sm
   switch (prec) {
     case ITERGP_BF16X3: return launch_stages<KIND, 3, 3, EPI>(nstage, ares, grid, smem, st, maps, a);
     case ITERGP_BF16_COMP: return launch_stages<KIND, 3, 1, EPI>(nstage, ares, grid, smem, st, maps, a);
+    case ITERGP_TF32: return launch_stages<KIND, 2, 3, EPI>(nstage, ares, grid, smem, st, maps, a);
     default: return launch_stages<KIND, 1, 1, EPI>(nstage, ares, grid, smem, st, maps, a);
   }
 }
@@ -861,6 +875,21 @@ int stages_that_fit(const DeviceContext* ctx, int nt1, int nt2, int p_tile, int 
   return ns;
 }
 
+int tc_nt1(int prec) { return precision_tf32_rows(prec) ? 2 : precision_splits_rows(prec) ? 3 : 1; }
+
+// Tensor maps of the row operands (maps[1] and [3] repeat the hi planes when rows are not split).
+bool encode_rows(CUtensorMap* maps, const RowOperand& A, const RowOperand& B, int nt1) {
+  if (nt1 == 2)
+    return encode_f32_sw128(&maps[0], A.hi, A.rows_pad, A.d_pad, A.d_pad, BM) &&
+           encode_f32_sw128(&maps[1], A.hi, A.rows_pad, A.d_pad, A.d_pad, BM) &&
+           encode_f32_sw128(&maps[2], B.hi, B.rows_pad, B.d_pad, B.d_pad, BN) &&
+           encode_f32_sw128(&maps[3], B.hi, B.rows_pad, B.d_pad, B.d_pad, BN);
+  return encode_bf16_sw128(&maps[0], A.hi, A.rows_pad, A.d_pad, A.d_pad, BM) &&
+         encode_bf16_sw128(&maps[1], nt1 == 3 ? A.lo : A.hi, A.rows_pad, A.d_pad, A.d_pad, BM) &&
+         encode_bf16_sw128(&maps[2], B.hi, B.rows_pad, B.d_pad, B.d_pad, BN) &&
+         encode_bf16_sw128(&maps[3], nt1 == 3 ? B.lo : B.hi, B.rows_pad, B.d_pad, B.d_pad, BN);
+}
+
 size_t tc_smem_bytes(int nt1, int nt2, int p_pad, int epi, int nstage, bool ares) {
   const size_t a_bytes = ares ? static_cast<size_t>(nt1 == 3 ? 2 : 1) * BM * BK * 2 : 0;
   const size_t stage = ares ? static_cast<size_t>(nt1 == 3 ? 2 : 1) * BN * BK * 2 : stage_bytes(nt1);
@@ -873,14 +902,14 @@ int kmv_tc_items(DeviceContext* ctx, int kind, const RowOperand& A, const RowOpe
                  const KmvItemTables& tab, const __nv_bfloat16* s_hi, const __nv_bfloat16* s_lo,
                  int64_t s_rows, int s_row0, int p16, cudaStream_t stream) {
   const int prec = B.precision;
-  const int nt1 = precision_splits_rows(prec) ? 3 : 1;
+  const int nt1 = tc_nt1(prec);
   const int nt2 = precision_splits_weights(prec) ? 3 : 1;
   if (p16 > 256 || p16 < 16 || p16 % 16 != 0 || tab.G <= 0 || A.precision != prec ||
       A.d_pad != B.d_pad || s_row0 < 0 || s_row0 + p16 > s_rows)
     return ITERGP_EINVAL;
   // P tile: the widest multiple of 16 (<= p16) that leaves room for >= 2 stages
   const TcVariant var = tc_variant(prec, kind, B.d_pad, p16, 1);
-  const bool can_ares = B.d_pad == BK && var.ares != 0;   // one K slice: A can stay resident
+  const bool can_ares = B.d_pad == BK && var.ares != 0 && nt1 != 2;   // one K slice: A can stay resident
   int p_tile = std::min(p16, 128), nstage = 0;
   bool ares = false;
   for (; p_tile >= 16; p_tile -= 16) {
@@ -893,10 +922,7 @@ int kmv_tc_items(DeviceContext* ctx, int kind, const RowOperand& A, const RowOpe
   }
   if (nstage < 2) return ITERGP_EUNSUPPORTED;
   CUtensorMap maps[6];
-  bool ok = encode_bf16_sw128(&maps[0], A.hi, A.rows_pad, A.d_pad, A.d_pad, BM) &&
-            encode_bf16_sw128(&maps[1], nt1 == 3 ? A.lo : A.hi, A.rows_pad, A.d_pad, A.d_pad, BM) &&
-            encode_bf16_sw128(&maps[2], B.hi, B.rows_pad, B.d_pad, B.d_pad, BN) &&
-            encode_bf16_sw128(&maps[3], nt1 == 3 ? B.lo : B.hi, B.rows_pad, B.d_pad, B.d_pad, BN);
+  bool ok = encode_rows(maps, A, B, nt1);
   if (!ok) return ITERGP_ECUDA;
   for (int p0 = 0; p0 < p16; p0 += p_tile) {
     const int pp = std::min(p_tile, p16 - p0);   // multiple of 16
@@ -906,7 +932,7 @@ int kmv_tc_items(DeviceContext* ctx, int kind, const RowOperand& A, const RowOpe
     TcArgs a{};
     a.na = A.norms;
     a.nb = B.norms;
-    a.nk = B.d_pad / BK;
+    a.nk = B.d_pad / slice_elems(nt1);
     a.p_pad = pp;
     a.p_valid = pp;
     a.s_row0 = s_row0 + p0;
@@ -930,7 +956,7 @@ int kmv_tc(DeviceContext* ctx, const KParams& kp, const RowOperand& A, const Row
            const float* S, int64_t ldS, int64_t p, float* Y, int64_t ldY, cudaStream_t stream,
            const int* active) {
   const int prec = A.precision;
-  const int nt1 = precision_splits_rows(prec) ? 3 : 1;
+  const int nt1 = tc_nt1(prec);
   const int nt2 = precision_splits_weights(prec) ? 3 : 1;
 
   // P tile: the largest multiple of 16 (<= 128) that leaves room for >= 2 stages; then the
@@ -939,7 +965,7 @@ int kmv_tc(DeviceContext* ctx, const KParams& kp, const RowOperand& A, const Row
   // the loop otherwise.)
   const int64_t p16 = (p + 15) / 16 * 16;
   const TcVariant var = tc_variant(prec, kp.kind, A.d_pad, static_cast<int>(std::min<int64_t>(p16, 128)), 0);
-  const bool can_ares = A.d_pad == BK && var.ares != 0;   // one K slice: A can stay resident
+  const bool can_ares = A.d_pad == BK && var.ares != 0 && nt1 != 2;   // one K slice: A can stay resident
   int p_tile = static_cast<int>(std::min<int64_t>(p16, 128));
   int nstage = 0;
   bool ares = false;
@@ -970,10 +996,7 @@ int kmv_tc(DeviceContext* ctx, const KParams& kp, const RowOperand& A, const Row
   }
 
   CUtensorMap maps[6];
-  bool ok = encode_bf16_sw128(&maps[0], A.hi, A.rows_pad, A.d_pad, A.d_pad, BM) &&
-            encode_bf16_sw128(&maps[1], nt1 == 3 ? A.lo : A.hi, A.rows_pad, A.d_pad, A.d_pad, BM) &&
-            encode_bf16_sw128(&maps[2], B.hi, B.rows_pad, B.d_pad, B.d_pad, BN) &&
-            encode_bf16_sw128(&maps[3], nt1 == 3 ? B.lo : B.hi, B.rows_pad, B.d_pad, B.d_pad, BN);
+  bool ok = encode_rows(maps, A, B, nt1);
   if (!ok) return ITERGP_ECUDA;
 
   const int64_t row_tiles = ceil_div(A.rows, BM);
@@ -996,7 +1019,7 @@ int kmv_tc(DeviceContext* ctx, const KParams& kp, const RowOperand& A, const Row
     a.m = A.rows;
     a.row_tiles = row_tiles;
     a.chunks = static_cast<int>(chunks);
-    a.nk = A.d_pad / BK;
+    a.nk = A.d_pad / slice_elems(nt1);
     a.p_pad = pp;
     a.p_valid = pw;
     a.s_row0 = static_cast<int>(p0);
@@ -1032,7 +1055,7 @@ int kmv_tc_tune(DeviceContext* ctx, const KParams& kp, const RowOperand& X, cons
                 int64_t p, float* Y, int items, int cap, int* count, int* epi_out, int* ns_out,
                 double* ms_out, int* best, cudaStream_t stream) {
   const int prec = X.precision;
-  const int nt1 = precision_splits_rows(prec) ? 3 : 1;
+  const int nt1 = tc_nt1(prec);
   const int nt2 = precision_splits_weights(prec) ? 3 : 1;
   const int p16 = static_cast<int>(std::min<int64_t>((p + 15) / 16 * 16, 128));
   // item mode: one problem covering all rows, weights staged as the batched fit stages them
@@ -1075,7 +1098,7 @@ int kmv_tc_tune(DeviceContext* ctx, const KParams& kp, const RowOperand& X, cons
   int n = 0, rc = ITERGP_OK;
   *best = -1;
   for (int ares : {0, 1}) for (int epi : {4, 8}) {
-    if (ares && X.d_pad != BK) continue;
+    if (ares && (X.d_pad != BK || nt1 == 2)) continue;
     // the P tile the launchers use with this variant: the widest that fits its ring
     int p_tile = p16;
     const int min_ns = ares ? 3 : 2;

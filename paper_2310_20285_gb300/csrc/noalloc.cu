@@ -98,7 +98,7 @@ extern "C" int itergp_kmatvec_noalloc(const itergp_kernel* kernel, int32_t preci
                                       int* device_status, itergp_stream stream) {
   if (!kernel || !(kernel->kind == ITERGP_RBF || kernel->kind == ITERGP_MATERN32) ||
       !(kernel->lengthscale > 0.f) || !(kernel->outputscale > 0.f) ||
-      precision < ITERGP_FP32 || precision > ITERGP_BF16_COMP)
+      precision < ITERGP_FP32 || precision > ITERGP_TF32)
     return ITERGP_EINVAL;
   if (m < 0 || n < 0 || p < 0 || d < 1 || d > 4096 || p > 65536) return ITERGP_EINVAL;
   if (m == 0 || p == 0) return ITERGP_OK;

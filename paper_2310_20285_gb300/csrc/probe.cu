@@ -1,8 +1,9 @@
 // Throughput probes of the units that bound the kernel product: the MUFU exp2 (one per
-// kernel value of RBF, the exponential of Matern), FP32 FFMA, and the tcgen05 MMA in the
-// shapes the product issues (SS M = 128 with N = 128 or 256, the same while other warps
-// stream TMEM loads, and the TS form of the weighted sum).  Results are operations per
-// second over the whole GPU, timed with CUDA events on the stream.
+// kernel value of RBF, the exponential of Matern) and rsqrt (Matern's distance), FP32
+// FFMA, FP64 DFMA, and the tcgen05 MMA in the shapes the product issues (SS M = 128 with
+// N = 128 or 256, the same while other warps stream TMEM loads, the TS form of the
+// weighted sum, and the SS form with TF32 operands).  Results are operations per second
+// over the whole GPU, timed with CUDA events on the stream.
 #include <algorithm>
 
 #include "internal.h"
@@ -34,6 +35,43 @@ __global__ void probe_ex2_kernel(int iters, float seed, float* sink) {
   if (acc == 12345.f) sink[blockIdx.x] = acc;   // keeps the chains live
 }
 
+__device__ __forceinline__ float rsqrt_approx(float x) {
+  float y;
+  asm volatile("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+// x <- 1 / sqrt(x) stays in [min(x0, 1/sqrt(x0)), max(...)] and tends to 1.
+__global__ void probe_rsqrt_kernel(int iters, float seed, float* sink) {
+  float v[kChains];
+#pragma unroll
+  for (int c = 0; c < kChains; ++c) v[c] = 0.5f + seed * (threadIdx.x + 1 + c) * 1e-4f;
+  for (int it = 0; it < iters; ++it) {
+#pragma unroll
+    for (int c = 0; c < kChains; ++c) v[c] = rsqrt_approx(v[c]);
+  }
+  float acc = 0.f;
+#pragma unroll
+  for (int c = 0; c < kChains; ++c) acc += v[c];
+  if (acc == 12345.f) sink[blockIdx.x] = acc;
+}
+
+// The FFMA chain in FP64.
+__global__ void probe_dfma_kernel(int iters, double seed, float* sink) {
+  double v[kChains];
+#pragma unroll
+  for (int c = 0; c < kChains; ++c) v[c] = seed * (threadIdx.x + c);
+  const double a = 0.999, b = 1e-3;
+  for (int it = 0; it < iters; ++it) {
+#pragma unroll
+    for (int c = 0; c < kChains; ++c) v[c] = fma(v[c], a, b);
+  }
+  double acc = 0.0;
+#pragma unroll
+  for (int c = 0; c < kChains; ++c) acc += v[c];
+  if (acc == 12345.0) sink[blockIdx.x] = static_cast<float>(acc);
+}
+
 // v <- v * a + b with |a| < 1 stays bounded.
 __global__ void probe_ffma_kernel(int iters, float seed, float* sink) {
   float v[kChains];
@@ -56,8 +94,10 @@ __global__ void probe_ffma_kernel(int iters, float seed, float* sink) {
 //   MODE 0: SS, A 128 x 64 and B N x 64 in shared memory (128-byte swizzle, K-major)
 //   MODE 1: MODE 0 while warps 4-7 stream tcgen05.ld of 32 columns from a third region
 //   MODE 2: TS, A (packed BF16 pairs) read from TMEM columns 256.., B N x 64 in shared memory
-// Operands are BF16 values in [0.5, 1) with random signs (finite sums).  Every wait is
-// bounded; on expiry ITERGP_ETIMEOUT goes to the status word.
+//   MODE 3: MODE 0 with kind::tf32 (the same 128-byte rows read as 32 FP32 values, K = 8)
+// Operands are BF16 values in [0.5, 1) with random signs, which read as FP32 are also in
+// [0.5, 1) (finite sums).  Every wait is bounded; on expiry ITERGP_ETIMEOUT goes to the
+// status word.
 constexpr uint64_t kProbeWaitNs = 2000000000ull;
 
 template <int N, int MODE>
@@ -107,7 +147,7 @@ __global__ void __launch_bounds__(256, 1) probe_mma_kernel(int iters, int* statu
   tc_fence_after();
   if (warp == 1) {
     if (lane == 0) {
-      const uint32_t idesc = idesc_bf16_f32(128, N);
+      const uint32_t idesc = MODE == 3 ? idesc_tf32_f32(128, N) : idesc_bf16_f32(128, N);
       const uint64_t dA = sdesc_kmajor_sw128(smem_u32(smem));
       const uint64_t dB = sdesc_kmajor_sw128(smem_u32(smem + A_BYTES));
       for (int it = 0; it < iters; ++it) {
@@ -117,6 +157,8 @@ __global__ void __launch_bounds__(256, 1) probe_mma_kernel(int iters, int* statu
           const uint32_t acc = (it < 2 && kk == 0) ? 0u : 1u;
           if (MODE == 2)
             mma_ts(tb + d, tb + 256 + 8 * kk, dB + 2 * kk, idesc, acc);
+          else if (MODE == 3)
+            mma_ss_tf32(tb + d, dA + 2 * kk, dB + 2 * kk, idesc, acc);
           else
             mma_ss(tb + d, dA + 2 * kk, dB + 2 * kk, idesc, acc);
         }
@@ -151,7 +193,7 @@ __global__ void __launch_bounds__(256, 1) probe_mma_kernel(int iters, int* statu
 }  // namespace
 
 // MMA-rate probe: what = 2 (SS, N = 128), 3 (SS, N = 256), 4 (SS, N = 128 with concurrent
-// TMEM loads), 5 (TS, N = 80); flops per second over the whole GPU.
+// TMEM loads), 5 (TS, N = 80), 6 (SS TF32, N = 128); flops per second over the whole GPU.
 int probe_mma(DeviceContext* ctx, int what, double* ops_per_s, cudaStream_t stream) {
   const int blocks = ctx->num_sms, iters = 20000;
   const size_t smem = 160 * 1024;   // one CTA per SM (the kernel allocates all of TMEM)
@@ -161,8 +203,10 @@ int probe_mma(DeviceContext* ctx, int what, double* ops_per_s, cudaStream_t stre
     case 2: fn = probe_mma_kernel<128, 0>; break;
     case 3: fn = probe_mma_kernel<256, 0>; n = 256; break;
     case 4: fn = probe_mma_kernel<128, 1>; break;
+    case 6: fn = probe_mma_kernel<128, 3>; break;
     default: fn = probe_mma_kernel<80, 2>; n = 80; break;
   }
+  const int k_per_mma = what == 6 ? 8 : 16;
   Scratch sink;
   ITERGP_CUDA_TRY(sink.alloc(ctx, sizeof(float) * blocks, stream));
   ITERGP_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)));
@@ -187,7 +231,7 @@ int probe_mma(DeviceContext* ctx, int what, double* ops_per_s, cudaStream_t stre
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   ITERGP_CUDA_TRY(err);
-  *ops_per_s = static_cast<double>(blocks) * iters * 4 * 2.0 * 128 * n * 16 / (best_ms * 1e-3);
+  *ops_per_s = static_cast<double>(blocks) * iters * 4 * 2.0 * 128 * n * k_per_mma / (best_ms * 1e-3);
   return ITERGP_OK;
 }
 
@@ -204,8 +248,12 @@ int probe_throughput(DeviceContext* ctx, int what, double* ops_per_s, cudaStream
     err = cudaEventRecord(e0, stream);
     if (what == 0)
       probe_ex2_kernel<<<blocks, threads, 0, stream>>>(iters, 0.5f, sink.as<float>()), ::itergp::note_launch();
-    else
+    else if (what == 1)
       probe_ffma_kernel<<<blocks, threads, 0, stream>>>(iters, 0.5f, sink.as<float>()), ::itergp::note_launch();
+    else if (what == 7)
+      probe_dfma_kernel<<<blocks, threads, 0, stream>>>(iters, 0.5, sink.as<float>()), ::itergp::note_launch();
+    else
+      probe_rsqrt_kernel<<<blocks, threads, 0, stream>>>(iters, 0.5f, sink.as<float>()), ::itergp::note_launch();
     if (err == cudaSuccess) err = cudaGetLastError();
     if (err == cudaSuccess) err = cudaEventRecord(e1, stream);
     if (err == cudaSuccess) err = cudaEventSynchronize(e1);
@@ -216,7 +264,8 @@ int probe_throughput(DeviceContext* ctx, int what, double* ops_per_s, cudaStream
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   ITERGP_CUDA_TRY(err);
-  const double ops = static_cast<double>(blocks) * threads * iters * kChains * (what == 0 ? 1.0 : 2.0);
+  // flops for the fused multiply-adds (2 each), operations for the MUFU probes
+  const double ops = static_cast<double>(blocks) * threads * iters * kChains * (what == 1 || what == 7 ? 2.0 : 1.0);
   *ops_per_s = ops / (best_ms * 1e-3);
   return ITERGP_OK;
 }
@@ -224,9 +273,9 @@ int probe_throughput(DeviceContext* ctx, int what, double* ops_per_s, cudaStream
 }  // namespace itergp
 
 extern "C" int itergp_probe_throughput(int32_t what, double* ops_per_s, itergp_stream stream) {
-  if (what < 0 || what > 5 || !ops_per_s) return ITERGP_EINVAL;
+  if (what < 0 || what > 8 || !ops_per_s) return ITERGP_EINVAL;
   itergp::DeviceContext* ctx = itergp::current_context();
   if (!ctx) return ITERGP_ECUDA;
-  if (what >= 2) return itergp::probe_mma(ctx, what, ops_per_s, static_cast<cudaStream_t>(stream));
+  if (what >= 2 && what <= 6) return itergp::probe_mma(ctx, what, ops_per_s, static_cast<cudaStream_t>(stream));
   return itergp::probe_throughput(ctx, what, ops_per_s, static_cast<cudaStream_t>(stream));
 }

@@ -16,12 +16,12 @@ _LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libitergp.
 OK, EINVAL, ENOMEM, ECUDA, ENUMERIC, ETIMEOUT, EUNSUPPORTED, ESCRATCH, EGONE = 0, -1, -2, -3, -4, -5, -6, -7, -8
 NOALLOC_SCRATCH_BYTES = 64 << 20
 RBF, MATERN32 = 0, 1
-FP32, BF16X3, BF16, BF16_COMP = 0, 1, 2, 3
+FP32, BF16X3, BF16, BF16_COMP, TF32 = 0, 1, 2, 3, 4
 POLICY_CG, POLICY_UNIT = 0, 1
 STOP_MAXITER, STOP_TOL, STOP_ETA = 0, 1, 2
 MAX_REPORT_STEPS = 64
 
-PRECISIONS = {"fp32": FP32, "bf16x3": BF16X3, "bf16": BF16, "bf16_comp": BF16_COMP}
+PRECISIONS = {"fp32": FP32, "bf16x3": BF16X3, "bf16": BF16, "bf16_comp": BF16_COMP, "tf32": TF32}
 LIKELIHOODS = {"softmax": 0, "bernoulli": 1, "poisson": 2, "gaussian": 3}
 KERNELS = {"rbf": RBF, "matern32": MATERN32}
 
@@ -459,13 +459,14 @@ def selftest_wait(limit_ns=20_000_000, stream=None):
 
 
 PROBES = {"ex2": 0, "ffma": 1, "mma_ss_n128": 2, "mma_ss_n256": 3, "mma_ss_n128_tmem_ld": 4,
-          "mma_ts_n80": 5}
+          "mma_ts_n80": 5, "mma_ss_n128_tf32": 6, "dfma": 7, "rsqrt": 8}
 
 
 def probe_throughput(what="ex2", stream=None) -> float:
     """Measured operations per second over the GPU: MUFU exp2 ("ex2"), FP32 FFMA ("ffma",
     flops) or BF16 tcgen05.mma flops in the product's shapes ("mma_ss_n128", "mma_ss_n256",
-    "mma_ss_n128_tmem_ld": N = 128 while other warps stream TMEM loads, "mma_ts_n80")."""
+    "mma_ss_n128_tmem_ld": N = 128 while other warps stream TMEM loads, "mma_ts_n80"), TF32
+    tcgen05.mma flops ("mma_ss_n128_tf32"), FP64 DFMA flops ("dfma") or MUFU rsqrt ("rsqrt")."""
     out = ct.c_double()
     _check(lib.itergp_probe_throughput(PROBES[what], ct.byref(out), _stream(stream)),
            "itergp_probe_throughput")

@@ -114,7 +114,7 @@ def test_batched_fit_matches_oracle_per_problem(native, prec, bf16_tol):
     check_against_oracle(native, small_batch(), prec, SCHED_TOL, bf16_tol=bf16_tol)
 
 
-@pytest.mark.parametrize("prec", ["fp32", "bf16x3", "bf16_comp"])
+@pytest.mark.parametrize("prec", ["fp32", "bf16x3", "bf16_comp", "tf32"])
 def test_batched_workload_shape_matches_oracle(native, prec):
     """The batched workload's distributions (D in {8, 16, 32, 64}, C in {2..10}, lengthscale
     log-uniform in [0.3, 3]) at N in [200, 2000], 24 problems."""

@@ -1,8 +1,9 @@
 """Parity of the CUDA kernel product Y = k(A, B) S (App. B.3.1) against the FP64 oracle.
 
 Bars: FP32 paths (fp32, bf16x3) -- normwise relative error <= 1e-4 and componentwise
-|Y - Y_ref| <= 1e-4 (|K| |S|) + tiny; BF16 paths -- normwise <= 1e-2 (their gated
-quantity is the predictive mean; the product's error is recorded here)."""
+|Y - Y_ref| <= 1e-4 (|K| |S|) + tiny; BF16 and TF32 paths -- normwise <= 1e-2 (their
+gated quantity is the predictive mean; the product's error is recorded here).  The TF32
+path also meets the FP32 bar against the product of its TF32-rounded inputs."""
 import math
 
 import numpy as np
@@ -15,7 +16,7 @@ from paper_2310_20285_gb300 import datagen
 pytestmark = pytest.mark.gpu
 
 FP32_PATHS = ["fp32", "bf16x3"]
-ALL_PATHS = ["fp32", "bf16x3", "bf16_comp", "bf16"]
+ALL_PATHS = ["fp32", "bf16x3", "bf16_comp", "bf16", "tf32"]
 KINDS = {"rbf": O.RBF, "matern32": O.MATERN32}
 
 
@@ -115,6 +116,37 @@ def test_empty_inputs(native, prec):
     assert torch.all(Y == 0)
     Y0 = native.kmatvec(torch.empty(0, 3, device=dev), A, torch.randn(5, 2, device=dev), precision=prec)
     assert Y0.shape == (0, 2)
+
+
+def round_tf32(x):
+    """FP32 values rounded to TF32 (10 mantissa bits), nearest with ties to even, on the
+    bit pattern; infinities and NaNs unchanged."""
+    u = np.ascontiguousarray(x, dtype=np.float32).view(np.uint32).astype(np.uint64)
+    finite = (u & 0x7F800000) != 0x7F800000
+    r = ((u + 0xFFF + ((u >> 13) & 1)) & 0xFFFFE000) & 0xFFFFFFFF
+    return np.where(finite, r, u).astype(np.uint32).view(np.float32)
+
+
+def test_round_tf32_helper():
+    x = np.array([1.0, 1.0 + 2.0 ** -11, 1.0 + 3 * 2.0 ** -11, 1.0 + 2.0 ** -10 + 2.0 ** -12,
+                  -2.5, np.inf], dtype=np.float32)
+    want = np.array([1.0, 1.0, 1.0 + 2.0 ** -9, 1.0 + 2.0 ** -10, -2.5, np.inf], dtype=np.float32)
+    assert np.array_equal(round_tf32(x), want)   # ties go to the even neighbour
+
+
+@pytest.mark.parametrize("kind,d", [("rbf", 2), ("matern32", 70), ("matern32", 784)])
+def test_tf32_path_is_exact_on_tf32_rounded_inputs(native, kind, d):
+    """The TF32 form rounds each coordinate once to 10 mantissa bits and otherwise computes
+    like BF16X3 (norms of the rounded rows, FP32 accumulation, split weights), so against
+    the FP64 product of the rounded inputs it meets the FP32 bar."""
+    g = np.random.default_rng(d)
+    m, n, p = 300, 517, 21
+    A = (g.standard_normal((m, d)) * 2).astype(np.float32)
+    B = (g.standard_normal((n, d)) * 2).astype(np.float32)
+    S = g.standard_normal((n, p)).astype(np.float32)
+    ell = 1.0 if d == 2 else math.sqrt(d)
+    Y = run(native, A, B, S, kind, ell, 1.0, "tf32")
+    check(Y, round_tf32(A), round_tf32(B), S, kind, ell, 1.0, "fp32")
 
 
 def test_paths_agree_and_are_deterministic(native):
