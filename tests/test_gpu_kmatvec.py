@@ -161,7 +161,7 @@ def test_paths_agree_and_are_deterministic(native):
     assert torch.linalg.norm(y1 - y3) / torch.linalg.norm(y3) < 1e-4
 
 
-@pytest.mark.parametrize("prec", ["bf16x3", "fp32"])
+@pytest.mark.parametrize("prec", ["bf16x3", "fp32", "tf32"])
 def test_full_size_kernel_bench_sampled_rows(native, prec):
     """N = 60000, D = 784, P = 80, Matern-3/2 l = 28 -- the kernel-bench workload in the
     launch configuration the bench times; 48 sampled output rows against the oracle."""
