@@ -429,6 +429,29 @@ def test_predictive_with_converged_cg_matches_mean_and_bounds_variance():
     assert np.all(var <= kern.outputscale + 1e-12)
 
 
+def test_predictive_variance_is_non_increasing_in_the_iterations():
+    """The predictive function's marginal variance (Eq. 10) shrinks with every IterGP
+    iteration (Prop. A.3: C_j grows by the PSD term d_j d_j^T / eta_j).  With an empty
+    buffer the root Q gains one column per iteration, so the variance after j iterations
+    uses its first j columns; it starts at the prior s, never increases, and ends strictly
+    below s at test points next to training points."""
+    X, y, kern = tiny_problem(n=10, ell=0.8)
+    C = 3
+    res = O.iterncgp_fit(X, O.Softmax(y, C), C, kern, max_newton=1, max_iters=12,
+                         tol_abs=0, tol_rel=0, recycle=False)
+    assert res.Q.shape[1] == res.infos[0].iters == 12
+    Xs = np.concatenate([X[:3] + 0.05, datagen.blobs(4, 2, 3, 98)[0]])
+    prev = None
+    for j in range(res.Q.shape[1] + 1):
+        _, var, _ = O.predict(Xs, X, res.v, res.Q[:, :j], kern, C)
+        if j == 0:
+            assert np.allclose(var, kern.outputscale)
+        else:
+            assert np.all(var <= prev + 1e-12)
+        prev = var
+    assert np.all(prev[:3] < kern.outputscale - 1e-3)
+
+
 def test_predictive_with_contrast_spanning_actions_equals_laplace_predictive():
     """A virtual solver run over actions spanning range(I kron P) (dependent columns are
     dropped as zero eigenpairs) gives C0 = K_hat^-1 restricted to the class contrasts,
