@@ -9,7 +9,7 @@ from paper_2310_20285_gb300 import datagen
 
 pytestmark = pytest.mark.gpu
 DEV = torch.device("cuda:0")
-PREC_CODE = {"bf16x3": 1, "bf16": 2, "bf16_comp": 3}
+PREC_CODE = {"bf16x3": 1, "bf16": 2, "bf16_comp": 3, "tf32": 4}
 
 
 def force(native, tmp_path, prec, kind, d, p16, items, epi, stages, ares=-1):
@@ -22,7 +22,7 @@ def force(native, tmp_path, prec, kind, d, p16, items, epi, stages, ares=-1):
     native.tune_load(path)
 
 
-@pytest.mark.parametrize("prec", ["bf16x3", "bf16_comp", "bf16"])
+@pytest.mark.parametrize("prec", ["bf16x3", "bf16_comp", "bf16", "tf32"])
 @pytest.mark.parametrize("items,p", [(False, 16), (True, 16), (True, 128), (False, 80)])
 def test_autotune_times_every_variant(native, prec, items, p):
     """Includes widths where the launchers tile P (128 split weights do not fit 2 stages)."""
@@ -33,11 +33,12 @@ def test_autotune_times_every_variant(native, prec, items, p):
     native.tune_clear()
 
 
-@pytest.mark.parametrize("prec", ["bf16x3", "bf16"])
+@pytest.mark.parametrize("prec", ["bf16x3", "bf16", "tf32"])
 @pytest.mark.parametrize("epi,stages,ares", [(8, 2, 0), (8, 4, 0), (4, 3, 0), (4, 3, 1), (8, 5, 1)])
 def test_variants_compute_the_same_product(native, tmp_path, prec, epi, stages, ares):
-    """D = 40 (one 64-wide K slice), so both the streamed and the resident-A rings apply;
-    the reference is the streamed 4-warp ring."""
+    """D = 40 (one 64-wide K slice), so both the streamed and the resident-A rings apply
+    (TF32 rows take two 32-wide slices and always stream; a resident-A entry falls back to
+    the streamed ring); the reference is the streamed 4-warp ring."""
     X = torch.as_tensor(datagen.normal((3000, 40), 3), device=DEV)
     S = torch.as_tensor(datagen.normal((3000, 24), 4), device=DEV)
     force(native, tmp_path, prec, 1, 40, 32, 0, 4, 2, 0)
