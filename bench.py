@@ -652,35 +652,54 @@ def main():
     t_e2e = max_over_ranks(t_e2e, dist, dev)
 
     pk, pk_kind = peaks()
+    prec = args.precision
     # what one CTA per SM gets from tcgen05.mma in the distance GEMM's shape (SS, M = N = 128,
-    # K = 16, issued back to back): the ceiling of the tile shape, probed here
-    mma_ceiling = native.probe_throughput("mma_ss_n128") / 1e12
+    # issued back to back): the ceiling of the tile shape, probed here
+    mma_ceiling = native.probe_throughput("mma_ss_n128_tf32" if prec == "tf32" else "mma_ss_n128") / 1e12
     flops = 2.0 * n * n * (D + P)
     kernel_s = (kern_ms / max(kern_n, 1)) / 1e3
     achieved = flops / kernel_s / 1e12
+    # MMA flops issued per algorithmic flop: split operands take three products per
+    # contraction (distance over D, weighted sum over the points)
+    d_terms = {"bf16x3": 3, "bf16_comp": 3, "bf16": 1, "tf32": 1}.get(prec, 1)
+    p_terms = {"bf16x3": 3, "bf16_comp": 1, "bf16": 1, "tf32": 3}.get(prec, 1)
+    issued = 2.0 * n * n * (D * d_terms + P * p_terms)
+    # the peak of the dominant contraction's dtype: BF16 measured; TF32 = measured BF16 x the
+    # nominal dense ratio 1.1 / 2.25; the FP32 form runs on the CUDA cores (probed FFMA)
+    if prec == "fp32":
+        peak, peak_kind, bound, kname = native.probe_throughput("ffma") / 1e12, "FP32 FFMA probed here", "alu", "kmv_simt_kernel"
+    elif prec == "tf32":
+        peak, peak_kind, bound, kname = pk["bf16_tflops"] * 1.1 / 2.25, f"{pk_kind} bf16 dense (burst) x 1.1/2.25 (tf32)", "tensor", "kmv_tc_kernel"
+    else:
+        peak, peak_kind, bound, kname = pk["bf16_tflops"], f"{pk_kind} bf16 dense (burst)", "tensor", "kmv_tc_kernel"
     # DRAM bytes per launch from the ncu capture of this kernel version at N = 40000 (bf16x3,
     # D = 784, P = 80: 1.5492 GB read + 16.4 MB written), scaled by the pairs processed
     # (the lockstep schedule re-reads the B side once per wave, so traffic grows like N^2)
     traffic = None
     if args.precision == "bf16x3":
         traffic = (1.5492e9 + 16.4e6) * (n / 40000.0) ** 2
-    roof = {"bound": "tensor", "achieved": achieved, "peak": pk["bf16_tflops"], "unit": "TFLOP/s",
-            "frac": achieved / pk["bf16_tflops"], "traffic": traffic,
+    roof = {"bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+            "frac": achieved / peak, "traffic": traffic,
             "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of one launch at N=40000, "
                               "scaled by (N/40000)^2" if traffic else None,
             "algorithmic_bytes_per_launch": float(n * 832 * 4 + n * P * 4 * 2),
-            "peak_kind": f"{pk_kind} bf16 dense (burst)",
-            "frac_of_sustained": achieved / pk.get("bf16_tflops_sustained", pk["bf16_tflops"]),
-            "kernel": "kmv_tc_kernel", "kernel_ms": kernel_s * 1e3,
-            "algorithmic_flops_per_launch": flops,
-            "tensor_flops_issued_per_launch": flops * (3.0 if args.precision == "bf16x3" else 1.0),
-            "mma_shape_ceiling_tflops": mma_ceiling,
-            "issued_frac_of_mma_shape_ceiling": achieved * (3.0 if args.precision == "bf16x3" else 1.0) / mma_ceiling}
+            "peak_kind": peak_kind,
+            "kernel": kname, "kernel_ms": kernel_s * 1e3,
+            "algorithmic_flops_per_launch": flops}
+    if prec == "bf16x3":
+        roof["frac_of_sustained"] = achieved / pk.get("bf16_tflops_sustained", pk["bf16_tflops"])
+    if prec != "fp32":
+        roof.update({"tensor_flops_issued_per_launch": issued, "mma_shape_ceiling_tflops": mma_ceiling,
+                     "issued_frac_of_mma_shape_ceiling": issued / kernel_s / 1e12 / mma_ceiling})
 
     out = {"metric": METRIC, "value": value, "unit": "kernel-pairs/s", "n_gpus": world,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_max * 1e3,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-           "dtype": "bf16x3 (BF16 hi/lo split operands, FP32 accumulate; FP32-accurate)",
+           "dtype": {"bf16x3": "bf16x3 (BF16 hi/lo split operands, FP32 accumulate; FP32-accurate)",
+                     "bf16_comp": "bf16_comp (split BF16 distance, BF16 weighted sum, FP32 accumulate)",
+                     "bf16": "bf16 (BF16 operands, FP32 accumulate)",
+                     "tf32": "tf32 (TF32 distance operands, split BF16 weighted sum, FP32 accumulate)",
+                     "fp32": "f32"}[prec],
            "data": "synthetic",
            "config": {"workload": f"kernel product K(X,X)S, N={n}, D={D}, P={P}, Matern-3/2 l=28, s=1; "
                                   "784-D sparse clusters (19% non-zero), S ~ N(0,1)",
