@@ -72,7 +72,7 @@ typedef struct {
  *   ITERGP_TF32      tensor cores; the distance from TF32 operands (rows rounded once to
  *                    10 mantissa bits, nearest-even; norms of the rounded rows; one
  *                    product, K = 8 per instruction), the kernel-weighted sum as in
- *                    BF16X3.  Not offered by the serving loop (ITERGP_EINVAL there). */
+ *                    BF16X3. */
 typedef enum {
   ITERGP_FP32 = 0,
   ITERGP_BF16X3 = 1,
@@ -339,8 +339,7 @@ const char* itergp_last_error(void);
  * least recently used first to make room.  `work_bytes` bounds the workspace of the fits
  * in flight.  A request that can never fit fails with ITERGP_ENOMEM.
  *
- * All models of a server share kernel.kind, precision (FP32, BF16X3, BF16 or BF16_COMP;
- * TF32 is ITERGP_EINVAL here) and the fit schedule.  Data passed
+ * All models of a server share kernel.kind, precision and the fit schedule.  Data passed
  * to submit calls is copied before the call returns; predict outputs are written to the
  * caller's host buffers, which must stay valid until the request's completion event. */
 typedef struct itergp_server itergp_server;

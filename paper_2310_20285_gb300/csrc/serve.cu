@@ -374,9 +374,13 @@ int itergp_server::install(itergp_model* m, const FitReq& r) {
   if (tensor()) {
     __nv_bfloat16* lo = precision_splits_rows(cfg.precision)
                             ? const_cast<__nv_bfloat16*>(rows_op.lo) + r.row0 * d_pad : nullptr;
+    // TF32 rows are FP32 values: the block starts r.row0 rows of 4-byte elements in
+    __nv_bfloat16* hi = precision_tf32_rows(cfg.precision)
+                            ? reinterpret_cast<__nv_bfloat16*>(
+                                  const_cast<float*>(reinterpret_cast<const float*>(rows_op.hi)) + r.row0 * d_pad)
+                            : const_cast<__nv_bfloat16*>(rows_op.hi) + r.row0 * d_pad;
     int rc = prepare_rows_into(cfg.precision, m->X, n, static_cast<int>(m->d), m->d, rows_pad, d_pad,
-                               const_cast<__nv_bfloat16*>(rows_op.hi) + r.row0 * d_pad, lo,
-                               const_cast<float*>(rows_op.norms) + r.row0, s);
+                               hi, lo, const_cast<float*>(rows_op.norms) + r.row0, s);
     if (rc != ITERGP_OK) return rc;
     if (precision_splits_weights(cfg.precision))
       slab_weights_tc_kernel<true><<<blocks_rows, 256, 0, s>>>(m->v, m->Q, n, m->c, m->B, rows_pad, r.row0,
@@ -726,7 +730,7 @@ int itergp_server_create(const itergp_server_config* cfg, itergp_server** out) {
       cfg->c_max < 2 || cfg->c_max > kMeanRows || cfg->max_fit_batch < 1 || cfg->max_predict_batch < 1 ||
       cfg->max_predict_rows < 4096 || cfg->max_newton < 1 || cfg->max_iters < 1 ||
       !(cfg->kind == ITERGP_RBF || cfg->kind == ITERGP_MATERN32) || cfg->precision < ITERGP_FP32 ||
-      cfg->precision > ITERGP_BF16_COMP || !(cfg->tol_abs >= 0) || !(cfg->tol_rel >= 0))
+      cfg->precision > ITERGP_TF32 || !(cfg->tol_abs >= 0) || !(cfg->tol_rel >= 0))
     return ITERGP_EINVAL;
   itergp_fit_params probe{};
   probe.n = int64_t(1) << 40;
@@ -748,7 +752,7 @@ int itergp_server_create(const itergp_server_config* cfg, itergp_server** out) {
   srv->t0 = std::chrono::steady_clock::now();
   const bool tc = precision_is_tensor(cfg->precision);
   srv->d_pad = tc ? (cfg->d_max + 63) / 64 * 64 : cfg->d_max;
-  const int planes = tc ? (precision_splits_rows(cfg->precision) ? 2 : 1) : 0;
+  const int planes = tc ? precision_row_planes(cfg->precision) : 0;   // 2-byte planes per row
   const int wplanes = tc ? (precision_splits_weights(cfg->precision) ? 2 : 1) : 0;
   // bytes per slab row: rows, norm, weights
   const size_t per_row = tc ? (static_cast<size_t>(planes) * srv->d_pad * 2 + 4 + static_cast<size_t>(wplanes) * kWeightRows * 2)
@@ -764,8 +768,10 @@ int itergp_server_create(const itergp_server_config* cfg, itergp_server** out) {
   const size_t o_norm = take(sizeof(float) * R);
   size_t o_hi = 0, o_lo = 0, o_whi = 0, o_wlo = 0, o_x = 0, o_w = 0;
   if (tc) {
-    o_hi = take(static_cast<size_t>(R) * srv->d_pad * 2);
-    if (planes == 2) o_lo = take(static_cast<size_t>(R) * srv->d_pad * 2);
+    // TF32: one FP32 plane in the bytes of two BF16 planes
+    const bool tf32 = precision_tf32_rows(cfg->precision);
+    o_hi = take(static_cast<size_t>(R) * srv->d_pad * 2 * (tf32 ? 2 : 1));
+    if (planes == 2 && !tf32) o_lo = take(static_cast<size_t>(R) * srv->d_pad * 2);
     o_whi = take(static_cast<size_t>(R) * kWeightRows * 2);
     if (wplanes == 2) o_wlo = take(static_cast<size_t>(R) * kWeightRows * 2);
   } else {
@@ -821,7 +827,7 @@ int itergp_server_create(const itergp_server_config* cfg, itergp_server** out) {
     op.X = nullptr;
     op.ldX = cfg->d_max;
     op.hi = reinterpret_cast<__nv_bfloat16*>(b + o_hi);
-    op.lo = planes == 2 ? reinterpret_cast<__nv_bfloat16*>(b + o_lo) : nullptr;
+    op.lo = precision_splits_rows(cfg->precision) ? reinterpret_cast<__nv_bfloat16*>(b + o_lo) : nullptr;
     srv->w_hi = reinterpret_cast<__nv_bfloat16*>(b + o_whi);
     srv->w_lo = wplanes == 2 ? reinterpret_cast<__nv_bfloat16*>(b + o_wlo) : nullptr;
   } else {

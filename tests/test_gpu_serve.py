@@ -63,7 +63,7 @@ def serve(native, probs, prec, mix=True, **kw):
     return out, ev, ids, reqs, stats
 
 
-@pytest.mark.parametrize("prec,tol", [("fp32", 1e-4), ("bf16x3", 1e-4)])
+@pytest.mark.parametrize("prec,tol", [("fp32", 1e-4), ("bf16x3", 1e-4), ("tf32", 1e-4)])
 def test_each_result_is_the_same_alone_and_in_the_mix(native, prec, tol):
     probs = problems(6, seed=5)
     mixed, ev, ids, reqs, stats = serve(native, probs, prec)
@@ -74,8 +74,11 @@ def test_each_result_is_the_same_alone_and_in_the_mix(native, prec, tol):
             assert rel(a, b) <= tol, (prec, i, rel(a, b))
 
 
-@pytest.mark.parametrize("prec,tol", [("fp32", 1e-4), ("bf16x3", 1e-4)])
+@pytest.mark.parametrize("prec,tol", [("fp32", 1e-4), ("bf16x3", 1e-4), ("tf32", 1e-4)])
 def test_served_results_match_the_standalone_api_and_the_oracle(native, prec, tol):
+    """Served and standalone results share their arithmetic (tol); against the FP64 oracle
+    the FP32-accurate forms meet 1e-4 and TF32 the mixed-precision bar of 1e-2."""
+    oracle_tol = 1e-2 if prec == "tf32" else tol
     probs = problems(4, seed=8)
     served, *_ = serve(native, probs, prec)
     for i, p in enumerate(probs):
@@ -92,8 +95,8 @@ def test_served_results_match_the_standalone_api_and_the_oracle(native, prec, to
     ref = O.iterncgp_fit(p.X.astype(np.float64), O.Softmax(p.y, p.c), p.c, kern, max_newton=5,
                          max_iters=5, R=50, tol_abs=1e-5, tol_rel=1e-5)
     em, ev_, ep = O.predict(p.Xs.astype(np.float64), p.X.astype(np.float64), ref.v, ref.Q, kern, p.c)
-    assert rel(served[0][0], em) <= tol
-    assert np.max(np.abs(served[0][1] - ev_)) <= 1e-3
+    assert rel(served[0][0], em) <= oracle_tol
+    assert np.max(np.abs(served[0][1] - ev_)) <= max(1e-3, oracle_tol)
 
 
 def test_predicts_wait_for_their_fit(native):
