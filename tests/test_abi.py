@@ -32,6 +32,26 @@ def test_header_declares_the_boundary():
         assert required in names
 
 
+def header_enum_values():
+    """NAME = value pairs of every enumerator in the header."""
+    src = re.sub(r"/\*.*?\*/", "", open(HEADER).read(), flags=re.S)
+    return {m.group(1): int(m.group(2)) for m in re.finditer(r"\b(ITERGP_[A-Z0-9_]+)\s*=\s*(-?\d+)", src)}
+
+
+def test_binding_constants_match_the_header(lib):
+    """The Python binding's codes for precisions, kernels, likelihoods and policies are the
+    header's enumerators (the binding is loaded on the host only; no CUDA call is made)."""
+    from paper_2310_20285_gb300 import native
+    h = header_enum_values()
+    assert native.PRECISIONS == {"fp32": h["ITERGP_FP32"], "bf16x3": h["ITERGP_BF16X3"], "bf16": h["ITERGP_BF16"],
+                                 "bf16_comp": h["ITERGP_BF16_COMP"], "tf32": h["ITERGP_TF32"]}
+    assert native.KERNELS == {"rbf": h["ITERGP_RBF"], "matern32": h["ITERGP_MATERN32"]}
+    assert native.LIKELIHOODS == {"softmax": h["ITERGP_LIK_SOFTMAX"], "bernoulli": h["ITERGP_LIK_BERNOULLI"],
+                                  "poisson": h["ITERGP_LIK_POISSON"], "gaussian": h["ITERGP_LIK_GAUSSIAN"]}
+    assert (native.POLICY_CG, native.POLICY_UNIT) == (h["ITERGP_POLICY_CG"], h["ITERGP_POLICY_UNIT"])
+    assert native.TUNE_MAX == int(re.search(r"#define ITERGP_TUNE_MAX (\d+)", open(HEADER).read()).group(1))
+
+
 def test_library_exports_every_declared_symbol(lib):
     missing = [n for n in declared_functions() if not hasattr(lib, n)]
     assert not missing, missing
@@ -54,6 +74,8 @@ class Kernel(ct.Structure):
     (0, 0.0, 1.0, 0, 4, 4, 2, 1),      # zero lengthscale
     (0, 1.0, -1.0, 0, 4, 4, 2, 1),     # negative outputscale
     (0, 1.0, 1.0, 9, 4, 4, 2, 1),      # unknown precision
+    (0, 1.0, 1.0, 5, 4, 4, 2, 1),      # the first code past ITERGP_TF32
+    (0, 1.0, 1.0, -1, 4, 4, 2, 1),     # negative precision
     (0, 1.0, 1.0, 0, -1, 4, 2, 1),     # negative m
     (0, 1.0, 1.0, 0, 4, 4, 0, 1),      # d = 0
     (0, 1.0, 1.0, 0, 4, 4, 5000, 1),   # d too large
