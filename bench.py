@@ -148,6 +148,42 @@ def cpu_baseline(X, S, seconds: float):
             "seconds": round(dt, 2)}
 
 
+_ONE_CORE_CHILD = r"""
+import json, sys, time
+sys.path.insert(0, sys.argv[1])
+import numpy as np
+import oracle.itergp_oracle as O
+from paper_2310_20285_gb300 import datagen
+n, seconds, ell, out = int(sys.argv[2]), float(sys.argv[3]), float(sys.argv[4]), float(sys.argv[5])
+X, _, _, _, S = datagen.workload_kernel_bench(n=n)
+X64, S64 = X.astype(np.float64), S.astype(np.float64)
+kern = O.Kernel(O.MATERN32, ell, out)
+rows, t0 = 0, time.perf_counter()
+while time.perf_counter() - t0 < seconds and rows < n:
+    O.kmatvec(X64[rows:rows + 64], X64, S64, kern)
+    rows += 64
+dt = time.perf_counter() - t0
+print(json.dumps({"rows": rows, "seconds": dt}))
+"""
+
+
+def cpu_baseline_one_core(n: int, seconds: float):
+    """The same oracle product on one host core: a child process with every BLAS/OpenMP
+    pool limited to one thread (the pools size themselves when NumPy loads).  Never raises;
+    a failure is reported in the result."""
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
+               BLIS_NUM_THREADS="1", VECLIB_MAXIMUM_THREADS="1", NUMEXPR_NUM_THREADS="1")
+    try:
+        r = subprocess.run([sys.executable, "-c", _ONE_CORE_CHILD, ROOT, str(n), str(seconds), str(ELL), str(OUT)],
+                           env=env, capture_output=True, text=True, timeout=seconds + 180)
+        d = json.loads(r.stdout.strip().splitlines()[-1])
+        return {"value": d["rows"] * n / d["seconds"], "unit": "kernel-pairs/s", "cores": 1,
+                "sample": f"{d['rows']} of {n} output rows (FP64 NumPy, BLAS and OpenMP pools of one thread)",
+                "seconds": round(d["seconds"], 2)}
+    except Exception as e:   # the bench line must not depend on this side measurement
+        return {"error": f"{type(e).__name__}: {str(e)[:200]}"}
+
+
 def reference_arm(args):
     """Oracle on the host cores as the reference implementation (rank 0 only)."""
     rank = int(os.environ.get("RANK", "0"))
@@ -772,6 +808,7 @@ def main():
                       for prec in ("bf16x3", "fp32")]}
     if rank == 0 and world == 1:
         out["cpu_baseline"] = cpu_baseline(X, S, args.cpu_seconds)
+        out["cpu_baseline"]["one_core"] = cpu_baseline_one_core(X.shape[0], min(5.0, args.cpu_seconds / 3))
     if rank == 0:
         print(json.dumps(out))
     if world > 1:
