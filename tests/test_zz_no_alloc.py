@@ -28,9 +28,9 @@ def _call_noalloc(native, A, B, S, prec, ell, status):
     return rc, Y
 
 
-@pytest.mark.parametrize("prec", ["fp32", "bf16x3", "bf16"])
+@pytest.mark.parametrize("prec", ["fp32", "bf16x3", "bf16", "tf32"])
 def test_noalloc_matches_regular_entry_point_on_two_calls_in_a_row(native, prec):
-    tol = 1e-4 if prec in ("fp32", "bf16x3") else 1e-2
+    tol = 1e-4 if prec in ("fp32", "bf16x3", "tf32") else 1e-2
     g = np.random.default_rng(123)
     shapes = [(300, 517, 70, 21), (129, 260, 33, 80)]       # second call: other sizes
     status = torch.zeros(1, dtype=torch.int32, device=DEV)
