@@ -11,6 +11,7 @@ import pytest
 import torch
 
 import oracle.itergp_oracle as O
+from numerics import round_tf32
 from paper_2310_20285_gb300 import datagen
 
 pytestmark = pytest.mark.gpu
@@ -54,6 +55,23 @@ def test_grouped_product_matches_the_oracle(native, prec, m, n, p):
     assert native.sync_status() == 0
     ref = O.kmatvec_classes(A.astype(np.float64), B.astype(np.float64), S.astype(np.float64), okerns(KERNS3), 3)
     assert rel(Y, ref) <= split_tol(prec, np.vstack([A, B]), KERNS3), rel(Y, ref)
+
+
+@pytest.mark.parametrize("m,n,p", [(700, 700, 6), (300, 1041, 7)])
+def test_grouped_tf32_product_is_exact_on_tf32_rounded_inputs(native, m, n, p):
+    """The TF32 form with one kernel per class: against the FP64 grouped product of the
+    TF32-rounded inputs it meets the FP32 bar."""
+    g = np.random.default_rng(m + n + p + 1)
+    A = g.standard_normal((m, 5)).astype(np.float32)
+    B = A if m == n else g.standard_normal((n, 5)).astype(np.float32)
+    S = g.standard_normal((n, p)).astype(np.float32)
+    tA = t32(A)
+    tB = tA if B is A else t32(B)
+    Y = native.kmatvec_classes(tA, tB, t32(S), KERNS3, precision="tf32").cpu().numpy()
+    assert native.sync_status() == 0
+    Ar, Br = round_tf32(A).astype(np.float64), round_tf32(B).astype(np.float64)
+    ref = O.kmatvec_classes(Ar, Br, S.astype(np.float64), okerns(KERNS3), 3)
+    assert rel(Y, ref) <= 1e-4, rel(Y, ref)
 
 
 def test_equal_class_kernels_reduce_to_the_shared_product(native):

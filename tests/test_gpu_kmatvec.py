@@ -11,6 +11,7 @@ import pytest
 import torch
 
 import oracle.itergp_oracle as O
+from numerics import round_tf32
 from paper_2310_20285_gb300 import datagen
 
 pytestmark = pytest.mark.gpu
@@ -116,22 +117,6 @@ def test_empty_inputs(native, prec):
     assert torch.all(Y == 0)
     Y0 = native.kmatvec(torch.empty(0, 3, device=dev), A, torch.randn(5, 2, device=dev), precision=prec)
     assert Y0.shape == (0, 2)
-
-
-def round_tf32(x):
-    """FP32 values rounded to TF32 (10 mantissa bits), nearest with ties to even, on the
-    bit pattern; infinities and NaNs unchanged."""
-    u = np.ascontiguousarray(x, dtype=np.float32).view(np.uint32).astype(np.uint64)
-    finite = (u & 0x7F800000) != 0x7F800000
-    r = ((u + 0xFFF + ((u >> 13) & 1)) & 0xFFFFE000) & 0xFFFFFFFF
-    return np.where(finite, r, u).astype(np.uint32).view(np.float32)
-
-
-def test_round_tf32_helper():
-    x = np.array([1.0, 1.0 + 2.0 ** -11, 1.0 + 3 * 2.0 ** -11, 1.0 + 2.0 ** -10 + 2.0 ** -12,
-                  -2.5, np.inf], dtype=np.float32)
-    want = np.array([1.0, 1.0, 1.0 + 2.0 ** -9, 1.0 + 2.0 ** -10, -2.5, np.inf], dtype=np.float32)
-    assert np.array_equal(round_tf32(x), want)   # ties go to the even neighbour
 
 
 @pytest.mark.parametrize("kind,d", [("rbf", 2), ("matern32", 70), ("matern32", 784)])
