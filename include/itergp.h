@@ -420,7 +420,7 @@ int itergp_server_get_stats(itergp_server* server, itergp_server_stats* stats);
  * itergp_tune_save / _load write / merge the table as text lines
  * "precision kind d_pad p_tile items epilogue_warps stages resident_a" (resident_a: 1, 0,
  * or -1 = where possible; a missing last column reads as -1); _clear empties it. */
-#define ITERGP_TUNE_MAX 6
+#define ITERGP_TUNE_MAX 12
 typedef struct {
   int32_t epilogue_warps, stages;
   double ms;

@@ -88,7 +88,7 @@ class ServerStats(ct.Structure):
 
 
 REQ_FIT, REQ_PREDICT = 0, 1
-TUNE_MAX = 6
+TUNE_MAX = 12
 
 
 class TuneVariant(ct.Structure):
