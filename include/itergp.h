@@ -407,8 +407,9 @@ int itergp_server_get_stats(itergp_server* server, itergp_server_stats* stats);
  * Autotuning of the tensor-core product (a project addition; the paper has no such part).
  * A launch variant is the number of epilogue warps (4, or 8 with two warps per TMEM lane
  * quadrant splitting the columns), the depth of the TMA stage ring (2-4 stages of A and B
- * tiles) and, where D fits one 64-wide slice, a resident-A ring (the row tile's A stays in
- * shared memory; 3 or 5 stages of B tiles).  The library
+ * tiles) and, where D fits one 64-wide slice of BF16 rows, a resident-A ring (the row
+ * tile's A stays in shared memory; 3 or 5 stages of B tiles; not for TF32 rows, which
+ * take two slices per 64 columns).  The library
  * keeps a process-wide table keyed by (precision, kernel kind, D padded to 64, P tile,
  * schedule); launches not in the table use 4 warps and the deepest ring that fits.
  *
