@@ -227,6 +227,33 @@ def test_newton_converges_to_stationary_point():
     assert all(b >= a - 1e-9 for a, b in zip(psi, psi[1:]))
 
 
+def test_objective_gradient_by_finite_differences_vanishes_at_the_newton_limit():
+    """Brute force, independent of the identity grad log p = v: central differences of
+    Psi(f) = log p(y|f) - 1/2 f^T K^-1 f (Eq. 2, m = 0, K^-1 by a dense solve) vanish at
+    the exact Newton iteration's limit and not at its starting point."""
+    X, y, kern = tiny_problem(n=6, ell=1.0)
+    C = 3
+    lik = O.Softmax(y, C)
+    fs, _ = O.exact_newton(X, lik, C, kern, steps=15)
+    K = O.dense_K(X, C, kern)
+
+    def psi(fflat):
+        return lik.loglik(fflat.reshape(-1, C)) - 0.5 * fflat @ np.linalg.solve(K, fflat)
+
+    def fd_grad(f, h=1e-5):
+        f = f.reshape(-1)
+        g = np.zeros_like(f)
+        for i in range(f.size):
+            e = np.zeros_like(f)
+            e[i] = h
+            g[i] = (psi(f + e) - psi(f - e)) / (2 * h)
+        return g
+
+    assert np.max(np.abs(fd_grad(fs[-1]))) < 1e-6
+    # after one step the gradient is still far from zero
+    assert np.max(np.abs(fd_grad(fs[1]))) > 1e-3
+
+
 # ---------------------------------------------------------------------- IterGP (Alg. 2)
 
 def _system(n=10, c=3, seed=7, ell=0.6):
