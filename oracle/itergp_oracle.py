@@ -320,6 +320,22 @@ def exact_newton(X, lik, C, kern: Kernel, steps: int, shift: float | None = None
     return fs, vs
 
 
+def contrast_condition(X, lik, f, kern: Kernel, C: int) -> float:
+    """Condition number of K_hat = K + W^+ restricted to the class contrasts range(I kron P),
+    the subspace the softmax solves live in (reading of Lemma A.6: W^+ vanishes on the
+    per-point class sums).  Dense FP64 eigenvalues of B^T K_hat B, with B an orthonormal
+    basis of range(I kron P); for tiny N only.  It bounds how far FP32 products can move a
+    solve on this subspace."""
+    N = len(X)
+    Khat = dense_K(X, C, kern) + lik.Winv_dense(f)
+    P = np.eye(C) - np.ones((C, C)) / C
+    w, V = np.linalg.eigh(P)
+    Bc = V[:, w > 0.5]                       # the C - 1 unit eigenvectors of the projector
+    B = np.kron(np.eye(N), Bc)
+    lam = np.linalg.eigvalsh(B.T @ Khat @ B)
+    return float(lam.max() / lam.min())
+
+
 def objective(lik, f, v, m):
     """Psi(f) = log p(y|f) - 1/2 (f - m)^T K^-1 (f - m)  (Eq. 2), evaluated without K^-1
     through f - m = K v (Prop. A.1): (f - m)^T K^-1 (f - m) = v^T (f - m)."""

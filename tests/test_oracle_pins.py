@@ -254,6 +254,28 @@ def test_objective_gradient_by_finite_differences_vanishes_at_the_newton_limit()
     assert np.max(np.abs(fd_grad(fs[1]))) > 1e-3
 
 
+def test_contrast_condition_lies_within_its_weyl_bounds():
+    """On range(I kron P) the eigenvalues of K_hat lie in [min 1/pi, lambda_max(k) +
+    max 1/pi] (W^+ = P diag(1/pi) P has Rayleigh quotients in [min 1/pi, max 1/pi] there
+    and K = k kron I_C adds [0, lambda_max(k)]), so 1 <= cond <= (lambda_max(k) +
+    max 1/pi) / min 1/pi along the whole Newton path; without K the condition is that of
+    diag(1/pi) on the contrasts."""
+    X, y, kern = tiny_problem(n=7, ell=0.9)
+    C = 3
+    lik = O.Softmax(y, C)
+    fs, _ = O.exact_newton(X, lik, C, kern, steps=6)
+    lam_k = float(np.linalg.eigvalsh(O.kernel_matrix(X, X, kern)).max())
+    for f in fs:
+        ip = lik.inv_pi(f)
+        kappa = O.contrast_condition(X, lik, f, kern, C)
+        assert 1.0 <= kappa <= (lam_k + ip.max()) / ip.min() * (1 + 1e-12)
+    # K -> 0 (tiny outputscale): the bound tightens to the spread of 1/pi on the contrasts
+    tiny = O.Kernel(kern.kind, kern.lengthscale, 1e-12)
+    f = fs[-1]
+    ip = lik.inv_pi(f)
+    assert O.contrast_condition(X, lik, f, tiny, C) <= ip.max() / ip.min() * (1 + 1e-9)
+
+
 # ---------------------------------------------------------------------- IterGP (Alg. 2)
 
 def _system(n=10, c=3, seed=7, ell=0.6):
