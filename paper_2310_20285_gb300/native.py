@@ -27,16 +27,20 @@ KERNELS = {"rbf": RBF, "matern32": MATERN32}
 
 
 class ItergpError(RuntimeError):
+    """A non-zero status of a library call; `code` is the itergp_status value."""
+
     def __init__(self, code: int, where: str):
         super().__init__(f"{where}: {status_string(code)} ({code})")
         self.code = code
 
 
 class Kernel(ct.Structure):
+    """itergp_kernel: kind (RBF or MATERN32), lengthscale l, outputscale s."""
     _fields_ = [("kind", ct.c_int32), ("lengthscale", ct.c_float), ("outputscale", ct.c_float)]
 
 
 class FitParams(ct.Structure):
+    """itergp_fit_params (field order and types as in include/itergp.h)."""
     _fields_ = [("n", ct.c_int64), ("d", ct.c_int64), ("c", ct.c_int32),
                 ("X", ct.c_void_p), ("y", ct.c_void_p), ("kernel", Kernel),
                 ("precision", ct.c_int32), ("policy", ct.c_int32),
@@ -49,6 +53,8 @@ class FitParams(ct.Structure):
 
 
 class FitReport(ct.Structure):
+    """itergp_fit_report: per Newton step iterations, stop reasons, kept buffer columns,
+    objective and relative change; final residual norm and device bytes."""
     _fields_ = [("newton_steps", ct.c_int32), ("total_iters", ct.c_int32),
                 ("buffer_cols", ct.c_int32), ("stop_reason", ct.c_int32),
                 ("iters", ct.c_int32 * MAX_REPORT_STEPS), ("stops", ct.c_int32 * MAX_REPORT_STEPS),
@@ -60,12 +66,14 @@ class FitReport(ct.Structure):
 
 
 class ModelView(ct.Structure):
+    """itergp_model_view: sizes and device pointers of a model's X, v, f and Q."""
     _fields_ = [("n", ct.c_int64), ("d", ct.c_int64), ("c", ct.c_int32),
                 ("buffer_cols", ct.c_int32), ("kernel", Kernel),
                 ("X", ct.c_void_p), ("v", ct.c_void_p), ("f", ct.c_void_p), ("Q", ct.c_void_p)]
 
 
 class ServerConfig(ct.Structure):
+    """itergp_server_config: memory budgets, shared kernel kind, precision and schedule."""
     _fields_ = [("model_bytes", ct.c_int64), ("work_bytes", ct.c_int64), ("kind", ct.c_int32),
                 ("precision", ct.c_int32), ("d_max", ct.c_int32), ("c_max", ct.c_int32),
                 ("max_fit_batch", ct.c_int32), ("max_predict_batch", ct.c_int32),
@@ -75,12 +83,14 @@ class ServerConfig(ct.Structure):
 
 
 class ServerEvent(ct.Structure):
+    """itergp_server_event: one completed request with its submit, start and done times."""
     _fields_ = [("id", ct.c_int64), ("model", ct.c_int64), ("kind", ct.c_int32),
                 ("status", ct.c_int32), ("submit_s", ct.c_double), ("start_s", ct.c_double),
                 ("done_s", ct.c_double), ("batch", ct.c_int32), ("reserved", ct.c_int32)]
 
 
 class ServerStats(ct.Structure):
+    """itergp_server_stats: resident models and rows, completed work and queue lengths."""
     _fields_ = [(n, ct.c_int64) for n in ("resident_models", "resident_rows", "slab_rows",
                                           "fits_done", "predicts_done", "fit_batches",
                                           "predict_batches", "evicted", "queued_fits",
@@ -92,10 +102,12 @@ TUNE_MAX = 12
 
 
 class TuneVariant(ct.Structure):
+    """One timed launch variant: epilogue warps, ring stages (< 0: resident A), ms."""
     _fields_ = [("epilogue_warps", ct.c_int32), ("stages", ct.c_int32), ("ms", ct.c_double)]
 
 
 class TuneResult(ct.Structure):
+    """itergp_tune_result: up to TUNE_MAX timed variants and the index of the fastest."""
     _fields_ = [("count", ct.c_int32), ("best", ct.c_int32), ("variants", TuneVariant * TUNE_MAX)]
 
 
@@ -159,6 +171,7 @@ lib = _load()
 
 
 def status_string(code: int) -> str:
+    """The library's text for an itergp_status code."""
     return lib.itergp_status_string(int(code)).decode()
 
 
@@ -248,6 +261,7 @@ def kmatvec_noalloc(A, B, S, kind="rbf", lengthscale=1.0, outputscale=1.0, preci
 
 
 def winv_apply(f, x, out=None, stream=None):
+    """W^+ x for the softmax likelihood at f (Lemma A.6): per point P diag(1/pi) P x."""
     n, c = f.shape
     out = torch.empty_like(x) if out is None else out
     _check(lib.itergp_winv_apply(_dev(f, torch.float32, "f"), n, c, _dev(x, torch.float32, "x"),
@@ -256,6 +270,7 @@ def winv_apply(f, x, out=None, stream=None):
 
 
 def pseudo_targets(f, y, out=None, stream=None):
+    """y_hat = f + W^+ grad log p(y|f) for the softmax likelihood (Alg. 1)."""
     n, c = f.shape
     out = torch.empty_like(f) if out is None else out
     _check(lib.itergp_pseudo_targets(_dev(f, torch.float32, "f"), _dev(y, torch.int32, "y"), n, c,
@@ -265,6 +280,8 @@ def pseudo_targets(f, y, out=None, stream=None):
 
 
 def sym_eig(M, stream=None):
+    """Eigenvalues (descending) and eigenvectors of a symmetric FP64 matrix on the GPU
+    (the Jacobi solver of Alg. 3's virtual solver run)."""
     b = M.shape[0]
     lam = torch.empty(b, device=M.device, dtype=torch.float64)
     U = torch.empty((b, b), device=M.device, dtype=torch.float64)
@@ -291,6 +308,7 @@ def launch_count() -> int:
 
 
 def sync_status(stream=None) -> int:
+    """Wait for the stream, then read and clear the device status word (0: no error)."""
     return int(lib.itergp_sync_status(_stream(stream)))
 
 
@@ -303,6 +321,7 @@ class Model:
         self.device = device
 
     def view(self) -> ModelView:
+        """Sizes and device pointers of the model's arrays (owned by the model)."""
         v = ModelView()
         _check(lib.itergp_model_get_view(self._h, ct.byref(v)), "itergp_model_get_view")
         return v
@@ -315,12 +334,16 @@ class Model:
         return view.clone()
 
     def arrays(self):
+        """Copies of v (n x c), f (n x c) and the root Q (buffer columns x n x c)."""
         v = self.view()
         n, c, B = v.n, v.c, v.buffer_cols
         return {"v": self._wrap(v.v, (n, c)), "f": self._wrap(v.f, (n, c)),
                 "Q": self._wrap(v.Q, (B, n, c))}
 
     def predict(self, Xs, want_var=True, want_probs=True, stream=None):
+        """Predictive mean, marginal variance and the likelihood's third output (class
+        probabilities by the probit approximation for softmax and Bernoulli, E[e^f] for
+        Poisson, the mean for Gaussian) at the rows of Xs (Eqs. 9-10)."""
         m = Xs.shape[0]
         c = self.view().c
         mean = torch.empty((m, c), device=Xs.device, dtype=torch.float32)
@@ -335,6 +358,7 @@ class Model:
         return mean, var, probs
 
     def free(self):
+        """Release the model's device memory (idempotent)."""
         if self._h:
             lib.itergp_model_free(self._h)
             self._h = None
@@ -474,14 +498,17 @@ def probe_throughput(what="ex2", stream=None) -> float:
 
 
 def tune_save(path):
+    """Write the launch-variant table as text lines (see include/itergp.h)."""
     _check(lib.itergp_tune_save(str(path).encode()), "itergp_tune_save")
 
 
 def tune_load(path):
+    """Merge a text table written by tune_save into the library's table."""
     _check(lib.itergp_tune_load(str(path).encode()), "itergp_tune_load")
 
 
 def tune_clear():
+    """Empty the launch-variant table (untuned launches use the defaults)."""
     _check(lib.itergp_tune_clear(), "itergp_tune_clear")
 
 
@@ -507,6 +534,8 @@ class Server:
         self._out = {}        # request id -> (mean, var, probs, inputs kept alive)
 
     def submit_fit(self, X, y, c, lengthscale=1.0, outputscale=1.0) -> int:
+        """Queue a fit of host arrays X (n x d) and labels y; returns the model id.  The
+        data are copied before the call returns."""
         np = self._np
         X = np.ascontiguousarray(X, dtype=np.float32)
         y = np.ascontiguousarray(y, dtype=np.int32)
@@ -519,6 +548,8 @@ class Server:
         return mid.value
 
     def submit_predict(self, model_id, Xs, var=True, probs=True) -> int:
+        """Queue a predict against a model (it waits for the model's fit); returns the
+        request id.  Its outputs land in host buffers read back with result()."""
         np = self._np
         Xs = np.ascontiguousarray(Xs, dtype=np.float32)
         c = self._c[model_id]
@@ -548,14 +579,17 @@ class Server:
         return self._out.pop(request_id)
 
     def release(self, model_id):
+        """Drop a resident model once its queued predicts are done."""
         _check(lib.itergp_server_release(self._h, int(model_id)), "itergp_server_release")
 
     def stats(self) -> dict:
+        """Resident models and rows, completed work and queue lengths."""
         st = ServerStats()
         _check(lib.itergp_server_get_stats(self._h, ct.byref(st)), "itergp_server_get_stats")
         return {n: getattr(st, n) for n, _ in ServerStats._fields_}
 
     def close(self):
+        """Stop the request loop and free the server's device memory."""
         if self._h:
             _check(lib.itergp_server_destroy(self._h), "itergp_server_destroy")
             self._h = None
