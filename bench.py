@@ -55,6 +55,15 @@ def aggregate_rate(units_per_rank: float, world: int, t_max: float) -> float:
     return world * units_per_rank / t_max
 
 
+def guarded(fn, *args, **kwargs):
+    """An extra section's result, or its error as {"error": ...}: the headline JSON line
+    must not depend on the sections printed beside it."""
+    try:
+        return fn(*args, **kwargs)
+    except Exception as e:   # noqa: BLE001 -- reported in the line, never swallowed silently
+        return {"error": f"{type(e).__name__}: {str(e)[:300]}"}
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -757,61 +766,66 @@ def main():
                    "d2h_gbs": hY.numel() * 4 / (d2h_ms * 1e6)}}
 
     if rank == 0 and not args.no_extras:
-        paths = {}
-        for prec, k in (("bf16", 5), ("bf16_comp", 5), ("tf32", 5), ("fp32", 2)):
-            step(prec)
-            torch.cuda.synchronize()
-            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            a.record()
-            for _ in range(k):
+        try:
+            paths = {}
+            for prec, k in (("bf16", 5), ("bf16_comp", 5), ("tf32", 5), ("fp32", 2)):
                 step(prec)
-            b.record()
-            torch.cuda.synchronize()
-            tp = a.elapsed_time(b) / 1e3 / k
-            paths[prec] = {"kernel_pairs_per_s": n * n / tp, "ms": tp * 1e3}
-        paths[args.precision] = {"kernel_pairs_per_s": n * n / t_step, "ms": t_step * 1e3}
-        out["paths"] = paths
-        # full IterNCGP fit on the same data: 5 Newton steps x <= 5 iterations, R = 200
-        fits = {}
-        ty = torch.as_tensor(y, device=dev)
-        for prec in ("bf16x3", "bf16", "fp32"):
-            torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            try:
-                m = native.fit(tX, ty, 10, kind="matern32", lengthscale=ELL, outputscale=OUT,
-                               precision=prec, max_newton=5, max_iters=5, rank=200)
-            except native.ItergpError as e:
-                fits[prec] = {"error": str(e)}
-                continue
-            torch.cuda.synchronize()
-            dt = time.perf_counter() - t0
-            mean, var, probs = m.predict(torch.as_tensor(Xs, device=dev))
-            acc = float((probs.argmax(1).cpu().numpy() == ys).mean())
-            r = m.report
-            fits[prec] = {"newton_step_ms": dt * 1e3 / max(r.newton_steps, 1),
-                          "fit_s": dt, "iters": int(r.total_iters), "test_acc": acc,
-                          "objective": [round(r.objective[i], 1) for i in range(r.newton_steps)]}
-            m.free()
-        out["fit"] = {"workload": "IterNCGP fit, same data, C=10, 5 Newton steps x 5 iterations, R=200",
-                      "note": "the undamped Newton trajectory on this kernel (l = sqrt(D): K ~ 0.88 11^T) "
-                              "changes under product perturbations of 1e-7 relative (FP64 oracle with "
-                              "injected noise, N = 20000), so FP32/BF16 fits cannot follow it; times "
-                              "per Newton step are comparable, accuracies are not",
-                      **fits}
+                torch.cuda.synchronize()
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record()
+                for _ in range(k):
+                    step(prec)
+                b.record()
+                torch.cuda.synchronize()
+                tp = a.elapsed_time(b) / 1e3 / k
+                paths[prec] = {"kernel_pairs_per_s": n * n / tp, "ms": tp * 1e3}
+            paths[args.precision] = {"kernel_pairs_per_s": n * n / t_step, "ms": t_step * 1e3}
+            out["paths"] = paths
+            # full IterNCGP fit on the same data: 5 Newton steps x <= 5 iterations, R = 200
+            fits = {}
+            ty = torch.as_tensor(y, device=dev)
+            for prec in ("bf16x3", "bf16", "fp32"):
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                try:
+                    m = native.fit(tX, ty, 10, kind="matern32", lengthscale=ELL, outputscale=OUT,
+                                   precision=prec, max_newton=5, max_iters=5, rank=200)
+                except native.ItergpError as e:
+                    fits[prec] = {"error": str(e)}
+                    continue
+                torch.cuda.synchronize()
+                dt = time.perf_counter() - t0
+                mean, var, probs = m.predict(torch.as_tensor(Xs, device=dev))
+                acc = float((probs.argmax(1).cpu().numpy() == ys).mean())
+                r = m.report
+                fits[prec] = {"newton_step_ms": dt * 1e3 / max(r.newton_steps, 1),
+                              "fit_s": dt, "iters": int(r.total_iters), "test_acc": acc,
+                              "objective": [round(r.objective[i], 1) for i in range(r.newton_steps)]}
+                m.free()
+            out["fit"] = {"workload": "IterNCGP fit, same data, C=10, 5 Newton steps x 5 iterations, R=200",
+                          "note": "the undamped Newton trajectory on this kernel (l = sqrt(D): K ~ 0.88 11^T) "
+                                  "changes under product perturbations of 1e-7 relative (FP64 oracle with "
+                                  "injected noise, N = 20000), so FP32/BF16 fits cannot follow it; times "
+                                  "per Newton step are comparable, accuracies are not",
+                          **fits}
+        except Exception as e:   # noqa: BLE001 -- recorded in the line
+            err = {"error": f"{type(e).__name__}: {str(e)[:300]}"}
+            out.setdefault("paths", err)
+            out.setdefault("fit", err)
     if rank == 0 and not args.no_extras:
-        out["small_d_roofline"] = small_d_roofline(native, torch, dev)
-        out["batched"] = bench_batched(native, datagen, torch, dev, args.batch_count)
+        out["small_d_roofline"] = guarded(small_d_roofline, native, torch, dev)
+        out["batched"] = guarded(bench_batched, native, datagen, torch, dev, args.batch_count)
     if rank == 0 and not args.no_extras:
-        out["gmm_large"] = bench_gmm(native, datagen, torch, dev)
-        out["class_kernels"] = bench_class_kernels(native, datagen, torch, dev)
-        out["likelihoods"] = bench_likelihoods(native, datagen, torch, dev)
+        out["gmm_large"] = guarded(bench_gmm, native, datagen, torch, dev)
+        out["class_kernels"] = guarded(bench_class_kernels, native, datagen, torch, dev)
+        out["likelihoods"] = guarded(bench_likelihoods, native, datagen, torch, dev)
     if rank == 0 and not args.no_extras and args.serve_seconds > 0:
         out["serving"] = {
             "workload": f"{args.serve_seconds:g} s of Poisson arrivals: fits 50/s (N log-U[1e3,5e4], D=32, C=5, "
                         "RBF l log-U[0.3,3], 5 Newton x <=5 iters, R=50) and predicts 2000/s (M U[1,4096], "
                         "D=32) against resident models; 80 GB model budget; latency = results in host "
                         "buffers minus submission",
-            "forms": [bench_serving(native, datagen, prec, args.serve_seconds)
+            "forms": [guarded(bench_serving, native, datagen, prec, args.serve_seconds)
                       for prec in ("bf16x3", "fp32")]}
     if rank == 0 and world == 1:
         out["cpu_baseline"] = cpu_baseline(X, S, args.cpu_seconds)

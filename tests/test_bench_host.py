@@ -1,6 +1,7 @@
-"""The bench's clock record: median SM clock under load, the maximum clock and every
-throttle reason seen while the timed region ran (a run that saw a hardware or thermal
-slowdown is rejected, so the reasons must not be lost)."""
+"""Host-side helpers of bench.py.  The clock record: median SM clock under load, the
+maximum clock and every throttle reason seen while the timed region ran (a run that saw
+a hardware or thermal slowdown is rejected, so the reasons must not be lost).  The extra
+sections: a failing one is recorded in the line instead of losing the line."""
 import bench
 
 
@@ -23,3 +24,10 @@ def test_clock_summary_of_a_quiet_run_and_of_no_samples():
     assert c == {"sm_mhz": 2070.0, "sm_max_mhz": 2070.0, "reasons": [], "samples": 5}
     empty = bench.summarize_clock_samples([])
     assert empty["sm_mhz"] is None and empty["samples"] == 0
+
+
+def test_a_failing_extra_section_is_recorded_not_raised():
+    def boom(x):
+        raise RuntimeError(f"device said no ({x})")
+    assert bench.guarded(lambda a, b=0: a + b, 2, b=3) == 5
+    assert bench.guarded(boom, 7) == {"error": "RuntimeError: device said no (7)"}
