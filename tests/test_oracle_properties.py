@@ -1,0 +1,79 @@
+"""Property-based pins of the oracle (host only): the identities the fixed-seed pins check,
+over random shapes, class counts, logits and kernels.  Each property is fixed by the
+mathematics, not by the oracle's own formulas."""
+import numpy as np
+import pytest
+from scipy.spatial.distance import cdist
+
+import oracle.itergp_oracle as O
+
+hypothesis = pytest.importorskip("hypothesis")
+from hypothesis import given, settings, strategies as st  # noqa: E402
+
+SETTINGS = settings(max_examples=30, deadline=None)
+
+
+@SETTINGS
+@given(n=st.integers(1, 6), c=st.integers(2, 6), scale=st.floats(0.1, 6.0), seed=st.integers(0, 2**31 - 1))
+def test_w_pseudo_inverse_is_moore_penrose(n, c, scale, seed):
+    """Lemma A.6 at random logits: P diag(1/pi) P is the Moore-Penrose inverse of each
+    softmax Hessian block, W W^+ = P, and W^+ 1 = 0."""
+    g = np.random.default_rng(seed)
+    f = scale * g.standard_normal((n, c))
+    lik = O.Softmax(g.integers(0, c, n), c)
+    Wb = lik.W_blocks(f)
+    Wd = lik.Winv_dense(f)
+    P = np.eye(c) - np.ones((c, c)) / c
+    for k in range(n):
+        A, Ap = Wb[k], Wd[k * c:(k + 1) * c, k * c:(k + 1) * c]
+        assert np.allclose(A @ Ap @ A, A, atol=1e-10 * max(1.0, np.abs(A).max()))
+        assert np.allclose(A @ Ap, P, atol=1e-9)
+        assert np.allclose(A.sum(axis=1), 0.0, atol=1e-12)      # rows of W sum to zero
+    assert np.allclose(lik.Winv_apply(f, np.ones((n, c))), 0.0, atol=1e-9)
+
+
+@SETTINGS
+@given(m=st.integers(1, 7), n=st.integers(1, 7), d=st.integers(1, 5), p=st.integers(1, 4),
+       kind=st.sampled_from([O.RBF, O.MATERN32]), ell=st.floats(0.2, 5.0), s=st.floats(0.1, 3.0),
+       seed=st.integers(0, 2**31 - 1))
+def test_kernel_product_equals_the_double_loop(m, n, d, p, kind, ell, s, seed):
+    """k(A, B) S against a double loop over the textbook kernel formulas on scipy's
+    Euclidean distances."""
+    g = np.random.default_rng(seed)
+    A, B, S = g.standard_normal((m, d)), g.standard_normal((n, d)), g.standard_normal((n, p))
+    r = cdist(A, B)
+    want = np.zeros((m, p))
+    for i in range(m):
+        for j in range(n):
+            if kind == O.RBF:
+                k = s * np.exp(-r[i, j] ** 2 / (2 * ell ** 2))
+            else:
+                z = np.sqrt(3.0) * r[i, j] / ell
+                k = s * (1 + z) * np.exp(-z)
+            want[i] += k * S[j]
+    got = O.kmatvec(A, B, S, O.Kernel(kind, ell, s))
+    assert np.allclose(got, want, rtol=1e-10, atol=1e-12)
+
+
+@SETTINGS
+@given(n=st.integers(2, 8), d=st.integers(1, 4), kind=st.sampled_from([O.RBF, O.MATERN32]),
+       ell=st.floats(0.3, 3.0), seed=st.integers(0, 2**31 - 1))
+def test_kernel_matrix_is_symmetric_psd_with_the_outputscale_on_its_diagonal(n, d, kind, ell, seed):
+    g = np.random.default_rng(seed)
+    X = g.standard_normal((n, d))
+    K = O.kernel_matrix(X, X, O.Kernel(kind, ell, 1.7))
+    assert np.allclose(K, K.T, atol=1e-14)
+    assert np.allclose(np.diag(K), 1.7, atol=1e-12)
+    assert np.linalg.eigvalsh(K).min() >= -1e-10 * 1.7
+
+
+@SETTINGS
+@given(n=st.integers(1, 6), c=st.integers(2, 6), seed=st.integers(0, 2**31 - 1))
+def test_softmax_gradient_sums_to_zero_and_pseudo_targets_stay_in_the_contrasts(n, c, seed):
+    """sum_c grad_c = 0 per point, so W^+ grad and y_hat - f have zero class mean."""
+    g = np.random.default_rng(seed)
+    f = 2 * g.standard_normal((n, c))
+    lik = O.Softmax(g.integers(0, c, n), c)
+    assert np.allclose(lik.grad(f).sum(axis=1), 0.0, atol=1e-12)
+    yhat = O.pseudo_targets(lik, f)
+    assert np.allclose((yhat - f).sum(axis=1), 0.0, atol=1e-9)
