@@ -122,3 +122,22 @@ def test_the_root_stays_khat_orthonormal(n, c, iters, seed):
                                 policy=O.CG, max_iters=iters, tol_abs=0, tol_rel=0)
     assert np.allclose(Q.T @ Khat @ Q, np.eye(Q.shape[1]), atol=1e-7)
     assert np.allclose(v, Q @ (Q.T @ b), rtol=1e-8, atol=1e-9)   # v_j = C_j b from v_0 = 0
+
+
+@SETTINGS
+@given(n=st.integers(2, 5), c=st.integers(2, 3), k=st.integers(1, 5), seed=st.integers(0, 2**31 - 1))
+def test_virtual_solver_run_projects_out_the_recycled_actions(n, c, k, seed):
+    """Alg. 3 on k random recycled actions (k <= NC): S^T r_0 = 0 (Prop. A.4), the
+    recycled root equals S (S^T K_hat S)^-1 S^T (Eq. 12) and T stays K S."""
+    Khat, b, kmv, winv = _random_system(n, c, seed, ell=0.5)
+    NC = b.size
+    k = min(k, NC)
+    S = np.random.default_rng(seed + 1).standard_normal((NC, k))
+    T = np.stack([kmv(S[:, j]) for j in range(k)], axis=1)
+    winv_cols = lambda M: np.stack([winv(M[:, j]) for j in range(M.shape[1])], axis=1)  # noqa: E731
+    Q0, S2, T2, dropped = O.virtual_solver_run(S, T, winv_cols, R=None)
+    assert dropped == 0
+    v0 = Q0 @ (Q0.T @ b)
+    assert np.allclose(S.T @ (b - Khat @ v0), 0.0, atol=1e-8 * np.linalg.norm(b))
+    assert np.allclose(Q0 @ Q0.T, S @ np.linalg.solve(S.T @ Khat @ S, S.T), atol=1e-8)
+    assert np.allclose(T2, np.stack([kmv(S2[:, j]) for j in range(S2.shape[1])], axis=1), atol=1e-10)
