@@ -164,6 +164,136 @@ def cpu_baseline(X, S, seconds: float):
             "seconds": round(dt, 2)}
 
 
+def newton_step_ms_small(native, datagen, torch, dev, reps=5):
+    """The small multi-class workload (N = 500 blobs, D = 2, C = 3, RBF l = 1, 10 Newton
+    steps x <= 50 CG iterations, R = 50, tolerances 1e-5) on the GPU: ms per Newton step of
+    whole fits (median of `reps`, after one warm-up), FP32 against BF16X3, with the fit
+    captured into one CUDA graph and with direct launches."""
+    import numpy as np
+    X, y, _, _ = datagen.workload_small()
+    tX = torch.as_tensor(X.astype(np.float32), device=dev)
+    ty = torch.as_tensor(y, device=dev)
+    out = {"workload": "N=500, D=2, C=3 blobs, RBF l=1, 10 Newton x <=50 CG, R=50, tol 1e-5"}
+    for prec in ("fp32", "bf16x3"):
+        row = {}
+        for graph in (True, False):
+            ts, steps = [], 10
+            for r in range(reps + 1):
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                m = native.fit(tX, ty, 3, kind="rbf", lengthscale=1.0, precision=prec, max_newton=10,
+                               max_iters=50, rank=50, graph=graph)
+                torch.cuda.synchronize()
+                dt = time.perf_counter() - t0
+                steps = int(m.report.newton_steps)
+                m.free()
+                if r > 0:
+                    ts.append(dt)
+            row["graph" if graph else "direct"] = {"newton_step_ms": round(float(np.median(ts)) * 1e3 / steps, 4),
+                                                    "fit_ms": round(float(np.median(ts)) * 1e3, 3)}
+        out[prec] = row
+    return out
+
+
+def cpu_baseline_oracle_runs(native, datagen, torch, dev, X, S, seconds):
+    """The FP64 oracle beyond the headline product, on the host cores, and the error of
+    every GPU result against it:
+      - the small workload's full fit (10 x 50, R = 50) timed;
+      - the precision report of the 5000-point inputs (the small workload's generator at
+        N = 5000 and the first 5000 rows of the kernel-bench data): K.S (24 columns), every
+        Newton iterate f_i and the predictive mean of a 10 x 50, R = 50 fit, per precision;
+      - the kernel-bench fit (N = 60000, 5 Newton x 5 iterations, R = 200) estimated from
+        the oracle's own pieces timed on a row block: its dense kernel matrix and its K
+        products (the solver's O(N C B) work is small next to them);
+      - the oracle's FP32 matrix-free product on a row sample."""
+    import numpy as np
+
+    import oracle.itergp_oracle as O
+    res = {}
+    X1, y1, _, _ = datagen.workload_small()
+    t0 = time.perf_counter()
+    O.iterncgp_fit(X1.astype(np.float32).astype(np.float64), O.Softmax(y1, 3), 3, O.Kernel(O.RBF, 1.0, 1.0),
+                   max_newton=10, max_iters=50, R=50)
+    res["small_fit_s"] = round(time.perf_counter() - t0, 3)
+
+    def rel(a, b):
+        a = np.asarray(a, dtype=np.float64)
+        b = np.asarray(b, dtype=np.float64)
+        return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+    precs = ["fp32", "bf16x3", "bf16_comp", "bf16", "tf32"]
+    acc = {"workload": "5000-point inputs: blobs (the small workload's generator, D=2, RBF l=1) and "
+                       "the first 5000 rows of the kernel-bench data (D=784, Matern l=28); errors are "
+                       "normwise relative against the FP64 oracle"}
+    for data in ("blobs5000", "kernel_bench5000"):
+        if data == "blobs5000":
+            Xa, ya, Xsa, _ = datagen.blobs_train_test(5000, 200, d=2, c=3, seed=0)
+            kern, kind = O.Kernel(O.RBF, 1.0, 1.0), "rbf"
+        else:
+            Xa, ya, Xsa, _, _ = datagen.workload_kernel_bench(n=5000, n_test=10)
+            kern, kind = O.Kernel(O.MATERN32, 28.0, 1.0), "matern32"
+        Xa = np.asarray(Xa, dtype=np.float32)
+        Sa = datagen.normal((5000, 24), 77)
+        t0 = time.perf_counter()
+        ref = O.kmatvec(Xa.astype(np.float64), Xa.astype(np.float64), Sa.astype(np.float64), kern)
+        res[f"kmatvec_{data}_s"] = round(time.perf_counter() - t0, 3)
+        tX, tS = torch.as_tensor(Xa, device=dev), torch.as_tensor(Sa, device=dev)
+        acc[f"K.S {data}"] = {p: rel(native.kmatvec(tX, tX, tS, kind=kind, lengthscale=kern.lengthscale,
+                                                     precision=p).cpu(), ref) for p in precs}
+        if data == "blobs5000":
+            t0 = time.perf_counter()
+            fref = O.iterncgp_fit(Xa.astype(np.float64), O.Softmax(ya, 3), 3, kern, max_newton=10,
+                                  max_iters=50, R=50)
+            res["blobs5000_fit_s"] = round(time.perf_counter() - t0, 3)
+            em, _, _ = O.predict(Xsa.astype(np.float32).astype(np.float64), Xa.astype(np.float64), fref.v,
+                                 fref.Q, kern, 3)
+            ty = torch.as_tensor(ya, device=dev)
+            tXs = torch.as_tensor(Xsa.astype(np.float32), device=dev)
+            fit = {}
+            for p in precs:
+                fi, mean_err = [], None
+                for i in range(1, 11):
+                    m = native.fit(tX, ty, 3, kind="rbf", lengthscale=1.0, precision=p, max_newton=i,
+                                   max_iters=50, rank=50)
+                    fi.append(rel(m.arrays()["f"].cpu(), fref.fs[i]))
+                    if i == 10:
+                        mean, _, _ = m.predict(tXs)
+                        mean_err = rel(mean.cpu(), em)
+                    m.free()
+                fit[p] = {"f_i": [float(f"{e:.3g}") for e in fi], "mean": mean_err}
+            acc["fit blobs5000 (10 x 50, R=50)"] = fit
+    res["accuracy"] = acc
+    # kernel-bench fit, estimated from the oracle's own pieces on a row block
+    n = X.shape[0]
+    blk = 1000
+    kern2 = O.Kernel(O.MATERN32, ELL, OUT)
+    X64 = X.astype(np.float64)
+    t0 = time.perf_counter()
+    Kb = O.kernel_matrix(X64[:blk], X64, kern2)
+    t_k = time.perf_counter() - t0
+    W = np.asarray(S[:, :10], dtype=np.float64)
+    t0 = time.perf_counter()
+    for _ in range(3):
+        Kb @ W
+    t_p = (time.perf_counter() - t0) / 3
+    products = 5 * 5 + 5   # one K product per solver iteration plus f = K v per Newton step
+    est = (t_k + products * t_p) * n / blk
+    res["kernel_bench_fit_s_estimated"] = {"value": round(est, 1), "kernel_matrix_s": round(t_k * n / blk, 1),
+                                           "products": products, "product_s": round(t_p * n / blk, 3),
+                                           "note": f"oracle pieces timed on {blk} of {n} rows and scaled by rows; "
+                                                   "the dense K it builds holds 28.8 GB in FP64"}
+    # the oracle's FP32 matrix-free product
+    rows, t0 = 0, time.perf_counter()
+    while time.perf_counter() - t0 < seconds and rows < n:
+        O.kmatvec_fp32(X[rows:rows + 64], X, S, kern2)
+        rows += 64
+    dt = time.perf_counter() - t0
+    res["kmatvec_fp32"] = {"value": rows * n / dt, "unit": "kernel-pairs/s", "cores": os.cpu_count(),
+                           "sample": f"{rows} of {n} output rows (FP32 NumPy, D={X.shape[1]}, P={S.shape[1]})",
+                           "seconds": round(dt, 2)}
+    return res
+
+
 _ONE_CORE_CHILD = r"""
 import json, sys, time
 sys.path.insert(0, sys.argv[1])
@@ -498,6 +628,75 @@ def bench_likelihoods(native, datagen, torch, dev, n=20000, n_test=10000):
     return out
 
 
+def mc_nll(mu, var, y, samples, rng):
+    """Monte-Carlo negative log predictive density of Poisson counts y under latent
+    N(mu, var) per point (App. C): -log mean_k Poisson(y | e^{f_k}), averaged over the
+    points."""
+    import numpy as np
+    from math import lgamma
+    z = rng.standard_normal((samples, 1))
+    f = mu[None, :] + np.sqrt(np.maximum(var, 0.0))[None, :] * z       # samples x n
+    lp = y[None, :] * f - np.exp(f) - np.array([lgamma(v + 1.0) for v in y])[None, :]
+    mx = lp.max(axis=0)
+    return float(np.mean(-(mx + np.log(np.mean(np.exp(lp - mx), axis=0)))))
+
+
+def bench_poisson_study(native, datagen, torch, dev, runs=10, samples=10000):
+    """The Poisson-regression budget study (App. C): 100 points in [0, 1], a log-rate drawn
+    from an RBF GP (l = 0.1, s = 5), counts y ~ Poisson(e^f); the prior uses the same
+    kernel.  A budget of 100 solver iterations is spread over 5, 10, 20 or 100 Newton steps
+    (j <= 20, 10, 5, 1), CG actions with recycling and no compression, outer tolerance
+    0.001; `runs` training sets re-drawn at the same rates, and a test set drawn the same
+    way.  Fits run through itergp_fit (Poisson likelihood, FP32); the NLL is a Monte-Carlo
+    estimate over `samples` draws per point, outside the timed region.  Two starts: f_0 =
+    m = 0 as Alg. 1 prints it, and the constant f_0 = log(mean y)."""
+    import numpy as np
+    X, f_true, Y, Yt = datagen.poisson_study(seed=11, runs=runs)
+    tX = torch.as_tensor(X, device=dev)
+    rng = np.random.default_rng(12)
+    out = {"workload": f"Poisson regression, N=100 in [0,1], RBF l=0.1 s=5, {runs} runs, budget 100 "
+                       f"solver iterations, outer tol 1e-3, R unbounded, fp32; MC-NLL with {samples} "
+                       "draws per point (the paper uses 1e5)"}
+    for start in ("zero", "log_mean"):
+        rows = {}
+        for steps in (5, 10, 20, 100):
+            j = 100 // steps
+            tr, te, ms, used, errs = [], [], [], [], []
+            for r in range(runs):
+                ty = torch.as_tensor(Y[r], device=dev)
+                kw = {}
+                if start == "log_mean":
+                    kw["f0"] = torch.full((100, 1), float(np.log(max(Y[r].mean(), 1e-3))), device=dev)
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                try:
+                    m = native.fit(tX, ty, 1, kind="rbf", lengthscale=0.1, outputscale=5.0, likelihood="poisson",
+                                   precision="fp32", max_newton=steps, max_iters=j, rank=-1, tol_newton=1e-3, **kw)
+                except native.ItergpError as e:
+                    errs.append(str(e)[:60])
+                    continue
+                torch.cuda.synchronize()
+                ms.append((time.perf_counter() - t0) * 1e3)
+                used.append(int(m.report.newton_steps))
+                mean, var, _ = m.predict(tX)
+                mu = mean.double().cpu().numpy().reshape(-1)
+                vv = var.double().cpu().numpy().reshape(-1)
+                m.free()
+                if not np.all(np.isfinite(mu)):
+                    errs.append("non-finite predictive mean")
+                    continue
+                tr.append(mc_nll(mu, vv, Y[r].astype(np.float64), samples, rng))
+                te.append(mc_nll(mu, vv, Yt[r].astype(np.float64), samples, rng))
+            rows[f"{steps}x{j}"] = {
+                "runs_ok": len(tr), "failed": errs[:3] + ([f"... {len(errs) - 3} more"] if len(errs) > 3 else []),
+                "train_nll": [round(float(np.mean(tr)), 4), round(float(np.std(tr)), 4)] if tr else None,
+                "test_nll": [round(float(np.mean(te)), 4), round(float(np.std(te)), 4)] if te else None,
+                "fit_ms": round(float(np.mean(ms)), 3) if ms else None,
+                "newton_steps_used": [int(min(used)), int(max(used))] if used else None}
+        out[f"start_{start}"] = rows
+    return out
+
+
 def bench_serving(native, datagen, precision, seconds, seed=5, drain_s=10.0):
     """Serving: Poisson arrivals over `seconds` of fit requests at 50/s (N log-uniform in
     [1e3, 5e4], D = 32, C = 5 blobs, RBF l log-uniform in [0.3, 3]; 5 Newton x <= 5
@@ -633,10 +832,12 @@ def main():
                                        lengthscale=ELL if kind == "matern32" else 1.0)
             tuning.append({"shape": label, "n": tn, "d": td, "p": tp, "precision": prec,
                            "schedule": "items" if items else "single",
-                           "variants_ms": {f"{e}w/{abs(st)}st{'/residentA' if st < 0 else ''}": round(ms, 4)
-                                           for e, st, ms in vs},
+                           "variants_ms": {f"{e}w/{abs(st)}st{'/residentA' if st < 0 else ''}"
+                                           f"{'/pair' if pr else ''}": round(ms, 4)
+                                           for e, st, pr, ms in vs},
                            "chosen": (f"{best[0]} epilogue warps, {abs(best[1])} stages"
-                                      f"{', resident A' if best[1] < 0 else ''}") if best else None})
+                                      f"{', resident A' if best[1] < 0 else ''}"
+                                      f"{', CTA pairs' if best[2] else ''}") if best else None})
 
     for _ in range(max(args.warmup, 3)):
         step()
@@ -819,6 +1020,7 @@ def main():
         out["gmm_large"] = guarded(bench_gmm, native, datagen, torch, dev)
         out["class_kernels"] = guarded(bench_class_kernels, native, datagen, torch, dev)
         out["likelihoods"] = guarded(bench_likelihoods, native, datagen, torch, dev)
+        out["poisson_study"] = guarded(bench_poisson_study, native, datagen, torch, dev)
     if rank == 0 and not args.no_extras and args.serve_seconds > 0:
         out["serving"] = {
             "workload": f"{args.serve_seconds:g} s of Poisson arrivals: fits 50/s (N log-U[1e3,5e4], D=32, C=5, "
@@ -827,9 +1029,16 @@ def main():
                         "buffers minus submission",
             "forms": [guarded(bench_serving, native, datagen, prec, args.serve_seconds)
                       for prec in ("bf16x3", "fp32")]}
+    if rank == 0 and not args.no_extras:
+        out["newton_step_small"] = guarded(newton_step_ms_small, native, datagen, torch, dev)
     if rank == 0 and world == 1:
         out["cpu_baseline"] = cpu_baseline(X, S, args.cpu_seconds)
         out["cpu_baseline"]["one_core"] = cpu_baseline_one_core(X.shape[0], min(5.0, args.cpu_seconds / 3))
+        if not args.no_extras:
+            runs = guarded(cpu_baseline_oracle_runs, native, datagen, torch, dev, X, S, min(10.0, args.cpu_seconds))
+            if isinstance(runs, dict) and "accuracy" in runs:
+                out["accuracy"] = runs.pop("accuracy")
+            out["cpu_baseline"]["oracle_runs"] = runs
     if rank == 0:
         print(json.dumps(out))
     if world > 1:

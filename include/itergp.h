@@ -135,7 +135,10 @@ int itergp_kmatvec_classes(const itergp_kernel* kernels, int32_t c, int32_t prec
  *    operand, so e.g. m = n = 8192, d = 784 fits; the FP32 precision needs far less).
  *  - The first call on a device looks up the array's device address with
  *    cudaGetSymbolAddress (device set-up, once per device); make that first call before
- *    any stream capture.
+ *    any stream capture.  Under CUDA's default lazy module loading the 64 MiB array is
+ *    created on the device at that lookup (under eager loading, when the library loads),
+ *    so the first call needs 64 MiB of free device memory: make it before reserving the
+ *    rest of the device.  A call with m = 0 (or p = 0) performs only this set-up.
  *  - Every call shares the one array, which keeps the previous call's contents; all of it
  *    that is read is written first within the call.  Calls whose work overlaps on the GPU
  *    (different streams, or host threads without ordering) race on the array: serialise
@@ -226,6 +229,10 @@ typedef struct {
    * Alg. 1 as printed converges to a point off the posterior mode.  Copied by the fit;
    * batched fits with per-class kernels run their problems one after another. */
   const itergp_kernel* class_kernels;
+  uint64_t wait_limit_ns; /* bound of every device-side wait of the fit's kernel products,
+                             1e6 .. 6e10 ns, or 0 for the default 4 s; a wait that runs
+                             out ends the product with ITERGP_ETIMEOUT (the fit returns
+                             it) instead of hanging                                 */
 } itergp_fit_params;
 
 #define ITERGP_MAX_REPORT_STEPS 64
@@ -245,6 +252,9 @@ typedef struct {
   int32_t status;         /* this problem's outcome: ITERGP_OK, ITERGP_EINVAL (a    */
                           /* label out of range) or ITERGP_ENUMERIC (1/pi overflow)  */
   int32_t reserved;
+  int64_t peak_bytes;     /* library-pool bytes the call held at its peak: models,
+                             fit workspace and product scratch (all problems of a
+                             batched call together)                                  */
 } itergp_fit_report;
 
 typedef struct itergp_model itergp_model;
@@ -407,9 +417,11 @@ int itergp_server_get_stats(itergp_server* server, itergp_server_stats* stats);
  * Autotuning of the tensor-core product (a project addition; the paper has no such part).
  * A launch variant is the number of epilogue warps (4, or 8 with two warps per TMEM lane
  * quadrant splitting the columns), the depth of the TMA stage ring (2-4 stages of A and B
- * tiles) and, where D fits one 64-wide slice of BF16 rows, a resident-A ring (the row
+ * tiles), where D fits one 64-wide slice of BF16 rows a resident-A ring (the row
  * tile's A stays in shared memory; 3 or 5 stages of B tiles; not for TF32 rows, which
- * take two slices per 64 columns).  The library
+ * take two slices per 64 columns), and for the single-problem schedule the CTA-pair form
+ * (clusters of two CTAs on two SMs sharing 256-row tiles through cta_group::2 MMAs of
+ * M = 256; by default on wherever A is streamed).  The library
  * keeps a process-wide table keyed by (precision, kernel kind, D padded to 64, P tile,
  * schedule); launches not in the table use 4 warps and the deepest ring that fits.
  *
@@ -419,11 +431,12 @@ int itergp_server_get_stats(itergp_server* server, itergp_server_stats* stats);
  * the fastest in the table and reports all timings (ms per launch; stages < 0 mark the
  * resident-A ring).  It waits for the stream.  Tensor-core precisions only.
  * itergp_tune_save / _load write / merge the table as text lines
- * "precision kind d_pad p_tile items epilogue_warps stages resident_a" (resident_a: 1, 0,
- * or -1 = where possible; a missing last column reads as -1); _clear empties it. */
-#define ITERGP_TUNE_MAX 12
+ * "precision kind d_pad p_tile items epilogue_warps stages resident_a cta_pair"
+ * (resident_a, cta_pair: 1, 0, or -1 = where possible; missing last columns read as -1);
+ * _clear empties it. */
+#define ITERGP_TUNE_MAX 20
 typedef struct {
-  int32_t epilogue_warps, stages;
+  int32_t epilogue_warps, stages, cta_pair;   /* stages < 0: resident-A ring; cta_pair 1: pair form */
   double ms;
 } itergp_tune_variant;
 typedef struct {
@@ -443,18 +456,7 @@ int itergp_tune_clear(void);
  * returns; the context stays usable.  No fault, trap or hang is involved. */
 int itergp_selftest_wait(uint64_t limit_ns, itergp_stream stream);
 
-/* Throughput probe (a project addition): operations per second over the whole GPU on the
- * current device.  what = 0: MUFU exp2 (ex2.approx); 1: FP32 FFMA (2 flops each); these
- * bound the kernel product when D is small (one exp per kernel value).  what = 2..5: BF16
- * tcgen05.mma flops (FP32 accumulate, K = 16 per instruction, one CTA per SM issuing
- * back to back) in the shapes the product issues: 2 = SS M = 128, N = 128 (the distance
- * GEMM); 3 = SS M = 128, N = 256; 4 = as 2 while four other warps stream tcgen05.ld (the
- * epilogue's reads); 5 = TS (A from TMEM) M = 128, N = 80 (the weighted sum); 6 = as 2
- * with TF32 operands (kind::tf32, K = 8; the ITERGP_TF32 distance).  7: FP64 DFMA (2 flops
- * each); 8: MUFU rsqrt (rsqrt.approx, Matern's distance).  Returns ITERGP_EINVAL for
- * another `what`; a probe wait that exceeds its 2 s bound is reported through
- * itergp_sync_status.  Waits for the stream. */
-int itergp_probe_throughput(int32_t what, double* ops_per_s, itergp_stream stream);
+/* Throughput probes: measurement tooling of the bench, in libitergp_probe.so (include/itergp_probe.h). */
 
 /* Library version "major.minor.patch". */
 const char* itergp_version(void);

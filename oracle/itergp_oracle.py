@@ -104,6 +104,26 @@ def kmatvec(A: np.ndarray, B: np.ndarray, S: np.ndarray, kern: Kernel) -> np.nda
     return kernel_matrix(A, B, kern) @ np.asarray(S, dtype=np.float64)
 
 
+def kmatvec_fp32(A: np.ndarray, B: np.ndarray, S: np.ndarray, kern: Kernel) -> np.ndarray:
+    """The same product in FP32 arithmetic throughout (distances, kernel values and the
+    weighted sum), K never stored beyond the block of rows of A passed in: the timed FP32
+    baseline of the matrix-free product.  Not used as a reference."""
+    A = np.asarray(A, dtype=np.float32)
+    B = np.asarray(B, dtype=np.float32)
+    na = np.einsum("ij,ij->i", A, A)
+    nb = np.einsum("ij,ij->i", B, B)
+    r2 = np.maximum(na[:, None] + nb[None, :] - np.float32(2.0) * (A @ B.T), np.float32(0.0))
+    ell, s = np.float32(kern.lengthscale), np.float32(kern.outputscale)
+    if kern.kind == RBF:
+        k = s * np.exp(-r2 / (np.float32(2.0) * ell * ell))
+    elif kern.kind == MATERN32:
+        u = np.float32(math.sqrt(3.0)) * np.sqrt(r2) / ell
+        k = s * (np.float32(1.0) + u) * np.exp(-u)
+    else:
+        raise ValueError(f"unknown kernel kind {kern.kind}")
+    return k @ np.asarray(S, dtype=np.float32)
+
+
 def dense_K(X: np.ndarray, C: int, kern) -> np.ndarray:
     """K = k(X, X) kron I_C in CN ordering (NC x NC), for tiny problems only; with one
     kernel per class, K = sum_c k_c(X, X) kron e_c e_c^T."""

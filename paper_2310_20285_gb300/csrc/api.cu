@@ -9,6 +9,8 @@
 #include <mutex>
 #include <vector>
 
+#include <unordered_map>
+
 #include "internal.h"
 
 namespace itergp {
@@ -118,6 +120,47 @@ thread_local ScratchArena* t_arena = nullptr;
 
 void set_thread_arena(ScratchArena* arena) { t_arena = arena; }
 
+namespace {
+thread_local uint64_t t_wait_ns = kDefaultWaitNs;
+}  // namespace
+uint64_t thread_wait_limit() { return t_wait_ns; }
+void set_thread_wait_limit(uint64_t ns) { t_wait_ns = ns; }
+
+// Pool bytes this thread holds while a fit tracks them (host order of allocation and
+// release, which is the order the stream reuses the memory in).
+namespace {
+struct PoolTrack {
+  bool on = false;
+  int64_t live = 0, peak = 0;
+  std::unordered_map<void*, size_t> sizes;
+};
+thread_local PoolTrack t_track;
+}  // namespace
+
+void pool_track_begin() {
+  t_track.on = true;
+  t_track.live = t_track.peak = 0;
+  t_track.sizes.clear();
+}
+int64_t pool_track_end() {
+  t_track.on = false;
+  t_track.sizes.clear();
+  return t_track.peak;
+}
+void pool_track_add(void* p, size_t bytes) {
+  if (!t_track.on || !p) return;
+  t_track.sizes[p] = bytes;
+  t_track.live += static_cast<int64_t>(bytes);
+  t_track.peak = std::max(t_track.peak, t_track.live);
+}
+void pool_track_remove(void* p) {
+  if (!t_track.on) return;
+  auto it = t_track.sizes.find(p);
+  if (it == t_track.sizes.end()) return;
+  t_track.live -= static_cast<int64_t>(it->second);
+  t_track.sizes.erase(it);
+}
+
 cudaError_t scratch_alloc(DeviceContext* ctx, void** p, size_t bytes, cudaStream_t s) {
   if (t_arena != nullptr) {
     const size_t off = align_up(t_arena->used, 256);
@@ -126,24 +169,20 @@ cudaError_t scratch_alloc(DeviceContext* ctx, void** p, size_t bytes, cudaStream
     t_arena->used = off + bytes;
     return cudaSuccess;
   }
-  return cudaMallocFromPoolAsync(p, bytes, ctx->pool, s);
+  const cudaError_t e = cudaMallocFromPoolAsync(p, bytes, ctx->pool, s);
+  if (e == cudaSuccess) pool_track_add(*p, bytes);
+  return e;
 }
 
 void scratch_free(void* p, cudaStream_t s) {
   if (t_arena != nullptr && static_cast<char*>(p) >= t_arena->base &&
       static_cast<char*>(p) < t_arena->base + t_arena->size)
     return;
+  pool_track_remove(p);
   cudaFreeAsync(p, s);
 }
 
 namespace {
-
-bool kernel_ok(const itergp_kernel* k) {
-  return k && (k->kind == ITERGP_RBF || k->kind == ITERGP_MATERN32) && std::isfinite(k->lengthscale) &&
-         k->lengthscale > 0.f && std::isfinite(k->outputscale) && k->outputscale > 0.f;
-}
-
-bool precision_ok(int p) { return p >= ITERGP_FP32 && p <= ITERGP_TF32; }
 
 // mean = Y[:, :C]; var_c = s - sum_b Y[:, C + b C + c]^2; probs = softmax(mean / sqrt(1 + pi/8 var))
 // probs: softmax -- probit-approximated class probabilities (App. C.3); Bernoulli --
@@ -280,6 +319,8 @@ int validate_fit_params(const itergp_fit_params* prm) {
   if (prm->policy != ITERGP_POLICY_CG && prm->policy != ITERGP_POLICY_UNIT) return ITERGP_EINVAL;
   if (prm->max_newton < 1 || prm->max_iters < 0 || prm->max_newton > 100000) return ITERGP_EINVAL;
   if (!(prm->tol_abs >= 0) || !(prm->tol_rel >= 0)) return ITERGP_EINVAL;
+  if (prm->wait_limit_ns != 0 && (prm->wait_limit_ns < 1000000ull || prm->wait_limit_ns > 60000000000ull))
+    return ITERGP_EINVAL;
   return ITERGP_OK;
 }
 
@@ -315,6 +356,14 @@ int fit_many(const itergp_fit_params* params, int count, itergp_model** out,
   std::vector<int> finalB(count, 0);
   std::vector<int> status(count, ITERGP_OK);
   std::vector<FitProblem> probs(count);
+  struct TrackGuard {   // the call's peak pool bytes: models, workspace and product scratch
+    int64_t* peak;
+    explicit TrackGuard(int64_t* p) : peak(p) { pool_track_begin(); }
+    ~TrackGuard() { *peak = pool_track_end(); }
+  };
+  int64_t peak_bytes = 0;
+  std::unique_ptr<TrackGuard> track(new TrackGuard(&peak_bytes));
+  WaitLimitGuard wait_guard(params[0].wait_limit_ns);
   for (int i = 0; i < count; ++i) {
     const itergp_fit_params& prm = params[i];
     const int64_t n = prm.n, nc = n * prm.c;
@@ -345,6 +394,7 @@ int fit_many(const itergp_fit_params* params, int count, itergp_model** out,
       free_models(models, s);
       return ITERGP_ENOMEM;
     }
+    pool_track_add(mdl->mem, static_cast<size_t>(mdl->bytes));
     char* base = static_cast<char*>(mdl->mem);
     mdl->X = reinterpret_cast<float*>(base);
     mdl->v = reinterpret_cast<float*>(base + xb + rb);
@@ -384,8 +434,10 @@ int fit_many(const itergp_fit_params* params, int count, itergp_model** out,
     free_models(models, s);
     return status[0];
   }
+  track.reset();   // ends the tracking: peak_bytes holds the call's peak
   for (int i = 0; i < count; ++i) {
     reps[i].device_bytes = status[i] == ITERGP_OK ? models[i]->bytes : 0;
+    reps[i].peak_bytes = peak_bytes;
     if (reports) reports[i] = reps[i];
     if (status[i] != ITERGP_OK) {   // this problem failed alone; the others stand
       model_release(models[i], s);
@@ -689,16 +741,17 @@ int itergp_autotune(const itergp_kernel* kernel, int32_t precision, int64_t n, i
   RowOperand op;
   int rc = prepare_rows(precision, X, n, static_cast<int>(d), d, ws.as<char>(bx + 2 * bs), &op, s);
   if (rc != ITERGP_OK) return rc;
-  int count = 0, best = -1, epi[ITERGP_TUNE_MAX], ns[ITERGP_TUNE_MAX];
+  int count = 0, best = -1, epi[ITERGP_TUNE_MAX], ns[ITERGP_TUNE_MAX], pr[ITERGP_TUNE_MAX];
   double ms[ITERGP_TUNE_MAX];
   rc = kmv_tc_tune(ctx, make_kparams(*kernel), op, S, p, Y, items ? 1 : 0, ITERGP_TUNE_MAX, &count, epi,
-                   ns, ms, &best, s);
+                   ns, pr, ms, &best, s);
   if (rc != ITERGP_OK) return rc;
   result->count = count;
   result->best = best;
   for (int i = 0; i < count; ++i) {
     result->variants[i].epilogue_warps = epi[i];
     result->variants[i].stages = ns[i];
+    result->variants[i].cta_pair = pr[i];
     result->variants[i].ms = ms[i];
   }
   return ITERGP_OK;

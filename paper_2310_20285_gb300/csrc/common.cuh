@@ -130,6 +130,29 @@ struct Scratch {
   }
 };
 
+// Pool accounting of a fit: between begin and end, every scratch_alloc / scratch_free of
+// the calling thread (and pool_track_add of other pool blocks) updates the live bytes;
+// end returns their peak.
+void pool_track_begin();
+int64_t pool_track_end();
+void pool_track_add(void* p, size_t bytes);
+void pool_track_remove(void* p);
+
+// Bound of every device-side wait of the tensor-core product launched by this thread
+// (default 4 s); a fit installs its wait_limit_ns for its duration.
+constexpr uint64_t kDefaultWaitNs = 4000000000ull;
+uint64_t thread_wait_limit();
+void set_thread_wait_limit(uint64_t ns);
+struct WaitLimitGuard {
+  uint64_t prev;
+  explicit WaitLimitGuard(uint64_t ns) : prev(thread_wait_limit()) {
+    if (ns != 0) set_thread_wait_limit(ns);
+  }
+  ~WaitLimitGuard() { set_thread_wait_limit(prev); }
+  WaitLimitGuard(const WaitLimitGuard&) = delete;
+  WaitLimitGuard& operator=(const WaitLimitGuard&) = delete;
+};
+
 // Launch accounting: every kernel launch site calls note_launch(); the fused product
 // kernel's launches are optionally bracketed by events (timing_begin / timing_end).
 void note_launch(int64_t n = 1);

@@ -9,7 +9,13 @@
 namespace itergp {
 
 // One side of the kernel product k(A, B): the FP32 rows plus, for the tensor-core
-// paths, their BF16 hi/lo split copies and row norms, zero-padded to tile multiples.
+// paths, their 16-bit copies and row norms, zero-padded to tile multiples.
+//
+// Split-row precisions (BF16X3, BF16_COMP) store each 128-row tile T scaled by a power of
+// two 2^e_T that brings the tile's largest |x| into [128, 256), as FP16 hi = fp16(2^e x)
+// and lo = fp16(2^e x - hi): 22 significant bits, and the exponent range of FP16 no
+// longer limits the data.  tscale[T] = 2^-e_T; a product of tiles I and J reads
+// a.b = tscale[I] tscale[J] (a_hi.b_hi + a_hi.b_lo + a_lo.b_hi) exactly as scaled.
 struct RowOperand {
   const float* X = nullptr;          // rows x d, row pitch ldX (FP32, caller-owned)
   int64_t rows = 0;
@@ -19,8 +25,9 @@ struct RowOperand {
   int d_pad = 0;                     // multiple of 64 (tensor paths) / d (FP32 path)
   int precision = ITERGP_FP32;
   const float* norms = nullptr;      // [rows_pad] squared row norms (see prepare_rows)
-  const __nv_bfloat16* hi = nullptr; // [rows_pad][d_pad] (TF32: FP32 values, see precision_tf32_rows)
-  const __nv_bfloat16* lo = nullptr; // [rows_pad][d_pad] (split precisions only)
+  const __nv_bfloat16* hi = nullptr; // [rows_pad][d_pad] (TF32: FP32 values; split rows: FP16 bits)
+  const __nv_bfloat16* lo = nullptr; // [rows_pad][d_pad] (split precisions only, FP16 bits)
+  const float* tscale = nullptr;     // [rows_pad / 128] tile scales (split precisions only)
 };
 
 constexpr int kRowTile = 128;
@@ -146,6 +153,14 @@ int fit_run_batch(DeviceContext* ctx, const std::vector<FitProblem>& probs, cuda
                   bool use_graph);
 
 // ---------------------------------------------------------------- models (api.cu)
+// Host-side argument checks shared by the entry points: a known kernel kind with finite,
+// positive lengthscale and outputscale; a known precision.
+inline bool kernel_ok(const itergp_kernel* k) {
+  return k && (k->kind == ITERGP_RBF || k->kind == ITERGP_MATERN32) && std::isfinite(k->lengthscale) &&
+         k->lengthscale > 0.f && std::isfinite(k->outputscale) && k->outputscale > 0.f;
+}
+inline bool precision_ok(int p) { return p >= ITERGP_FP32 && p <= ITERGP_TF32; }
+
 int validate_fit_params(const itergp_fit_params* prm);
 void clear_stale_error();
 // Buffer columns a fit keeps at most: min(max_newton * max_iters, R + max_iters, N C).
@@ -163,24 +178,26 @@ void model_release(itergp_model* m, cudaStream_t s);
 void plan_items(const std::vector<WorkItem>& items, int G, std::vector<WorkItem>* ordered,
                 std::vector<int32_t>* begin);
 
-// Times every launch variant of the tensor-core product (epilogue warps x stages) on X
+// Times every launch variant of the tensor-core product (epilogue warps x stages x form:
+// one CTA with a streamed or resident-A ring, or CTA pairs) on X
 // (A = B = X, weights S: rows x p, output Y) in the single (items = 0) or item-mode
 // schedule, records the fastest for (precision, kind, d_pad, P tile, schedule) and
 // returns the timings (up to cap variants).
 int kmv_tc_tune(DeviceContext* ctx, const KParams& kp, const RowOperand& X, const float* S,
                 int64_t p, float* Y, int items, int cap, int* count, int* epi_out, int* ns_out,
-                double* ms_out, int* best, cudaStream_t stream);
+                int* pair_out, double* ms_out, int* best, cudaStream_t stream);
 
 // Self-test of the bounded waits: one CTA waits on an mbarrier nothing arrives on and
 // records ITERGP_ETIMEOUT in ctx->status after limit_ns.
 int wait_selftest_launch(DeviceContext* ctx, uint64_t limit_ns, cudaStream_t stream);
 
 // Prepared rows written into caller-provided planes with pitch d_pad (>= d, multiple of
-// 64 for tensor precisions): BF16 hi (and lo for split precisions) [rows_pad][d_pad] and
-// FP32 squared norms [rows_pad]; rows beyond `rows` are zero.
+// 64 for tensor precisions): the 16-bit hi (and lo for split precisions) [rows_pad][d_pad],
+// FP32 squared norms [rows_pad] and, for split precisions, the tile scales
+// [rows_pad / 128] (rows_pad a multiple of 128 there); rows beyond `rows` are zero.
 int prepare_rows_into(int precision, const float* X, int64_t rows, int d, int64_t ldX,
                       int64_t rows_pad, int d_pad, __nv_bfloat16* hi, __nv_bfloat16* lo,
-                      float* norms, cudaStream_t stream);
+                      float* norms, float* tscale, cudaStream_t stream);
 
 }  // namespace itergp
 

@@ -1,19 +1,74 @@
 // Operand preparation and dispatch of the kernel product Y = k(A, B) S.
 #include <algorithm>
 
+#include <cuda_fp16.h>
+
 #include "internal.h"
 
 namespace itergp {
 namespace {
 
-// One warp per row: BF16 hi (and lo = bf16(x - hi)) copies zero-padded to d_pad, and the
-// squared row norm used by r^2 = |a|^2 + |b|^2 - 2 a.b.  NORM_ROUNDED selects the norm of
-// the BF16-rounded row, which keeps r^2 the exact distance between the rounded points
-// when the dot product is formed from the hi parts only.
-template <bool SPLIT, bool NORM_ROUNDED>
+// 2^e for -126 <= e <= 127, built from its bit pattern (exact).
+__device__ __forceinline__ float pow2i(int e) { return __int_as_float((e + 127) << 23); }
+
+// Split rows (BF16X3, BF16_COMP), one CTA of 8 warps per 128-row tile.  Pass 1 finds the
+// tile's largest |x| = m 2^k (m in [0.5, 1)) and takes e = 8 - k, so that 2^e |x| < 256
+// with the largest in [128, 256); pass 2 writes hi = fp16(2^e x) and
+// lo = fp16(2^e x - hi), zero-padded to d_pad (2^e x and the difference are exact in FP32,
+// so hi + lo holds 2^e x to 22 bits), and the squared norm of the unscaled FP32 row (FP64
+// accumulation).  tscale = 2^-e.  FP16 keeps its relative precision over the whole scaled
+// range: elements below 4 (of up to 256) only lose lo bits below 2^-24, i.e. an absolute
+// 2^-33 of the tile's largest value.
+__global__ void prep_rows_split_kernel(const float* __restrict__ X, int64_t ldX, int64_t rows, int d, int d_pad,
+                                       __half* __restrict__ hi, __half* __restrict__ lo, float* __restrict__ norms,
+                                       float* __restrict__ tscale) {
+  const int64_t r0 = static_cast<int64_t>(blockIdx.x) * 128;
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+  __shared__ float wmax[8];
+  __shared__ int e_s;
+  float mx = 0.f;
+  for (int rr = warp; rr < 128 && r0 + rr < rows; rr += 8)
+    for (int col = lane; col < d; col += 32) mx = fmaxf(mx, fabsf(X[(r0 + rr) * ldX + col]));
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  if (lane == 0) wmax[warp] = mx;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float m = 0.f;
+    for (int w = 0; w < 8; ++w) m = fmaxf(m, wmax[w]);
+    int e = 0;
+    const uint32_t bits = __float_as_uint(m);
+    const int bexp = static_cast<int>((bits >> 23) & 0xFFu);
+    if (m > 0.f && bexp != 0xFF) e = 8 - (bexp == 0 ? -125 : bexp - 126);   // non-finite data: no scaling
+    e = max(-126, min(126, e));
+    e_s = e;
+    tscale[blockIdx.x] = pow2i(-e);
+  }
+  __syncthreads();
+  const float sc = pow2i(e_s);
+  for (int rr = warp; rr < 128; rr += 8) {
+    const int64_t row = r0 + rr;
+    double acc = 0.0;
+    for (int col = lane; col < d_pad; col += 32) {
+      const float x = (row < rows && col < d) ? X[row * ldX + col] : 0.f;
+      const float xs = x * sc;
+      const __half h = __float2half_rn(xs);
+      hi[row * d_pad + col] = h;
+      lo[row * d_pad + col] = __float2half_rn(xs - __half2float(h));
+      acc += static_cast<double>(x) * x;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) norms[row] = static_cast<float>(acc);
+  }
+}
+
+// BF16 rows (one warp per row): BF16 copies zero-padded to d_pad and the squared norm of
+// the BF16-rounded row, which keeps r^2 = |a|^2 + |b|^2 - 2 a.b the exact distance between
+// the rounded points (the dot product is formed from those same values).
 __global__ void prep_rows_kernel(const float* __restrict__ X, int64_t ldX, int64_t rows, int d,
                                  int64_t rows_pad, int d_pad, __nv_bfloat16* __restrict__ hi,
-                                 __nv_bfloat16* __restrict__ lo, float* __restrict__ norms) {
+                                 float* __restrict__ norms) {
   const int64_t row = static_cast<int64_t>(blockIdx.x) * (blockDim.x / 32) + threadIdx.x / 32;
   const int lane = threadIdx.x % 32;
   if (row >= rows_pad) return;
@@ -23,9 +78,7 @@ __global__ void prep_rows_kernel(const float* __restrict__ X, int64_t ldX, int64
     const __nv_bfloat16 h = __float2bfloat16_rn(x);
     const float hf = __bfloat162float(h);
     hi[row * d_pad + col] = h;
-    if (SPLIT) lo[row * d_pad + col] = __float2bfloat16_rn(x - hf);
-    const float nv = NORM_ROUNDED ? hf : x;
-    acc += static_cast<double>(nv) * nv;
+    acc += static_cast<double>(hf) * hf;
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
@@ -91,7 +144,7 @@ __global__ void zero_rows_kernel(float* __restrict__ Y, int64_t m, int64_t p, in
 
 int prepare_rows_into(int precision, const float* X, int64_t rows, int d, int64_t ldX,
                       int64_t rows_pad, int d_pad, __nv_bfloat16* hi, __nv_bfloat16* lo,
-                      float* norms, cudaStream_t stream) {
+                      float* norms, float* tscale, cudaStream_t stream) {
   if (rows_pad <= 0) return ITERGP_OK;
   if (rows_pad < rows || d_pad < d || !norms) return ITERGP_EINVAL;
   if (!precision_is_tensor(precision)) {
@@ -101,14 +154,16 @@ int prepare_rows_into(int precision, const float* X, int64_t rows, int d, int64_
     }
     return ITERGP_OK;
   }
-  if (!hi || d_pad % 64 != 0 || (precision_splits_rows(precision) && !lo)) return ITERGP_EINVAL;
+  if (!hi || d_pad % 64 != 0 || (precision_splits_rows(precision) && (!lo || !tscale || rows_pad % kRowTile != 0)))
+    return ITERGP_EINVAL;
   const unsigned blocks = static_cast<unsigned>(ceil_div(rows_pad, 8));
   if (precision_tf32_rows(precision))
     prep_rows_tf32_kernel<<<blocks, 256, 0, stream>>>(X, ldX, rows, d, rows_pad, d_pad, reinterpret_cast<float*>(hi), norms), ::itergp::note_launch();
   else if (precision_splits_rows(precision))
-    prep_rows_kernel<true, false><<<blocks, 256, 0, stream>>>(X, ldX, rows, d, rows_pad, d_pad, hi, lo, norms), ::itergp::note_launch();
+    prep_rows_split_kernel<<<static_cast<unsigned>(rows_pad / kRowTile), 256, 0, stream>>>(
+        X, ldX, rows, d, d_pad, reinterpret_cast<__half*>(hi), reinterpret_cast<__half*>(lo), norms, tscale), ::itergp::note_launch();
   else
-    prep_rows_kernel<false, true><<<blocks, 256, 0, stream>>>(X, ldX, rows, d, rows_pad, d_pad, hi, nullptr, norms), ::itergp::note_launch();
+    prep_rows_kernel<<<blocks, 256, 0, stream>>>(X, ldX, rows, d, rows_pad, d_pad, hi, norms), ::itergp::note_launch();
   ITERGP_CUDA_TRY(cudaGetLastError());
   return ITERGP_OK;
 }
@@ -116,6 +171,7 @@ int prepare_rows_into(int precision, const float* X, int64_t rows, int d, int64_
 size_t rows_workspace_bytes(int precision, int64_t rows, int d) {
   const int64_t rows_pad = (rows + kRowTile - 1) / kRowTile * kRowTile;
   size_t bytes = align_up(sizeof(float) * std::max<int64_t>(rows_pad, 1), 256);
+  if (precision_splits_rows(precision)) bytes += align_up(sizeof(float) * std::max<int64_t>(rows_pad / kRowTile, 1), 256);
   if (precision_is_tensor(precision)) {
     const int64_t d_pad = (d + 63) / 64 * 64;
     const size_t plane = align_up(static_cast<size_t>(rows_pad) * d_pad * 2, 256);
@@ -139,6 +195,7 @@ int prepare_rows(int precision, const float* X, int64_t rows, int d, int64_t ldX
   if (!precision_is_tensor(precision)) {
     op->d_pad = d;
     op->hi = op->lo = nullptr;
+    op->tscale = nullptr;
     if (rows > 0) {
       row_norms_kernel<<<static_cast<unsigned>(ceil_div(rows, 8)), 256, 0, stream>>>(X, ldX, rows, d, norms), ::itergp::note_launch();
       ITERGP_CUDA_TRY(cudaGetLastError());
@@ -147,21 +204,26 @@ int prepare_rows(int precision, const float* X, int64_t rows, int d, int64_t ldX
   }
   op->d_pad = (d + 63) / 64 * 64;
   const size_t plane = align_up(static_cast<size_t>(op->rows_pad) * op->d_pad * 2, 256);
-  __nv_bfloat16* hi = reinterpret_cast<__nv_bfloat16*>(base + norm_bytes);
-  __nv_bfloat16* lo = precision_splits_rows(precision)
-                          ? reinterpret_cast<__nv_bfloat16*>(base + norm_bytes + plane)
-                          : nullptr;
+  // split rows: the tile scales follow the norms
+  const bool split = precision_splits_rows(precision);
+  float* tscale = split ? reinterpret_cast<float*>(base + norm_bytes) : nullptr;
+  const size_t planes0 =
+      norm_bytes + (split ? align_up(sizeof(float) * std::max<int64_t>(op->rows_pad / kRowTile, 1), 256) : 0);
+  __nv_bfloat16* hi = reinterpret_cast<__nv_bfloat16*>(base + planes0);
+  __nv_bfloat16* lo = split ? reinterpret_cast<__nv_bfloat16*>(base + planes0 + plane) : nullptr;
   op->hi = hi;
   op->lo = lo;
+  op->tscale = tscale;
   if (op->rows_pad == 0) return ITERGP_OK;
   const unsigned blocks = static_cast<unsigned>(ceil_div(op->rows_pad, 8));
   if (precision_tf32_rows(precision))   // one FP32 plane in the bytes of two BF16 planes
     prep_rows_tf32_kernel<<<blocks, 256, 0, stream>>>(X, ldX, rows, d, op->rows_pad, op->d_pad,
                                                       reinterpret_cast<float*>(hi), norms), ::itergp::note_launch();
   else if (lo)
-    prep_rows_kernel<true, false><<<blocks, 256, 0, stream>>>(X, ldX, rows, d, op->rows_pad, op->d_pad, hi, lo, norms), ::itergp::note_launch();
+    prep_rows_split_kernel<<<static_cast<unsigned>(op->rows_pad / kRowTile), 256, 0, stream>>>(
+        X, ldX, rows, d, op->d_pad, reinterpret_cast<__half*>(hi), reinterpret_cast<__half*>(lo), norms, tscale), ::itergp::note_launch();
   else
-    prep_rows_kernel<false, true><<<blocks, 256, 0, stream>>>(X, ldX, rows, d, op->rows_pad, op->d_pad, hi, lo, norms), ::itergp::note_launch();
+    prep_rows_kernel<<<blocks, 256, 0, stream>>>(X, ldX, rows, d, op->rows_pad, op->d_pad, hi, norms), ::itergp::note_launch();
   ITERGP_CUDA_TRY(cudaGetLastError());
   return ITERGP_OK;
 }

@@ -96,16 +96,15 @@ extern "C" int itergp_kmatvec_noalloc(const itergp_kernel* kernel, int32_t preci
                                       const float* A, int64_t m, const float* B, int64_t n,
                                       int64_t d, const float* S, int64_t p, float* Y,
                                       int* device_status, itergp_stream stream) {
-  if (!kernel || !(kernel->kind == ITERGP_RBF || kernel->kind == ITERGP_MATERN32) ||
-      !(kernel->lengthscale > 0.f) || !(kernel->outputscale > 0.f) ||
-      precision < ITERGP_FP32 || precision > ITERGP_TF32)
-    return ITERGP_EINVAL;
+  clear_stale_error();
+  if (!kernel_ok(kernel) || !precision_ok(precision)) return ITERGP_EINVAL;
   if (m < 0 || n < 0 || p < 0 || d < 1 || d > 4096 || p > 65536) return ITERGP_EINVAL;
-  if (m == 0 || p == 0) return ITERGP_OK;
-  if (!Y || (n > 0 && (!A || !B || !S))) return ITERGP_EINVAL;
+  // device set-up first, so that a call with m = 0 or p = 0 performs only the set-up
   NoAllocDevice* nd = nullptr;
   int rc = setup_current_device(&nd);
   if (rc != ITERGP_OK) return rc;
+  if (m == 0 || p == 0) return ITERGP_OK;
+  if (!Y || (n > 0 && (!A || !B || !S))) return ITERGP_EINVAL;
   if (precision_is_tensor(precision) && !nd->ctx.tcgen05) return ITERGP_EUNSUPPORTED;
   const bool same = (A == B) && (m == n);
   if (scratch_bound(nd->ctx, precision, m, n, static_cast<int>(d), p, same) > ITERGP_NOALLOC_SCRATCH_BYTES)

@@ -15,7 +15,8 @@
 // only when no predict uses it).
 //
 // Slab layout (rows in 128-row blocks, one block range per model):
-//  tensor precisions: BF16 hi (and lo) rows [slab_rows][d_pad], FP32 norms [slab_rows],
+//  tensor precisions: 16-bit hi (and lo) rows [slab_rows][d_pad], FP32 norms [slab_rows],
+//                     split rows: tile scales [slab_rows / 128],
 //                     weights transposed BF16 hi (and lo) [144][slab_rows];
 //  FP32:              FP32 rows [slab_rows][d_max], norms, weights [slab_rows][144].
 // Weight row w of a model: w < 16: v[:, w] (zero for w >= C); w >= 16: column
@@ -379,8 +380,9 @@ int itergp_server::install(itergp_model* m, const FitReq& r) {
                             ? reinterpret_cast<__nv_bfloat16*>(
                                   const_cast<float*>(reinterpret_cast<const float*>(rows_op.hi)) + r.row0 * d_pad)
                             : const_cast<__nv_bfloat16*>(rows_op.hi) + r.row0 * d_pad;
+    float* ts = rows_op.tscale ? const_cast<float*>(rows_op.tscale) + r.row0 / kRowTile : nullptr;
     int rc = prepare_rows_into(cfg.precision, m->X, n, static_cast<int>(m->d), m->d, rows_pad, d_pad,
-                               hi, lo, const_cast<float*>(rows_op.norms) + r.row0, s);
+                               hi, lo, const_cast<float*>(rows_op.norms) + r.row0, ts, s);
     if (rc != ITERGP_OK) return rc;
     if (precision_splits_weights(cfg.precision))
       slab_weights_tc_kernel<true><<<blocks_rows, 256, 0, s>>>(m->v, m->Q, n, m->c, m->B, rows_pad, r.row0,
@@ -395,7 +397,7 @@ int itergp_server::install(itergp_model* m, const FitReq& r) {
     slab_rows32_kernel<<<b2, 256, 0, s>>>(m->X, n, static_cast<int>(m->d), rows_pad, cfg.d_max, x32), ::itergp::note_launch();
     ITERGP_CUDA_TRY(cudaGetLastError());
     int rc = prepare_rows_into(ITERGP_FP32, x32, rows_pad, cfg.d_max, cfg.d_max, rows_pad, cfg.d_max,
-                               nullptr, nullptr, const_cast<float*>(rows_op.norms) + r.row0, s);
+                               nullptr, nullptr, const_cast<float*>(rows_op.norms) + r.row0, nullptr, s);
     if (rc != ITERGP_OK) return rc;
     slab_weights32_kernel<<<blocks_rows, 256, 0, s>>>(m->v, m->Q, n, m->c, m->B, rows_pad,
                                                       w32 + r.row0 * kWeightRows), ::itergp::note_launch();
@@ -766,6 +768,8 @@ int itergp_server_create(const itergp_server_config* cfg, itergp_server** out) {
   size_t off = 0;
   auto take = [&](size_t b) { const size_t o = off; off += align_up(b, 256); return o; };
   const size_t o_norm = take(sizeof(float) * R);
+  // split rows: one scale per 128-row block (R is a multiple of 128)
+  const size_t o_tscale = precision_splits_rows(cfg->precision) ? take(sizeof(float) * (R / 128)) : 0;
   size_t o_hi = 0, o_lo = 0, o_whi = 0, o_wlo = 0, o_x = 0, o_w = 0;
   if (tc) {
     // TF32: one FP32 plane in the bytes of two BF16 planes
@@ -823,6 +827,7 @@ int itergp_server_create(const itergp_server_config* cfg, itergp_server** out) {
   op.d_pad = srv->d_pad;
   op.precision = cfg->precision;
   op.norms = reinterpret_cast<float*>(b + o_norm);
+  op.tscale = precision_splits_rows(cfg->precision) ? reinterpret_cast<float*>(b + o_tscale) : nullptr;
   if (tc) {
     op.X = nullptr;
     op.ldX = cfg->d_max;

@@ -24,18 +24,20 @@ inline PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
   return fn;
 }
 
-// Row-major BF16 matrix [rows][cols] (cols contiguous, row pitch `pitch_elems`), boxes of
-// box_rows x 64 elements (64 BF16 = one 128-byte swizzle row).  Requirements checked by
-// the caller: base 16-byte aligned, pitch a multiple of 8 elements.
+// Row-major 16-bit matrix [rows][cols] (cols contiguous, row pitch `pitch_elems`), boxes of
+// box_rows x 64 elements (64 values = one 128-byte swizzle row); BF16 unless `type` says
+// FP16.  Requirements checked by the caller: base 16-byte aligned, pitch a multiple of 8
+// elements.
 inline bool encode_bf16_sw128(CUtensorMap* map, const void* base, uint64_t rows, uint64_t cols,
-                              uint64_t pitch_elems, uint32_t box_rows) {
+                              uint64_t pitch_elems, uint32_t box_rows,
+                              CUtensorMapDataType type = CU_TENSOR_MAP_DATA_TYPE_BFLOAT16) {
   auto fn = tensor_map_encoder();
   if (!fn) return false;
   cuuint64_t dims[2] = {cols, rows};
   cuuint64_t strides[1] = {pitch_elems * 2};
   cuuint32_t box[2] = {64, box_rows};
   cuuint32_t estr[2] = {1, 1};
-  CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides,
+  CUresult r = fn(map, type, 2, const_cast<void*>(base), dims, strides,
                   box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
                   CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS;

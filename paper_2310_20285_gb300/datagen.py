@@ -20,6 +20,8 @@ Workloads (shapes and distributions follow the paper's experiments, Sec. 5 and A
                     lambda uniform in [0.001, 0.1].
 * ``batch_problems`` -- 256 independent blob problems of uneven N, D, C, lengthscale.
 * ``normal``     -- standard-normal right-hand sides S for the kernel product bench.
+* ``poisson_study`` -- the Poisson-regression study (App. C): 100 points in [0, 1], a
+                    log-rate drawn from an RBF GP (random Fourier features), Poisson counts.
 """
 from __future__ import annotations
 
@@ -149,6 +151,30 @@ def one_latent(kind: str, n: int, seed: int, d: int = 2, n_test: int = 100):
         y = (lat + 0.1 * g.standard_normal(n + n_test)).astype(np.float32)
     X = X.astype(np.float32)
     return X[:n], y[:n], X[n:]
+
+
+def poisson_study(seed: int, runs: int = 10, n: int = 100, lengthscale: float = 0.1,
+                  outputscale: float = 5.0, features: int = 4096):
+    """The Poisson-regression study's data (App. C): n inputs linearly spaced in [0, 1]; one
+    fixed log-rate function f drawn from a zero-mean GP with an RBF covariance of the given
+    lengthscale and outputscale; `runs` training count vectors y_r ~ Poisson(e^f(x)) at
+    those inputs, plus `runs` test count vectors drawn the same way.
+
+    The GP draw is a random-Fourier-feature sample, f(x) = sqrt(2 s / M) sum_m
+    w_m cos(omega_m x + b_m) with omega_m ~ N(0, 1 / l^2), b_m ~ U[0, 2 pi), w_m ~ N(0, 1)
+    and M = `features`: a sample whose covariance tends to s exp(-(x - x')^2 / (2 l^2))
+    as M grows, made of random numbers only.  Returns X (n x 1 float32), f (n, float64),
+    Y (runs x n int32), Y_test (runs x n int32)."""
+    g = _rng(seed)
+    x = np.linspace(0.0, 1.0, n)
+    om = g.standard_normal(features) / lengthscale
+    b = g.uniform(0.0, 2.0 * math.pi, size=features)
+    w = g.standard_normal(features)
+    f = math.sqrt(2.0 * outputscale / features) * (np.cos(np.outer(x, om) + b) @ w)
+    lam = np.exp(f)
+    Y = g.poisson(lam, size=(runs, n)).astype(np.int32)
+    Yt = g.poisson(lam, size=(runs, n)).astype(np.int32)
+    return x.reshape(n, 1).astype(np.float32), f, Y, Yt
 
 
 def poisson_arrivals(rate: float, duration: float, seed: int) -> np.ndarray:

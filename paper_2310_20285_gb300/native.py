@@ -49,12 +49,13 @@ class FitParams(ct.Structure):
                 ("tol_newton", ct.c_double), ("tol_abs", ct.c_double), ("tol_rel", ct.c_double),
                 ("graph", ct.c_int32), ("f0", ct.c_void_p), ("likelihood", ct.c_int32),
                 ("noise", ct.c_float), ("y_real", ct.c_void_p),
-                ("class_kernels", ct.POINTER(Kernel))]
+                ("class_kernels", ct.POINTER(Kernel)), ("wait_limit_ns", ct.c_uint64)]
 
 
 class FitReport(ct.Structure):
     """itergp_fit_report: per Newton step iterations, stop reasons, kept buffer columns,
-    objective and relative change; final residual norm and device bytes."""
+    objective and relative change; final residual norm, the model's device bytes and the
+    call's peak pool bytes."""
     _fields_ = [("newton_steps", ct.c_int32), ("total_iters", ct.c_int32),
                 ("buffer_cols", ct.c_int32), ("stop_reason", ct.c_int32),
                 ("iters", ct.c_int32 * MAX_REPORT_STEPS), ("stops", ct.c_int32 * MAX_REPORT_STEPS),
@@ -62,7 +63,7 @@ class FitReport(ct.Structure):
                 ("objective", ct.c_double * MAX_REPORT_STEPS),
                 ("rel_change", ct.c_double * MAX_REPORT_STEPS),
                 ("resid_norm", ct.c_double), ("device_bytes", ct.c_int64),
-                ("status", ct.c_int32), ("reserved", ct.c_int32)]
+                ("status", ct.c_int32), ("reserved", ct.c_int32), ("peak_bytes", ct.c_int64)]
 
 
 class ModelView(ct.Structure):
@@ -98,12 +99,14 @@ class ServerStats(ct.Structure):
 
 
 REQ_FIT, REQ_PREDICT = 0, 1
-TUNE_MAX = 12
+TUNE_MAX = 20
 
 
 class TuneVariant(ct.Structure):
-    """One timed launch variant: epilogue warps, ring stages (< 0: resident A), ms."""
-    _fields_ = [("epilogue_warps", ct.c_int32), ("stages", ct.c_int32), ("ms", ct.c_double)]
+    """One timed launch variant: epilogue warps, ring stages (< 0: resident A), CTA-pair
+    form (1) or one CTA per tile (0), ms."""
+    _fields_ = [("epilogue_warps", ct.c_int32), ("stages", ct.c_int32), ("cta_pair", ct.c_int32),
+                ("ms", ct.c_double)]
 
 
 class TuneResult(ct.Structure):
@@ -155,8 +158,6 @@ def _load():
     lib.itergp_tune_clear.argtypes = []
     lib.itergp_selftest_wait.argtypes = [ct.c_uint64, vp]
     lib.itergp_selftest_wait.restype = ct.c_int
-    lib.itergp_probe_throughput.argtypes = [i32, ct.POINTER(ct.c_double), vp]
-    lib.itergp_probe_throughput.restype = ct.c_int
     for name in ("itergp_autotune", "itergp_tune_save", "itergp_tune_load", "itergp_tune_clear",
                  "itergp_kmatvec", "itergp_kmatvec_noalloc", "itergp_winv_apply", "itergp_pseudo_targets",
                  "itergp_sym_eig", "itergp_fit", "itergp_fit_batch", "itergp_predict",
@@ -380,9 +381,10 @@ class _CudaArray:
 
 def _params(X, y, c, kind, lengthscale, outputscale, precision, policy, max_newton, max_iters,
             rank, recycle, literal_kv, tol_newton, tol_abs, tol_rel, graph, f0=None,
-            likelihood="softmax", noise=1.0, class_kernels=None) -> FitParams:
+            likelihood="softmax", noise=1.0, class_kernels=None, wait_limit_ns=0) -> FitParams:
     n, d = X.shape
     prm = FitParams()
+    prm.wait_limit_ns = int(wait_limit_ns)
     prm.n, prm.d, prm.c = n, d, int(c)
     prm.X = _dev(X, torch.float32, "X").value
     prm.likelihood = LIKELIHOODS[likelihood]
@@ -416,16 +418,17 @@ def _params(X, y, c, kind, lengthscale, outputscale, precision, policy, max_newt
 def fit(X, y, c, kind="rbf", lengthscale=1.0, outputscale=1.0, precision="fp32",
         policy="cg", max_newton=10, max_iters=50, rank=-1, recycle=True, literal_kv=False,
         tol_newton=0.0, tol_abs=1e-5, tol_rel=1e-5, graph=False, stream=None, f0=None,
-        likelihood="softmax", noise=1.0, class_kernels=None) -> Model:
+        likelihood="softmax", noise=1.0, class_kernels=None, wait_limit_ns=0) -> Model:
     """IterNCGP fit (Alg. 1-3) on the GPU.  likelihood: "softmax" (c >= 2 classes, integer
     labels), "bernoulli" (c = 1, labels 0/1), "poisson" (c = 1, counts) or "gaussian"
     (real targets y of n x c, noise variance `noise`).  f0 (n x c, device) starts Newton's
     method at that iterate instead of m = 0.  class_kernels: [(kind, lengthscale,
     outputscale)] * c gives each output GP its own kernel (then kind / lengthscale /
-    outputscale are unused)."""
+    outputscale are unused).  wait_limit_ns bounds every device-side wait of the fit's
+    kernel products (0: the default 4 s)."""
     prm = _params(X, y, c, kind, lengthscale, outputscale, precision, policy, max_newton,
                   max_iters, rank, recycle, literal_kv, tol_newton, tol_abs, tol_rel, graph, f0,
-                  likelihood, noise, class_kernels)
+                  likelihood, noise, class_kernels, wait_limit_ns)
     h = ct.c_void_p()
     rep = FitReport()
     rc = lib.itergp_fit(ct.byref(prm), ct.byref(h), ct.byref(rep), _stream(stream))
@@ -467,12 +470,14 @@ def fit_batch(problems, kind="rbf", precision="fp32", policy="cg", max_newton=5,
 
 def autotune(n, d, p, kind="rbf", precision="bf16x3", items=False, lengthscale=1.0, stream=None):
     """Times every launch variant of the tensor-core product for this shape, records the
-    fastest in the library's table; returns [(epilogue_warps, stages, ms)] and the best."""
+    fastest in the library's table; returns [(epilogue_warps, stages, cta_pair, ms)] and the
+    best."""
     res = TuneResult()
     _check(lib.itergp_autotune(ct.byref(_kernel(kind, lengthscale, 1.0)), _prec(precision), int(n), int(d),
                                int(p), 1 if items else 0, ct.byref(res), _stream(stream)),
            "itergp_autotune")
-    vs = [(v.epilogue_warps, v.stages, v.ms) for v in res.variants[:res.count]]   # stages < 0: resident A
+    # (epilogue warps, stages (< 0: resident A), cta_pair, ms)
+    vs = [(v.epilogue_warps, v.stages, v.cta_pair, v.ms) for v in res.variants[:res.count]]
     return vs, (vs[res.best] if res.best >= 0 else None)
 
 
@@ -483,16 +488,34 @@ def selftest_wait(limit_ns=20_000_000, stream=None):
 
 
 PROBES = {"ex2": 0, "ffma": 1, "mma_ss_n128": 2, "mma_ss_n256": 3, "mma_ss_n128_tmem_ld": 4,
-          "mma_ts_n80": 5, "mma_ss_n128_tf32": 6, "dfma": 7, "rsqrt": 8}
+          "mma_ts_n80": 5, "mma_ss_n128_tf32": 6, "dfma": 7, "rsqrt": 8,
+          "pair_mma_ss_n128_f16": 9, "pair_mma_ss_n256_f16": 10, "pair_mma_ts_n80": 11}
+_PROBE_LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libitergp_probe.so")
+_probe_lib = None
+
+
+def probe_lib():
+    """The bench's throughput-probe library (libitergp_probe.so), loaded on first use."""
+    global _probe_lib
+    if _probe_lib is None:
+        if not os.path.exists(_PROBE_LIB_PATH):
+            raise ImportError(f"libitergp_probe.so not built ({_PROBE_LIB_PATH})")
+        pl = ct.CDLL(_PROBE_LIB_PATH)
+        pl.itergp_probe_throughput.argtypes = [ct.c_int32, ct.POINTER(ct.c_double), ct.c_void_p]
+        pl.itergp_probe_throughput.restype = ct.c_int
+        _probe_lib = pl
+    return _probe_lib
 
 
 def probe_throughput(what="ex2", stream=None) -> float:
-    """Measured operations per second over the GPU: MUFU exp2 ("ex2"), FP32 FFMA ("ffma",
-    flops) or BF16 tcgen05.mma flops in the product's shapes ("mma_ss_n128", "mma_ss_n256",
-    "mma_ss_n128_tmem_ld": N = 128 while other warps stream TMEM loads, "mma_ts_n80"), TF32
-    tcgen05.mma flops ("mma_ss_n128_tf32"), FP64 DFMA flops ("dfma") or MUFU rsqrt ("rsqrt")."""
+    """Measured operations per second over the GPU (include/itergp_probe.h): MUFU exp2
+    ("ex2"), FP32 FFMA ("ffma", flops), tcgen05.mma flops in the one-CTA product's shapes
+    ("mma_ss_n128", "mma_ss_n256", "mma_ss_n128_tmem_ld": N = 128 while other warps stream
+    TMEM loads, "mma_ts_n80", TF32 "mma_ss_n128_tf32") and in the CTA-pair form's
+    ("pair_mma_ss_n128_f16", "pair_mma_ss_n256_f16", "pair_mma_ts_n80"), FP64 DFMA flops
+    ("dfma") or MUFU rsqrt ("rsqrt")."""
     out = ct.c_double()
-    _check(lib.itergp_probe_throughput(PROBES[what], ct.byref(out), _stream(stream)),
+    _check(probe_lib().itergp_probe_throughput(PROBES[what], ct.byref(out), _stream(stream)),
            "itergp_probe_throughput")
     return out.value
 

@@ -11,8 +11,8 @@ HEADER = os.path.join(ROOT, "include", "itergp.h")
 LIB = os.path.join(ROOT, "paper_2310_20285_gb300", "libitergp.so")
 
 
-def declared_functions():
-    src = open(HEADER).read()
+def declared_functions(header=HEADER):
+    src = open(header).read()
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
     return sorted(set(re.findall(r"\b(itergp_[a-z_0-9]+)\s*\(", src)))
 
@@ -55,6 +55,20 @@ def test_binding_constants_match_the_header(lib):
 def test_library_exports_every_declared_symbol(lib):
     missing = [n for n in declared_functions() if not hasattr(lib, n)]
     assert not missing, missing
+
+
+def test_probe_library_is_separate_and_exports_its_header():
+    """The bench's throughput probes live in their own library, not in the product's."""
+    probe_h = os.path.join(ROOT, "include", "itergp_probe.h")
+    probe_so = os.path.join(ROOT, "paper_2310_20285_gb300", "libitergp_probe.so")
+    if not os.path.exists(probe_so):
+        from paper_2310_20285_gb300 import build
+        build.build()
+    names = declared_functions(probe_h)
+    assert names == ["itergp_probe_throughput"]
+    plib = ct.CDLL(probe_so)
+    assert all(hasattr(plib, n) for n in names)
+    assert not hasattr(ct.CDLL(LIB), "itergp_probe_throughput")
 
 
 def test_status_strings(lib):
@@ -110,7 +124,8 @@ def test_fit_rejects_bad_arguments_on_the_host(lib):
                 tol_abs=1e-5, tol_rel=1e-5)
     for bad in (dict(n=0), dict(c=1), dict(c=65), dict(d=0), dict(X=None), dict(y=None),
                 dict(policy=5), dict(max_newton=0), dict(max_iters=-1), dict(precision=8),
-                dict(kernel=K(0, -1.0, 1.0)), dict(tol_abs=-1.0)):
+                dict(kernel=K(0, -1.0, 1.0)), dict(tol_abs=-1.0),
+                dict(wait_limit_ns=999), dict(wait_limit_ns=10 ** 11)):   # outside 1e6 .. 6e10 ns
         prm = FitParams(**{**base, **bad})
         h = ct.c_void_p()
         assert f(ct.byref(prm), ct.byref(h), None, None) == -1, bad
@@ -167,26 +182,31 @@ def test_tune_cache_round_trip(lib, tmp_path):
     lib.itergp_tune_load.argtypes = [ct.c_char_p]
     lib.itergp_tune_save.argtypes = [ct.c_char_p]
     src = tmp_path / "in.txt"
-    src.write_text("# comment\n1 0 64 16 1 8 2\n3 1 832 80 0 4 0 0\n2 0 64 16 1 4 5 1\n")
+    src.write_text("# comment\n1 0 64 16 1 8 2\n3 1 832 80 0 4 0 0\n2 0 64 16 1 4 5 1\n"
+                   "1 1 832 80 0 8 3 0 1\n")
     assert lib.itergp_tune_clear() == 0
     assert lib.itergp_tune_load(str(src).encode()) == 0
     out = tmp_path / "out.txt"
     assert lib.itergp_tune_save(str(out).encode()) == 0
     rows = [l for l in out.read_text().splitlines() if not l.startswith("#")]
-    assert sorted(rows) == sorted(["1 0 64 16 1 8 2 -1", "3 1 832 80 0 4 0 0", "2 0 64 16 1 4 5 1"])
+    # missing resident-A / CTA-pair columns read as -1 (automatic)
+    assert sorted(rows) == sorted(["1 0 64 16 1 8 2 -1 -1", "3 1 832 80 0 4 0 0 -1", "2 0 64 16 1 4 5 1 -1",
+                                   "1 1 832 80 0 8 3 0 1"])
     bad = tmp_path / "bad.txt"
     bad.write_text("1 0 64 16 1 6 2\n")          # 6 epilogue warps is not a variant
+    assert lib.itergp_tune_load(str(bad).encode()) == -1
+    bad.write_text("1 0 64 16 1 8 2 0 2\n")      # the pair column takes -1, 0 or 1
     assert lib.itergp_tune_load(str(bad).encode()) == -1
     assert lib.itergp_tune_clear() == 0
 
 
-def test_throughput_probe_rejects_bad_arguments(lib):
+def test_throughput_probe_rejects_bad_arguments():
     """Unknown probes and a null result pointer fail with EINVAL before any CUDA call."""
-    f = lib.itergp_probe_throughput
+    f = ct.CDLL(os.path.join(ROOT, "paper_2310_20285_gb300", "libitergp_probe.so")).itergp_probe_throughput
     f.restype = ct.c_int
     f.argtypes = [ct.c_int32, ct.POINTER(ct.c_double), ct.c_void_p]
     out = ct.c_double()
-    for what in (-1, 9, 99):
+    for what in (-1, 12, 99):
         assert f(what, ct.byref(out), None) == -1
     assert f(0, None, None) == -1
 

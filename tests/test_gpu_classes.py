@@ -35,10 +35,8 @@ def okerns(ks):
 
 
 def split_tol(prec, X, ks):
-    if prec != "bf16x3":
-        return 1e-4
-    ell = min(k[1] for k in ks)
-    return min(max(1e-4, 2.0 ** -15 * float(np.max(np.sum(X.astype(np.float64) ** 2, axis=1))) / ell ** 2), 1e-2)
+    """FP32 and BF16X3 (FP16 hi/lo rows, 22 significant bits) are held to the same 1e-4."""
+    return 1e-4
 
 
 @pytest.mark.parametrize("prec", ["fp32", "bf16x3"])
@@ -105,7 +103,7 @@ def test_fit_and_predict_with_class_kernels_match_the_oracle(native, prec):
     mean, var, probs = m.predict(t32(Xs32))
     em, ev, ep = O.predict(Xs32.astype(np.float64), X32.astype(np.float64), ref.v, ref.Q, kerns, 3)
     assert rel(mean.cpu(), em) <= tol
-    assert np.max(np.abs(var.cpu().numpy() - ev)) <= 1e-3 * max(k[2] for k in KERNS3)
+    assert np.max(np.abs(var.cpu().numpy() - ev)) <= 1e-4 * max(k[2] for k in KERNS3)
     assert np.max(np.abs(probs.cpu().numpy() - ep)) <= 10 * tol
     m.free()
 

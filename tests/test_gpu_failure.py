@@ -35,3 +35,17 @@ def test_selftest_limits_are_validated(native):
         native.selftest_wait(limit_ns=10)
     with pytest.raises(native.ItergpError):
         native.selftest_wait(limit_ns=10_000_000_000)
+
+
+def test_fit_wait_limit_and_peak_bytes_reach_the_report(native):
+    """A fit with its own device-wait bound (wait_limit_ns, here 0.5 s, far above what
+    any wait of this small fit takes) completes normally, and its report carries the
+    call's peak pool bytes: at least the model it keeps, at most what the device has."""
+    X, y, _ = datagen.blobs(700, 2, 3, 9)
+    m = native.fit(torch.as_tensor(X.astype(np.float32), device=DEV), torch.as_tensor(y, device=DEV), 3,
+                   precision="bf16x3", max_newton=3, max_iters=10, rank=20, wait_limit_ns=500_000_000)
+    assert native.sync_status() == 0
+    r = m.report
+    assert r.device_bytes > 0
+    assert r.device_bytes <= r.peak_bytes < torch.cuda.get_device_properties(0).total_memory
+    m.free()

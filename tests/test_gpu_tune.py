@@ -12,12 +12,12 @@ DEV = torch.device("cuda:0")
 PREC_CODE = {"bf16x3": 1, "bf16": 2, "bf16_comp": 3, "tf32": 4}
 
 
-def force(native, tmp_path, prec, kind, d, p16, items, epi, stages, ares=-1):
+def force(native, tmp_path, prec, kind, d, p16, items, epi, stages, ares=-1, pair=-1):
     """Install one table entry through the text cache (ares: resident-A ring, one K slice
-    only; -1 automatic)."""
+    only; pair: the CTA-pair form, single schedule only; -1 automatic)."""
     path = tmp_path / "tune.txt"
     d_pad = (d + 63) // 64 * 64
-    path.write_text(f"{PREC_CODE[prec]} {kind} {d_pad} {p16} {items} {epi} {stages} {ares}\n")
+    path.write_text(f"{PREC_CODE[prec]} {kind} {d_pad} {p16} {items} {epi} {stages} {ares} {pair}\n")
     native.tune_clear()
     native.tune_load(path)
 
@@ -29,7 +29,8 @@ def test_autotune_times_every_variant(native, prec, items, p):
     vs, best = native.autotune(4096, 32, p, precision=prec, items=items)
     assert len(vs) >= 2 and best in vs   # wide split P tiles leave room for 2 stages only
     assert {v[0] for v in vs} == {4, 8}
-    assert all(v[2] > 0 for v in vs)
+    assert all(v[3] > 0 for v in vs)
+    assert {v[2] for v in vs} == ({0} if items else {0, 1})   # the pair form: single schedule
     native.tune_clear()
 
 
@@ -41,9 +42,9 @@ def test_variants_compute_the_same_product(native, tmp_path, prec, epi, stages, 
     the streamed ring); the reference is the streamed 4-warp ring."""
     X = torch.as_tensor(datagen.normal((3000, 40), 3), device=DEV)
     S = torch.as_tensor(datagen.normal((3000, 24), 4), device=DEV)
-    force(native, tmp_path, prec, 1, 40, 32, 0, 4, 2, 0)
+    force(native, tmp_path, prec, 1, 40, 32, 0, 4, 2, 0, 0)
     ref = native.kmatvec(X, X, S, kind="matern32", lengthscale=3.0, precision=prec).clone()
-    force(native, tmp_path, prec, 1, 40, 32, 0, epi, stages, ares)
+    force(native, tmp_path, prec, 1, 40, 32, 0, epi, stages, ares, 0)
     got = native.kmatvec(X, X, S, kind="matern32", lengthscale=3.0, precision=prec)
     native.tune_clear()
     assert torch.equal(got, ref)
@@ -65,3 +66,35 @@ def test_variants_give_the_same_batched_fit(native, tmp_path, epi, stages, ares)
         assert torch.equal(a.arrays()["f"], b.arrays()["f"])
         a.free()
         b.free()
+
+
+@pytest.mark.parametrize("prec", ["bf16x3", "bf16_comp", "bf16", "tf32"])
+@pytest.mark.parametrize("m,n,d,p,epi,stages", [
+    (3000, 3000, 40, 24, 4, 2),        # one K slice, three G buffers
+    (2345, 1999, 300, 80, 8, 3),       # several slices, ragged rows, two G buffers
+    (700, 4100, 784, 200, 8, 2),       # P split into tiles; tail rows shared by pairs
+    (257, 300, 130, 16, 4, 4),         # one pair tile plus one row
+])
+def test_pair_form_computes_the_one_cta_product(native, tmp_path, prec, m, n, d, p, epi, stages):
+    """The CTA-pair form (cta_group::2 MMAs of M = 256 issued for two SMs) issues the same
+    MMAs per output element in the same order as the one-CTA form.  Only the split of the
+    tail row tiles over CTAs (or pairs) differs, which regroups the FP32 partial sums of a
+    row: the two agree to FP32 re-association (2^-18 of the row's largest output), far
+    inside the 1e-4 product bar.  The ragged shapes exercise pair tiles past the last row
+    and the tail fix-up."""
+    A = torch.as_tensor(datagen.normal((m, d), 5), device=DEV)
+    B = torch.as_tensor(datagen.normal((n, d), 6), device=DEV)
+    S = torch.as_tensor(datagen.normal((n, p), 7), device=DEV)
+    p16 = min((p + 15) // 16 * 16, 128)
+    ell = float(np.sqrt(d))
+    force(native, tmp_path, prec, 1, d, p16, 0, epi, stages, 0, 0)
+    ref = native.kmatvec(A, B, S, kind="matern32", lengthscale=ell, precision=prec).clone()
+    force(native, tmp_path, prec, 1, d, p16, 0, epi, stages, 0, 1)
+    got = native.kmatvec(A, B, S, kind="matern32", lengthscale=ell, precision=prec)
+    torch.cuda.synchronize()
+    native.tune_clear()
+    assert native.sync_status() == 0
+    assert torch.isfinite(got).all()
+    scale = ref.abs().amax(dim=1, keepdim=True).clamp_min(1e-30)
+    err = float(((got - ref).abs() / scale).max())
+    assert err <= 2.0 ** -18, err

@@ -37,6 +37,28 @@ def test_sqdist_matches_scipy_cdist():
     assert np.all(O.sqdist(A, A) >= 0.0)
 
 
+
+def test_fp32_product_matches_the_brute_force_double_loop():
+    """The FP32 timed baseline against a brute-force double loop in FP64, for both kernels:
+    within FP32 rounding (1e-5 normwise)."""
+    g = np.random.default_rng(3)
+    A, B = g.standard_normal((23, 4)), g.standard_normal((31, 4))
+    S = g.standard_normal((31, 5))
+    for kern in (O.Kernel(O.RBF, 0.9, 1.3), O.Kernel(O.MATERN32, 1.7, 0.6)):
+        ref = np.zeros((23, 5))
+        for i in range(23):
+            for j in range(31):
+                r = float(np.sqrt(((A[i] - B[j]) ** 2).sum()))
+                if kern.kind == O.RBF:
+                    k = kern.outputscale * math.exp(-r * r / (2 * kern.lengthscale ** 2))
+                else:
+                    u = math.sqrt(3.0) * r / kern.lengthscale
+                    k = kern.outputscale * (1 + u) * math.exp(-u)
+                ref[i] += k * S[j]
+        got = O.kmatvec_fp32(A, B, S, kern)
+        assert got.dtype == np.float32
+        assert np.linalg.norm(got - ref) <= 1e-5 * np.linalg.norm(ref)
+
 def test_rbf_closed_form_points_and_gaussian_pdf():
     ell, s = 1.7, 2.5
     kern = O.Kernel(O.RBF, ell, s)
@@ -209,6 +231,26 @@ def test_exact_newton_shift_does_not_change_solution():
     v1, _ = O.exact_newton_step(X, lik, f, m, kern, shift=0.3)
     v2, _ = O.exact_newton_step(X, lik, f, m, kern, shift=5.0)
     assert np.allclose(v1, v2, atol=1e-9)
+
+
+def test_exact_newton_shift_matches_lu_of_the_unshifted_system():
+    """The shifted Cholesky reading of the exact step against the plain definition: an LU
+    solve of the unshifted K_hat = K + W^+ (invertible at tiny N when k(X, X) is well
+    conditioned, which a short lengthscale gives)."""
+    import scipy.linalg as sla
+    X, y, kern = tiny_problem(n=9, ell=0.3)
+    lik = O.Softmax(y, 3)
+    m = np.zeros((9, 3))
+    f = np.random.default_rng(2).standard_normal((9, 3))
+    f -= f.mean(axis=1, keepdims=True)        # Newton iterates f = K v have zero class sums
+    K = O.dense_K(X, 3, kern)
+    Khat = K + lik.Winv_dense(f)
+    assert np.linalg.cond(Khat) < 1e6
+    b = (O.pseudo_targets(lik, f) - m).reshape(-1)
+    v_lu = sla.lu_solve(sla.lu_factor(Khat), b)
+    v, f_next = O.exact_newton_step(X, lik, f, m, kern)          # default shift gamma = s
+    assert np.allclose(v.reshape(-1), v_lu, rtol=1e-9, atol=1e-10)
+    assert np.allclose(f_next.reshape(-1), K @ v_lu, rtol=1e-9, atol=1e-10)
 
 
 def test_newton_converges_to_stationary_point():
