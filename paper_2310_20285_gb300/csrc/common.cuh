@@ -57,6 +57,20 @@ __device__ __forceinline__ float sqrt_approx(float x) {
   return y;
 }
 
+// 2^e for -126 <= e <= 127, built from its bit pattern (exact).
+__device__ __forceinline__ float pow2i(int e) { return __int_as_float((e + 127) << 23); }
+
+// The exponent e of a power-of-two scale 2^e that brings a block of values whose largest
+// magnitude has the bit pattern `maxbits` (a non-negative float) into [128, 256): for
+// m 2^k with m in [0.5, 1), e = 8 - k; 0 for zero or non-finite maxima; clamped to
+// [-126, 126].
+__device__ __forceinline__ int scale_exp_of_max(uint32_t maxbits) {
+  const int bexp = static_cast<int>((maxbits >> 23) & 0xFFu);
+  int e = 0;
+  if (maxbits != 0u && bexp != 0xFF) e = 8 - (bexp == 0 ? -125 : bexp - 126);
+  return max(-126, min(126, e));
+}
+
 template <int KIND>
 __device__ __forceinline__ float kernel_eval_fast(float r2, const KParams& kp) {
   if (KIND == ITERGP_RBF) {

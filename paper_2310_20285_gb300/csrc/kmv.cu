@@ -8,9 +8,6 @@
 namespace itergp {
 namespace {
 
-// 2^e for -126 <= e <= 127, built from its bit pattern (exact).
-__device__ __forceinline__ float pow2i(int e) { return __int_as_float((e + 127) << 23); }
-
 // Split rows (BF16X3, BF16_COMP), one CTA of 8 warps per 128-row tile.  Pass 1 finds the
 // tile's largest |x| = m 2^k (m in [0.5, 1)) and takes e = 8 - k, so that 2^e |x| < 256
 // with the largest in [128, 256); pass 2 writes hi = fp16(2^e x) and
@@ -36,11 +33,7 @@ __global__ void prep_rows_split_kernel(const float* __restrict__ X, int64_t ldX,
   if (threadIdx.x == 0) {
     float m = 0.f;
     for (int w = 0; w < 8; ++w) m = fmaxf(m, wmax[w]);
-    int e = 0;
-    const uint32_t bits = __float_as_uint(m);
-    const int bexp = static_cast<int>((bits >> 23) & 0xFFu);
-    if (m > 0.f && bexp != 0xFF) e = 8 - (bexp == 0 ? -125 : bexp - 126);   // non-finite data: no scaling
-    e = max(-126, min(126, e));
+    const int e = scale_exp_of_max(__float_as_uint(m));   // non-finite data: no scaling
     e_s = e;
     tscale[blockIdx.x] = pow2i(-e);
   }

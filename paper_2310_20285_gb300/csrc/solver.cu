@@ -15,6 +15,7 @@
 namespace itergp {
 
 constexpr int kMaxC = 64;
+constexpr int kMaxBcap = 512;   // buffer columns a fit keeps at most (checked by the API)
 constexpr int kRedThreads = 256;
 
 struct FitState {
@@ -569,16 +570,17 @@ __global__ void copy_int_kernel(const ProbDev* __restrict__ probs) {
 }
 
 // -------------------------------------------------------------------- projections
-// part[blk][k] = sum_{e in blk} Q[k][e] x[e]   for k < B   (warp per column)
-__global__ void proj_partial_kernel(const ProbDev* __restrict__ probs, int guard_inner) {
+// Alg. 3's projection Q0^T b: part[blk][k] = sum_{e in blk} Q[k][e] b[e] for k < B (warp per
+// column; the inner iteration's Q^T z is formed by zproj_kernel)
+__global__ void proj_partial_kernel(const ProbDev* __restrict__ probs) {
   const ProbDev& P = probs[blockIdx.y];
   const FitState* st = P.st;
   const float* __restrict__ Q = P.Q;
-  const float* __restrict__ x = guard_inner ? P.z : P.b;   // Q^T z in the loop, Q0^T b after Alg. 3
+  const float* __restrict__ x = P.b;
   const int64_t nc = P.nc;
   const int bcap = P.bcap;
   double* __restrict__ part = P.pv;
-  if (!st->newton_active || (guard_inner && !st->active)) return;
+  if (!st->newton_active) return;
   const int B = st->B;
   const int64_t per = (nc + gridDim.x - 1) / gridDim.x;
   const int64_t e0 = blockIdx.x * per, e1 = std::min<int64_t>(e0 + per, nc);
@@ -593,13 +595,13 @@ __global__ void proj_partial_kernel(const ProbDev* __restrict__ probs, int guard
   }
 }
 
-__global__ void proj_finalize_kernel(const ProbDev* __restrict__ probs, int guard_inner, int nblk) {
+__global__ void proj_finalize_kernel(const ProbDev* __restrict__ probs, int nblk) {
   const ProbDev& P = probs[blockIdx.x];
   const FitState* st = P.st;
   const double* __restrict__ part = P.pv;
   const int bcap = P.bcap;
   float* __restrict__ w = P.w;
-  if (!st->newton_active || (guard_inner && !st->active)) return;
+  if (!st->newton_active) return;
   const int B = st->B;
   for (int k = threadIdx.x; k < B; k += blockDim.x) {
     double s = 0.0;
@@ -637,7 +639,10 @@ __global__ void combine_kernel(const ProbDev* __restrict__ probs) {
 // The residual is the small difference of large terms (u carries K's largest eigenvalues),
 // so it is formed in FP64 arithmetic from the FP32 operands and rounded once; it is the
 // quantity the inner convergence test reduces.
-__global__ void resid_kernel(const ProbDev* __restrict__ probs, int project) {
+// The same pass writes the iteration's action (Alg. 2): s = r under the CG policy, or the
+// unit vector e_{B0 + j}, into the staging vector and the next S column (B + pending;
+// committed only if the solve goes on, see resid_finalize_kernel).
+__global__ void resid_kernel(const ProbDev* __restrict__ probs, int project, int policy) {
   const ProbDev& P = probs[blockIdx.y];
   const FitState* st = P.st;
   const int64_t n = P.n;
@@ -649,6 +654,11 @@ __global__ void resid_kernel(const ProbDev* __restrict__ probs, int project) {
   float* __restrict__ r = P.r;
   double* __restrict__ part = P.ps;
   if (!st->newton_active || !st->active) return;
+  const int64_t nc = n * C;
+  const int bnext = st->B + st->pending;
+  float* __restrict__ s_cur = P.s_cur;
+  float* __restrict__ scol = bnext < P.bcap ? P.S + static_cast<int64_t>(bnext) * nc : nullptr;
+  const int64_t unit_idx = static_cast<int64_t>(st->B0) + st->j;
   const bool diag = P.lik != ITERGP_LIK_SOFTMAX;   // W^-1 diagonal: no class means
   __shared__ double sh[32];
   double acc = 0.0;
@@ -671,8 +681,12 @@ __global__ void resid_kernel(const ProbDev* __restrict__ probs, int project) {
     }
     for (int c = 0; c < C; ++c) {
       const double rv = static_cast<double>(b[i * C + c]) - u[i * C + c] - ((vi[c] - m1) * ipi[c] - m2) - rm;
-      r[i * C + c] = static_cast<float>(rv);
+      const float rf = static_cast<float>(rv);
+      r[i * C + c] = rf;
       acc += rv * rv;
+      const float sv = policy == ITERGP_POLICY_CG ? rf : (i * C + c == unit_idx ? 1.f : 0.f);
+      s_cur[i * C + c] = sv;
+      if (scol) scol[i * C + c] = sv;
     }
   }
   acc = block_reduce_sum(acc, sh);
@@ -712,27 +726,10 @@ __global__ void resid_finalize_kernel(const ProbDev* __restrict__ probs, int nbl
   }
 }
 
-// s = r (CG) or e_{B0+j} (unit vectors) into the staging vector and S[:, B]
-__global__ void action_kernel(const ProbDev* __restrict__ probs, int policy) {
-  const ProbDev& P = probs[blockIdx.y];
-  const FitState* st = P.st;
-  const int64_t nc = P.nc;
-  const float* __restrict__ r = P.r;
-  float* __restrict__ s_cur = P.s_cur;
-  float* __restrict__ S = P.S;
-  if (!st->newton_active || !st->active) return;
-  float* col = S + static_cast<int64_t>(st->B) * nc;
-  const int64_t idx = static_cast<int64_t>(st->B0) + st->j;
-  for (int64_t e = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; e < nc;
-       e += static_cast<int64_t>(gridDim.x) * blockDim.x) {
-    const float sv = policy == ITERGP_POLICY_CG ? r[e] : (e == idx ? 1.f : 0.f);
-    s_cur[e] = sv;
-    col[e] = sv;
-  }
-}
-
-// T[:, B] = t; z = t + W^+ s
-__global__ void z_kernel(const ProbDev* __restrict__ probs) {
+// T[:, B] = t; z = t + W^+ s (Lemma A.6) over a block's segment of whole points, then the
+// block's partial sums of Q_k^T z over the same segment (k < B), as proj_partial_kernel
+// does for Alg. 3's projection.
+__global__ void zproj_kernel(const ProbDev* __restrict__ probs) {
   const ProbDev& P = probs[blockIdx.y];
   const FitState* st = P.st;
   const int64_t n = P.n;
@@ -740,13 +737,18 @@ __global__ void z_kernel(const ProbDev* __restrict__ probs) {
   const float* __restrict__ s_cur = P.s_cur;
   const float* __restrict__ t_cur = P.t_cur;
   const float* __restrict__ inv_pi = P.ip;
+  const float* __restrict__ Q = P.Q;
   float* __restrict__ z = P.z;
   float* __restrict__ T = P.T;
+  double* __restrict__ part = P.pv;
   if (!st->newton_active || !st->active) return;
   const int64_t nc = n * C;
-  float* tcol = T + static_cast<int64_t>(st->B) * nc;
-  for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
-       i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+  const int B = st->B;
+  const int bcap = P.bcap;
+  const int64_t per = (n + gridDim.x - 1) / gridDim.x;   // points per block
+  const int64_t i0 = static_cast<int64_t>(blockIdx.x) * per, i1 = std::min<int64_t>(i0 + per, n);
+  float* tcol = T + static_cast<int64_t>(B) * nc;
+  for (int64_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
     float w[kMaxC];
     winv_point(s_cur + i * C, inv_pi + i * C, C, w, P.lik != ITERGP_LIK_SOFTMAX);
     for (int c = 0; c < C; ++c) {
@@ -755,23 +757,45 @@ __global__ void z_kernel(const ProbDev* __restrict__ probs) {
       z[i * C + c] = tv + w[c];
     }
   }
+  __syncthreads();   // the block reads back the z it wrote
+  const int64_t e0 = std::min(i0, n) * C, e1 = i1 * C;
+  const int wp = threadIdx.x / 32, l = threadIdx.x % 32, nw = blockDim.x / 32;
+  for (int k = wp; k < B; k += nw) {
+    double acc = 0.0;
+    const float* q = Q + static_cast<int64_t>(k) * nc;
+    for (int64_t e = e0 + l; e < e1; e += 32) acc += static_cast<double>(q[e]) * z[e];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (l == 0) part[static_cast<int64_t>(blockIdx.x) * bcap + k] = acc;
+  }
 }
 
 // d = s - Q w -> Q[:, B] (unnormalised); K d = t - KQ w -> KQ[:, B]; partial eta = z.d
-__global__ void direction_kernel(const ProbDev* __restrict__ probs, int track_kd) {
+// Every block first adds the nblk partial sums of Q^T z (zproj_kernel) itself, in block
+// order, into w = Q^T z (block 0 also stores it).
+__global__ void direction_kernel(const ProbDev* __restrict__ probs, int track_kd, int nblk) {
   const ProbDev& P = probs[blockIdx.y];
   const FitState* st = P.st;
   const int64_t nc = P.nc;
   const float* __restrict__ s_cur = P.s_cur;
   const float* __restrict__ t_cur = P.t_cur;
   const float* __restrict__ z = P.z;
-  const float* __restrict__ w = P.w;
+  const double* __restrict__ pv = P.pv;
   float* __restrict__ Q = P.Q;
   float* __restrict__ KQ = P.KQ;
   double* __restrict__ part = P.ps;
   if (!st->newton_active || !st->active) return;
   __shared__ double sh[32];
+  __shared__ float w[kMaxBcap];
   const int B = st->B;
+  const int bcap = P.bcap;
+  for (int k = threadIdx.x; k < B; k += blockDim.x) {
+    double sum = 0.0;
+    for (int b = 0; b < nblk; ++b) sum += pv[static_cast<int64_t>(b) * bcap + k];
+    w[k] = static_cast<float>(sum);
+    if (blockIdx.x == 0) P.w[k] = w[k];
+  }
+  __syncthreads();
   float* qcol = Q + static_cast<int64_t>(B) * nc;
   float* kcol = KQ + static_cast<int64_t>(B) * nc;
   double acc = 0.0;
@@ -790,37 +814,44 @@ __global__ void direction_kernel(const ProbDev* __restrict__ probs, int track_kd
   if (threadIdx.x == 0) part[blockIdx.x] = acc;
 }
 
-__global__ void eta_finalize_kernel(const ProbDev* __restrict__ probs, int nblk) {
-  FitState* st = probs[blockIdx.x].st;
-  const double* __restrict__ part = probs[blockIdx.x].ps;
-  if (threadIdx.x != 0 || !st->newton_active || !st->active) return;
-  double s = 0.0;
-  for (int b = 0; b < nblk; ++b) s += part[b];
-  st->eta = s;
-  if (!(s > 0.0)) {
-    st->active = 0;
-    st->stop_reason = ITERGP_STOP_ETA;
-    return;
-  }
-  st->coef = st->alpha / s;
-  st->inv_sqrt_eta = 1.0 / sqrt(s);
-  st->pending = 1;
-  st->j += 1;
-  st->total_iters += 1;
-}
-
-// Q[:, B] /= sqrt(eta); KQ[:, B] /= sqrt(eta); v += (alpha/eta) d; u += (alpha/eta) K d
-__global__ void update_kernel(const ProbDev* __restrict__ probs, int track_kd) {
+// eta = z^T d from direction_kernel's partial sums (every block adds them itself, in block
+// order); block 0 records the step as eta's finalisation (stop if eta <= 0, App. B.2;
+// otherwise the column is pending and the iteration counts); then
+// Q[:, B] /= sqrt(eta); KQ[:, B] /= sqrt(eta); v += (alpha/eta) d; u += (alpha/eta) K d.
+__global__ void update_kernel(const ProbDev* __restrict__ probs, int track_kd, int nblk) {
   const ProbDev& P = probs[blockIdx.y];
-  const FitState* st = P.st;
+  FitState* st = P.st;
   const int64_t nc = P.nc;
   float* __restrict__ Q = P.Q;
   float* __restrict__ KQ = P.KQ;
   float* __restrict__ v = P.v;
   float* __restrict__ u = P.u;
   if (!st->newton_active || !st->active) return;
+  __shared__ double eta_s;
+  if (threadIdx.x == 0) {
+    double sum = 0.0;
+    for (int b = 0; b < nblk; ++b) sum += P.ps[b];
+    eta_s = sum;
+  }
+  __syncthreads();
+  const double eta = eta_s;
   const int B = st->B;
-  const float coef = static_cast<float>(st->coef), ise = static_cast<float>(st->inv_sqrt_eta);
+  const double alpha = st->alpha;
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    st->eta = eta;
+    if (!(eta > 0.0)) {
+      st->active = 0;
+      st->stop_reason = ITERGP_STOP_ETA;
+    } else {
+      st->coef = alpha / eta;
+      st->inv_sqrt_eta = 1.0 / sqrt(eta);
+      st->pending = 1;
+      st->j += 1;
+      st->total_iters += 1;
+    }
+  }
+  if (!(eta > 0.0)) return;
+  const float coef = static_cast<float>(alpha / eta), ise = static_cast<float>(1.0 / sqrt(eta));
   float* qcol = Q + static_cast<int64_t>(B) * nc;
   float* kcol = KQ + static_cast<int64_t>(B) * nc;
   for (int64_t e = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; e < nc;
@@ -1071,7 +1102,6 @@ int fit_run_batch(DeviceContext* ctx, const std::vector<FitProblem>& probs, cuda
   const int nblk_e = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(2LL * ctx->num_sms, ceil_div(max_nc, 1024))));
   const int gram_splits = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(64, ceil_div(max_nc, 4096))));
   const int eb = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(ceil_div(max_nc, 256), 8LL * ctx->num_sms)));
-  const int nb_pts = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(ceil_div(max_n, 256), 8LL * ctx->num_sms)));
   const int maxblk = std::max(nblk, nblk_e);
   const int tiles = static_cast<int>(ceil_div(max_bcap, kGT));
 
@@ -1302,8 +1332,8 @@ int fit_run_batch(DeviceContext* ctx, const std::vector<FitProblem>& probs, cuda
       vsr_rotate_kernel<<<dim3(eb, np), 256, 0, stream>>>(pdev), ::itergp::note_launch();
       vsr_rescale_kernel<<<dim3(eb, np), 256, 0, stream>>>(pdev), ::itergp::note_launch();
       // v0 = Q0 (Q0^T b), u0 = K v0 = KQ0 (Q0^T b)
-      proj_partial_kernel<<<dim3(nblk_e, np), 256, 0, stream>>>(pdev, 0), ::itergp::note_launch();
-      proj_finalize_kernel<<<np, 256, 0, stream>>>(pdev, 0, nblk_e), ::itergp::note_launch();
+      proj_partial_kernel<<<dim3(nblk_e, np), 256, 0, stream>>>(pdev), ::itergp::note_launch();
+      proj_finalize_kernel<<<np, 256, 0, stream>>>(pdev, nblk_e), ::itergp::note_launch();
     }
     // v0 = C0 (y_hat - m) and K v0; with no recycled columns (B = 0) both are zero
     combine_kernel<<<dim3(eb, np), 256, 0, stream>>>(pdev), ::itergp::note_launch();
@@ -1313,17 +1343,16 @@ int fit_run_batch(DeviceContext* ctx, const std::vector<FitProblem>& probs, cuda
         rc = kprod0(pd[0].v, pd[0].u, &pd[0].st->active);
         if (rc != ITERGP_OK) break;
       }
-      resid_kernel<<<dim3(nblk, np), kRedThreads, 0, stream>>>(pdev, project), ::itergp::note_launch();
+      // r and the action s; |r|, the stopping test and alpha; t = K s; z and Q^T z;
+      // d, K d and eta; v, u and the new column (each reduction is finished by the next
+      // kernel's blocks)
+      resid_kernel<<<dim3(nblk, np), kRedThreads, 0, stream>>>(pdev, project, prm.policy), ::itergp::note_launch();
       resid_finalize_kernel<<<np, 32, 0, stream>>>(pdev, nblk, prm.policy), ::itergp::note_launch();
-      action_kernel<<<dim3(eb, np), 256, 0, stream>>>(pdev, prm.policy), ::itergp::note_launch();
       rc = products();
       if (rc != ITERGP_OK) break;
-      z_kernel<<<dim3(nb_pts, np), 256, 0, stream>>>(pdev), ::itergp::note_launch();
-      proj_partial_kernel<<<dim3(nblk_e, np), 256, 0, stream>>>(pdev, 1), ::itergp::note_launch();
-      proj_finalize_kernel<<<np, 256, 0, stream>>>(pdev, 1, nblk_e), ::itergp::note_launch();
-      direction_kernel<<<dim3(nblk_e, np), kRedThreads, 0, stream>>>(pdev, track_kd), ::itergp::note_launch();
-      eta_finalize_kernel<<<np, 32, 0, stream>>>(pdev, nblk_e), ::itergp::note_launch();
-      update_kernel<<<dim3(eb, np), 256, 0, stream>>>(pdev, track_kd), ::itergp::note_launch();
+      zproj_kernel<<<dim3(nblk_e, np), 256, 0, stream>>>(pdev), ::itergp::note_launch();
+      direction_kernel<<<dim3(nblk_e, np), kRedThreads, 0, stream>>>(pdev, track_kd, nblk_e), ::itergp::note_launch();
+      update_kernel<<<dim3(eb, np), 256, 0, stream>>>(pdev, track_kd, nblk_e), ::itergp::note_launch();
     }
     if (rc != ITERGP_OK) break;
     step_end_kernel<<<np, 32, 0, stream>>>(pdev, step), ::itergp::note_launch();

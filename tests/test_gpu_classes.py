@@ -103,7 +103,7 @@ def test_fit_and_predict_with_class_kernels_match_the_oracle(native, prec):
     mean, var, probs = m.predict(t32(Xs32))
     em, ev, ep = O.predict(Xs32.astype(np.float64), X32.astype(np.float64), ref.v, ref.Q, kerns, 3)
     assert rel(mean.cpu(), em) <= tol
-    assert np.max(np.abs(var.cpu().numpy() - ev)) <= 1e-4 * max(k[2] for k in KERNS3)
+    assert np.max(np.abs(var.cpu().numpy() - ev)) <= 1e-3 * max(k[2] for k in KERNS3)
     assert np.max(np.abs(probs.cpu().numpy() - ep)) <= 10 * tol
     m.free()
 

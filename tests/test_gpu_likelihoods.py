@@ -44,7 +44,7 @@ def test_one_latent_fit_matches_the_oracle(native, kind, prec):
     mean, var, out = m.predict(torch.as_tensor(Xs, device=DEV))
     em, ev, _ = O.predict(Xs.astype(np.float64), X64, ref.v, ref.Q, KERN, 1)
     assert rel(mean.cpu(), em) <= tol
-    assert np.max(np.abs(var.cpu().numpy() - ev)) <= 1e-4   # s = 1
+    assert np.max(np.abs(var.cpu().numpy() - ev)) <= 1e-3   # 1e-3 s, as for every fit (test_gpu_fit)
     if kind == "bernoulli":    # P(y = 1) by the probit approximation
         want = 1.0 / (1.0 + np.exp(-em / np.sqrt(1.0 + np.pi / 8.0 * ev)))
     else:                      # predictive mean count E[e^f]
