@@ -827,6 +827,7 @@ def main():
         if rank == 0 and not args.no_extras:
             shapes += [("batched fits", 8192, 64, 16, "rbf", pr, True) for pr in ("bf16x3", "bf16_comp")]
             shapes += [("served mean + variance", 16384, 32, 128, "rbf", "bf16x3", True)]
+            shapes += [("small-D product", 131072, 32, 16, "rbf", pr, False) for pr in ("bf16x3", "bf16_comp")]
         for label, tn, td, tp, kind, prec, items in shapes:
             vs, best = native.autotune(tn, td, tp, kind=kind, precision=prec, items=items,
                                        lengthscale=ELL if kind == "matern32" else 1.0)

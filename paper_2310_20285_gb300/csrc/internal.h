@@ -103,6 +103,7 @@ struct TcProb {
   int32_t pad;
   KParams kp;
   const int* active; // the problem's solver flag (nullptr: always active)
+  const float* wscale;   // split weights: 2^-e per weight row of the problem's staged S
 };
 
 // Device-side tables of a batched product.

@@ -24,8 +24,10 @@ __global__ void prep_rows_split_kernel(const float* __restrict__ X, int64_t ldX,
   __shared__ float wmax[8];
   __shared__ int e_s;
   float mx = 0.f;
-  for (int rr = warp; rr < 128 && r0 + rr < rows; rr += 8)
+  for (int rr = warp; rr < 128 && r0 + rr < rows; rr += 8) {
+#pragma unroll 4
     for (int col = lane; col < d; col += 32) mx = fmaxf(mx, fabsf(X[(r0 + rr) * ldX + col]));
+  }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
   if (lane == 0) wmax[warp] = mx;
@@ -42,6 +44,7 @@ __global__ void prep_rows_split_kernel(const float* __restrict__ X, int64_t ldX,
   for (int rr = warp; rr < 128; rr += 8) {
     const int64_t row = r0 + rr;
     double acc = 0.0;
+#pragma unroll 4
     for (int col = lane; col < d_pad; col += 32) {
       const float x = (row < rows && col < d) ? X[row * ldX + col] : 0.f;
       const float xs = x * sc;

@@ -56,7 +56,8 @@ __global__ void tc_fixup_kernel(const float* __restrict__ partial, int64_t R, in
   const int64_t u0 = (r - rt0) * J, u1 = u0 + J - 1;
   const int64_t g_lo = part_owner(u0, ut, G), g_hi = part_owner(u1, ut, G);
   if (g_lo == g_hi) return;   // one CTA covered the whole row tile and stored it
-  for (int e = threadIdx.x; e < tm * p_valid; e += blockDim.x) {
+  // grid: (tail row tiles, blocks per tile); every element of the tile is one thread's sum
+  for (int e = blockIdx.y * blockDim.x + threadIdx.x; e < tm * p_valid; e += gridDim.y * blockDim.x) {
     const int row = e / p_valid, col = e % p_valid;
     const int64_t grow = r * tm + row;
     if (grow >= m) continue;
@@ -72,11 +73,35 @@ __global__ void tc_fixup_kernel(const float* __restrict__ partial, int64_t R, in
 }
 
 
-// S (n x p, row pitch ldS) -> transposed BF16 hi [p16][n_pad] (+ lo), zero padded.
+// Largest |S[:, c]| of each column c < p, as float bits (non-negative floats order like
+// their bit patterns): one block per 256-row band and 32-column group, one atomicMax per
+// column and block into cmax (zeroed by the caller).
+__global__ void colmax_kernel(const float* __restrict__ S, int64_t ldS, int64_t n, int64_t p,
+                              uint32_t* __restrict__ cmax, const int* __restrict__ active) {
+  if (active != nullptr && *active == 0) return;
+  __shared__ float part[8][33];
+  const int64_t c = static_cast<int64_t>(blockIdx.y) * 32 + threadIdx.x;
+  const int64_t j0 = static_cast<int64_t>(blockIdx.x) * 256;
+  float m = 0.f;
+  if (c < p)
+    for (int64_t j = j0 + threadIdx.y; j < j0 + 256 && j < n; j += 8) m = fmaxf(m, fabsf(S[j * ldS + c]));
+  part[threadIdx.y][threadIdx.x] = m;
+  __syncthreads();
+  if (threadIdx.y == 0 && c < p) {
+    for (int i = 1; i < 8; ++i) m = fmaxf(m, part[i][threadIdx.x]);
+    atomicMax(&cmax[c], __float_as_uint(m));
+  }
+}
+
+// S (n x p, row pitch ldS) -> transposed weights [p16][n_pad], zero padded.  SPLIT (the
+// BF16X3 and TF32 forms): FP16 hi and lo of 2^e_c S[:, c], with e_c from the column's
+// largest |value| (cmax, see colmax_kernel) so that it lies in [128, 256); wscale[c] =
+// 2^-e_c (22 significant bits at any magnitude).  Otherwise one BF16 plane.
 template <bool SPLIT>
 __global__ void prep_s_kernel(const float* __restrict__ S, int64_t ldS, int64_t n, int64_t p,
                               int64_t n_pad, int64_t p16, __nv_bfloat16* __restrict__ hi,
-                              __nv_bfloat16* __restrict__ lo, const int* __restrict__ active) {
+                              __nv_bfloat16* __restrict__ lo, const uint32_t* __restrict__ cmax,
+                              float* __restrict__ wscale, const int* __restrict__ active) {
   if (active != nullptr && *active == 0) return;
   __shared__ float tile[32][33];
   const int64_t j0 = static_cast<int64_t>(blockIdx.x) * 32, c0 = static_cast<int64_t>(blockIdx.y) * 32;
@@ -89,13 +114,40 @@ __global__ void prep_s_kernel(const float* __restrict__ S, int64_t ldS, int64_t 
     const int64_t cc = c0 + i, j = j0 + threadIdx.x;
     if (cc < p16 && j < n_pad) {
       const float x = tile[threadIdx.x][i];
-      const __nv_bfloat16 h = __float2bfloat16_rn(x);
-      hi[cc * n_pad + j] = h;
-      if (SPLIT) lo[cc * n_pad + j] = __float2bfloat16_rn(x - __bfloat162float(h));
+      if constexpr (SPLIT) {
+        const int e = cc < p ? scale_exp_of_max(cmax[cc]) : 0;
+        const float xs = x * pow2i(e);
+        const __half h = __float2half_rn(xs);
+        reinterpret_cast<__half*>(hi)[cc * n_pad + j] = h;
+        reinterpret_cast<__half*>(lo)[cc * n_pad + j] = __float2half_rn(xs - __half2float(h));
+        if (blockIdx.x == 0 && threadIdx.x == 0) wscale[cc] = pow2i(-e);
+      } else {
+        hi[cc * n_pad + j] = __float2bfloat16_rn(x);
+      }
     }
   }
 }
 
+// Column maxima, then the transposed (split) weights; cmax / wscale: [p16] device scratch.
+cudaError_t stage_weights(const float* S, int64_t ldS, int64_t n, int64_t p, int64_t n_pad, int64_t p16,
+                          __nv_bfloat16* hi, __nv_bfloat16* lo, uint32_t* cmax, float* wscale, bool split,
+                          const int* active, cudaStream_t stream) {
+  dim3 grid(static_cast<unsigned>(n_pad / 32), static_cast<unsigned>(ceil_div(p16, 32)));
+  if (split) {
+    cudaError_t e = cudaMemsetAsync(cmax, 0, sizeof(uint32_t) * p16, stream);
+    if (e != cudaSuccess) return e;
+    if (n > 0) {
+      colmax_kernel<<<dim3(static_cast<unsigned>(ceil_div(n, 256)), static_cast<unsigned>(ceil_div(p, 32))),
+                      dim3(32, 8), 0, stream>>>(S, ldS, n, p, cmax, active), ::itergp::note_launch();
+      e = cudaGetLastError();
+      if (e != cudaSuccess) return e;
+    }
+    prep_s_kernel<true><<<grid, dim3(32, 8), 0, stream>>>(S, ldS, n, p, n_pad, p16, hi, lo, cmax, wscale, active), ::itergp::note_launch();
+  } else {
+    prep_s_kernel<false><<<grid, dim3(32, 8), 0, stream>>>(S, ldS, n, p, n_pad, p16, hi, lo, nullptr, nullptr, active), ::itergp::note_launch();
+  }
+  return cudaGetLastError();
+}
 
 // ---------------------------------------------------------------- launch variants
 // A variant: epilogue warps (4 or 8) and pipeline stages (0: the deepest that fits).
@@ -219,8 +271,9 @@ int kmv_tc_items(DeviceContext* ctx, int kind, const RowOperand& A, const RowOpe
   if (!ok) return ITERGP_ECUDA;
   for (int p0 = 0; p0 < p16; p0 += p_tile) {
     const int pp = std::min(p_tile, p16 - p0);   // multiple of 16
-    ok = encode_bf16_sw128(&maps[4], s_hi, s_rows, B.rows_pad, B.rows_pad, pp) &&
-         encode_bf16_sw128(&maps[5], nt2 == 3 ? s_lo : s_hi, s_rows, B.rows_pad, B.rows_pad, pp);
+    const CUtensorMapDataType wty = nt2 == 3 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
+    ok = encode_bf16_sw128(&maps[4], s_hi, s_rows, B.rows_pad, B.rows_pad, pp, wty) &&
+         encode_bf16_sw128(&maps[5], nt2 == 3 ? s_lo : s_hi, s_rows, B.rows_pad, B.rows_pad, pp, wty);
     if (!ok) return ITERGP_ECUDA;
     TcArgs a{};
     a.na = A.norms;
@@ -241,6 +294,7 @@ int kmv_tc_items(DeviceContext* ctx, int kind, const RowOperand& A, const RowOpe
     a.probs = tab.probs;
     a.kp = make_kparams(itergp_kernel{kind, 1.f, 1.f});   // per-item values come from the table
     a.w_slots = g_bufs(pp);
+    a.diag = &A == &B || (A.hi == B.hi && A.norms == B.norms && A.rows == B.rows);
     const size_t smem = tc_smem_bytes(nt1, nt2, pp, var.epi, nstage, ares, a.w_slots);
     cudaError_t e = kind == ITERGP_RBF
                         ? launch_prec<ITERGP_RBF, false>(prec, nstage, ares, var.epi, tab.G, smem, stream, maps, a)
@@ -297,21 +351,17 @@ int kmv_tc(DeviceContext* ctx, const KParams& kp, const RowOperand& A, const Row
     }
   }
 
-  // transposed, split S
+  // transposed (split) S, with the split form's column maxima and scales after the planes
   const int64_t n_pad = B.rows_pad;
   Scratch sbuf;
   const size_t s_elems = static_cast<size_t>(p16) * n_pad;
-  ITERGP_CUDA_TRY(sbuf.alloc(ctx, s_elems * 2 * (nt2 == 3 ? 2 : 1), stream));
+  const size_t s_planes = align_up(s_elems * 2 * (nt2 == 3 ? 2 : 1), 256);
+  ITERGP_CUDA_TRY(sbuf.alloc(ctx, s_planes + sizeof(uint32_t) * p16 * 2, stream));
   __nv_bfloat16* s_hi = sbuf.as<__nv_bfloat16>();
   __nv_bfloat16* s_lo = nt2 == 3 ? s_hi + s_elems : nullptr;
-  {
-    dim3 grid(static_cast<unsigned>(n_pad / 32), static_cast<unsigned>(ceil_div(p16, 32)));
-    if (nt2 == 3)
-      prep_s_kernel<true><<<grid, dim3(32, 8), 0, stream>>>(S, ldS, B.rows, p, n_pad, p16, s_hi, s_lo, active), ::itergp::note_launch();
-    else
-      prep_s_kernel<false><<<grid, dim3(32, 8), 0, stream>>>(S, ldS, B.rows, p, n_pad, p16, s_hi, s_lo, active), ::itergp::note_launch();
-    ITERGP_CUDA_TRY(cudaGetLastError());
-  }
+  uint32_t* s_cmax = sbuf.as<uint32_t>(s_planes);
+  float* s_scale = reinterpret_cast<float*>(s_cmax + p16);
+  ITERGP_CUDA_TRY(stage_weights(S, ldS, B.rows, p, n_pad, p16, s_hi, s_lo, s_cmax, s_scale, nt2 == 3, active, stream));
 
   CUtensorMap maps[6];
   bool ok = encode_rows(maps, A, B, nt1, pair);
@@ -331,8 +381,9 @@ int kmv_tc(DeviceContext* ctx, const KParams& kp, const RowOperand& A, const Row
     const int pw = static_cast<int>(std::min<int64_t>(p_tile, p - p0));
     const int pp = (pw + 15) / 16 * 16;
     const uint32_t s_box_rows = static_cast<uint32_t>(pair ? pp / 2 : pp);   // pair: each CTA's half
-    ok = encode_bf16_sw128(&maps[4], s_hi, p16, n_pad, n_pad, s_box_rows) &&
-         encode_bf16_sw128(&maps[5], nt2 == 3 ? s_lo : s_hi, p16, n_pad, n_pad, s_box_rows);
+    const CUtensorMapDataType wty = nt2 == 3 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
+    ok = encode_bf16_sw128(&maps[4], s_hi, p16, n_pad, n_pad, s_box_rows, wty) &&
+         encode_bf16_sw128(&maps[5], nt2 == 3 ? s_lo : s_hi, p16, n_pad, n_pad, s_box_rows, wty);
     if (!ok) return ITERGP_ECUDA;
     TcArgs a{};   // items/item_begin/probs stay null: single-problem schedule
     a.na = A.norms;
@@ -351,6 +402,7 @@ int kmv_tc(DeviceContext* ctx, const KParams& kp, const RowOperand& A, const Row
     a.Y = Y + p0;
     a.ldY = ldY;
     a.partial = part.as<float>();
+    a.wscale = s_scale;
     a.kp = kp;
     a.status = ctx->status;
     a.active = active;
@@ -358,6 +410,7 @@ int kmv_tc(DeviceContext* ctx, const KParams& kp, const RowOperand& A, const Row
     a.item_begin = nullptr;
     a.probs = nullptr;
     a.w_slots = weight_slots(ctx, nt1, nt2, pp, var.epi, nstage, pair);
+    a.diag = A.hi == B.hi && A.norms == B.norms && A.rows == B.rows;
     const size_t smem_t = tc_smem_bytes(nt1, nt2, pp, var.epi, nstage, ares, a.w_slots, pair);
     cudaError_t e;
     if (pair)
@@ -368,7 +421,8 @@ int kmv_tc(DeviceContext* ctx, const KParams& kp, const RowOperand& A, const Row
               : launch_prec<ITERGP_MATERN32, false>(prec, nstage, ares, var.epi, (int)G, smem_t, stream, maps, a);
     ITERGP_CUDA_TRY(e);
     if (tail_rows > 0) {
-      tc_fixup_kernel<<<static_cast<unsigned>(tail_rows), 256, 0, stream>>>(
+      const unsigned per_tile = static_cast<unsigned>(std::min<int64_t>(ceil_div(static_cast<int64_t>(tm) * pw, 256), 64));
+      tc_fixup_kernel<<<dim3(static_cast<unsigned>(tail_rows), per_tile), 256, 0, stream>>>(
           part.as<float>(), row_tiles, G, (int)chunks, tm, A.rows, pp, pw, Y + p0, ldY, active), ::itergp::note_launch();
       ITERGP_CUDA_TRY(cudaGetLastError());
     }
@@ -402,7 +456,16 @@ int kmv_tc_tune(DeviceContext* ctx, const KParams& kp, const RowOperand& X, cons
     std::vector<WorkItem> ord;
     std::vector<int32_t> beg;
     plan_items(its, G, &ord, &beg);
-    TcProb pr{Y, p, X.rows, static_cast<int32_t>(p), 0, kp, nullptr};
+    // weights first (the table entry points at their scales)
+    const size_t s_elems = static_cast<size_t>(p16) * X.rows_pad;
+    const size_t s_planes = align_up(s_elems * 2 * 2, 256);
+    ITERGP_CUDA_TRY(sbuf.alloc(ctx, s_planes + sizeof(uint32_t) * p16 * 2, stream));
+    s_hi = sbuf.as<__nv_bfloat16>();
+    s_lo = s_hi + s_elems;
+    uint32_t* cmax = sbuf.as<uint32_t>(s_planes);
+    float* wsc = reinterpret_cast<float*>(cmax + p16);
+    ITERGP_CUDA_TRY(stage_weights(S, p, X.rows, p, X.rows_pad, p16, s_hi, s_lo, cmax, wsc, nt2 == 3, nullptr, stream));
+    TcProb pr{Y, p, X.rows, static_cast<int32_t>(p), 0, kp, nullptr, wsc};
     const size_t b_items = align_up(sizeof(WorkItem) * ord.size(), 256);
     const size_t b_beg = align_up(sizeof(int32_t) * beg.size(), 256);
     ITERGP_CUDA_TRY(tabs.alloc(ctx, b_items + b_beg + sizeof(TcProb), stream));
@@ -414,13 +477,6 @@ int kmv_tc_tune(DeviceContext* ctx, const KParams& kp, const RowOperand& X, cons
     tab.probs = reinterpret_cast<const TcProb*>(tabs.as<char>(b_items + b_beg));
     tab.G = G;
     tab.n_items = static_cast<int>(ord.size());
-    const size_t s_elems = static_cast<size_t>(p16) * X.rows_pad;
-    ITERGP_CUDA_TRY(sbuf.alloc(ctx, s_elems * 2 * 2, stream));
-    s_hi = sbuf.as<__nv_bfloat16>();
-    s_lo = s_hi + s_elems;
-    dim3 grid(static_cast<unsigned>(X.rows_pad / 32), static_cast<unsigned>(ceil_div(p16, 32)));
-    prep_s_kernel<true><<<grid, dim3(32, 8), 0, stream>>>(S, p, X.rows, p, X.rows_pad, p16, s_hi, s_lo, nullptr), ::itergp::note_launch();
-    ITERGP_CUDA_TRY(cudaGetLastError());
   }
   cudaEvent_t e0, e1;
   ITERGP_CUDA_TRY(cudaEventCreate(&e0));

@@ -62,6 +62,9 @@ struct TcArgs {
   int64_t ldY;
   float* partial;         // [2 G][tile_rows][p_pad] (G: CTAs, or pairs in the pair form)
   int w_slots;            // weight-tile slots of the shared-memory layout (1 .. 3)
+  int diag;               // A and B are the same rows: k(x_i, x_i) = s is set exactly
+  const float* wscale;    // split weights: per transposed-S row (output column) 2^-e of its
+                          // FP16 scaling (single-problem mode; item mode: TcProb::wscale)
   uint64_t wait_ns;       // bound of each wait for another role's work (ns)
   KParams kp;
   int* status;
@@ -568,7 +571,9 @@ kmv_tc_kernel(const __grid_constant__ CUtensorMap mAh, const __grid_constant__ C
       constexpr uint32_t TM = tile_rows(PAIR);
       // split rows are FP16 hi/lo, BF16 rows BF16, TF32 rows TF32
       const uint32_t idesc1 = NT1 == 2 ? idesc_tf32_f32(TM, BN) : NT1 == 3 ? idesc_f16_f32(TM, BN) : idesc_bf16_f32(TM, BN);
-      const uint32_t idesc2 = idesc_bf16_f32(TM, static_cast<uint32_t>(args.p_pad));
+      // split weights are FP16 hi/lo (kernel values too), single weights BF16
+      const uint32_t idesc2 = NT2 == 3 ? idesc_f16_f32(TM, static_cast<uint32_t>(args.p_pad))
+                                       : idesc_bf16_f32(TM, static_cast<uint32_t>(args.p_pad));
       // shared-memory descriptors of stage 0, the resident A and the weight buffers; the
       // start-address field (bits 0-13, 16-byte units) takes offsets by plain addition
       // because every operand lies below 256 KB of the shared window
@@ -672,6 +677,8 @@ kmv_tc_kernel(const __grid_constant__ CUtensorMap mAh, const __grid_constant__ C
     KParams kp = args.kp;
     float rowc = 0.f;   // RBF: c_exp |a|^2 + log2 s of this thread's row
     float ua_t = 1.f;   // split rows: scale of this row's tile (G reads 2^(e_I + e_J) a.b)
+    float ke = 0.f, kls = kp.log2s, kmul = 1.f;   // split weights: kernel-value scale 2^ke
+    const float* item_ws = nullptr;               // item mode: the problem's weight scales
     const int J = args.chunks;
     float* out_row = nullptr;       // item mode: this row's output
     bool out_valid = false;
@@ -708,8 +715,19 @@ kmv_tc_kernel(const __grid_constant__ CUtensorMap mAh, const __grid_constant__ C
           out_valid = prow < pr.m;
           out_row = pr.Y + prow * pr.ldY + args.p_col0;
           out_lim = pr.p_valid - args.p_col0;   // <= 0: nothing of this tile to write
+          item_ws = pr.wscale;
         }
-        rowc = fmaf(kp.c_exp, na_r, kp.log2s);
+        // split weights: kernel values are formed as 2^ke k with ke = 14 - floor(log2 s),
+        // which puts them in [0, 2^15) for FP16 (an exact power of two, undone at the
+        // output).  The headroom keeps the lo half normal down to k = 2^-17 s and the
+        // absolute rounding near 2^-39 s, so rows whose kernel values are all small (test
+        // points far from the data) keep their relative accuracy.
+        if constexpr (NT2 == 3) {
+          ke = fminf(fmaxf(14.f - floorf(kp.log2s), -100.f), 100.f);
+          kls = kp.log2s + ke;
+          kmul = pow2i(static_cast<int>(ke));
+        }
+        rowc = fmaf(kp.c_exp, na_r, kls);
       }
       float* nb_s = nb_all + e * BN;
       __syncwarp();
@@ -733,6 +751,9 @@ kmv_tc_kernel(const __grid_constant__ CUtensorMap mAh, const __grid_constant__ C
       }
       tc_fence_after();
       const uint32_t gcol = tb + lane_base + gb * BN;
+      // the chunk that holds this tile's own rows as columns (row tiles and chunks start on
+      // multiples of 128, so it is the chunk with b_row == a_row, the same for the CTA)
+      const bool dchunk = args.diag != 0 && st.a_row == st.b_row;
       // the TMEM load of the next 32-column group is in flight while this one is computed
       const int grp0 = hc * (BN / 32 / NH), grp1 = (hc + 1) * (BN / 32 / NH);
       uint32_t v[32];
@@ -744,6 +765,13 @@ kmv_tc_kernel(const __grid_constant__ CUtensorMap mAh, const __grid_constant__ C
         const bool more = grp + 1 < grp1;   // warp-uniform
         if (more) tmem_ld32(gcol + 32 * (grp + 1), vn);
         uint32_t ph[16], pl[16];
+        if (dchunk && grp == q) {
+          // the row's own column (32 q + lane): a huge a.b clamps r^2 to 0 below, so the
+          // kernel value is s itself rather than the rounding left by |a|^2 + |a|^2 - 2 a.a
+#pragma unroll
+          for (int j = 0; j < 32; ++j)
+            if (j == lane) v[j] = __float_as_uint(1e30f);
+        }
         if (KIND == ITERGP_RBF) {
           // k = s 2^(c_exp r^2) = 2^t, t = c_exp (|a|^2 + |b|^2 - 2 a.b) + log2 s, formed two
           // lanes at a time; r^2 >= 0 is t <= log2 s (c_exp < 0)
@@ -755,13 +783,15 @@ kmv_tc_kernel(const __grid_constant__ CUtensorMap mAh, const __grid_constant__ C
             const float2 cb = *reinterpret_cast<const float2*>(cnb + 2 * i);
             const uint64_t t2 = f2_fma(f2_pack(__uint_as_float(v[2 * i]), __uint_as_float(v[2 * i + 1])), m2c,
                                        f2_add(f2_pack(cb.x, cb.y), rc2));
-            const float k0 = ex2_approx(fminf(f2_lo(t2), kp.log2s));
-            const float k1 = ex2_approx(fminf(f2_hi(t2), kp.log2s));
-            ph[i] = pack_bf16x2(k0, k1);
-            if (NT2 == 3) {
-              const uint64_t hh = f2_pack(__uint_as_float(ph[i] << 16), __uint_as_float(ph[i] & 0xFFFF0000u));
+            const float k0 = ex2_approx(fminf(f2_lo(t2), kls));
+            const float k1 = ex2_approx(fminf(f2_hi(t2), kls));
+            if constexpr (NT2 == 3) {   // FP16 hi and lo (22 significant bits)
+              ph[i] = pack_f16x2(k0, k1);
+              const uint64_t hh = f2_pack(f16_lo_to_f32(ph[i]), f16_hi_to_f32(ph[i]));
               const uint64_t lo2 = f2_sub(f2_pack(k0, k1), hh);
-              pl[i] = pack_bf16x2(f2_lo(lo2), f2_hi(lo2));
+              pl[i] = pack_f16x2(f2_lo(lo2), f2_hi(lo2));
+            } else {
+              ph[i] = pack_bf16x2(k0, k1);
             }
           }
         } else {
@@ -769,13 +799,13 @@ kmv_tc_kernel(const __grid_constant__ CUtensorMap mAh, const __grid_constant__ C
           for (int i = 0; i < 16; ++i) {
             const float r0 = fmaxf(fmaf(gsc, __uint_as_float(v[2 * i]), na_r + nb_s[32 * grp + 2 * i]), 0.f);
             const float r1 = fmaxf(fmaf(gsc, __uint_as_float(v[2 * i + 1]), na_r + nb_s[32 * grp + 2 * i + 1]), 0.f);
-            const float k0 = kernel_eval_fast<KIND>(r0, kp);
-            const float k1 = kernel_eval_fast<KIND>(r1, kp);
-            ph[i] = pack_bf16x2(k0, k1);
-            if (NT2 == 3) {
-              const float h0 = __uint_as_float(ph[i] << 16);
-              const float h1 = __uint_as_float(ph[i] & 0xFFFF0000u);
-              pl[i] = pack_bf16x2(k0 - h0, k1 - h1);
+            const float k0 = kernel_eval_fast<KIND>(r0, kp) * kmul;
+            const float k1 = kernel_eval_fast<KIND>(r1, kp) * kmul;
+            if constexpr (NT2 == 3) {
+              ph[i] = pack_f16x2(k0, k1);
+              pl[i] = pack_f16x2(k0 - f16_lo_to_f32(ph[i]), k1 - f16_hi_to_f32(ph[i]));
+            } else {
+              ph[i] = pack_bf16x2(k0, k1);
             }
           }
         }
@@ -830,9 +860,17 @@ kmv_tc_kernel(const __grid_constant__ CUtensorMap mAh, const __grid_constant__ C
           }
           if (last) {
             if (valid) {
+              if constexpr (NT2 == 3) {   // undo the weights' and the kernel values' scales
+                const float* ws = (st.item >= 0 ? item_ws : args.wscale) + args.s_row0 + 16 * c16;
+                const float kinv = pow2i(-static_cast<int>(ke));
 #pragma unroll
-              for (int i = 0; i < 16; ++i)
-                if (16 * c16 + i < lim) dst[16 * c16 + i] = __uint_as_float(o[i]);
+                for (int i = 0; i < 16; ++i)
+                  if (16 * c16 + i < lim) dst[16 * c16 + i] = (__uint_as_float(o[i]) * ws[i]) * kinv;
+              } else {
+#pragma unroll
+                for (int i = 0; i < 16; ++i)
+                  if (16 * c16 + i < lim) dst[16 * c16 + i] = __uint_as_float(o[i]);
+              }
             }
           } else {
             tmem_st16(tb + lane_base + o2col + 16 * c16, o);

@@ -64,7 +64,8 @@ size_t scratch_bound(const DeviceContext& ctx, int prec, int64_t m, int64_t n, i
   if (precision_is_tensor(prec)) {
     const int64_t p16 = (p + 15) / 16 * 16;
     const int64_t n_pad = (n + kRowTile - 1) / kRowTile * kRowTile;
-    bytes += align_up(static_cast<size_t>(p16) * n_pad * 2 * (precision_splits_weights(prec) ? 2 : 1), 256);
+    bytes += align_up(static_cast<size_t>(p16) * n_pad * 2 * (precision_splits_weights(prec) ? 2 : 1), 256) +
+             sizeof(uint32_t) * p16 * 2;   // column maxima and scales of split weights
     const int64_t units = ceil_div(m, kRowTile) * ceil_div(n, kRowTile);
     const int64_t G = std::min<int64_t>(ctx.num_sms, units);
     bytes += align_up(sizeof(float) * 2 * G * kRowTile * std::min<int64_t>(p16, 128), 256);

@@ -32,6 +32,8 @@
 #include <thread>
 #include <vector>
 
+#include <cuda_fp16.h>
+
 #include "internal.h"
 
 namespace itergp {
@@ -64,21 +66,50 @@ __device__ __forceinline__ float weight_value(const float* __restrict__ v, const
   return Q[static_cast<int64_t>(b) * n * C + r * C + c];
 }
 
-// Weights of a model, transposed BF16 hi (and lo) [kWeightRows][slab_rows].
+// Largest |weight| of each of a model's weight rows (columns of [v | Q]), as float bits,
+// into wmax [kWeightRows] (zeroed by the caller): a shared maximum per row and block, then
+// one atomicMax per row and block.
+__global__ void slab_wmax_kernel(const float* __restrict__ v, const float* __restrict__ Q, int64_t n, int C,
+                                 int B, uint32_t* __restrict__ wmax) {
+  __shared__ uint32_t m[kWeightRows];
+  for (int w = threadIdx.x; w < kWeightRows; w += blockDim.x) m[w] = 0u;
+  __syncthreads();
+  const int64_t total = n * kWeightRows;
+  for (int64_t e = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; e < total;
+       e += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const int w = static_cast<int>(e % kWeightRows);
+    atomicMax(&m[w], __float_as_uint(fabsf(weight_value(v, Q, n, C, B, e / kWeightRows, w))));
+  }
+  __syncthreads();
+  for (int w = threadIdx.x; w < kWeightRows; w += blockDim.x)
+    if (m[w] != 0u) atomicMax(&wmax[w], m[w]);
+}
+
+// Weights of a model, transposed [kWeightRows][slab_rows].  SPLIT (BF16X3, TF32): FP16 hi
+// and lo of 2^e_w times weight row w, e_w from its maximum (wmax) so that it lies in
+// [128, 256), scales 2^-e_w into wscale [kWeightRows]; otherwise one BF16 plane.
 template <bool SPLIT>
 __global__ void slab_weights_tc_kernel(const float* __restrict__ v, const float* __restrict__ Q,
                                        int64_t n, int C, int B, int64_t rows_pad, int64_t row0,
                                        int64_t slab_rows, __nv_bfloat16* __restrict__ hi,
-                                       __nv_bfloat16* __restrict__ lo) {
+                                       __nv_bfloat16* __restrict__ lo, const uint32_t* __restrict__ wmax,
+                                       float* __restrict__ wscale) {
   const int64_t total = rows_pad * kWeightRows;
   for (int64_t e = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; e < total;
        e += static_cast<int64_t>(gridDim.x) * blockDim.x) {
     const int w = static_cast<int>(e / rows_pad);
     const int64_t r = e % rows_pad;
     const float x = weight_value(v, Q, n, C, B, r, w);
-    const __nv_bfloat16 h = __float2bfloat16_rn(x);
-    hi[w * slab_rows + row0 + r] = h;
-    if (SPLIT) lo[w * slab_rows + row0 + r] = __float2bfloat16_rn(x - __bfloat162float(h));
+    if constexpr (SPLIT) {
+      const int ex = scale_exp_of_max(wmax[w]);
+      const float xs = x * pow2i(ex);
+      const __half h = __float2half_rn(xs);
+      reinterpret_cast<__half*>(hi)[w * slab_rows + row0 + r] = h;
+      reinterpret_cast<__half*>(lo)[w * slab_rows + row0 + r] = __float2half_rn(xs - __half2float(h));
+      if (r == 0) wscale[w] = pow2i(-ex);
+    } else {
+      hi[w * slab_rows + row0 + r] = __float2bfloat16_rn(x);
+    }
   }
 }
 
@@ -250,6 +281,8 @@ struct itergp_server {
   int bcap = 0;
   RowOperand rows_op;                 // problem side of the predict products (rows = slab)
   __nv_bfloat16 *w_hi = nullptr, *w_lo = nullptr;
+  uint32_t* w_max = nullptr;          // split weights: scratch of an install [kWeightRows]
+  float* w_scale = nullptr;           // split weights: per 128-row block [slab_rows / 128][kWeightRows]
   float* w32 = nullptr;
   RowBlocks blocks;
   // state (guarded by mu)
@@ -384,12 +417,19 @@ int itergp_server::install(itergp_model* m, const FitReq& r) {
     int rc = prepare_rows_into(cfg.precision, m->X, n, static_cast<int>(m->d), m->d, rows_pad, d_pad,
                                hi, lo, const_cast<float*>(rows_op.norms) + r.row0, ts, s);
     if (rc != ITERGP_OK) return rc;
-    if (precision_splits_weights(cfg.precision))
+    if (precision_splits_weights(cfg.precision)) {
+      ITERGP_CUDA_TRY(cudaMemsetAsync(w_max, 0, sizeof(uint32_t) * kWeightRows, s));
+      const unsigned blocks_max = static_cast<unsigned>(std::min<int64_t>(ceil_div(n * kWeightRows, 256), 1024));
+      slab_wmax_kernel<<<blocks_max, 256, 0, s>>>(m->v, m->Q, n, m->c, m->B, w_max), ::itergp::note_launch();
       slab_weights_tc_kernel<true><<<blocks_rows, 256, 0, s>>>(m->v, m->Q, n, m->c, m->B, rows_pad, r.row0,
-                                                              slab_rows, w_hi, w_lo), ::itergp::note_launch();
-    else
+                                                              slab_rows, w_hi, w_lo, w_max,
+                                                              w_scale + (r.row0 / 128) * kWeightRows),
+          ::itergp::note_launch();
+    } else {
       slab_weights_tc_kernel<false><<<blocks_rows, 256, 0, s>>>(m->v, m->Q, n, m->c, m->B, rows_pad, r.row0,
-                                                               slab_rows, w_hi, w_lo), ::itergp::note_launch();
+                                                               slab_rows, w_hi, w_lo, nullptr, nullptr),
+          ::itergp::note_launch();
+    }
     ITERGP_CUDA_TRY(cudaGetLastError());
   } else {
     float* x32 = const_cast<float*>(rows_op.X) + r.row0 * cfg.d_max;
@@ -657,10 +697,11 @@ void itergp_server::run_predicts(std::vector<PredReq*>& batch, const std::vector
     const Resident& r = models[i];
     float* yi = ybuf + o0[i] * kWeightRows;
     if (tc) {   // one pass over weight rows [0, 16 + C B): mean and variance columns together
-      pm[i] = TcProb{yi, kWeightRows, batch[i]->m, kMeanRows + r.c * r.B, 0, r.kp, nullptr};
+      const float* wsc = w_scale ? w_scale + (r.row0 / 128) * kWeightRows : nullptr;
+      pm[i] = TcProb{yi, kWeightRows, batch[i]->m, kMeanRows + r.c * r.B, 0, r.kp, nullptr, wsc};
     } else {    // FP32: a mean pass (columns 0..C-1) and a variance pass (columns 16..)
-      pm[i] = TcProb{yi, kWeightRows, batch[i]->m, r.c, 0, r.kp, nullptr};
-      pv[i] = TcProb{yi + kMeanRows, kWeightRows, batch[i]->m, r.c * r.B, 0, r.kp, nullptr};
+      pm[i] = TcProb{yi, kWeightRows, batch[i]->m, r.c, 0, r.kp, nullptr, nullptr};
+      pv[i] = TcProb{yi + kMeanRows, kWeightRows, batch[i]->m, r.c * r.B, 0, r.kp, nullptr, nullptr};
     }
     ds[i] = PredDesc{yi, out + oo[i], batch[i]->m, r.c, r.B, r.outputscale, 0};
   }
@@ -770,7 +811,7 @@ int itergp_server_create(const itergp_server_config* cfg, itergp_server** out) {
   const size_t o_norm = take(sizeof(float) * R);
   // split rows: one scale per 128-row block (R is a multiple of 128)
   const size_t o_tscale = precision_splits_rows(cfg->precision) ? take(sizeof(float) * (R / 128)) : 0;
-  size_t o_hi = 0, o_lo = 0, o_whi = 0, o_wlo = 0, o_x = 0, o_w = 0;
+  size_t o_hi = 0, o_lo = 0, o_whi = 0, o_wlo = 0, o_x = 0, o_w = 0, o_wmax = 0, o_wscale = 0;
   if (tc) {
     // TF32: one FP32 plane in the bytes of two BF16 planes
     const bool tf32 = precision_tf32_rows(cfg->precision);
@@ -778,6 +819,10 @@ int itergp_server_create(const itergp_server_config* cfg, itergp_server** out) {
     if (planes == 2 && !tf32) o_lo = take(static_cast<size_t>(R) * srv->d_pad * 2);
     o_whi = take(static_cast<size_t>(R) * kWeightRows * 2);
     if (wplanes == 2) o_wlo = take(static_cast<size_t>(R) * kWeightRows * 2);
+    if (wplanes == 2) {   // a model's weight scales live at its first 128-row block's entry
+      o_wmax = take(sizeof(uint32_t) * kWeightRows);
+      o_wscale = take(sizeof(float) * (R / 128) * kWeightRows);
+    }
   } else {
     o_x = take(sizeof(float) * R * cfg->d_max);
     o_w = take(sizeof(float) * R * kWeightRows);
@@ -835,6 +880,8 @@ int itergp_server_create(const itergp_server_config* cfg, itergp_server** out) {
     op.lo = precision_splits_rows(cfg->precision) ? reinterpret_cast<__nv_bfloat16*>(b + o_lo) : nullptr;
     srv->w_hi = reinterpret_cast<__nv_bfloat16*>(b + o_whi);
     srv->w_lo = wplanes == 2 ? reinterpret_cast<__nv_bfloat16*>(b + o_wlo) : nullptr;
+    srv->w_max = wplanes == 2 ? reinterpret_cast<uint32_t*>(b + o_wmax) : nullptr;
+    srv->w_scale = wplanes == 2 ? reinterpret_cast<float*>(b + o_wscale) : nullptr;
   } else {
     op.X = reinterpret_cast<float*>(b + o_x);
     op.ldX = cfg->d_max;

@@ -10,6 +10,8 @@
 #include <algorithm>
 #include <vector>
 
+#include <cuda_fp16.h>
+
 #include "internal.h"
 
 namespace itergp {
@@ -998,10 +1000,31 @@ struct SSource {
   int c;
   const int* active;
 };
-// Transposed, split BF16 weights [p16][arena rows] (tensor-core path).
+// Column maxima of every problem's weights (its N x C block), as float bits: per block a
+// shared maximum per column, then one atomicMax per column into cmax [nprob][p16] (zeroed
+// by the caller).
+__global__ void s_colmax_kernel(const SSource* __restrict__ tab, int p16, uint32_t* __restrict__ cmax) {
+  const SSource t = tab[blockIdx.y];
+  if (t.active != nullptr && *t.active == 0) return;
+  __shared__ uint32_t m[kMaxC];
+  for (int c = threadIdx.x; c < kMaxC; c += blockDim.x) m[c] = 0u;
+  __syncthreads();
+  const int64_t total = t.rows * t.c;
+  for (int64_t e = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; e < total;
+       e += static_cast<int64_t>(gridDim.x) * blockDim.x)
+    atomicMax(&m[e % t.c], __float_as_uint(fabsf(t.S[e])));
+  __syncthreads();
+  for (int c = threadIdx.x; c < t.c && c < p16; c += blockDim.x)
+    if (m[c] != 0u) atomicMax(&cmax[static_cast<int64_t>(blockIdx.y) * p16 + c], m[c]);
+}
+
+// Transposed weights [p16][arena rows] (tensor-core path).  SPLIT (BF16X3, TF32): FP16 hi
+// and lo of 2^e_c S[:, c] with e_c from the column maximum (see prep_s_kernel), scale
+// 2^-e_c into wsc [nprob][p16]; otherwise one BF16 plane.
 template <bool SPLIT>
 __global__ void s_stage_tc_kernel(const SSource* __restrict__ tab, int p16, int64_t arena_rows,
-                                  __nv_bfloat16* __restrict__ hi, __nv_bfloat16* __restrict__ lo) {
+                                  __nv_bfloat16* __restrict__ hi, __nv_bfloat16* __restrict__ lo,
+                                  const uint32_t* __restrict__ cmax, float* __restrict__ wsc) {
   const SSource t = tab[blockIdx.y];
   if (t.active != nullptr && *t.active == 0) return;
   const int64_t rows_pad = (t.rows + 127) / 128 * 128;
@@ -1011,9 +1034,16 @@ __global__ void s_stage_tc_kernel(const SSource* __restrict__ tab, int p16, int6
     const int cc = static_cast<int>(e / rows_pad);
     const int64_t r = e % rows_pad;
     const float x = (r < t.rows && cc < t.c) ? t.S[r * t.c + cc] : 0.f;
-    const __nv_bfloat16 h = __float2bfloat16_rn(x);
-    hi[cc * arena_rows + t.row0 + r] = h;
-    if (SPLIT) lo[cc * arena_rows + t.row0 + r] = __float2bfloat16_rn(x - __bfloat162float(h));
+    if constexpr (SPLIT) {
+      const int ex = cc < t.c ? scale_exp_of_max(cmax[static_cast<int64_t>(blockIdx.y) * p16 + cc]) : 0;
+      const float xs = x * pow2i(ex);
+      const __half h = __float2half_rn(xs);
+      reinterpret_cast<__half*>(hi)[cc * arena_rows + t.row0 + r] = h;
+      reinterpret_cast<__half*>(lo)[cc * arena_rows + t.row0 + r] = __float2half_rn(xs - __half2float(h));
+      if (r == 0) wsc[static_cast<int64_t>(blockIdx.y) * p16 + cc] = pow2i(-ex);
+    } else {
+      hi[cc * arena_rows + t.row0 + r] = __float2bfloat16_rn(x);
+    }
   }
 }
 // FP32 weights [arena rows][p_max] (SIMT path).
@@ -1040,6 +1070,8 @@ struct BatchProduct {
   KmvItemTables tab;
   const SSource* src = nullptr;      // device [nprob]
   __nv_bfloat16 *s_hi = nullptr, *s_lo = nullptr;
+  uint32_t* cmax = nullptr;          // split weights: column maxima [nprob][p16]
+  float* wsc = nullptr;              // split weights: their scales 2^-e [nprob][p16]
   float* s32 = nullptr;
   int64_t max_rows_pad = 0;
 };
@@ -1141,7 +1173,7 @@ int fit_run_batch(DeviceContext* ctx, const std::vector<FitProblem>& probs, cuda
   std::vector<SSource> src_host;
   std::vector<ArenaCopy> ac_host;
   size_t o_arena = 0, o_rows = 0, o_items = 0, o_begin = 0, o_tcp = 0, o_src = 0, o_ac = 0, o_shi = 0,
-         o_slo = 0, o_s32 = 0;
+         o_slo = 0, o_s32 = 0, o_cmx = 0, o_wsc = 0;
   if (batched) {
     bp.precision = prm.precision;
     bp.kind = prm.kernel.kind;
@@ -1175,6 +1207,8 @@ int fit_run_batch(DeviceContext* ctx, const std::vector<FitProblem>& probs, cuda
     if (precision_is_tensor(prm.precision)) {
       o_shi = take(sizeof(__nv_bfloat16) * bp.p16 * bp.arena_rows);
       o_slo = take(sizeof(__nv_bfloat16) * bp.p16 * bp.arena_rows);
+      o_cmx = take(sizeof(uint32_t) * np * bp.p16);
+      o_wsc = take(sizeof(float) * np * bp.p16);
     } else {
       o_s32 = take(sizeof(float) * bp.arena_rows * c_max);
     }
@@ -1237,7 +1271,8 @@ int fit_run_batch(DeviceContext* ctx, const std::vector<FitProblem>& probs, cuda
   std::vector<TcProb> tcp_lit;
   if (batched) {
     for (int i = 0; i < np; ++i) {
-      tcp_host.push_back(TcProb{pd[i].t_cur, pd[i].c, pd[i].n, pd[i].c, 0, probs[i].kp, &pd[i].st->active});
+      float* wsc_i = precision_is_tensor(prm.precision) ? reinterpret_cast<float*>(base + o_wsc) + i * bp.p16 : nullptr;
+      tcp_host.push_back(TcProb{pd[i].t_cur, pd[i].c, pd[i].n, pd[i].c, 0, probs[i].kp, &pd[i].st->active, wsc_i});
       src_host.push_back(SSource{pd[i].s_cur, pd[i].n, ac_host[i].row0, pd[i].c, &pd[i].st->active});
     }
     bp.arena.X = nullptr;
@@ -1266,6 +1301,8 @@ int fit_run_batch(DeviceContext* ctx, const std::vector<FitProblem>& probs, cuda
     if (precision_is_tensor(prm.precision)) {
       bp.s_hi = reinterpret_cast<__nv_bfloat16*>(base + o_shi);
       bp.s_lo = reinterpret_cast<__nv_bfloat16*>(base + o_slo);
+      bp.cmax = reinterpret_cast<uint32_t*>(base + o_cmx);
+      bp.wsc = reinterpret_cast<float*>(base + o_wsc);
     } else {
       bp.s32 = reinterpret_cast<float*>(base + o_s32);
     }
@@ -1287,10 +1324,15 @@ int fit_run_batch(DeviceContext* ctx, const std::vector<FitProblem>& probs, cuda
     if (!batched) return kprod0(pd[0].s_cur, pd[0].t_cur, &pd[0].st->active);
     dim3 grid(static_cast<unsigned>(std::min<int64_t>(ceil_div(bp.max_rows_pad * bp.p16, 256), 512)), np);
     if (precision_is_tensor(prm.precision)) {
-      if (precision_splits_weights(prm.precision))
-        s_stage_tc_kernel<true><<<grid, 256, 0, stream>>>(bp.src, bp.p16, bp.arena_rows, bp.s_hi, bp.s_lo), ::itergp::note_launch();
-      else
-        s_stage_tc_kernel<false><<<grid, 256, 0, stream>>>(bp.src, bp.p16, bp.arena_rows, bp.s_hi, bp.s_lo), ::itergp::note_launch();
+      if (precision_splits_weights(prm.precision)) {
+        ITERGP_CUDA_TRY(cudaMemsetAsync(bp.cmax, 0, sizeof(uint32_t) * np * bp.p16, stream));
+        s_colmax_kernel<<<grid, 256, 0, stream>>>(bp.src, bp.p16, bp.cmax), ::itergp::note_launch();
+        s_stage_tc_kernel<true><<<grid, 256, 0, stream>>>(bp.src, bp.p16, bp.arena_rows, bp.s_hi, bp.s_lo, bp.cmax,
+                                                         bp.wsc), ::itergp::note_launch();
+      } else {
+        s_stage_tc_kernel<false><<<grid, 256, 0, stream>>>(bp.src, bp.p16, bp.arena_rows, bp.s_hi, bp.s_lo, nullptr,
+                                                          nullptr), ::itergp::note_launch();
+      }
       ITERGP_CUDA_TRY(cudaGetLastError());
       return kmv_tc_items(ctx, bp.kind, bp.arena, bp.arena, bp.tab, bp.s_hi, bp.s_lo, bp.p16, 0,
                           bp.p16, stream);
