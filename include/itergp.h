@@ -421,7 +421,9 @@ int itergp_server_get_stats(itergp_server* server, itergp_server_stats* stats);
  * tile's A stays in shared memory; 3 or 5 stages of B tiles; not for TF32 rows, which
  * take two slices per 64 columns), and for the single-problem schedule the CTA-pair form
  * (clusters of two CTAs on two SMs sharing 256-row tiles through cta_group::2 MMAs of
- * M = 256; by default on wherever A is streamed).  The library
+ * M = 256; by default on wherever A is streamed), with chunks of 128 rows of B (MMA
+ * N = 128) or, where all of P fits one tile of <= 80 columns, wide chunks of 192 rows
+ * (MMA N = 192, three stages; the default there).  The library
  * keeps a process-wide table keyed by (precision, kernel kind, D padded to 64, P tile,
  * schedule); launches not in the table use 4 warps and the deepest ring that fits.
  *
@@ -432,11 +434,12 @@ int itergp_server_get_stats(itergp_server* server, itergp_server_stats* stats);
  * resident-A ring).  It waits for the stream.  Tensor-core precisions only.
  * itergp_tune_save / _load write / merge the table as text lines
  * "precision kind d_pad p_tile items epilogue_warps stages resident_a cta_pair"
- * (resident_a, cta_pair: 1, 0, or -1 = where possible; missing last columns read as -1);
- * _clear empties it. */
+ * (resident_a: 1, 0, or -1 = where possible; cta_pair: 1 pair form, 2 pair form with wide
+ * chunks, 0 off, -1 where possible; missing last columns read as -1); _clear empties it. */
 #define ITERGP_TUNE_MAX 20
 typedef struct {
-  int32_t epilogue_warps, stages, cta_pair;   /* stages < 0: resident-A ring; cta_pair 1: pair form */
+  int32_t epilogue_warps, stages, cta_pair;   /* stages < 0: resident-A ring; cta_pair 1: pair
+                                               form, 2: pair form with wide chunks */
   double ms;
 } itergp_tune_variant;
 typedef struct {

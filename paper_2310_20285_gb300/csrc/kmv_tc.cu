@@ -157,7 +157,8 @@ struct TcVariant {
   int epi = 4;
   int nstage = 0;
   int ares = -1;   // resident A (one K slice only): 1 on, 0 off, -1 on where possible
-  int pair = -1;   // CTA-pair form (single-problem streamed ring): 1 on, 0 off, -1 on where possible
+  int pair = -1;   // CTA-pair form (single-problem streamed ring): 1 on with 128-row chunks, 2 on
+                   // with wide (192-row) chunks, 0 off, -1 on where possible (wide for P <= 80)
 };
 
 std::mutex g_tune_mu;
@@ -178,12 +179,14 @@ TcVariant tc_variant(int prec, int kind, int d_pad, int p_pad, int items) {
 size_t smem_cap_bytes(const DeviceContext* ctx) { return std::min<size_t>(ctx->smem_optin, 232448) - 2048; }
 
 int stages_that_fit(const DeviceContext* ctx, int nt1, int nt2, int p_tile, int epi, int want,
-                    bool ares = false, bool pair = false) {
+                    bool ares = false, bool pair = false, int cw = BN) {
   const size_t smem_cap = smem_cap_bytes(ctx);
   const size_t a_bytes = ares ? static_cast<size_t>(nt1 == 3 ? 2 : 1) * BM * BK * 2 : 0;
-  const size_t stage = ares ? static_cast<size_t>(nt1 == 3 ? 2 : 1) * BN * BK * 2 : stage_bytes(nt1, pair);
-  const size_t fixed = (pair ? 1 : g_bufs(p_tile)) * s_buf_bytes(nt2, p_tile, pair) + smem_extra(epi) + a_bytes;
+  const size_t stage = ares ? static_cast<size_t>(nt1 == 3 ? 2 : 1) * BN * BK * 2 : stage_bytes(nt1, pair, cw);
+  const size_t fixed = (pair ? 1 : g_bufs(p_tile)) * s_buf_bytes(nt2, p_tile, pair, cw) + smem_extra(epi, cw) + a_bytes;
   const int fit = static_cast<int>((smem_cap > fixed ? smem_cap - fixed : 0) / stage);
+  if (cw != BN)   // wide chunks: P tiles <= 80 (TMEM), three streamed stages only
+    return (pair && !ares && p_tile <= 80 && fit >= 3 && (want <= 0 || want == 3)) ? 3 : 0;
   int ns = ares ? (fit >= 5 ? 5 : fit >= 3 ? 3 : 0) : (fit >= 4 ? 4 : fit >= 3 ? 3 : fit >= 2 ? 2 : 0);
   if (want >= 2 && ns > want) ns = ares ? (want >= 5 ? 5 : want >= 3 ? 3 : 0) : want;
   return ns;
@@ -194,8 +197,9 @@ int tc_nt1(int prec) { return precision_tf32_rows(prec) ? 2 : precision_splits_r
 // Tensor maps of the row operands (maps[1] and [3] repeat the hi planes when rows are not
 // split).  Boxes: 128 rows of A; 128 rows of B, or 64 in the pair form (each CTA of a pair
 // stages half of every chunk).
-bool encode_rows(CUtensorMap* maps, const RowOperand& A, const RowOperand& B, int nt1, bool pair = false) {
-  const uint32_t bb = static_cast<uint32_t>(b_rows_cta(pair));
+bool encode_rows(CUtensorMap* maps, const RowOperand& A, const RowOperand& B, int nt1, bool pair = false,
+                 int cw = BN) {
+  const uint32_t bb = static_cast<uint32_t>(b_rows_cta(pair, cw));
   if (nt1 == 2)
     return encode_f32_sw128(&maps[0], A.hi, A.rows_pad, A.d_pad, A.d_pad, BM) &&
            encode_f32_sw128(&maps[1], A.hi, A.rows_pad, A.d_pad, A.d_pad, BM) &&
@@ -210,32 +214,35 @@ bool encode_rows(CUtensorMap* maps, const RowOperand& A, const RowOperand& B, in
 }
 
 // Weight-tile slots with nstage stages (see stages_that_fit).
-int weight_slots(const DeviceContext* ctx, int nt1, int nt2, int p_tile, int epi, int nstage, bool pair) {
+int weight_slots(const DeviceContext* ctx, int nt1, int nt2, int p_tile, int epi, int nstage, bool pair,
+                 int cw = BN) {
   if (!pair) return g_bufs(p_tile);
-  const size_t used = nstage * static_cast<size_t>(stage_bytes(nt1, true)) + smem_extra(epi);
+  const size_t used = nstage * static_cast<size_t>(stage_bytes(nt1, true, cw)) + smem_extra(epi, cw);
   const size_t cap = smem_cap_bytes(ctx);
-  const size_t fit = cap > used ? (cap - used) / s_buf_bytes(nt2, p_tile, true) : 0;
-  return static_cast<int>(std::max<size_t>(1, std::min<size_t>(fit, g_bufs(p_tile))));
+  const size_t fit = cap > used ? (cap - used) / s_buf_bytes(nt2, p_tile, true, cw) : 0;
+  const int bufs = cw == BN ? g_bufs(p_tile) : 2;   // wide chunks: two G buffers
+  return static_cast<int>(std::max<size_t>(1, std::min<size_t>(fit, bufs)));
 }
 
-size_t tc_smem_bytes(int nt1, int nt2, int p_pad, int epi, int nstage, bool ares, int slots, bool pair = false) {
+size_t tc_smem_bytes(int nt1, int nt2, int p_pad, int epi, int nstage, bool ares, int slots, bool pair = false,
+                     int cw = BN) {
   const size_t a_bytes = ares ? static_cast<size_t>(nt1 == 3 ? 2 : 1) * BM * BK * 2 : 0;
-  const size_t stage = ares ? static_cast<size_t>(nt1 == 3 ? 2 : 1) * BN * BK * 2 : stage_bytes(nt1, pair);
-  return nstage * stage + a_bytes + slots * s_buf_bytes(nt2, p_pad, pair) + smem_extra(epi);
+  const size_t stage = ares ? static_cast<size_t>(nt1 == 3 ? 2 : 1) * BN * BK * 2 : stage_bytes(nt1, pair, cw);
+  return nstage * stage + a_bytes + slots * s_buf_bytes(nt2, p_pad, pair, cw) + smem_extra(epi, cw);
 }
 
 // Pairs of the pair form that can be resident at once with this configuration (cached per
 // configuration: the answer depends on the GPU's GPC layout, not on the problem).
-int pair_clusters(int kind, int prec, int nstage, int epi, size_t smem) {
+int pair_clusters(int kind, int prec, int nstage, int epi, size_t smem, int cw = BN) {
   static std::mutex mu;
-  static std::map<std::tuple<int, int, int, int, size_t>, int> cache;
-  const auto key = std::make_tuple(kind, prec, nstage, epi, smem);
+  static std::map<std::tuple<int, int, int, int, size_t, int>, int> cache;
+  const auto key = std::make_tuple(kind, prec, nstage, epi, smem, cw);
   {
     std::lock_guard<std::mutex> lk(mu);
     auto it = cache.find(key);
     if (it != cache.end()) return it->second;
   }
-  const int n = pair_max_clusters(kind, prec, nstage, epi, smem);
+  const int n = pair_max_clusters(kind, prec, nstage, epi, smem, cw);
   std::lock_guard<std::mutex> lk(mu);
   cache[key] = n;
   return n;
@@ -282,6 +289,7 @@ int kmv_tc_items(DeviceContext* ctx, int kind, const RowOperand& A, const RowOpe
     a.ub = B.tscale;
     a.wait_ns = thread_wait_limit();
     a.a_rows_pad = A.rows_pad;
+    a.b_rows_pad = B.rows_pad;
     a.nk = B.d_pad / slice_elems(nt1);
     a.p_pad = pp;
     a.p_valid = pp;
@@ -333,9 +341,27 @@ int kmv_tc(DeviceContext* ctx, const KParams& kp, const RowOperand& A, const Row
 
   // The CTA-pair form (streamed ring) replaces the one-CTA form unless the variant says
   // otherwise: by default wherever A is not kept resident and there is a full 256-row tile.
+  // Wide chunks (192 rows of B) where the whole P fits one tile of <= 80 columns.
   bool pair = false;
+  int cw = BN;
   int64_t pair_cap = 0;
-  if ((var.pair == 1 || (var.pair == -1 && !ares)) && A.rows >= 2 * BM) {
+  if ((var.pair == 2 || (var.pair == -1 && !ares)) && A.rows >= 2 * BM && p16 <= 80) {
+    const int pt = static_cast<int>(p16);
+    const int ns = stages_that_fit(ctx, nt1, nt2, pt, var.epi, var.nstage, false, true, kWideCW);
+    if (ns == 3) {
+      const int ws = weight_slots(ctx, nt1, nt2, pt, var.epi, ns, true, kWideCW);
+      pair_cap = pair_clusters(kp.kind, prec, ns, var.epi,
+                               tc_smem_bytes(nt1, nt2, pt, var.epi, ns, false, ws, true, kWideCW), kWideCW);
+      if (pair_cap >= 1) {
+        pair = true;
+        cw = kWideCW;
+        ares = false;
+        p_tile = pt;
+        nstage = ns;
+      }
+    }
+  }
+  if (!pair && (var.pair == 1 || (var.pair == -1 && !ares)) && A.rows >= 2 * BM) {
     int pt = static_cast<int>(std::min<int64_t>(p16, 128)), ns = 0;
     for (; pt >= 16; pt -= 16)
       if ((ns = stages_that_fit(ctx, nt1, nt2, pt, var.epi, var.nstage, false, true)) >= 2) break;
@@ -364,12 +390,12 @@ int kmv_tc(DeviceContext* ctx, const KParams& kp, const RowOperand& A, const Row
   ITERGP_CUDA_TRY(stage_weights(S, ldS, B.rows, p, n_pad, p16, s_hi, s_lo, s_cmax, s_scale, nt2 == 3, active, stream));
 
   CUtensorMap maps[6];
-  bool ok = encode_rows(maps, A, B, nt1, pair);
+  bool ok = encode_rows(maps, A, B, nt1, pair, cw);
   if (!ok) return ITERGP_ECUDA;
 
   const int tm = tile_rows(pair);
   const int64_t row_tiles = ceil_div(A.rows, tm);
-  const int64_t chunks = ceil_div(B.rows, BN);
+  const int64_t chunks = ceil_div(B.rows, static_cast<int64_t>(cw));
   const int64_t units = row_tiles * chunks;
   // persistent grid: one CTA per SM, or as many pairs as can be resident together
   const int64_t G = std::min<int64_t>(pair ? pair_cap : ctx->num_sms, units);
@@ -393,6 +419,7 @@ int kmv_tc(DeviceContext* ctx, const KParams& kp, const RowOperand& A, const Row
     a.wait_ns = thread_wait_limit();
     a.m = A.rows;
     a.a_rows_pad = A.rows_pad;
+    a.b_rows_pad = B.rows_pad;
     a.row_tiles = row_tiles;
     a.chunks = static_cast<int>(chunks);
     a.nk = A.d_pad / slice_elems(nt1);
@@ -409,12 +436,12 @@ int kmv_tc(DeviceContext* ctx, const KParams& kp, const RowOperand& A, const Row
     a.items = nullptr;
     a.item_begin = nullptr;
     a.probs = nullptr;
-    a.w_slots = weight_slots(ctx, nt1, nt2, pp, var.epi, nstage, pair);
+    a.w_slots = weight_slots(ctx, nt1, nt2, pp, var.epi, nstage, pair, cw);
     a.diag = A.hi == B.hi && A.norms == B.norms && A.rows == B.rows;
-    const size_t smem_t = tc_smem_bytes(nt1, nt2, pp, var.epi, nstage, ares, a.w_slots, pair);
+    const size_t smem_t = tc_smem_bytes(nt1, nt2, pp, var.epi, nstage, ares, a.w_slots, pair, cw);
     cudaError_t e;
     if (pair)
-      e = launch_pair_form(kp.kind, prec, nstage, var.epi, (int)G, smem_t, stream, maps, a);
+      e = launch_pair_form(kp.kind, prec, nstage, var.epi, (int)G, smem_t, stream, maps, a, cw);
     else
       e = kp.kind == ITERGP_RBF
               ? launch_prec<ITERGP_RBF, false>(prec, nstage, ares, var.epi, (int)G, smem_t, stream, maps, a)
@@ -483,24 +510,28 @@ int kmv_tc_tune(DeviceContext* ctx, const KParams& kp, const RowOperand& X, cons
   ITERGP_CUDA_TRY(cudaEventCreate(&e1));
   int n = 0, rc = ITERGP_OK;
   *best = -1;
-  // forms: 0 one CTA, streamed ring; 1 one CTA, resident A; 2 CTA pairs (single schedule)
-  for (int form : {0, 1, 2}) for (int epi : {4, 8}) {
+  // forms: 0 one CTA, streamed ring; 1 one CTA, resident A; 2 CTA pairs (single schedule);
+  // 3 CTA pairs with wide chunks (P <= 80)
+  for (int form : {0, 1, 2, 3}) for (int epi : {4, 8}) {
     const int ares = form == 1 ? 1 : 0;
-    const bool pair = form == 2;
+    const bool pair = form >= 2;
+    const int cw = form == 3 ? kWideCW : BN;
     if (ares && (X.d_pad != BK || nt1 == 2)) continue;
     if (pair && (items || X.rows < 2 * BM)) continue;
+    if (form == 3 && p16 > 80) continue;
     // the P tile the launchers use with this variant: the widest that fits its ring
     int p_tile = p16;
     const int min_ns = ares ? 3 : 2;
-    while (p_tile > 16 && stages_that_fit(ctx, nt1, nt2, p_tile, epi, 0, ares != 0, pair) < min_ns) p_tile -= 16;
+    while (p_tile > 16 && stages_that_fit(ctx, nt1, nt2, p_tile, epi, 0, ares != 0, pair, cw) < min_ns) p_tile -= 16;
     for (int ns : {2, 3, 4, 5}) {
       if (n >= cap) break;
-      if (stages_that_fit(ctx, nt1, nt2, p_tile, epi, ns, ares != 0, pair) != ns) continue;
+      if (stages_that_fit(ctx, nt1, nt2, p_tile, epi, ns, ares != 0, pair, cw) != ns) continue;
       if (pair && pair_clusters(kp.kind, prec, ns, epi,
                                 tc_smem_bytes(nt1, nt2, p_tile, epi, ns, false,
-                                              weight_slots(ctx, nt1, nt2, p_tile, epi, ns, true), true)) < 1)
+                                              weight_slots(ctx, nt1, nt2, p_tile, epi, ns, true, cw), true, cw),
+                                cw) < 1)
         continue;
-      const TcVariant v{epi, ns, ares, pair ? 1 : 0};
+      const TcVariant v{epi, ns, ares, form == 3 ? 2 : pair ? 1 : 0};
       t_forced = &v;
       auto run = [&] {
         return items ? kmv_tc_items(ctx, kp.kind, X, X, tab, s_hi, s_lo, p16, 0, p16, stream)
@@ -519,7 +550,7 @@ int kmv_tc_tune(DeviceContext* ctx, const KParams& kp, const RowOperand& X, cons
       if (rc != ITERGP_OK) break;
       epi_out[n] = epi;
       ns_out[n] = ares ? -ns : ns;   // negative: resident-A ring
-      pair_out[n] = pair ? 1 : 0;
+      pair_out[n] = form == 3 ? 2 : pair ? 1 : 0;
       ms_out[n] = ms / reps;
       if (*best < 0 || ms_out[n] < ms_out[*best]) *best = n;
       ++n;
@@ -570,7 +601,7 @@ extern "C" int itergp_tune_load(const char* path) {
     const int got = std::sscanf(line, "%d %d %d %d %d %d %d %d %d", &a[0], &a[1], &a[2], &a[3], &a[4],
                                 &a[5], &a[6], &a[7], &a[8]);
     if (got < 7 || (a[5] != 4 && a[5] != 8) || a[6] < 0 || a[6] > 5 || a[7] < -1 || a[7] > 1 || a[8] < -1 ||
-        a[8] > 1) {
+        a[8] > 2) {
       rc = ITERGP_EINVAL;
       continue;
     }

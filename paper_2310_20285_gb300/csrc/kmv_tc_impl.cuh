@@ -20,9 +20,15 @@ namespace tcimpl {
 constexpr int BM = 128;   // rows of A per CTA (MMA M of the one-CTA form; half the pair's M = 256)
 constexpr int BN = 128;   // rows of B per chunk (MMA N of the distance GEMM, K of the product)
 constexpr int BK = 64;    // D slice per stage (one 128-byte swizzle row of BF16)
+// The wide pair form takes chunks of 192 rows of B (MMA N = 192): each SM's share of the
+// MMA then reads 10 KB of shared memory per 1.5 128 x 128 x 16 blocks instead of 8 KB per
+// block, and its ring refills 56 KB per 18 blocks instead of 48 KB per 12, which lets the
+// tensor pipe run at its issue rate while TMA refills the ring (at N = 128 the shared-memory
+// traffic of the operands and the refills holds it near three quarters of it).
+constexpr int kWideCW = 192;
 // Rows of A per tile and rows of each B chunk staged per CTA, in either form.
 __host__ __device__ constexpr int tile_rows(bool pair) { return pair ? 2 * BM : BM; }
-__host__ __device__ constexpr int b_rows_cta(bool pair) { return pair ? BN / 2 : BN; }
+__host__ __device__ constexpr int b_rows_cta(bool pair, int cw = BN) { return pair ? cw / 2 : cw; }
 // Row operand forms (NT1): 1 BF16 rows, 3 split BF16 rows (hi, lo), 2 TF32 rows (FP32
 // storage, 32 values per 128-byte swizzle row, kind::tf32 MMAs of K = 8).  A stage holds
 // one 128-byte row per tile row in every form, so the ring layout is the same.
@@ -40,6 +46,8 @@ constexpr uint32_t kO2Col = 384;   // FP32 running sum of flushed O (IEEE round-
 // G 3 x 128 columns, O at 384 and O2 at 384 + P.
 __host__ __device__ constexpr int g_bufs(int p_pad) { return p_pad <= 48 ? 3 : 2; }
 constexpr int kFlushChunks = 4;    // O is flushed into O2 at least every 4 chunks (512 rows)
+// Chunks per flush group for a chunk width: 4 x 128 or 3 x 192 rows of B.
+__host__ __device__ constexpr int flush_chunks(int cw) { return cw == BN ? kFlushChunks : 3; }
 // Waits for work of the kernel's own roles are bounded by TcArgs::wait_ns; the drains after
 // an abort (copies and MMAs already in flight) by a fixed 4 s.
 constexpr uint64_t kDrainLimitNs = 4000000000ull;
@@ -50,6 +58,7 @@ struct TcArgs {
   const float* ua;        // split rows: tile scales of A [A.rows_pad / 128] (else unused)
   const float* ub;        // split rows: tile scales of B [B.rows_pad / 128] (else unused)
   int64_t m;              // valid rows of A
+  int64_t b_rows_pad;     // rows of B's norms and tile scales (a wide chunk may pass the end)
   int64_t a_rows_pad;     // rows of A's prepared planes and norms (rows beyond read as zero)
   int64_t row_tiles;      // R (tiles of tile_rows(pair) rows)
   int chunks;             // J
@@ -75,19 +84,22 @@ struct TcArgs {
   const TcProb* probs;
 };
 
-__host__ __device__ constexpr uint32_t stage_bytes(int nt1, bool pair = false) {
-  return (nt1 == 3 ? 2u : 1u) * (BM * BK * 2u) + (nt1 == 3 ? 2u : 1u) * (b_rows_cta(pair) * BK * 2u);
+__host__ __device__ constexpr uint32_t stage_bytes(int nt1, bool pair = false, int cw = BN) {
+  return (nt1 == 3 ? 2u : 1u) * (BM * BK * 2u) + (nt1 == 3 ? 2u : 1u) * (b_rows_cta(pair, cw) * BK * 2u);
 }
 // One 64-row-wide box of the chunk's transposed weights: P rows (the pair form stages
 // P / 2 of them per CTA, its half of the product's N) x 128 bytes.
 __host__ __device__ constexpr uint32_t s_box_bytes(int p_pad, bool pair = false) {
   return static_cast<uint32_t>(pair ? p_pad / 2 : p_pad) * 128u;
 }
-__host__ __device__ constexpr uint32_t s_buf_bytes(int nt2, int p_pad, bool pair = false) {
-  return 2u * s_box_bytes(p_pad, pair) * (nt2 == 3 ? 2u : 1u);
+// A weight tile: the chunk's cw / 64 boxes per plane.
+__host__ __device__ constexpr uint32_t s_buf_bytes(int nt2, int p_pad, bool pair = false, int cw = BN) {
+  return static_cast<uint32_t>(cw / 64) * s_box_bytes(p_pad, pair) * (nt2 == 3 ? 2u : 1u);
 }
-// alignment slack + per-epilogue-warp staging of 128 column norms
-__host__ __device__ constexpr uint32_t smem_extra(int epi) { return 1024u + static_cast<uint32_t>(epi) * 512u; }
+// alignment slack + per-epilogue-warp staging of one chunk's column norms
+__host__ __device__ constexpr uint32_t smem_extra(int epi, int cw = BN) {
+  return 1024u + static_cast<uint32_t>(epi) * static_cast<uint32_t>(cw) * 4u;
+}
 
 // Per-CTA sequence of (row tile, chunk) steps of the partition described above.
 struct Schedule {
@@ -135,6 +147,7 @@ struct Walker {
   int64_t row = 0, lock = 0;                      // single problem: row tile, fw * J
   int32_t it_a_row = 0, it_b_row0 = 0, it_chunks = 0;   // item mode: the current item
   int32_t rows_per_tile = BM, row_off = 0;        // single problem: tile height, this CTA's rows in it
+  int32_t cw = BN;                                // rows of B per chunk
 
   __device__ bool item_active(int32_t kk) const {
     const int* a = probs[items[kk].prob].active;
@@ -156,11 +169,13 @@ struct Walker {
   }
   // G CTAs (or pairs) and this one's index g; pair form: tiles of 256 rows, of which the
   // CTA of rank h owns rows [128 h, 128 h + 128)
-  __device__ void init(const TcArgs& a, int64_t G, int64_t g, int32_t tile_h = BM, int32_t off = 0) {
+  __device__ void init(const TcArgs& a, int64_t G, int64_t g, int32_t tile_h = BM, int32_t off = 0,
+                       int32_t chunk_w = BN) {
     items = a.items;
     probs = a.probs;
     rows_per_tile = tile_h;
     row_off = off;
+    cw = chunk_w;
     t = 0;
     if (items == nullptr) {
       sch.init(a.row_tiles, a.chunks, G, g);
@@ -183,7 +198,7 @@ struct Walker {
     StepInfo s;
     if (items == nullptr) {
       s.a_row = static_cast<int32_t>(row * rows_per_tile) + row_off;
-      s.b_row = c * BN;
+      s.b_row = c * cw;
       s.c = c;
       // a row run starts at chunk 0, at step 0 and where the tail begins; it ends at the
       // row's last chunk and at the CTA's last step
@@ -192,7 +207,7 @@ struct Walker {
       s.item = -1;
     } else {
       s.a_row = it_a_row;
-      s.b_row = it_b_row0 + c * BN;
+      s.b_row = it_b_row0 + c * cw;
       s.c = c;
       s.first = (c == 0);
       s.last = (c == it_chunks - 1);
@@ -216,12 +231,13 @@ struct Walker {
   }
 };
 
-// The pair form's launcher (kmv_tc2.cu): grid_pairs clusters of two CTAs.
+// The pair form's launcher (kmv_tc2.cu): grid_pairs clusters of two CTAs; chunks of cw
+// (128, or kWideCW) rows of B.
 cudaError_t launch_pair_form(int kind, int prec, int nstage, int epi, int grid_pairs, size_t smem, cudaStream_t st,
-                             const CUtensorMap* maps, const TcArgs& a);
+                             const CUtensorMap* maps, const TcArgs& a, int cw = BN);
 // Clusters of two CTAs of the pair form with this configuration that can be resident at
 // once (the SM pairs available within the GPCs); 0 if it cannot launch.
-int pair_max_clusters(int kind, int prec, int nstage, int epi, size_t smem);
+int pair_max_clusters(int kind, int prec, int nstage, int epi, size_t smem, int cw = BN);
 
 namespace {
 
@@ -267,18 +283,18 @@ __device__ __forceinline__ void commit_x(uint64_t* bar) {
 // dozen cycles.
 // In the pair form a stage holds this CTA's 128 rows of A and 64 rows of B; the same
 // descriptors address the other CTA's stage, and the MMA's M = 256.
-template <int NT1, int NSTAGE, bool ARES, bool PAIR>
+template <int NT1, int NSTAGE, bool ARES, bool PAIR, int CW>
 __device__ __noinline__ int issue_gemm1(uint32_t gt, int nk, uint64_t dStage0, uint64_t dAres, uint64_t* full_bar,
                                         uint64_t* empty_bar, volatile int* ab, uint32_t idesc1, int pos,
                                         uint64_t lim) {
-  constexpr uint32_t A_PART = BM * BK * 2, B_PART = b_rows_cta(PAIR) * BK * 2;
-  constexpr uint32_t SB = ARES ? (NT1 == 3 ? 2u : 1u) * B_PART : stage_bytes(NT1, PAIR);
+  constexpr uint32_t A_PART = BM * BK * 2, B_PART = b_rows_cta(PAIR, CW) * BK * 2;
+  constexpr uint32_t SB = ARES ? (NT1 == 3 ? 2u : 1u) * B_PART : stage_bytes(NT1, PAIR, CW);
   int stage = pos & 0xFF;
   uint32_t phase = static_cast<uint32_t>(pos >> 8);
   for (int ks = 0; ks < nk; ++ks) {
     // operands arrive by TMA with completion on the mbarrier (async proxy on both sides):
     // no tcgen05 fence is needed here
-    if (!mbar_wait(&full_bar[stage], phase, ab, lim)) return -1;
+    if (!mbar_try_wait(&full_bar[stage], phase) && !mbar_wait_slow(&full_bar[stage], phase, ab, lim)) return -1;
     const uint64_t dSt = dStage0 + static_cast<uint64_t>(stage) * (SB >> 4);
     const uint64_t dAh = ARES ? dAres : dSt;
     const uint64_t dBh = ARES ? dSt : dSt + ((NT1 == 3 ? 2 : 1) * A_PART >> 4);
@@ -319,26 +335,26 @@ __device__ __noinline__ int issue_gemm1(uint32_t gt, int nk, uint64_t dStage0, u
 // group, hands O to the epilogue (ofull).
 // In the pair form P comes from both CTAs' TMEM and each CTA holds half of the weight
 // tile's P columns (the MMA's N).
-template <int NT2, bool PAIR>
+template <int NT2, bool PAIR, int CW>
 __device__ __noinline__ bool issue_gemm2(uint32_t tb, uint32_t a_col0, uint32_t o_col, uint32_t par, uint32_t spar,
                                          bool first, bool last, uint64_t* pfull_b, uint64_t* sfull_b, uint64_t* sempty_b,
                                          uint64_t* ofull_b, volatile int* ab, uint64_t dS0, uint64_t sbox16,
                                          uint32_t idesc2, uint64_t lim) {
   if constexpr (PAIR) {   // both CTAs' epilogue warps arrive on pfull
-    if (!mbar_try_wait_cluster(pfull_b, par) && !mbar_wait_cluster(pfull_b, par, ab, lim)) return false;
+    if (!mbar_try_wait_cluster(pfull_b, par) && !mbar_wait_cluster_slow(pfull_b, par, ab, lim)) return false;
   } else {
-    if (!mbar_try_wait(pfull_b, par) && !mbar_wait(pfull_b, par, ab, lim)) return false;
+    if (!mbar_try_wait(pfull_b, par) && !mbar_wait_slow(pfull_b, par, ab, lim)) return false;
   }
-  if (!mbar_try_wait(sfull_b, spar) && !mbar_wait(sfull_b, spar, ab, lim)) return false;
+  if (!mbar_try_wait(sfull_b, spar) && !mbar_wait_slow(sfull_b, spar, ab, lim)) return false;
   tc_fence_after();   // P was written by the epilogue's tcgen05.st
 #pragma unroll
-  for (int ks2 = 0; ks2 < BN / 16; ++ks2) {
+  for (int ks2 = 0; ks2 < CW / 16; ++ks2) {
     const int grp = ks2 >> 1, h = ks2 & 1;
     const uint32_t a_hi = tb + a_col0 + static_cast<uint32_t>(32 * grp + 8 * h);
     const uint64_t dSh = dS0 + static_cast<uint64_t>(ks2 >> 2) * sbox16 + static_cast<uint64_t>((ks2 & 3) * 2);
     mma_ts_x<PAIR>(tb + o_col, a_hi, dSh, idesc2, (first && ks2 == 0) ? 0u : 1u);
-    if (NT2 == 3) {
-      mma_ts_x<PAIR>(tb + o_col, a_hi, dSh + 2 * sbox16, idesc2, 1u);
+    if (NT2 == 3) {   // the lo plane's boxes follow the hi plane's CW / 64
+      mma_ts_x<PAIR>(tb + o_col, a_hi, dSh + (CW / 64) * sbox16, idesc2, 1u);
       mma_ts_x<PAIR>(tb + o_col, a_hi + 16, dSh, idesc2, 1u);
     }
   }
@@ -353,20 +369,25 @@ __device__ __noinline__ bool issue_gemm2(uint32_t tb, uint32_t a_col0, uint32_t 
 // G below counts pairs, g is the pair and h the CTA's rank in it.  Every early return is
 // taken by both CTAs of a pair (the conditions read the same values), so both always
 // meet at the cluster barriers.
-template <int KIND, int NT1, int NT2, int NSTAGE, int EPI, bool ARES, bool PAIR>
+template <int KIND, int NT1, int NT2, int NSTAGE, int EPI, bool ARES, bool PAIR, int CW = BN>
 __global__ void __launch_bounds__(tc_threads(EPI), 1)
 kmv_tc_kernel(const __grid_constant__ CUtensorMap mAh, const __grid_constant__ CUtensorMap mAl,
               const __grid_constant__ CUtensorMap mBh, const __grid_constant__ CUtensorMap mBl,
               const __grid_constant__ CUtensorMap mSh, const __grid_constant__ CUtensorMap mSl,
               const TcArgs args) {
   static_assert(!(PAIR && ARES), "the pair form streams A");
+  static_assert(CW == BN || (CW == kWideCW && PAIR), "wide chunks are a pair-form layout");
+  // Wide chunks: two G buffers of 192 columns and O at 384 (P tiles <= 80); O2, the flushed
+  // running sum, lives in the epilogue threads' registers instead of TMEM.
+  constexpr bool O2REG = CW != BN;
+  constexpr int FC = flush_chunks(CW);
   if (args.active != nullptr && *args.active == 0) return;
   if (PAIR && args.items != nullptr) return;   // the pair form has no item mode
   const uint32_t h = PAIR ? cluster_rank() : 0u;
   const bool leader = h == 0;   // the pair's MMA issuer and owner of its shared barriers
   const int64_t G = PAIR ? gridDim.x / 2 : gridDim.x, g = PAIR ? blockIdx.x / 2 : blockIdx.x;
   Walker walk0;
-  walk0.init(args, G, g, tile_rows(PAIR), static_cast<int32_t>(BM * h));
+  walk0.init(args, G, g, tile_rows(PAIR), static_cast<int32_t>(BM * h), CW);
   const int64_t T = walk0.total();
   if (T <= 0) return;
   const Schedule& sch = walk0.sch;
@@ -374,18 +395,18 @@ kmv_tc_kernel(const __grid_constant__ CUtensorMap mAh, const __grid_constant__ C
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
                                              ~static_cast<uintptr_t>(1023));
-  constexpr uint32_t A_PART = BM * BK * 2, B_PART = b_rows_cta(PAIR) * BK * 2;
+  constexpr uint32_t A_PART = BM * BK * 2, B_PART = b_rows_cta(PAIR, CW) * BK * 2;
   constexpr uint32_t A_BYTES = (NT1 == 3 ? 2u : 1u) * A_PART;   // resident A (ARES)
-  constexpr uint32_t SB = ARES ? (NT1 == 3 ? 2u : 1u) * B_PART : stage_bytes(NT1, PAIR);
-  const int ng = g_bufs(args.p_pad);                     // G buffers
+  constexpr uint32_t SB = ARES ? (NT1 == 3 ? 2u : 1u) * B_PART : stage_bytes(NT1, PAIR, CW);
+  const int ng = O2REG ? 2 : g_bufs(args.p_pad);         // G buffers
   const int nsl = args.w_slots;                          // weight-tile slots (1 .. 3)
-  const uint32_t ocol = ng == 3 ? 384u : kOCol;
-  const uint32_t o2col = ng == 3 ? 384u + static_cast<uint32_t>(args.p_pad) : kO2Col;
+  const uint32_t ocol = O2REG ? 2u * CW : ng == 3 ? 384u : kOCol;
+  const uint32_t o2col = ng == 3 ? 384u + static_cast<uint32_t>(args.p_pad) : kO2Col;   // TMEM O2 forms
   const uint32_t SBOX = s_box_bytes(args.p_pad, PAIR);
-  const uint32_t SBUF = s_buf_bytes(NT2, args.p_pad, PAIR);
+  const uint32_t SBUF = s_buf_bytes(NT2, args.p_pad, PAIR, CW);
   uint8_t* a_region = smem + NSTAGE * SB;                        // ARES only
   uint8_t* s_region = a_region + (ARES ? A_BYTES : 0u);
-  float* nb_all = reinterpret_cast<float*>(s_region + nsl * SBUF);   // [EPI warps][128]
+  float* nb_all = reinterpret_cast<float*>(s_region + nsl * SBUF);   // [EPI warps][CW]
 
   __shared__ __align__(8) uint64_t full_bar[NSTAGE], empty_bar[NSTAGE];
   __shared__ __align__(8) uint64_t gfull[3], pfull[3], sfull[3], sempty[3], ofull, oempty, drain;
@@ -451,7 +472,7 @@ kmv_tc_kernel(const __grid_constant__ CUtensorMap mAh, const __grid_constant__ C
         const StepInfo st = wk.cur();
         const int32_t a_y = st.a_row;
         // this CTA's rows of the B chunk (the pair form stages half of them per CTA)
-        const int32_t b_y = st.b_row + (PAIR ? b_rows_cta(true) * static_cast<int32_t>(h) : 0);
+        const int32_t b_y = st.b_row + (PAIR ? b_rows_cta(true, CW) * static_cast<int32_t>(h) : 0);
         if (ARES) {
           if (st.first) {
             // a new row segment: reload A once the previous segment's MMAs are done with it
@@ -546,11 +567,10 @@ kmv_tc_kernel(const __grid_constant__ CUtensorMap mAh, const __grid_constant__ C
         if constexpr (PAIR) {   // this CTA's half of the tile's P rows (the MMA's N)
           const uint32_t fb = lead(&sfull[sb]);
           const int32_t srow = args.s_row0 + static_cast<int32_t>(h) * (args.p_pad / 2);
-          tma_load_2d_pair(sbase, &mSh, fb, j0, srow);
-          tma_load_2d_pair(sbase + SBOX, &mSh, fb, j0 + 64, srow);
-          if (NT2 == 3) {
-            tma_load_2d_pair(sbase + 2 * SBOX, &mSl, fb, j0, srow);
-            tma_load_2d_pair(sbase + 3 * SBOX, &mSl, fb, j0 + 64, srow);
+#pragma unroll
+          for (int bx = 0; bx < CW / 64; ++bx) {
+            tma_load_2d_pair(sbase + bx * SBOX, &mSh, fb, j0 + 64 * bx, srow);
+            if (NT2 == 3) tma_load_2d_pair(sbase + (CW / 64 + bx) * SBOX, &mSl, fb, j0 + 64 * bx, srow);
           }
         } else {
           tma_load_2d(sbase, &mSh, &sfull[sb], j0, args.s_row0);
@@ -570,7 +590,7 @@ kmv_tc_kernel(const __grid_constant__ CUtensorMap mAh, const __grid_constant__ C
     if (lane == 0 && leader) {   // pair form: the even CTA issues for both
       constexpr uint32_t TM = tile_rows(PAIR);
       // split rows are FP16 hi/lo, BF16 rows BF16, TF32 rows TF32
-      const uint32_t idesc1 = NT1 == 2 ? idesc_tf32_f32(TM, BN) : NT1 == 3 ? idesc_f16_f32(TM, BN) : idesc_bf16_f32(TM, BN);
+      const uint32_t idesc1 = NT1 == 2 ? idesc_tf32_f32(TM, CW) : NT1 == 3 ? idesc_f16_f32(TM, CW) : idesc_bf16_f32(TM, CW);
       // split weights are FP16 hi/lo (kernel values too), single weights BF16
       const uint32_t idesc2 = NT2 == 3 ? idesc_f16_f32(TM, static_cast<uint32_t>(args.p_pad))
                                        : idesc_bf16_f32(TM, static_cast<uint32_t>(args.p_pad));
@@ -597,8 +617,8 @@ kmv_tc_kernel(const __grid_constant__ CUtensorMap mAh, const __grid_constant__ C
         const StepInfo st = wk2.cur();
         wk2.next();
         const int c = st.c;
-        const bool first = st.first || (c % kFlushChunks == 0);
-        const bool last = st.last || ((c + 1) % kFlushChunks == 0);
+        const bool first = st.first || (c % FC == 0);
+        const bool last = st.last || ((c + 1) % FC == 0);
         if (first) {
           ++sub;
           const uint32_t opar = static_cast<uint32_t>((sub - 1) & 1);
@@ -617,7 +637,7 @@ kmv_tc_kernel(const __grid_constant__ CUtensorMap mAh, const __grid_constant__ C
           w2 = 0;
           w2par ^= 1u;
         }
-        return issue_gemm2<NT2, PAIR>(tb, static_cast<uint32_t>(gb) * BN, ocol, par, wpar, first, last, &pfull[gb],
+        return issue_gemm2<NT2, PAIR, CW>(tb, static_cast<uint32_t>(gb) * CW, ocol, par, wpar, first, last, &pfull[gb],
                                       &sfull[wb], &sempty[wb], &ofull, ab,
                                       dS_base + static_cast<uint64_t>(wb) * (SBUF >> 4), sbox16, idesc2,
                                       args.wait_ns);
@@ -630,7 +650,7 @@ kmv_tc_kernel(const __grid_constant__ CUtensorMap mAh, const __grid_constant__ C
       for (int64_t t = 0; t < T && ok; ++t, wk1.next()) {
         const int gb = g1;
         if (++g1 == ng) g1 = 0;
-        const uint32_t gt = tb + static_cast<uint32_t>(gb) * BN;
+        const uint32_t gt = tb + static_cast<uint32_t>(gb) * CW;
         bool seg_last = false;
         if (ARES) {
           const StepInfo st1 = wk1.cur();
@@ -643,7 +663,7 @@ kmv_tc_kernel(const __grid_constant__ CUtensorMap mAh, const __grid_constant__ C
             }
           }
         }
-        const int pos = issue_gemm1<NT1, NSTAGE, ARES, PAIR>(gt, nk, dStage0, dAres, full_bar, empty_bar, ab, idesc1,
+        const int pos = issue_gemm1<NT1, NSTAGE, ARES, PAIR, CW>(gt, nk, dStage0, dAres, full_bar, empty_bar, ab, idesc1,
                                                              stage | static_cast<int>(phase << 8), args.wait_ns);
         if (pos < 0) {
           ok = false;
@@ -688,18 +708,23 @@ kmv_tc_kernel(const __grid_constant__ CUtensorMap mAh, const __grid_constant__ C
     uint32_t gpar = 0;
     // column norms of the next step are loaded while the current chunk is processed
     Walker wkn = walk0;
-    float nb_next[BN / 32];
+    // (a wide chunk may pass the end of B's rows: norms there read as 0, the weights and
+    // rows there are TMA zero fill, so those columns add nothing)
+    auto nb_at = [&](int64_t r) -> float { return r < args.b_rows_pad ? args.nb[r] : 0.f; };
+    float nb_next[CW / 32];
     {
       const StepInfo s0 = wkn.cur();
 #pragma unroll
-      for (int k = 0; k < BN / 32; ++k) nb_next[k] = args.nb[static_cast<int64_t>(s0.b_row) + lane + 32 * k];
+      for (int k = 0; k < CW / 32; ++k) nb_next[k] = nb_at(static_cast<int64_t>(s0.b_row) + lane + 32 * k);
     }
+    constexpr int O2G = O2REG ? (NH == 1 ? 5 : 3) : 1;   // 16-column groups of O per thread (P <= 80)
+    float o2r[O2G][16];                                  // wide chunks: O2 of this thread's row
     for (int64_t t = 0; t < T; ++t, wk.next()) {
       const StepInfo st = wk.cur();
       const int c = st.c;
       const bool first = st.first;
       const bool last = st.last;
-      const bool sub_last = last || ((c + 1) % kFlushChunks == 0);
+      const bool sub_last = last || ((c + 1) % FC == 0);
       if (first) {
         ++seg;
         seg_c0 = c;
@@ -729,20 +754,18 @@ kmv_tc_kernel(const __grid_constant__ CUtensorMap mAh, const __grid_constant__ C
         }
         rowc = fmaf(kp.c_exp, na_r, kls);
       }
-      float* nb_s = nb_all + e * BN;
+      float* nb_s = nb_all + e * CW;
       __syncwarp();
       // RBF stages c_exp |b|^2 (the column term of the exponent), Matern |b|^2
 #pragma unroll
-      for (int k = 0; k < BN / 32; ++k) nb_s[lane + 32 * k] = KIND == ITERGP_RBF ? kp.c_exp * nb_next[k] : nb_next[k];
+      for (int k = 0; k < CW / 32; ++k) nb_s[lane + 32 * k] = KIND == ITERGP_RBF ? kp.c_exp * nb_next[k] : nb_next[k];
       __syncwarp();
       wkn.next();
       if (t + 1 < T) {
         const StepInfo sn = wkn.cur();
 #pragma unroll
-        for (int k = 0; k < BN / 32; ++k) nb_next[k] = args.nb[static_cast<int64_t>(sn.b_row) + lane + 32 * k];
+        for (int k = 0; k < CW / 32; ++k) nb_next[k] = nb_at(static_cast<int64_t>(sn.b_row) + lane + 32 * k);
       }
-      // -2 a.b = gsc G: the chunk's tile scales undo the split rows' powers of two exactly
-      const float gsc = NT1 == 3 ? -2.f * ua_t * args.ub[st.b_row / BN] : -2.f;
       const int gb = gbuf;
       if (!mbar_wait_warp(&gfull[gb], gpar, ab, args.wait_ns)) break;
       if (++gbuf == ng) {
@@ -750,12 +773,15 @@ kmv_tc_kernel(const __grid_constant__ CUtensorMap mAh, const __grid_constant__ C
         gpar ^= 1u;
       }
       tc_fence_after();
-      const uint32_t gcol = tb + lane_base + gb * BN;
-      // the chunk that holds this tile's own rows as columns (row tiles and chunks start on
-      // multiples of 128, so it is the chunk with b_row == a_row, the same for the CTA)
-      const bool dchunk = args.diag != 0 && st.a_row == st.b_row;
+      const uint32_t gcol = tb + lane_base + gb * CW;
+      // this row's own column, when the chunk holds it (dcol in [0, CW)); the test is
+      // warp-uniform so that chunks without a diagonal skip the patch below
+      const int64_t dcol64 = grow - st.b_row;
+      const bool dhit = args.diag != 0 && dcol64 >= 0 && dcol64 < CW;
+      const bool dchunk = __any_sync(0xffffffffu, dhit);
+      const int dcol = dhit ? static_cast<int>(dcol64) : -1024;
       // the TMEM load of the next 32-column group is in flight while this one is computed
-      const int grp0 = hc * (BN / 32 / NH), grp1 = (hc + 1) * (BN / 32 / NH);
+      const int grp0 = hc * (CW / 32 / NH), grp1 = (hc + 1) * (CW / 32 / NH);
       uint32_t v[32];
       tmem_ld32(gcol + 32 * grp0, v);
       tmem_ld_wait();
@@ -765,12 +791,20 @@ kmv_tc_kernel(const __grid_constant__ CUtensorMap mAh, const __grid_constant__ C
         const bool more = grp + 1 < grp1;   // warp-uniform
         if (more) tmem_ld32(gcol + 32 * (grp + 1), vn);
         uint32_t ph[16], pl[16];
-        if (dchunk && grp == q) {
-          // the row's own column (32 q + lane): a huge a.b clamps r^2 to 0 below, so the
-          // kernel value is s itself rather than the rounding left by |a|^2 + |a|^2 - 2 a.a
+        if (dchunk) {
+          // the row's own column: a huge a.b clamps r^2 to 0 below, so the kernel value is
+          // s itself rather than the rounding left by |a|^2 + |a|^2 - 2 a.a
+          const int dj = dcol - 32 * grp;
 #pragma unroll
           for (int j = 0; j < 32; ++j)
-            if (j == lane) v[j] = __float_as_uint(1e30f);
+            if (j == dj) v[j] = __float_as_uint(1e30f);
+        }
+        // -2 a.b = gsc G: the tile scales of the row and of this group's columns undo the
+        // split rows' powers of two exactly (a wide chunk spans two 128-row tiles of B)
+        float gsc = -2.f;
+        if constexpr (NT1 == 3) {
+          const int64_t br = static_cast<int64_t>(st.b_row) + 32 * grp;
+          gsc = -2.f * ua_t * (br < args.b_rows_pad ? args.ub[br / BM] : 1.f);
         }
         if (KIND == ITERGP_RBF) {
           // k = s 2^(c_exp r^2) = 2^t, t = c_exp (|a|^2 + |b|^2 - 2 a.b) + log2 s, formed two
@@ -846,7 +880,36 @@ kmv_tc_kernel(const __grid_constant__ CUtensorMap mAh, const __grid_constant__ C
           }
         }
         const int lim = st.item >= 0 ? out_lim : (full_row ? args.p_valid : args.p_pad);
-        for (int c16 = hc; c16 < args.p_pad / 16; c16 += NH) {
+        if constexpr (O2REG) {
+          // O2 in registers: add the flushed O (IEEE round-to-nearest), write at the run's end
+          const int np16 = args.p_pad / 16;
+#pragma unroll
+          for (int gi = 0; gi < O2G; ++gi) {
+            const int c16 = hc + gi * NH;
+            if (c16 < np16) {   // warp-uniform
+              uint32_t o[16];
+              tmem_ld16(tb + lane_base + ocol + 16 * c16, o);
+              tmem_ld_wait();
+#pragma unroll
+              for (int i = 0; i < 16; ++i)
+                o2r[gi][i] = sub_in_seg > 0 ? o2r[gi][i] + __uint_as_float(o[i]) : __uint_as_float(o[i]);
+              if (last && valid) {
+                if constexpr (NT2 == 3) {   // undo the weights' and the kernel values' scales
+                  const float* ws = (st.item >= 0 ? item_ws : args.wscale) + args.s_row0 + 16 * c16;
+                  const float kinv = pow2i(-static_cast<int>(ke));
+#pragma unroll
+                  for (int i = 0; i < 16; ++i)
+                    if (16 * c16 + i < lim) dst[16 * c16 + i] = (o2r[gi][i] * ws[i]) * kinv;
+                } else {
+#pragma unroll
+                  for (int i = 0; i < 16; ++i)
+                    if (16 * c16 + i < lim) dst[16 * c16 + i] = o2r[gi][i];
+                }
+              }
+            }
+          }
+        }
+        for (int c16 = hc; !O2REG && c16 < args.p_pad / 16; c16 += NH) {
           uint32_t o[16];
           tmem_ld16(tb + lane_base + ocol + 16 * c16, o);
           if (sub_in_seg > 0) {
@@ -912,10 +975,10 @@ kmv_tc_kernel(const __grid_constant__ CUtensorMap mAh, const __grid_constant__ C
 // One launch of an instantiation, or (max_clusters non-null, pair form) the number of
 // its clusters that can be resident at once.  The pair form launches 2 * grid CTAs in
 // clusters of two.
-template <int KIND, int NT1, int NT2, int NSTAGE, int EPI, bool ARES, bool PAIR>
+template <int KIND, int NT1, int NT2, int NSTAGE, int EPI, bool ARES, bool PAIR, int CW = BN>
 cudaError_t launch_tc(int grid, size_t smem, cudaStream_t st, const CUtensorMap* maps, const TcArgs& a,
                       int* max_clusters) {
-  auto fn = kmv_tc_kernel<KIND, NT1, NT2, NSTAGE, EPI, ARES, PAIR>;
+  auto fn = kmv_tc_kernel<KIND, NT1, NT2, NSTAGE, EPI, ARES, PAIR, CW>;
   cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   if constexpr (PAIR) {
@@ -947,40 +1010,45 @@ cudaError_t launch_tc(int grid, size_t smem, cudaStream_t st, const CUtensorMap*
 }
 
 // Instantiated rings: streamed A+B 2, 3, 4 stages; resident A (B-only stages) 3, 5 (one-CTA
-// form only).
-template <int KIND, int NT1, int NT2, int EPI, bool PAIR>
+// form only); wide chunks (pair form): 3 streamed stages.
+template <int KIND, int NT1, int NT2, int EPI, bool PAIR, int CW = BN>
 cudaError_t launch_stages(int nstage, bool ares, int grid, size_t smem, cudaStream_t st,
                           const CUtensorMap* maps, const TcArgs& a, int* mc) {
-  if (ares) {
-    if constexpr (NT1 == 2 || PAIR)   // TF32 rows take two slices per 64 columns; pairs stream A
-      return cudaErrorInvalidValue;
-    else
-      return nstage == 5 ? launch_tc<KIND, NT1, NT2, 5, EPI, true, false>(grid, smem, st, maps, a, mc)
-                         : launch_tc<KIND, NT1, NT2, 3, EPI, true, false>(grid, smem, st, maps, a, mc);
-  }
-  switch (nstage) {
-    case 2: return launch_tc<KIND, NT1, NT2, 2, EPI, false, PAIR>(grid, smem, st, maps, a, mc);
-    case 3: return launch_tc<KIND, NT1, NT2, 3, EPI, false, PAIR>(grid, smem, st, maps, a, mc);
-    default: return launch_tc<KIND, NT1, NT2, 4, EPI, false, PAIR>(grid, smem, st, maps, a, mc);
+  if constexpr (CW != BN) {
+    if (ares || nstage != 3) return cudaErrorInvalidValue;
+    return launch_tc<KIND, NT1, NT2, 3, EPI, false, true, CW>(grid, smem, st, maps, a, mc);
+  } else {
+    if (ares) {
+      if constexpr (NT1 == 2 || PAIR)   // TF32 rows take two slices per 64 columns; pairs stream A
+        return cudaErrorInvalidValue;
+      else
+        return nstage == 5 ? launch_tc<KIND, NT1, NT2, 5, EPI, true, false>(grid, smem, st, maps, a, mc)
+                           : launch_tc<KIND, NT1, NT2, 3, EPI, true, false>(grid, smem, st, maps, a, mc);
+    }
+    switch (nstage) {
+      case 2: return launch_tc<KIND, NT1, NT2, 2, EPI, false, PAIR>(grid, smem, st, maps, a, mc);
+      case 3: return launch_tc<KIND, NT1, NT2, 3, EPI, false, PAIR>(grid, smem, st, maps, a, mc);
+      default: return launch_tc<KIND, NT1, NT2, 4, EPI, false, PAIR>(grid, smem, st, maps, a, mc);
+    }
   }
 }
 
-template <int KIND, int EPI, bool PAIR>
+template <int KIND, int EPI, bool PAIR, int CW = BN>
 cudaError_t launch_prec_epi(int prec, int nstage, bool ares, int grid, size_t smem, cudaStream_t st,
                             const CUtensorMap* maps, const TcArgs& a, int* mc) {
   switch (prec) {
-    case ITERGP_BF16X3: return launch_stages<KIND, 3, 3, EPI, PAIR>(nstage, ares, grid, smem, st, maps, a, mc);
-    case ITERGP_BF16_COMP: return launch_stages<KIND, 3, 1, EPI, PAIR>(nstage, ares, grid, smem, st, maps, a, mc);
-    case ITERGP_TF32: return launch_stages<KIND, 2, 3, EPI, PAIR>(nstage, ares, grid, smem, st, maps, a, mc);
-    default: return launch_stages<KIND, 1, 1, EPI, PAIR>(nstage, ares, grid, smem, st, maps, a, mc);
+    case ITERGP_BF16X3: return launch_stages<KIND, 3, 3, EPI, PAIR, CW>(nstage, ares, grid, smem, st, maps, a, mc);
+    case ITERGP_BF16_COMP: return launch_stages<KIND, 3, 1, EPI, PAIR, CW>(nstage, ares, grid, smem, st, maps, a, mc);
+    case ITERGP_TF32: return launch_stages<KIND, 2, 3, EPI, PAIR, CW>(nstage, ares, grid, smem, st, maps, a, mc);
+    default: return launch_stages<KIND, 1, 1, EPI, PAIR, CW>(nstage, ares, grid, smem, st, maps, a, mc);
   }
 }
 
-template <int KIND, bool PAIR>
+template <int KIND, bool PAIR, int CW = BN>
 cudaError_t launch_prec(int prec, int nstage, bool ares, int epi, int grid, size_t smem,
                         cudaStream_t st, const CUtensorMap* maps, const TcArgs& a, int* mc = nullptr) {
-  return epi == 8 ? launch_prec_epi<KIND, 8, PAIR>(prec, nstage, ares, grid, smem, st, maps, a, mc)
-                  : launch_prec_epi<KIND, 4, PAIR>(prec, nstage, ares, grid, smem, st, maps, a, mc);
+  return epi == 8 ? launch_prec_epi<KIND, 8, PAIR, CW>(prec, nstage, ares, grid, smem, st, maps, a, mc)
+                  : launch_prec_epi<KIND, 4, PAIR, CW>(prec, nstage, ares, grid, smem, st, maps, a, mc);
 }
 
 }  // namespace

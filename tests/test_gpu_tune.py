@@ -30,7 +30,8 @@ def test_autotune_times_every_variant(native, prec, items, p):
     assert len(vs) >= 2 and best in vs   # wide split P tiles leave room for 2 stages only
     assert {v[0] for v in vs} == {4, 8}
     assert all(v[3] > 0 for v in vs)
-    assert {v[2] for v in vs} == ({0} if items else {0, 1})   # the pair form: single schedule
+    # the pair form: single schedule; with wide chunks where P fits one tile of <= 80
+    assert {v[2] for v in vs} == ({0} if items else {0, 1, 2} if p <= 80 else {0, 1})
     native.tune_clear()
 
 
@@ -98,3 +99,53 @@ def test_pair_form_computes_the_one_cta_product(native, tmp_path, prec, m, n, d,
     scale = ref.abs().amax(dim=1, keepdim=True).clamp_min(1e-30)
     err = float(((got - ref).abs() / scale).max())
     assert err <= 2.0 ** -18, err
+
+
+@pytest.mark.parametrize("prec", ["bf16x3", "bf16_comp", "bf16", "tf32"])
+@pytest.mark.parametrize("m,n,d,p,epi", [
+    (3000, 3000, 40, 24, 4),           # one K slice
+    (2345, 1999, 300, 80, 8),          # several slices, ragged rows, P = 80
+    (700, 4100, 784, 80, 4),           # the kernel bench's D and P; a chunk past B's last row
+    (257, 300, 130, 16, 8),            # one pair tile plus one row, two chunks
+])
+def test_wide_pair_form_computes_the_one_cta_product(native, tmp_path, prec, m, n, d, p, epi):
+    """The wide pair form (chunks of 192 rows of B, MMA N = 192, the flushed running sum in
+    registers) forms each kernel value and weighted-sum term as the one-CTA form does;
+    its chunks and flush groups (3 x 192 rather than 4 x 128 rows) regroup the FP32 sums
+    of a row, so the two agree to FP32 re-association (2^-16 of the row's largest output,
+    far inside the 1e-4 product bar).  Chunks past the last row of B read zero rows,
+    norms and weights."""
+    A = torch.as_tensor(datagen.normal((m, d), 5), device=DEV)
+    B = torch.as_tensor(datagen.normal((n, d), 6), device=DEV)
+    S = torch.as_tensor(datagen.normal((n, p), 7), device=DEV)
+    p16 = (p + 15) // 16 * 16
+    ell = float(np.sqrt(d))
+    force(native, tmp_path, prec, 1, d, p16, 0, epi, 2, 0, 0)
+    ref = native.kmatvec(A, B, S, kind="matern32", lengthscale=ell, precision=prec).clone()
+    force(native, tmp_path, prec, 1, d, p16, 0, epi, 3, 0, 2)
+    got = native.kmatvec(A, B, S, kind="matern32", lengthscale=ell, precision=prec)
+    torch.cuda.synchronize()
+    native.tune_clear()
+    assert native.sync_status() == 0
+    assert torch.isfinite(got).all()
+    scale = ref.abs().amax(dim=1, keepdim=True).clamp_min(1e-30)
+    err = float(((got - ref).abs() / scale).max())
+    assert err <= 2.0 ** -16, err
+
+
+def test_wide_pair_form_keeps_the_exact_diagonal(native, tmp_path):
+    """K(X, X) S with the wide chunks: 192-row chunks straddle the 256-row pair tiles, so a
+    row's own column falls at any offset of a chunk; the kernel value there is s (to the
+    exp2 and FP16-split rounding, 2^-20), where |a|^2 + |a|^2 - 2 a.a in split FP16 would
+    leave about 3e-3 in r^2 and e^-0.6 in k.  The kernel is so narrow (|x| ~ 80, l = 0.05)
+    that every other value underflows to 0: K = s I."""
+    X = torch.as_tensor(datagen.normal((1000, 64), 8) * 10.0, device=DEV)
+    S = torch.as_tensor(datagen.normal((1000, 16), 9), device=DEV)
+    force(native, tmp_path, "bf16x3", 0, 64, 16, 0, 4, 3, 0, 2)
+    got = native.kmatvec(X, X, S, kind="rbf", lengthscale=0.05, outputscale=2.5, precision="bf16x3")
+    torch.cuda.synchronize()
+    native.tune_clear()
+    assert native.sync_status() == 0
+    want = 2.5 * S
+    err = float(((got - want).abs() / want.abs().amax(dim=1, keepdim=True)).max())
+    assert err <= 2.0 ** -20, err
