@@ -183,7 +183,7 @@ def test_tune_cache_round_trip(lib, tmp_path):
     lib.itergp_tune_save.argtypes = [ct.c_char_p]
     src = tmp_path / "in.txt"
     src.write_text("# comment\n1 0 64 16 1 8 2\n3 1 832 80 0 4 0 0\n2 0 64 16 1 4 5 1\n"
-                   "1 1 832 80 0 8 3 0 1\n")
+                   "1 1 832 80 0 8 3 0 1\n4 0 832 80 0 4 3 0 2\n")
     assert lib.itergp_tune_clear() == 0
     assert lib.itergp_tune_load(str(src).encode()) == 0
     out = tmp_path / "out.txt"
@@ -191,11 +191,11 @@ def test_tune_cache_round_trip(lib, tmp_path):
     rows = [l for l in out.read_text().splitlines() if not l.startswith("#")]
     # missing resident-A / CTA-pair columns read as -1 (automatic)
     assert sorted(rows) == sorted(["1 0 64 16 1 8 2 -1 -1", "3 1 832 80 0 4 0 0 -1", "2 0 64 16 1 4 5 1 -1",
-                                   "1 1 832 80 0 8 3 0 1"])
+                                   "1 1 832 80 0 8 3 0 1", "4 0 832 80 0 4 3 0 2"])
     bad = tmp_path / "bad.txt"
     bad.write_text("1 0 64 16 1 6 2\n")          # 6 epilogue warps is not a variant
     assert lib.itergp_tune_load(str(bad).encode()) == -1
-    bad.write_text("1 0 64 16 1 8 2 0 2\n")      # the pair column takes -1, 0 or 1
+    bad.write_text("1 0 64 16 1 8 2 0 3\n")      # the pair column takes -1, 0, 1 or 2 (wide chunks)
     assert lib.itergp_tune_load(str(bad).encode()) == -1
     assert lib.itergp_tune_clear() == 0
 
