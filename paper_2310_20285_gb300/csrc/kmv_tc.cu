@@ -194,6 +194,14 @@ int stages_that_fit(const DeviceContext* ctx, int nt1, int nt2, int p_tile, int 
 
 int tc_nt1(int prec) { return precision_tf32_rows(prec) ? 2 : precision_splits_rows(prec) ? 3 : 1; }
 
+// MMA K steps (32 bytes of a row each) of the last D slice that hold data: rows are zero
+// padded from d to d_pad, and the steps past d are skipped.
+int last_slice_ksteps(int d, int d_pad, int nt1) {
+  const int slice = slice_elems(nt1), step = nt1 == 2 ? 8 : 16;
+  const int rem = d - (d_pad / slice - 1) * slice;   // values in the last slice, 1 .. slice
+  return rem <= 0 ? slice / step : static_cast<int>(ceil_div(rem, step));
+}
+
 // Tensor maps of the row operands (maps[1] and [3] repeat the hi planes when rows are not
 // split).  Boxes: 128 rows of A; 128 rows of B, or 64 in the pair form (each CTA of a pair
 // stages half of every chunk).
@@ -291,6 +299,7 @@ int kmv_tc_items(DeviceContext* ctx, int kind, const RowOperand& A, const RowOpe
     a.a_rows_pad = A.rows_pad;
     a.b_rows_pad = B.rows_pad;
     a.nk = B.d_pad / slice_elems(nt1);
+    a.klast = last_slice_ksteps(std::max(A.d, B.d), B.d_pad, nt1);
     a.p_pad = pp;
     a.p_valid = pp;
     a.s_row0 = s_row0 + p0;
@@ -423,6 +432,7 @@ int kmv_tc(DeviceContext* ctx, const KParams& kp, const RowOperand& A, const Row
     a.row_tiles = row_tiles;
     a.chunks = static_cast<int>(chunks);
     a.nk = A.d_pad / slice_elems(nt1);
+    a.klast = last_slice_ksteps(std::max(A.d, B.d), A.d_pad, nt1);
     a.p_pad = pp;
     a.p_valid = pw;
     a.s_row0 = static_cast<int>(p0);

@@ -63,6 +63,8 @@ struct TcArgs {
   int64_t row_tiles;      // R (tiles of tile_rows(pair) rows)
   int chunks;             // J
   int nk;                 // D slices (d_pad / 64)
+  int klast;              // MMA K steps of the last slice that hold data (1 .. 4; the rest of
+                          // the padded slice is zeros, whose products are skipped)
   int p_pad;              // MMA N of the product (multiple of 16, <= 128)
   int p_valid;            // valid output columns of this P tile
   int s_row0;             // first row of this P tile in the transposed S
@@ -284,9 +286,9 @@ __device__ __forceinline__ void commit_x(uint64_t* bar) {
 // In the pair form a stage holds this CTA's 128 rows of A and 64 rows of B; the same
 // descriptors address the other CTA's stage, and the MMA's M = 256.
 template <int NT1, int NSTAGE, bool ARES, bool PAIR, int CW>
-__device__ __noinline__ int issue_gemm1(uint32_t gt, int nk, uint64_t dStage0, uint64_t dAres, uint64_t* full_bar,
-                                        uint64_t* empty_bar, volatile int* ab, uint32_t idesc1, int pos,
-                                        uint64_t lim) {
+__device__ __noinline__ int issue_gemm1(uint32_t gt, int nk, int klast, uint64_t dStage0, uint64_t dAres,
+                                        uint64_t* full_bar, uint64_t* empty_bar, volatile int* ab, uint32_t idesc1,
+                                        int pos, uint64_t lim) {
   constexpr uint32_t A_PART = BM * BK * 2, B_PART = b_rows_cta(PAIR, CW) * BK * 2;
   constexpr uint32_t SB = ARES ? (NT1 == 3 ? 2u : 1u) * B_PART : stage_bytes(NT1, PAIR, CW);
   int stage = pos & 0xFF;
@@ -301,7 +303,22 @@ __device__ __noinline__ int issue_gemm1(uint32_t gt, int nk, uint64_t dStage0, u
     const uint64_t dAl = dAh + (A_PART >> 4);
     const uint64_t dBl = dBh + (B_PART >> 4);
     // one MMA order for every ring and form, so that launch variants agree
-    if constexpr (NT1 == 3) {
+    if (ks + 1 == nk && klast < BK / 16) {
+      // the last slice with zero padding: its K steps past the data are skipped (adding
+      // zero products leaves the FP32 sums as they are)
+      for (int kk = 0; kk < klast; ++kk) {
+        if constexpr (NT1 == 3) {
+          mma_ss_x<PAIR>(gt, dAh + 2 * kk, dBl + 2 * kk, idesc1, (ks | kk) != 0 ? 1u : 0u);
+          mma_ss_x<PAIR>(gt, dAl + 2 * kk, dBh + 2 * kk, idesc1, 1u);
+        } else if constexpr (NT1 == 2) {
+          mma_ss_tf32_x<PAIR>(gt, dAh + 2 * kk, dBh + 2 * kk, idesc1, (ks | kk) != 0 ? 1u : 0u);
+        } else {
+          mma_ss_x<PAIR>(gt, dAh + 2 * kk, dBh + 2 * kk, idesc1, (ks | kk) != 0 ? 1u : 0u);
+        }
+      }
+      if constexpr (NT1 == 3)
+        for (int kk = 0; kk < klast; ++kk) mma_ss_x<PAIR>(gt, dAh + 2 * kk, dBh + 2 * kk, idesc1, 1u);
+    } else if constexpr (NT1 == 3) {
 #pragma unroll
       for (int kk = 0; kk < BK / 16; ++kk) {
         mma_ss_x<PAIR>(gt, dAh + 2 * kk, dBl + 2 * kk, idesc1, (ks | kk) != 0 ? 1u : 0u);
@@ -663,7 +680,7 @@ kmv_tc_kernel(const __grid_constant__ CUtensorMap mAh, const __grid_constant__ C
             }
           }
         }
-        const int pos = issue_gemm1<NT1, NSTAGE, ARES, PAIR, CW>(gt, nk, dStage0, dAres, full_bar, empty_bar, ab, idesc1,
+        const int pos = issue_gemm1<NT1, NSTAGE, ARES, PAIR, CW>(gt, nk, args.klast, dStage0, dAres, full_bar, empty_bar, ab, idesc1,
                                                              stage | static_cast<int>(phase << 8), args.wait_ns);
         if (pos < 0) {
           ok = false;
