@@ -916,9 +916,10 @@ def main():
 
     pk, pk_kind = peaks()
     prec = args.precision
-    # what one CTA per SM gets from tcgen05.mma in the distance GEMM's shape (SS, M = N = 128,
-    # issued back to back): the ceiling of the tile shape, probed here
-    mma_ceiling = native.probe_throughput("mma_ss_n128_tf32" if prec == "tf32" else "mma_ss_n128") / 1e12
+    # what back-to-back tcgen05.mma get in the distance GEMM's shape, probed here: the wide
+    # pair form's cta_group::2 SS MMAs of M = 256, N = 192 (16-bit operands); TF32 rows as
+    # one CTA per SM, SS M = N = 128 (kind::tf32)
+    mma_ceiling = native.probe_throughput("mma_ss_n128_tf32" if prec == "tf32" else "pair_mma_ss_n192_f16") / 1e12
     flops = 2.0 * n * n * (D + P)
     kernel_s = (kern_ms / max(kern_n, 1)) / 1e3
     achieved = flops / kernel_s / 1e12
@@ -935,12 +936,13 @@ def main():
         peak, peak_kind, bound, kname = pk["bf16_tflops"] * 1.1 / 2.25, f"{pk_kind} bf16 dense (burst) x 1.1/2.25 (tf32)", "tensor", "kmv_tc_kernel"
     else:
         peak, peak_kind, bound, kname = pk["bf16_tflops"], f"{pk_kind} bf16 dense (burst)", "tensor", "kmv_tc_kernel"
-    # DRAM bytes per launch from the ncu capture of this kernel version at N = 40000 (bf16x3,
-    # D = 784, P = 80: 1.5492 GB read + 16.4 MB written), scaled by the pairs processed
-    # (the lockstep schedule re-reads the B side once per wave, so traffic grows like N^2)
+    # DRAM bytes per launch from the ncu capture of this kernel version (the wide pair form)
+    # at N = 40000 (bf16x3, D = 784, P = 80: 962.1 MB read + 19.0 MB written), scaled by the
+    # pairs processed (the lockstep schedule re-reads the B side once per wave, so traffic
+    # grows like N^2)
     traffic = None
     if args.precision == "bf16x3":
-        traffic = (1.5492e9 + 16.4e6) * (n / 40000.0) ** 2
+        traffic = (962.06e6 + 19.03e6) * (n / 40000.0) ** 2
     roof = {"bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
             "frac": achieved / peak, "traffic": traffic,
             "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of one launch at N=40000, "
@@ -954,14 +956,19 @@ def main():
     if prec != "fp32":
         roof.update({"tensor_flops_issued_per_launch": issued, "mma_shape_ceiling_tflops": mma_ceiling,
                      "issued_frac_of_mma_shape_ceiling": issued / kernel_s / 1e12 / mma_ceiling})
+        # the pair form's distance GEMM fed by its TMA ring (no epilogue), N = 128 vs 192:
+        # why the product takes 192-row chunks
+        roof["ring_fed_mma_tflops"] = {"pair_n128": native.probe_throughput("ring_pair_n128") / 1e12,
+                                       "pair_n192": native.probe_throughput("ring_pair_n192") / 1e12}
 
     out = {"metric": METRIC, "value": value, "unit": "kernel-pairs/s", "n_gpus": world,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_max * 1e3,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-           "dtype": {"bf16x3": "bf16x3 (BF16 hi/lo split operands, FP32 accumulate; FP32-accurate)",
-                     "bf16_comp": "bf16_comp (split BF16 distance, BF16 weighted sum, FP32 accumulate)",
+           "dtype": {"bf16x3": "bf16x3 (FP16 hi/lo split operands with power-of-two scales, three MMA terms "
+                               "per contraction, FP32 accumulate; FP32-accurate)",
+                     "bf16_comp": "bf16_comp (FP16 hi/lo split distance, BF16 weighted sum, FP32 accumulate)",
                      "bf16": "bf16 (BF16 operands, FP32 accumulate)",
-                     "tf32": "tf32 (TF32 distance operands, split BF16 weighted sum, FP32 accumulate)",
+                     "tf32": "tf32 (TF32 distance operands, FP16 hi/lo split weighted sum, FP32 accumulate)",
                      "fp32": "f32"}[prec],
            "data": "synthetic",
            "config": {"workload": f"kernel product K(X,X)S, N={n}, D={D}, P={P}, Matern-3/2 l=28, s=1; "

@@ -17,9 +17,14 @@
  *   what = 9..11: the CTA-pair form (clusters of two CTAs; the even CTA issues
  *             cta_group::2 MMAs of M = 256 for both SMs, each SM holding 128 rows of A and
  *             half of B): 9 = SS N = 128, FP16 (the pair form's distance GEMM); 10 = SS
- *             N = 256; 11 = TS N = 80 (the pair form's weighted sum).
+ *             N = 256; 11 = TS N = 80 (the pair form's weighted sum); 12 = SS N = 192,
+ *             FP16 (the wide pair form's distance GEMM).
+ *   what = 13, 14: the pair form's distance GEMM fed by a TMA ring (3 stages of K = 64, A and
+ *             B hi/lo refilled from a 64 MB array through full/empty barriers, the
+ *             product's three-term MMA order, no epilogue): 13 = N = 128, 14 = N = 192.
+ *             Allocates (and frees) the 64 MB source array.
  * Returns ITERGP_EINVAL for another `what` or a null result, ITERGP_ETIMEOUT if a probe's
- * bounded wait (2 s) ran out, ITERGP_ECUDA on a CUDA error. */
+ * bounded wait (2 s) ran out, ITERGP_ENOMEM / ITERGP_ECUDA on a CUDA error. */
 #ifndef ITERGP_PROBE_H
 #define ITERGP_PROBE_H
 #include <stdint.h>

@@ -2,7 +2,8 @@
 // kernel value of RBF, the exponential of Matern) and rsqrt (Matern's distance), FP32
 // FFMA, FP64 DFMA, and the tcgen05 MMA in the shapes the product issues (SS M = 128 with
 // N = 128 or 256, the same while other warps stream TMEM loads, the TS form of the
-// weighted sum, the SS form with TF32 operands, and the CTA-pair forms of M = 256).
+// weighted sum, the SS form with TF32 operands, and the CTA-pair forms of M = 256, with
+// static operands or fed by a TMA ring like the product's distance GEMM).
 // Results are operations per second over the whole GPU, timed with CUDA events on the
 // stream.  Measurement tooling of the bench: built as its own library
 // (libitergp_probe.so), not part of the product library.
@@ -12,6 +13,7 @@
 
 #include "../../include/itergp_probe.h"
 #include "../csrc/tc_ptx.cuh"
+#include "../csrc/tma_host.h"
 
 namespace itergp {
 namespace {
@@ -274,6 +276,98 @@ __global__ void __launch_bounds__(256, 1) probe_mma_pair_kernel(int iters, int* 
   if (threadIdx.x == 0 && abort_s) atomicExch(status, ITERGP_ETIMEOUT);
 }
 
+// Ring-fed pair-form MMAs: clusters of two CTAs stream stages of K = 64 (A hi and lo, 128
+// rows per CTA; B hi and lo, N / 2 rows per CTA) from a 64 MB FP16 array through a ring of
+// 3 stages (TMA loads on the even CTA's full barriers, MMA commits on both CTAs' empty
+// barriers), and the even CTA issues the product's three-term order on every stage
+// (A_hi B_lo, A_lo B_hi per K step, then A_hi B_hi): the distance GEMM of the pair form
+// with its refills and without its epilogue.  Every wait is bounded.
+template <int N>
+__global__ void __launch_bounds__(128, 1)
+probe_ring_pair_kernel(const __grid_constant__ CUtensorMap mA, const __grid_constant__ CUtensorMap mB,
+                       int stages, int* status) {
+  constexpr int NST = 3, NC = N / 2;
+  constexpr uint32_t A_PART = 128 * 128, B_PART = NC * 128, SB = 2 * A_PART + 2 * B_PART;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
+                                             ~static_cast<uintptr_t>(1023));
+  __shared__ __align__(8) uint64_t full[NST], empty[NST], drain;
+  __shared__ uint32_t tmem_base_s;
+  __shared__ int abort_s;
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+  const uint32_t h = cluster_rank();
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < NST; ++i) {
+      mbar_init(&full[i], 1);
+      mbar_init(&empty[i], 1);
+    }
+    mbar_init(&drain, 1);
+    abort_s = 0;
+    fence_mbar_init();
+  }
+  if (warp == 2) {
+    tmem_alloc_pair(&tmem_base_s, 256);
+    tmem_relinquish_pair();
+  }
+  tc_fence_before();
+  __syncthreads();
+  cluster_sync_all();
+  tc_fence_after();
+  const uint32_t tb = tmem_base_s;
+  volatile int* ab = &abort_s;
+  const int pair_id = blockIdx.x / 2;
+  if (warp == 0 && lane == 0) {
+    for (int i = 0; i < stages; ++i) {
+      const int s = i % NST;
+      if (i >= NST && !mbar_wait_cluster(&empty[s], static_cast<uint32_t>((i / NST - 1) & 1), ab, kProbeWaitNs)) break;
+      uint8_t* base = smem + s * SB;
+      const int x = 64 * (i % 12);
+      const int ya = (128 * (2 * pair_id + static_cast<int>(h)) + 384 * (i % 7)) % 30000;   // this CTA's A rows
+      const int yb = (NC * (2 * (i % 50) + static_cast<int>(h))) % 30000;                 // the shared B chunk
+      if (h == 0) mbar_arrive_expect_tx(&full[s], 2 * SB);
+      const uint32_t fb = cluster_addr(smem_u32(&full[s]), 0u);
+      tma_load_2d_pair(base, &mA, fb, x, ya);
+      tma_load_2d_pair(base + A_PART, &mA, fb, x + 64, ya);
+      tma_load_2d_pair(base + 2 * A_PART, &mB, fb, x, yb);
+      tma_load_2d_pair(base + 2 * A_PART + B_PART, &mB, fb, x + 64, yb);
+    }
+  } else if (warp == 1 && lane == 0 && h == 0) {
+    const uint32_t idesc = idesc_f16_f32(256, N);
+    const uint64_t d0 = sdesc_kmajor_sw128(smem_u32(smem));
+    for (int i = 0; i < stages; ++i) {
+      const int s = i % NST;
+      const uint32_t ph = static_cast<uint32_t>((i / NST) & 1);
+      if (!mbar_try_wait(&full[s], ph) && !mbar_wait(&full[s], ph, ab, kProbeWaitNs)) break;
+      tc_fence_after();
+      const uint64_t dAh = d0 + static_cast<uint64_t>(s) * (SB >> 4);
+      const uint64_t dAl = dAh + (A_PART >> 4), dBh = dAh + (2 * A_PART >> 4), dBl = dBh + (B_PART >> 4);
+#pragma unroll
+      for (int kk = 0; kk < 4; ++kk) {
+        mma_ss_pair(tb, dAh + 2 * kk, dBl + 2 * kk, idesc, (i | kk) ? 1u : 0u);
+        mma_ss_pair(tb, dAl + 2 * kk, dBh + 2 * kk, idesc, 1u);
+      }
+#pragma unroll
+      for (int kk = 0; kk < 4; ++kk) mma_ss_pair(tb, dAh + 2 * kk, dBh + 2 * kk, idesc, 1u);
+      mma_commit_pair_both(&empty[s]);
+    }
+    mma_commit_pair_local(&drain);
+    mbar_wait_drain(&drain, 0, kProbeWaitNs);
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (abort_s) {   // copies in flight land before the CTA can exit
+    const uint64_t t0 = globaltimer_ns();
+    while (globaltimer_ns() - t0 < 1000000ull) {
+    }
+  }
+  cluster_sync_all();
+  if (warp == 2) {
+    tc_fence_after();
+    tmem_dealloc_pair(tb, 256);
+  }
+  if (threadIdx.x == 0 && abort_s) atomicExch(status, ITERGP_ETIMEOUT);
+}
+
 // Device buffers of one probe call (the probe library has no pool of its own).
 struct ProbeBufs {
   float* sink = nullptr;
@@ -358,7 +452,7 @@ int probe_mma(int sms, int what, double* ops_per_s, cudaStream_t stream) {
 }
 
 // Pair-form MMA rate: what = 9 (SS FP16, N = 128), 10 (SS FP16, N = 256), 11 (TS BF16,
-// N = 80); as many clusters as can be resident at once.
+// N = 80), 12 (SS FP16, N = 192); as many clusters as can be resident at once.
 int probe_mma_pair(int what, double* ops_per_s, cudaStream_t stream) {
   const int iters = 20000;
   const size_t smem = 160 * 1024;
@@ -367,6 +461,7 @@ int probe_mma_pair(int what, double* ops_per_s, cudaStream_t stream) {
   switch (what) {
     case 9: fn = probe_mma_pair_kernel<128, false, true>; break;
     case 10: fn = probe_mma_pair_kernel<256, false, true>; n = 256; break;
+    case 12: fn = probe_mma_pair_kernel<192, false, true>; n = 192; break;
     default: fn = probe_mma_pair_kernel<80, true, false>; n = 80; break;
   }
   cudaError_t err = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
@@ -399,6 +494,56 @@ int probe_mma_pair(int what, double* ops_per_s, cudaStream_t stream) {
   return ITERGP_OK;
 }
 
+// Ring-fed pair-form MMA rate: what = 13 (N = 128), 14 (N = 192); MMA flops per second of
+// as many clusters as can be resident at once.
+int probe_ring_pair(int what, double* ops_per_s, cudaStream_t stream) {
+  const int n = what == 13 ? 128 : 192, stages = 4000;
+  void (*fn)(const CUtensorMap, const CUtensorMap, int, int*) =
+      what == 13 ? probe_ring_pair_kernel<128> : probe_ring_pair_kernel<192>;
+  const size_t smem = 3 * (2 * 128 * 128 + 2 * (n / 2) * 128) + 1024;
+  cudaError_t err = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+  if (err != cudaSuccess) return to_status(err);
+  const uint64_t rows = 32768, cols = 1024;
+  void* src = nullptr;
+  err = cudaMalloc(&src, rows * cols * 2);
+  if (err != cudaSuccess) return to_status(err);
+  // FP16 0x3C3C (1.06) everywhere: finite sums
+  err = cudaMemsetAsync(src, 0x3C, rows * cols * 2, stream);
+  CUtensorMap maps[2];
+  if (err == cudaSuccess &&
+      !(encode_bf16_sw128(&maps[0], src, rows, cols, cols, 128, CU_TENSOR_MAP_DATA_TYPE_FLOAT16) &&
+        encode_bf16_sw128(&maps[1], src, rows, cols, cols, static_cast<uint32_t>(n / 2), CU_TENSOR_MAP_DATA_TYPE_FLOAT16)))
+    err = cudaErrorInvalidValue;
+  cudaLaunchConfig_t cfg = {};
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = 2;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.blockDim = dim3(128);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = stream;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  cfg.gridDim = dim3(2);
+  int clusters = 0;
+  if (err == cudaSuccess) err = cudaOccupancyMaxActiveClusters(&clusters, fn, &cfg);
+  ProbeBufs b;
+  if (err == cudaSuccess) err = b.alloc(1);
+  float ms = 0.f;
+  if (err == cudaSuccess && clusters >= 1) {
+    cfg.gridDim = dim3(static_cast<unsigned>(2 * clusters));
+    err = time_best([&] { return cudaLaunchKernelEx(&cfg, fn, maps[0], maps[1], stages, b.status); }, stream, &ms);
+  }
+  if (err == cudaSuccess) err = cudaStreamSynchronize(stream);
+  cudaFree(src);
+  if (err != cudaSuccess) return to_status(err);
+  if (clusters < 1) return ITERGP_EUNSUPPORTED;
+  if (const int st = read_status(b)) return st;
+  *ops_per_s = static_cast<double>(clusters) * stages * 12 * 2.0 * 256 * n * 16 / (ms * 1e-3);
+  return ITERGP_OK;
+}
+
 int probe_units(int sms, int what, double* ops_per_s, cudaStream_t stream) {
   const int blocks = 8 * sms, threads = 256, iters = 4096;
   ProbeBufs b;
@@ -427,13 +572,14 @@ int probe_units(int sms, int what, double* ops_per_s, cudaStream_t stream) {
 }  // namespace itergp
 
 extern "C" int itergp_probe_throughput(int32_t what, double* ops_per_s, itergp_stream stream) {
-  if (what < 0 || what > 11 || !ops_per_s) return ITERGP_EINVAL;
+  if (what < 0 || what > 14 || !ops_per_s) return ITERGP_EINVAL;
   (void)cudaGetLastError();
   int dev = 0, sms = 0;
   if (cudaGetDevice(&dev) != cudaSuccess ||
       cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
     return ITERGP_ECUDA;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (what >= 13) return itergp::probe_ring_pair(what, ops_per_s, s);
   if (what >= 9) return itergp::probe_mma_pair(what, ops_per_s, s);
   if (what >= 2 && what <= 6) return itergp::probe_mma(sms, what, ops_per_s, s);
   return itergp::probe_units(sms, what, ops_per_s, s);

@@ -489,7 +489,8 @@ def selftest_wait(limit_ns=20_000_000, stream=None):
 
 PROBES = {"ex2": 0, "ffma": 1, "mma_ss_n128": 2, "mma_ss_n256": 3, "mma_ss_n128_tmem_ld": 4,
           "mma_ts_n80": 5, "mma_ss_n128_tf32": 6, "dfma": 7, "rsqrt": 8,
-          "pair_mma_ss_n128_f16": 9, "pair_mma_ss_n256_f16": 10, "pair_mma_ts_n80": 11}
+          "pair_mma_ss_n128_f16": 9, "pair_mma_ss_n256_f16": 10, "pair_mma_ts_n80": 11,
+          "pair_mma_ss_n192_f16": 12, "ring_pair_n128": 13, "ring_pair_n192": 14}
 _PROBE_LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libitergp_probe.so")
 _probe_lib = None
 

@@ -206,7 +206,7 @@ def test_throughput_probe_rejects_bad_arguments():
     f.restype = ct.c_int
     f.argtypes = [ct.c_int32, ct.POINTER(ct.c_double), ct.c_void_p]
     out = ct.c_double()
-    for what in (-1, 12, 99):
+    for what in (-1, 15, 99):
         assert f(what, ct.byref(out), None) == -1
     assert f(0, None, None) == -1
 
