@@ -32,7 +32,7 @@ struct FitState {
   int total_iters;
   int stop_reason;
   int status;
-  int pad_;
+  int zdone;           // blocks of zproj_kernel finished in this iteration (the last resets it)
   double alpha, eta, coef, inv_sqrt_eta;
   double bnorm, thresh, rnorm;
   int iters[ITERGP_MAX_REPORT_STEPS];
@@ -324,16 +324,30 @@ __global__ void gram_partial_kernel(const ProbDev* __restrict__ probs, int tiles
 }
 
 // ---------------------------------------------------------------- FP64 Jacobi (1 CTA)
-// Cyclic Jacobi with round-robin (tournament) pairing: in each round the n/2 disjoint
-// pairs are rotated simultaneously; column rotations then row rotations, each thread
-// owning the two elements it updates.  A (n x n) is overwritten by a near-diagonal
-// matrix, V accumulates the rotations (A_in = V diag V^T).
-__device__ void jacobi_eig(double* A, double* V, int n, int ld, double* cs, double* sn, int* partner,
-                           int* role, double* sh) {
+// Cyclic Jacobi with round-robin (tournament) pairing: in each round the m/2 disjoint pairs
+// (m = n rounded up to even; index n is a dummy) are rotated simultaneously.  A rotation
+// J_k acts on the index pair (lo_k, hi_k); the pairs partition the indices, so A' = J^T A J
+// splits into independent 2 x 2 blocks A[{lo_a, hi_a}, {lo_b, hi_b}] <- J_a^T X J_b.  Each
+// thread updates whole blocks of the upper block triangle and mirrors them (A stays exactly
+// symmetric), half the FP64 work of separate column and row passes; the rotated pairs'
+// diagonal entries take the usual t-form (a_pp - t a_pq, a_qq + t a_pq) and their
+// off-diagonal entry is set to 0.  A rotation whose off-diagonal entry is below 1e-18 of
+// the geometric mean of its diagonal is replaced by setting that entry to 0.  V accumulates
+// the rotations (A_in = V diag V^T).  The SM's FP64 rate bounds the routine.
+__device__ __forceinline__ void rr_pair(int k, int r, int m, int* lo, int* hi) {
+  const int i0 = k, i1 = m - 1 - k;
+  const int p = (i0 == 0) ? 0 : ((i0 - 1 + r) % (m - 1)) + 1;
+  const int q = ((i1 - 1 + r) % (m - 1)) + 1;
+  *lo = p < q ? p : q;
+  *hi = p < q ? q : p;
+}
+
+__device__ void jacobi_eig(double* A, double* V, int n, int ld, double* cs, double* sn, int* plo, int* phi,
+                           double* sh) {
   const int tid = threadIdx.x, nt = blockDim.x;
   const int m = (n + 1) / 2 * 2;   // even number of players (index n is a dummy if n odd)
+  const int h = m / 2;
   for (int e = tid; e < n * n; e += nt) V[(e / n) * ld + e % n] = (e / n == e % n) ? 1.0 : 0.0;
-  __syncthreads();
   double fro = 0.0;
   for (int e = tid; e < n * n; e += nt) {
     const double a = A[(e / n) * ld + e % n];
@@ -348,9 +362,9 @@ __device__ void jacobi_eig(double* A, double* V, int n, int ld, double* cs, doub
     double off = 0.0;
     for (int e = tid; e < n * n; e += nt) {
       const int i = e / n, j = e % n;
-      if (i != j) {
+      if (i < j) {
         const double a = A[i * ld + j];
-        off += a * a;
+        off += 2.0 * a * a;
       }
     }
     off = block_reduce_sum(off, sh);
@@ -358,71 +372,84 @@ __device__ void jacobi_eig(double* A, double* V, int n, int ld, double* cs, doub
     __syncthreads();
     if (off_s <= tol2 || off_s == 0.0) break;
     for (int r = 0; r < m - 1; ++r) {
-      // pairs of this round
-      for (int k = tid; k < m / 2; k += nt) {
-        const int i0 = k, i1 = m - 1 - k;
-        const int p = (i0 == 0) ? 0 : ((i0 - 1 + r) % (m - 1)) + 1;
-        const int q = ((i1 - 1 + r) % (m - 1)) + 1;
-        const int lo = p < q ? p : q, hi = p < q ? q : p;
+      // the round's pairs and rotations; sn = 0 marks a pair left as it is
+      for (int k = tid; k < h; k += nt) {
+        int lo, hi;
+        rr_pair(k, r, m, &lo, &hi);
+        plo[k] = lo;
+        phi[k] = hi;
         double c = 1.0, s = 0.0;
         if (hi < n) {
           const double apq = A[lo * ld + hi];
           if (apq != 0.0) {
             const double app = A[lo * ld + lo], aqq = A[hi * ld + hi];
-            const double theta = (aqq - app) / (2.0 * apq);
-            const double t = (theta >= 0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
-            c = 1.0 / sqrt(t * t + 1.0);
-            s = t * c;
+            if (fabs(apq) <= 1e-18 * sqrt(fabs(app * aqq))) {
+              A[lo * ld + hi] = 0.0;   // negligible: this pair's block is this thread's alone
+              A[hi * ld + lo] = 0.0;
+            } else {
+              const double theta = (aqq - app) / (2.0 * apq);
+              const double t = (theta >= 0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
+              c = 1.0 / sqrt(t * t + 1.0);
+              s = t * c;
+            }
           }
         }
         cs[k] = c;
         sn[k] = s;
-        if (lo < n) { partner[lo] = hi; role[lo] = k; }
-        if (hi < n) { partner[hi] = lo; role[hi] = -k - 1; }
       }
       __syncthreads();
-      // columns: A[:, lo] = c A[:, lo] - s A[:, hi]; A[:, hi] = s A[:, lo] + c A[:, hi]
-      for (int e = tid; e < n * (m / 2); e += nt) {
-        const int row = e / (m / 2), k = e % (m / 2);
-        const double c = cs[k], s = sn[k];
-        if (s == 0.0) continue;
-        const int i0 = k, i1 = m - 1 - k;
-        const int p = (i0 == 0) ? 0 : ((i0 - 1 + r) % (m - 1)) + 1;
-        const int q = ((i1 - 1 + r) % (m - 1)) + 1;
-        const int lo = p < q ? p : q, hi = p < q ? q : p;
-        if (hi >= n) continue;
-        const double x = A[row * ld + lo], y = A[row * ld + hi];
-        A[row * ld + lo] = c * x - s * y;
-        A[row * ld + hi] = s * x + c * y;
-        const double vx = V[row * ld + lo], vy = V[row * ld + hi];
-        V[row * ld + lo] = c * vx - s * vy;
-        V[row * ld + hi] = s * vx + c * vy;
-      }
-      __syncthreads();
-      // rows: A[lo, :] = c A[lo, :] - s A[hi, :]; A[hi, :] = s A[lo, :] + c A[hi, :]
-      for (int e = tid; e < n * (m / 2); e += nt) {
-        const int col = e / (m / 2), k = e % (m / 2);
-        const double c = cs[k], s = sn[k];
-        if (s == 0.0) continue;
-        const int i0 = k, i1 = m - 1 - k;
-        const int p = (i0 == 0) ? 0 : ((i0 - 1 + r) % (m - 1)) + 1;
-        const int q = ((i1 - 1 + r) % (m - 1)) + 1;
-        const int lo = p < q ? p : q, hi = p < q ? q : p;
-        if (hi >= n) continue;
-        const double x = A[lo * ld + col], y = A[hi * ld + col];
-        A[lo * ld + col] = c * x - s * y;
-        A[hi * ld + col] = s * x + c * y;
-      }
-      __syncthreads();
-      // the rotated pair's off-diagonal entries are zero in exact arithmetic
-      for (int k = tid; k < m / 2; k += nt) {
-        const int i0 = k, i1 = m - 1 - k;
-        const int p = (i0 == 0) ? 0 : ((i0 - 1 + r) % (m - 1)) + 1;
-        const int q = ((i1 - 1 + r) % (m - 1)) + 1;
-        if (p < n && q < n && sn[k] != 0.0) {
-          A[p * ld + q] = 0.0;
-          A[q * ld + p] = 0.0;
+      // A <- J^T A J by 2 x 2 blocks (a <= b), mirrored; V <- V J (rows x pairs)
+      for (int e = tid; e < h * h; e += nt) {
+        const int a = e / h, b = e % h;
+        if (b < a) continue;
+        const double s1 = sn[a], s2 = sn[b];
+        if (s1 == 0.0 && s2 == 0.0) continue;
+        const double c1 = cs[a], c2 = cs[b];
+        const int p1 = plo[a], q1 = phi[a], p2 = plo[b], q2 = phi[b];
+        const bool v1 = q1 < n, v2 = q2 < n;   // the dummy index has no row or column
+        if (a == b) {   // the rotated pair itself: t-form of the new diagonal, zero off-diagonal
+          const double apq = A[p1 * ld + q1];
+          const double t = s1 / c1;
+          A[p1 * ld + p1] -= t * apq;
+          A[q1 * ld + q1] += t * apq;
+          A[p1 * ld + q1] = 0.0;
+          A[q1 * ld + p1] = 0.0;
+          continue;
         }
+        const double x00 = A[p1 * ld + p2];
+        const double x01 = v2 ? A[p1 * ld + q2] : 0.0;
+        const double x10 = v1 ? A[q1 * ld + p2] : 0.0;
+        const double x11 = (v1 && v2) ? A[q1 * ld + q2] : 0.0;
+        // X J_2: columns (p2, q2)
+        const double y00 = c2 * x00 - s2 * x01, y01 = s2 * x00 + c2 * x01;
+        const double y10 = c2 * x10 - s2 * x11, y11 = s2 * x10 + c2 * x11;
+        // J_1^T (X J_2): rows (p1, q1)
+        const double z00 = c1 * y00 - s1 * y10, z01 = c1 * y01 - s1 * y11;
+        const double z10 = s1 * y00 + c1 * y10, z11 = s1 * y01 + c1 * y11;
+        A[p1 * ld + p2] = z00;
+        A[p2 * ld + p1] = z00;
+        if (v2) {
+          A[p1 * ld + q2] = z01;
+          A[q2 * ld + p1] = z01;
+        }
+        if (v1) {
+          A[q1 * ld + p2] = z10;
+          A[p2 * ld + q1] = z10;
+        }
+        if (v1 && v2) {
+          A[q1 * ld + q2] = z11;
+          A[q2 * ld + q1] = z11;
+        }
+      }
+      for (int e = tid; e < n * h; e += nt) {
+        const int row = e / h, k = e % h;
+        const double s = sn[k];
+        if (s == 0.0) continue;
+        const int lo = plo[k], hi = phi[k];
+        const double c = cs[k];
+        const double x = V[row * ld + lo], y = V[row * ld + hi];
+        V[row * ld + lo] = c * x - s * y;
+        V[row * ld + hi] = s * x + c * y;
       }
       __syncthreads();
     }
@@ -443,10 +470,24 @@ __device__ void eig_order(const double* A, int n, int ld, int* order) {
   __syncthreads();
 }
 
+// Shared memory of the eigensolver kernels: rotations, pairs, order (b = largest buffer);
+// with ab_smem, also A and V (FP64) of a b x b problem.
+__host__ __device__ inline size_t eig_smem_base(int b) {
+  return (sizeof(double) * (2 * (b / 2 + 1) + 32) + sizeof(int) * (3 * (b + 1)) + 15) / 16 * 16;
+}
+inline size_t eig_smem_bytes(int b, bool ab_smem = false) {
+  return eig_smem_base(b) + (ab_smem ? static_cast<size_t>(b) * b * 2 * sizeof(double) : 0);
+}
+// Buffers up to this size keep A and V in shared memory (200 KB at 112).
+constexpr int kEigSmemMax = 112;
+
 // Sum Gram partials, symmetrise, eigendecompose, drop lambda <= 1e-12 lambda_max, keep
 // the R largest (Alg. 3), write rotation W[b][k] = U[b][k] lambda_k^-1/2 (FP32) and
-// sqrt(lambda_k); set B = B0 = kept columns.
-__global__ void vsr_eig_kernel(const ProbDev* __restrict__ probs, int splits, int rank, int step) {
+// sqrt(lambda_k); set B = B0 = kept columns.  ab_smem: the launch gave room for A and V in
+// shared memory.  (V stays FP64: a kept eigenvalue may be 1e-12 of the largest, and the
+// rotation W = U lambda^-1/2 magnifies an eigenvector's error by up to lambda_max /
+// lambda_k in the K-hat inner products of the compressed buffer.)
+__global__ void vsr_eig_kernel(const ProbDev* __restrict__ probs, int splits, int rank, int step, int ab_smem) {
   const ProbDev& P = probs[blockIdx.x];
   FitState* st = P.st;
   const double* __restrict__ part = P.pg;
@@ -461,13 +502,21 @@ __global__ void vsr_eig_kernel(const ProbDev* __restrict__ probs, int splits, in
     if (threadIdx.x == 0 && step < ITERGP_MAX_REPORT_STEPS) st->kept[step] = 0;
     return;
   }
-  extern __shared__ double dsh[];
-  double* cs = dsh;                 // bcap/2 + 1
-  double* sn = cs + bcap / 2 + 1;   // bcap/2 + 1
-  double* red = sn + bcap / 2 + 1;  // 32
-  int* partner = reinterpret_cast<int*>(red + 32);
-  int* role = partner + bcap + 1;
-  int* order = role + bcap + 1;
+  extern __shared__ __align__(16) uint8_t esh[];
+  double* cs = reinterpret_cast<double*>(esh);   // bcap/2 + 1
+  double* sn = cs + bcap / 2 + 1;                // bcap/2 + 1
+  double* red = sn + bcap / 2 + 1;               // 32
+  int* plo = reinterpret_cast<int*>(red + 32);
+  int* phi = plo + bcap + 1;
+  int* order = phi + bcap + 1;
+  double* A = Amat;
+  double* V = Vmat;
+  int ld = bcap;
+  if (ab_smem) {   // B <= bcap <= kEigSmemMax: compact B x B copies in shared memory
+    A = reinterpret_cast<double*>(esh + eig_smem_base(bcap));
+    V = A + B * B;
+    ld = B;
+  }
   for (int e = threadIdx.x; e < B * B; e += blockDim.x) {
     const int a = e / B, b = e % B;
     double s1 = 0.0, s2 = 0.0;
@@ -475,16 +524,16 @@ __global__ void vsr_eig_kernel(const ProbDev* __restrict__ probs, int splits, in
       s1 += part[static_cast<int64_t>(sp) * bcap * bcap + a * bcap + b];
       s2 += part[static_cast<int64_t>(sp) * bcap * bcap + b * bcap + a];
     }
-    Amat[a * bcap + b] = 0.5 * (s1 + s2);
+    A[a * ld + b] = 0.5 * (s1 + s2);
   }
   __syncthreads();
-  jacobi_eig(Amat, Vmat, B, bcap, cs, sn, partner, role, red);
-  eig_order(Amat, B, bcap, order);
+  jacobi_eig(A, V, B, ld, cs, sn, plo, phi, red);
+  eig_order(A, B, ld, order);
   __shared__ int keep_s;
   if (threadIdx.x == 0) {
-    const double lmax = Amat[order[0] * bcap + order[0]];
+    const double lmax = A[order[0] * ld + order[0]];
     int keep = 0;
-    while (keep < B && Amat[order[keep] * bcap + order[keep]] > 1e-12 * fmax(lmax, 0.0)) ++keep;
+    while (keep < B && A[order[keep] * ld + order[keep]] > 1e-12 * fmax(lmax, 0.0)) ++keep;
     if (rank >= 0 && keep > rank) keep = rank;
     keep_s = keep;
     st->B = keep;
@@ -495,11 +544,11 @@ __global__ void vsr_eig_kernel(const ProbDev* __restrict__ probs, int splits, in
   const int keep = keep_s;
   for (int e = threadIdx.x; e < B * keep; e += blockDim.x) {
     const int b = e / keep, k = e % keep;
-    const double lam = Amat[order[k] * bcap + order[k]];
-    W[b * bcap + k] = static_cast<float>(Vmat[b * bcap + order[k]] / sqrt(lam));
+    const double lam = A[order[k] * ld + order[k]];
+    W[b * bcap + k] = static_cast<float>(V[b * ld + order[k]] / sqrt(lam));
   }
   for (int k = threadIdx.x; k < keep; k += blockDim.x)
-    sq[k] = static_cast<float>(sqrt(Amat[order[k] * bcap + order[k]]));
+    sq[k] = static_cast<float>(sqrt(A[order[k] * ld + order[k]]));
 }
 
 // Q[:, k] = sum_b S[:, b] W[b][k];  KQ[:, k] = sum_b T[:, b] W[b][k]   (k < B_new, b < B_old)
@@ -730,10 +779,11 @@ __global__ void resid_finalize_kernel(const ProbDev* __restrict__ probs, int nbl
 
 // T[:, B] = t; z = t + W^+ s (Lemma A.6) over a block's segment of whole points, then the
 // block's partial sums of Q_k^T z over the same segment (k < B), as proj_partial_kernel
-// does for Alg. 3's projection.
+// does for Alg. 3's projection.  The last block to finish adds the partial sums in block
+// order into w = Q^T z (FP64 sums, rounded once).
 __global__ void zproj_kernel(const ProbDev* __restrict__ probs) {
   const ProbDev& P = probs[blockIdx.y];
-  const FitState* st = P.st;
+  FitState* st = P.st;
   const int64_t n = P.n;
   const int C = P.c;
   const float* __restrict__ s_cur = P.s_cur;
@@ -770,19 +820,31 @@ __global__ void zproj_kernel(const ProbDev* __restrict__ probs) {
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
     if (l == 0) part[static_cast<int64_t>(blockIdx.x) * bcap + k] = acc;
   }
+  __shared__ int last_s;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) last_s = atomicAdd(&st->zdone, 1) == static_cast<int>(gridDim.x) - 1;
+  __syncthreads();
+  if (last_s) {
+    __threadfence();
+    for (int k = threadIdx.x; k < B; k += blockDim.x) {
+      double sum = 0.0;
+      for (int b = 0; b < static_cast<int>(gridDim.x); ++b) sum += __ldcg(part + static_cast<int64_t>(b) * bcap + k);
+      P.w[k] = static_cast<float>(sum);
+    }
+    if (threadIdx.x == 0) st->zdone = 0;
+  }
 }
 
 // d = s - Q w -> Q[:, B] (unnormalised); K d = t - KQ w -> KQ[:, B]; partial eta = z.d
-// Every block first adds the nblk partial sums of Q^T z (zproj_kernel) itself, in block
-// order, into w = Q^T z (block 0 also stores it).
-__global__ void direction_kernel(const ProbDev* __restrict__ probs, int track_kd, int nblk) {
+// (w = Q^T z from zproj_kernel).
+__global__ void direction_kernel(const ProbDev* __restrict__ probs, int track_kd) {
   const ProbDev& P = probs[blockIdx.y];
   const FitState* st = P.st;
   const int64_t nc = P.nc;
   const float* __restrict__ s_cur = P.s_cur;
   const float* __restrict__ t_cur = P.t_cur;
   const float* __restrict__ z = P.z;
-  const double* __restrict__ pv = P.pv;
   float* __restrict__ Q = P.Q;
   float* __restrict__ KQ = P.KQ;
   double* __restrict__ part = P.ps;
@@ -790,13 +852,7 @@ __global__ void direction_kernel(const ProbDev* __restrict__ probs, int track_kd
   __shared__ double sh[32];
   __shared__ float w[kMaxBcap];
   const int B = st->B;
-  const int bcap = P.bcap;
-  for (int k = threadIdx.x; k < B; k += blockDim.x) {
-    double sum = 0.0;
-    for (int b = 0; b < nblk; ++b) sum += pv[static_cast<int64_t>(b) * bcap + k];
-    w[k] = static_cast<float>(sum);
-    if (blockIdx.x == 0) P.w[k] = w[k];
-  }
+  for (int k = threadIdx.x; k < B; k += blockDim.x) w[k] = P.w[k];
   __syncthreads();
   float* qcol = Q + static_cast<int64_t>(B) * nc;
   float* kcol = KQ + static_cast<int64_t>(B) * nc;
@@ -947,29 +1003,25 @@ __global__ void pseudo_targets_kernel(const float* __restrict__ f, const int32_t
 
 __global__ void sym_eig_kernel(const double* __restrict__ M, int b, double* __restrict__ lam,
                                double* __restrict__ U, double* __restrict__ A, double* __restrict__ V) {
-  extern __shared__ double dsh[];
-  double* cs = dsh;
+  extern __shared__ __align__(16) uint8_t esh[];
+  double* cs = reinterpret_cast<double*>(esh);
   double* sn = cs + b / 2 + 1;
   double* red = sn + b / 2 + 1;
-  int* partner = reinterpret_cast<int*>(red + 32);
-  int* role = partner + b + 1;
-  int* order = role + b + 1;
+  int* plo = reinterpret_cast<int*>(red + 32);
+  int* phi = plo + b + 1;
+  int* order = phi + b + 1;
   for (int e = threadIdx.x; e < b * b; e += blockDim.x) {
     const int i = e / b, j = e % b;
     A[i * b + j] = 0.5 * (M[i * b + j] + M[j * b + i]);
   }
   __syncthreads();
-  jacobi_eig(A, V, b, b, cs, sn, partner, role, red);
+  jacobi_eig(A, V, b, b, cs, sn, plo, phi, red);
   eig_order(A, b, b, order);
   for (int e = threadIdx.x; e < b * b; e += blockDim.x) {
     const int i = e / b, k = e % b;
     U[i * b + k] = V[i * b + order[k]];
   }
   for (int k = threadIdx.x; k < b; k += blockDim.x) lam[k] = A[order[k] * b + order[k]];
-}
-
-inline size_t eig_smem_bytes(int b) {
-  return sizeof(double) * (2 * (b / 2 + 1) + 32) + sizeof(int) * (3 * (b + 1));
 }
 
 // ------------------------------------------------------------ batched product staging
@@ -1130,8 +1182,10 @@ int fit_run_batch(DeviceContext* ctx, const std::vector<FitProblem>& probs, cuda
     c_max = std::max(c_max, static_cast<int>(fp.prm->c));
     d_max = std::max(d_max, static_cast<int>(fp.prm->d));
   }
-  const int nblk = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(2LL * ctx->num_sms, ceil_div(max_n, 256))));
-  const int nblk_e = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(2LL * ctx->num_sms, ceil_div(max_nc, 1024))));
+  // Blocks of the per-iteration vector kernels: enough to spread small problems over many
+  // SMs (their FP64 partial sums run at the SM's low FP64 rate), at most two per SM.
+  const int nblk = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(2LL * ctx->num_sms, ceil_div(max_n, 64))));
+  const int nblk_e = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(2LL * ctx->num_sms, ceil_div(max_nc, 64))));
   const int gram_splits = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(64, ceil_div(max_nc, 4096))));
   const int eb = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(ceil_div(max_nc, 256), 8LL * ctx->num_sms)));
   const int maxblk = std::max(nblk, nblk_e);
@@ -1342,8 +1396,11 @@ int fit_run_batch(DeviceContext* ctx, const std::vector<FitProblem>& probs, cuda
     return kmv_simt_items(ctx, bp.kind, bp.arena, bp.arena, bp.tab, bp.s32, c_max, c_max, stream);
   };
 
-  const size_t eig_smem = eig_smem_bytes(max_bcap);
+  const bool eig_ab_smem = max_bcap <= kEigSmemMax;
+  const size_t eig_smem = eig_smem_bytes(max_bcap, eig_ab_smem);
   const int eig_threads = 512;
+  ITERGP_CUDA_TRY(cudaFuncSetAttribute(vsr_eig_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       static_cast<int>(eig_smem)));
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   // The schedule is captured on a private stream (the caller's may be the legacy default
@@ -1370,7 +1427,8 @@ int fit_run_batch(DeviceContext* ctx, const std::vector<FitProblem>& probs, cuda
       copy_int_kernel<<<np, 32, 0, stream>>>(pdev), ::itergp::note_launch();
       vsr_z_kernel<<<dim3(eb, np), 256, 0, stream>>>(pdev), ::itergp::note_launch();
       gram_partial_kernel<<<dim3(tiles * tiles, gram_splits, np), 256, 0, stream>>>(pdev, tiles), ::itergp::note_launch();
-      vsr_eig_kernel<<<np, eig_threads, eig_smem, stream>>>(pdev, gram_splits, prm.rank, step), ::itergp::note_launch();
+      vsr_eig_kernel<<<np, eig_threads, eig_smem, stream>>>(pdev, gram_splits, prm.rank, step, eig_ab_smem ? 1 : 0),
+          ::itergp::note_launch();
       vsr_rotate_kernel<<<dim3(eb, np), 256, 0, stream>>>(pdev), ::itergp::note_launch();
       vsr_rescale_kernel<<<dim3(eb, np), 256, 0, stream>>>(pdev), ::itergp::note_launch();
       // v0 = Q0 (Q0^T b), u0 = K v0 = KQ0 (Q0^T b)
@@ -1393,7 +1451,7 @@ int fit_run_batch(DeviceContext* ctx, const std::vector<FitProblem>& probs, cuda
       rc = products();
       if (rc != ITERGP_OK) break;
       zproj_kernel<<<dim3(nblk_e, np), 256, 0, stream>>>(pdev), ::itergp::note_launch();
-      direction_kernel<<<dim3(nblk_e, np), kRedThreads, 0, stream>>>(pdev, track_kd, nblk_e), ::itergp::note_launch();
+      direction_kernel<<<dim3(nblk_e, np), kRedThreads, 0, stream>>>(pdev, track_kd), ::itergp::note_launch();
       update_kernel<<<dim3(eb, np), 256, 0, stream>>>(pdev, track_kd, nblk_e), ::itergp::note_launch();
     }
     if (rc != ITERGP_OK) break;
