@@ -333,7 +333,39 @@ __global__ void gram_partial_kernel(const ProbDev* __restrict__ probs, int tiles
 // diagonal entries take the usual t-form (a_pp - t a_pq, a_qq + t a_pq) and their
 // off-diagonal entry is set to 0.  A rotation whose off-diagonal entry is below 1e-18 of
 // the geometric mean of its diagonal is replaced by setting that entry to 0.  V accumulates
-// the rotations (A_in = V diag V^T).  The SM's FP64 rate bounds the routine.
+// the rotations (A_in = V diag V^T).  The SM's FP64 rate bounds the routine (one SM has
+// about 1.7 FP64 FMA per cycle here).
+// Rotation (c, s) = (1, t) / sqrt(1 + t^2) that zeroes a_pq, t the smaller root of
+// a_pq t^2 + (a_qq - a_pp) t - a_pq = 0.  The operands are scaled by a power of two into
+// [-1, 1]; t is found in FP32 and polished by one FP64 Newton step on the quadratic, and
+// 1 / sqrt(1 + t^2) by two FP64 Newton steps from an FP32 seed: a few FP64 operations in
+// place of the FP64 divisions and square roots (each a long sequence on this GPU's small
+// FP64 unit), with t and c accurate to FP64 rounding.
+__device__ __forceinline__ void jacobi_rotation(double app, double aqq, double apq, double* c_out, double* s_out) {
+  const double mx = fmax(fmax(fabs(app), fabs(aqq)), fabs(apq));
+  const int ex = static_cast<int>((__double_as_longlong(mx) >> 52) & 0x7FF) - 1023;   // mx = m 2^ex, m in [1, 2)
+  const double sc = __longlong_as_double(static_cast<long long>(1023 - ex - 1) << 52);   // 2^-(ex + 1)
+  const double a = apq * sc, d = (aqq - app) * sc;   // |a| < 1, |d| < 2
+  const float a32 = static_cast<float>(a), d32 = static_cast<float>(d);
+  float t32;
+  if (a32 == 0.f) {
+    t32 = 0.f;
+  } else {
+    const float th = d32 / (2.f * a32);
+    t32 = fabsf(th) > 1e18f ? 0.5f / th : copysignf(1.f, th) / (fabsf(th) + sqrtf(fmaf(th, th, 1.f)));
+  }
+  double t = t32;
+  const double q = fma(a * t, t, fma(d, t, -a));        // a t^2 + d t - a
+  const double qp = fma(2.0 * a, t, d);                 // its derivative (|qp| >= 2|a| at the root)
+  t -= q * static_cast<double>(1.f / static_cast<float>(qp));
+  const double y = fma(t, t, 1.0);                      // in [1, 2]
+  double r = static_cast<double>(rsqrtf(static_cast<float>(y)));
+  r = r * fma(-0.5 * y, r * r, 1.5);
+  r = r * fma(-0.5 * y, r * r, 1.5);
+  *c_out = r;
+  *s_out = t * r;
+}
+
 __device__ __forceinline__ void rr_pair(int k, int r, int m, int* lo, int* hi) {
   const int i0 = k, i1 = m - 1 - k;
   const int p = (i0 == 0) ? 0 : ((i0 - 1 + r) % (m - 1)) + 1;
@@ -383,14 +415,11 @@ __device__ void jacobi_eig(double* A, double* V, int n, int ld, double* cs, doub
           const double apq = A[lo * ld + hi];
           if (apq != 0.0) {
             const double app = A[lo * ld + lo], aqq = A[hi * ld + hi];
-            if (fabs(apq) <= 1e-18 * sqrt(fabs(app * aqq))) {
+            if (apq * apq <= 1e-36 * fabs(app * aqq)) {
               A[lo * ld + hi] = 0.0;   // negligible: this pair's block is this thread's alone
               A[hi * ld + lo] = 0.0;
             } else {
-              const double theta = (aqq - app) / (2.0 * apq);
-              const double t = (theta >= 0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
-              c = 1.0 / sqrt(t * t + 1.0);
-              s = t * c;
+              jacobi_rotation(app, aqq, apq, &c, &s);
             }
           }
         }
@@ -398,10 +427,13 @@ __device__ void jacobi_eig(double* A, double* V, int n, int ld, double* cs, doub
         sn[k] = s;
       }
       __syncthreads();
-      // A <- J^T A J by 2 x 2 blocks (a <= b), mirrored; V <- V J (rows x pairs)
-      for (int e = tid; e < h * h; e += nt) {
-        const int a = e / h, b = e % h;
-        if (b < a) continue;
+      // A <- J^T A J by 2 x 2 blocks (a <= b, enumerated densely: e = b (b + 1) / 2 + a),
+      // mirrored; V <- V J (rows x pairs)
+      for (int e = tid; e < h * (h + 1) / 2; e += nt) {
+        int b = static_cast<int>((sqrtf(8.f * static_cast<float>(e) + 1.f) - 1.f) * 0.5f);
+        if ((b + 1) * (b + 2) / 2 <= e) ++b;
+        if (b * (b + 1) / 2 > e) --b;
+        const int a = e - b * (b + 1) / 2;
         const double s1 = sn[a], s2 = sn[b];
         if (s1 == 0.0 && s2 == 0.0) continue;
         const double c1 = cs[a], c2 = cs[b];
