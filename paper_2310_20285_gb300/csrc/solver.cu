@@ -811,8 +811,8 @@ __global__ void resid_finalize_kernel(const ProbDev* __restrict__ probs, int nbl
 
 // T[:, B] = t; z = t + W^+ s (Lemma A.6) over a block's segment of whole points, then the
 // block's partial sums of Q_k^T z over the same segment (k < B), as proj_partial_kernel
-// does for Alg. 3's projection.  The last block to finish adds the partial sums in block
-// order into w = Q^T z (FP64 sums, rounded once).
+// does for Alg. 3's projection.  The last block to finish adds the partial sums (FP64, in a
+// fixed order) into w = Q^T z, rounded once.
 __global__ void zproj_kernel(const ProbDev* __restrict__ probs) {
   const ProbDev& P = probs[blockIdx.y];
   FitState* st = P.st;
@@ -857,12 +857,14 @@ __global__ void zproj_kernel(const ProbDev* __restrict__ probs) {
   __syncthreads();
   if (threadIdx.x == 0) last_s = atomicAdd(&st->zdone, 1) == static_cast<int>(gridDim.x) - 1;
   __syncthreads();
-  if (last_s) {
+  if (last_s) {   // one warp per column k: lanes take strided blocks, then a fixed shuffle tree
     __threadfence();
-    for (int k = threadIdx.x; k < B; k += blockDim.x) {
+    for (int k = wp; k < B; k += nw) {
       double sum = 0.0;
-      for (int b = 0; b < static_cast<int>(gridDim.x); ++b) sum += __ldcg(part + static_cast<int64_t>(b) * bcap + k);
-      P.w[k] = static_cast<float>(sum);
+      for (int b = l; b < static_cast<int>(gridDim.x); b += 32) sum += __ldcg(part + static_cast<int64_t>(b) * bcap + k);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+      if (l == 0) P.w[k] = static_cast<float>(sum);
     }
     if (threadIdx.x == 0) st->zdone = 0;
   }
@@ -892,7 +894,22 @@ __global__ void direction_kernel(const ProbDev* __restrict__ probs, int track_kd
   for (int64_t e = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; e < nc;
        e += static_cast<int64_t>(gridDim.x) * blockDim.x) {
     float d = s_cur[e], kd = t_cur[e];
-    for (int k = 0; k < B; ++k) {
+    int k = 0;
+    // eight columns' loads in flight at a time (the loop is bound by load latency)
+    for (; k + 8 <= B; k += 8) {
+      float qv[8], kv[8];
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        qv[i] = Q[(k + i) * nc + e];
+        kv[i] = track_kd ? KQ[(k + i) * nc + e] : 0.f;
+      }
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        d = fmaf(-qv[i], w[k + i], d);
+        kd = fmaf(-kv[i], w[k + i], kd);
+      }
+    }
+    for (; k < B; ++k) {
       d = fmaf(-Q[k * nc + e], w[k], d);
       if (track_kd) kd = fmaf(-KQ[k * nc + e], w[k], kd);
     }
