@@ -19,10 +19,12 @@ def rel(a, b):
     return float(np.linalg.norm(a - b) / np.linalg.norm(b))
 
 
-@pytest.mark.parametrize("prec,tol", [("fp32", 1e-4), ("bf16x3", 1e-2)])
+@pytest.mark.parametrize("prec,tol", [("fp32", 1e-4), ("bf16x3", 1e-4)])
 def test_full_size_product_rows(native, prec, tol):
     """l = 0.05 against |x| ~ 2: the |a|^2 + |b|^2 - 2 a.b form loses digits to
-    cancellation (CPU emulation of the FP32 form: 3e-5; of the BF16X3 split: 2.6e-3)."""
+    cancellation (CPU emulation of the FP32 form: 3e-5).  The split rows keep 22
+    significant bits (FP16 hi and lo with a power-of-two scale per row tile), so BF16X3
+    is held to the FP32 bar here too."""
     X, _ = datagen.gmm3d(10000, seed_model=1, seed_draw=2)
     X = X.astype(np.float32)
     S = datagen.normal((X.shape[0], 10), 5)
