@@ -1231,10 +1231,13 @@ int fit_run_batch(DeviceContext* ctx, const std::vector<FitProblem>& probs, cuda
     c_max = std::max(c_max, static_cast<int>(fp.prm->c));
     d_max = std::max(d_max, static_cast<int>(fp.prm->d));
   }
-  // Blocks of the per-iteration vector kernels: enough to spread small problems over many
-  // SMs (their FP64 partial sums run at the SM's low FP64 rate), at most two per SM.
-  const int nblk = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(2LL * ctx->num_sms, ceil_div(max_n, 64))));
-  const int nblk_e = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(2LL * ctx->num_sms, ceil_div(max_nc, 64))));
+  // Blocks of the per-iteration vector kernels, at most two per SM: a single problem spreads
+  // even small vectors over many SMs (their FP64 partial sums run at the SM's low FP64
+  // rate); a batch, whose grid repeats the largest problem's block count for every
+  // problem, takes fewer, larger blocks.
+  const int64_t per_pt = np > 1 ? 256 : 64, per_el = np > 1 ? 1024 : 64;
+  const int nblk = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(2LL * ctx->num_sms, ceil_div(max_n, per_pt))));
+  const int nblk_e = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(2LL * ctx->num_sms, ceil_div(max_nc, per_el))));
   const int gram_splits = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(64, ceil_div(max_nc, 4096))));
   const int eb = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(ceil_div(max_nc, 256), 8LL * ctx->num_sms)));
   const int maxblk = std::max(nblk, nblk_e);
