@@ -75,7 +75,7 @@ def parse():
     ap.add_argument("--no-extras", action="store_true", help="skip other precisions and fit timings")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--batch-count", type=int, default=256, help="problems of the batched-fit extra")
-    ap.add_argument("--serve-seconds", type=float, default=20.0, help="arrival window of the serving extra")
+    ap.add_argument("--serve-seconds", type=float, default=60.0, help="arrival window of the serving extra")
     ap.add_argument("--no-tune", action="store_true", help="skip autotuning the product's launch variants")
     return ap.parse_args()
 
@@ -731,6 +731,7 @@ def bench_serving(native, datagen, precision, seconds, seed=5, drain_s=10.0):
                         c_max=5, max_fit_batch=64, max_predict_batch=512, max_predict_rows=1 << 18,
                         max_newton=5, max_iters=5, rank=50, graph=True)
     resident, lat = [], {0: [], 1: []}
+    queue, service = {0: [], 1: []}, {0: [], 1: []}   # submission -> start, start -> done
     done_fit, skipped, kinds = 0, 0, {}
     submitted = {0: 0, 1: 0}
 
@@ -742,6 +743,8 @@ def bench_serving(native, datagen, precision, seconds, seed=5, drain_s=10.0):
             if status != 0:
                 continue
             lat[kind].append(td - ts)
+            queue[kind].append(t0 - ts)
+            service[kind].append(td - t0)
             if kind == 0:
                 resident.append(model)
                 done_fit += 1
@@ -781,11 +784,15 @@ def bench_serving(native, datagen, precision, seconds, seed=5, drain_s=10.0):
     def pct(x, q):
         return float(np.percentile(np.asarray(x), q) * 1e3) if x else None
 
+    def split(kind):   # where the latency goes: waiting for admission vs on the GPU
+        return {"queue_p50_ms": pct(queue[kind], 50), "queue_p99_ms": pct(queue[kind], 99),
+                "service_p50_ms": pct(service[kind], 50), "service_p99_ms": pct(service[kind], 99)}
+
     return {"precision": precision, "arrival_s": round(t_arr, 3), "wall_s": round(wall, 3),
             "fits": {"submitted": submitted[0], "done": len(lat[0]), "req_per_s": len(lat[0]) / wall,
-                     "p50_ms": pct(lat[0], 50), "p99_ms": pct(lat[0], 99)},
+                     "p50_ms": pct(lat[0], 50), "p99_ms": pct(lat[0], 99), **split(0)},
             "predicts": {"submitted": submitted[1], "done": len(lat[1]), "req_per_s": len(lat[1]) / wall,
-                         "p50_ms": pct(lat[1], 50), "p99_ms": pct(lat[1], 99),
+                         "p50_ms": pct(lat[1], 50), "p99_ms": pct(lat[1], 99), **split(1),
                          "skipped_no_model": skipped},
             "backlog_at_end": {"fits": st["queued_fits"], "predicts": st["queued_predicts"]},
             "fit_batches": st["fit_batches"], "predict_batches": st["predict_batches"],

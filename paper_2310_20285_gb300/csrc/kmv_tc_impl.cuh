@@ -438,16 +438,16 @@ kmv_tc_kernel(const __grid_constant__ CUtensorMap mAh, const __grid_constant__ C
       mbar_init(&full_bar[i], 1);
       mbar_init(&empty_bar[i], 1);
     }
-    // the pair form counts one arrival per epilogue warp of each CTA on the even CTA's
-    // pfull and oempty; the one-CTA form one per epilogue thread
+    // pfull and oempty count one arrival per epilogue warp (after the warp's lanes meet), of
+    // each CTA in the pair form (on the even CTA's barriers)
     for (int i = 0; i < 3; ++i) {
       mbar_init(&gfull[i], 1);
-      mbar_init(&pfull[i], PAIR ? 2 * EPI : 32 * EPI);
+      mbar_init(&pfull[i], PAIR ? 2 * EPI : EPI);
       mbar_init(&sfull[i], 1);
       mbar_init(&sempty[i], 1);
     }
     mbar_init(&ofull, 1);
-    mbar_init(&oempty, PAIR ? 2 * EPI : 32 * EPI);
+    mbar_init(&oempty, PAIR ? 2 * EPI : EPI);
     mbar_init(&drain, 1);
     mbar_init(&afull, 1);
     mbar_init(&aempty, 1);
@@ -870,11 +870,9 @@ kmv_tc_kernel(const __grid_constant__ CUtensorMap mAh, const __grid_constant__ C
       }
       tmem_st_wait();
       tc_fence_before();
-      if constexpr (PAIR) {   // one arrival per warp, on the even CTA's barrier
-        __syncwarp();
-        if (lane == 0) mbar_arrive_remote(lead(&pfull[gb]));
-      } else {
-        mbar_arrive(&pfull[gb]);
+      __syncwarp();   // one arrival per warp (the pair form's on the even CTA's barrier)
+      if (lane == 0) {
+        if constexpr (PAIR) mbar_arrive_remote(lead(&pfull[gb])); else mbar_arrive(&pfull[gb]);
       }
       if (sub_last) {
         ++sub;
@@ -958,11 +956,9 @@ kmv_tc_kernel(const __grid_constant__ CUtensorMap mAh, const __grid_constant__ C
         }
         tmem_st_wait();
         tc_fence_before();
-        if constexpr (PAIR) {
-          __syncwarp();
-          if (lane == 0) mbar_arrive_remote(lead(&oempty));
-        } else {
-          mbar_arrive(&oempty);
+        __syncwarp();
+        if (lane == 0) {
+          if constexpr (PAIR) mbar_arrive_remote(lead(&oempty)); else mbar_arrive(&oempty);
         }
         ++sub_in_seg;
       }
