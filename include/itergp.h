@@ -62,9 +62,12 @@ typedef struct {
 /* Arithmetic of the two contractions inside the kernel product (distance over D and the
  * kernel-weighted sum over the data points).  Accumulation is FP32 in every mode.
  *   ITERGP_FP32      plain FP32 SIMT (FFMA) for both contractions.
- *   ITERGP_BF16X3    tensor cores; each operand split into BF16 hi + lo parts and each
- *                    contraction formed from the three products hi*hi + hi*lo + lo*hi.
- *                    FP32-level accuracy (normwise relative error ~1e-5).
+ *   ITERGP_BF16X3    tensor cores; each operand split into 16-bit hi + lo parts (FP16 with
+ *                    a power-of-two scale per 128-row tile of the rows, per weight column,
+ *                    and for the kernel values; 22 significant bits) and each contraction
+ *                    formed from the three products hi*hi + hi*lo + lo*hi.  FP32-level
+ *                    accuracy (normwise relative error ~1e-6 on products).  The name
+ *                    keeps the first version's (BF16 parts).
  *   ITERGP_BF16      tensor cores; one BF16 product per contraction; the squared distance
  *                    uses the norms of the BF16-rounded rows.
  *   ITERGP_BF16_COMP tensor cores; split-precision (3-product) distance with FP32 norms,

@@ -1,24 +1,27 @@
-// Tensor-core kernel product Y = k(A, B) S for sm_103a (tcgen05 + TMEM + TMA).
+// Tensor-core kernel product Y = k(A, B) S for sm_103a (tcgen05 + TMEM + TMA): host side,
+// the one-CTA instantiations, the tail fix-up, the weight staging and the tuner.
 //
 // The product of App. B.3.1 is evaluated flash-style and K is never stored:
-//   for each CTA-owned (row tile of A, column chunk of B):
-//     G   = A_tile . B_chunk^T        tcgen05.mma, BF16 operands, FP32 accumulator in TMEM
-//     P   = k(|a|^2 + |b|^2 - 2 G)    epilogue warps: TMEM -> registers -> BF16 -> TMEM
+//   for each (row tile of A, column chunk of B):
+//     G   = A_tile . B_chunk^T        tcgen05.mma, 16-bit operands, FP32 accumulator in TMEM
+//     P   = k(|a|^2 + |b|^2 - 2 G)    epilogue warps: TMEM -> registers -> 16-bit -> TMEM
 //     O  += P . S_chunk               tcgen05.mma with P read from TMEM (A operand)
-// Operands are staged by TMA with 128-byte swizzle.  Split precisions use BF16 hi/lo
-// parts: a.b ~ ah.bh + ah.bl + al.bh and P S ~ Ph Sh + Ph Sl + Pl Sh.
+// Operands are staged by TMA with 128-byte swizzle.  The split precisions use FP16 hi/lo
+// parts with power-of-two scales (rows per 128-row tile, weights per column, kernel
+// values by 2^ke): a.b ~ ah.bh + ah.bl + al.bh and P S ~ Ph Sh + Ph Sl + Pl Sh.
 //
-// Warp roles (256 threads): warp 0 issues TMA loads, warp 1 issues the MMAs (one thread),
-// warp 2 owns the TMEM allocation, warps 4-7 (one per TMEM lane quadrant) run the kernel
-// evaluation and the output stores.  TMEM columns: G0 [0,128), G1 [128,256) (double
-// buffer, P aliases the G it came from), O [256, 256 + p_tile).
+// Forms (kmv_tc_impl.cuh): one CTA per 128-row tile (128-row chunks; instantiated here),
+// and CTA pairs sharing 256-row tiles through cta_group::2 MMAs with 128- or 192-row
+// chunks (kmv_tc2.cu).  Warp roles: warp 0 issues the A/B TMA loads, warp 1 the MMAs
+// (one thread), warp 2 owns TMEM, warp 3 loads the weight tiles, warps 4-7 (or 4-11) run
+// the kernel evaluation and the output stores.
 //
 // The tensor core accumulates in FP32 with truncation, which biases long sums; O is
-// therefore accumulated over sub-runs of at most kFlushChunks chunks and each sub-run
-// is added into the running sum O2 [384, 384 + p_tile) by the epilogue with ordinary
-// FP32 adds.
+// therefore accumulated over sub-runs of a few chunks and each sub-run is added into a
+// running sum (TMEM, or registers in the wide form) by the epilogue with ordinary FP32
+// adds.
 //
-// Work partition (G persistent CTAs, R row tiles, J column chunks): the first
+// Work partition (G persistent CTAs or pairs, R row tiles, J column chunks): the first
 // floor(R / G) * G row tiles are processed whole, one wave at a time, and every CTA sweeps
 // the column chunks in the same order 0 .. J-1, so at any moment all CTAs read the same
 // tile of B and the L2 serves it to all of them (B is larger than the L2 at the large
@@ -26,10 +29,6 @@
 // contiguous ranges over the G CTAs; partial runs there (at most the first and last of a
 // CTA) go to scratch and a fix-up kernel adds them in CTA order, so results are
 // deterministic.
-//
-// The single-problem schedule also runs in a CTA-pair form (kmv_tc_impl.cuh, instantiated
-// in kmv_tc2.cu): the same partition over pairs of SMs and 256-row tiles, with one thread
-// of each pair issuing cta_group::2 MMAs for both SMs.
 #include <algorithm>
 #include <map>
 #include <mutex>

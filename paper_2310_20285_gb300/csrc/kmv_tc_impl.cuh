@@ -344,9 +344,10 @@ __device__ __noinline__ int issue_gemm1(uint32_t gt, int nk, int klast, uint64_t
   return stage | static_cast<int>(phase << 8);
 }
 
-// GEMM2 of one chunk: O (+)= P . S with P (the chunk's kernel values, BF16 hi/lo pairs
+// GEMM2 of one chunk: O (+)= P . S with P (the chunk's kernel values, 16-bit hi/lo pairs
 // packed in the G buffer's TMEM columns) as the A operand and the chunk's transposed
-// weights from shared memory as B; 8 K steps of 16 rows, 3 MMAs each for split weights.
+// weights from shared memory as B; CW / 16 K steps of 16 rows, 3 MMAs each for split
+// weights.
 // Waits for the epilogue's P (pfull, parity par of its G buffer) and the weight tile (sfull,
 // parity spar of its slot); releases the weight tile (sempty) and, at the end of a flush
 // group, hands O to the epilogue (ofull).

@@ -17,7 +17,8 @@
 // Slab layout (rows in 128-row blocks, one block range per model):
 //  tensor precisions: 16-bit hi (and lo) rows [slab_rows][d_pad], FP32 norms [slab_rows],
 //                     split rows: tile scales [slab_rows / 128],
-//                     weights transposed BF16 hi (and lo) [144][slab_rows];
+//                     weights transposed [144][slab_rows]: FP16 hi and lo with per-model
+//                     column scales (BF16X3, TF32), one BF16 plane otherwise;
 //  FP32:              FP32 rows [slab_rows][d_max], norms, weights [slab_rows][144].
 // Weight row w of a model: w < 16: v[:, w] (zero for w >= C); w >= 16: column
 // (w - 16) = b C + c of Q, i.e. Q_b[:, c] (zero beyond C B).
