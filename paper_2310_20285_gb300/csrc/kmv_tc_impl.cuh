@@ -736,6 +736,10 @@ kmv_tc_kernel(const __grid_constant__ CUtensorMap mAh, const __grid_constant__ C
       for (int k = 0; k < CW / 32; ++k) nb_next[k] = nb_at(static_cast<int64_t>(s0.b_row) + lane + 32 * k);
     }
     constexpr int O2G = O2REG ? (NH == 1 ? 5 : 3) : 1;   // 16-column groups of O per thread (P <= 80)
+    // the next 32-column group of G is loaded while the current one is computed, except in
+    // the wide form with 8 epilogue warps, whose 168 registers per thread leave no room for
+    // the second buffer beside the running sum (two warps per SMSP hide the load instead)
+    constexpr bool PREF = !(O2REG && NH == 2);
     float o2r[O2G][16];                                  // wide chunks: O2 of this thread's row
     for (int64_t t = 0; t < T; ++t, wk.next()) {
       const StepInfo st = wk.cur();
@@ -807,7 +811,7 @@ kmv_tc_kernel(const __grid_constant__ CUtensorMap mAh, const __grid_constant__ C
       for (int grp = grp0; grp < grp1; ++grp) {
         uint32_t vn[32];
         const bool more = grp + 1 < grp1;   // warp-uniform
-        if (more) tmem_ld32(gcol + 32 * (grp + 1), vn);
+        if (PREF && more) tmem_ld32(gcol + 32 * (grp + 1), vn);
         uint32_t ph[16], pl[16];
         if (dchunk) {
           // the row's own column: a huge a.b clamps r^2 to 0 below, so the kernel value is
@@ -864,9 +868,14 @@ kmv_tc_kernel(const __grid_constant__ CUtensorMap mAh, const __grid_constant__ C
         tmem_st16(gcol + 32 * grp, ph);
         if (NT2 == 3) tmem_st16(gcol + 32 * grp + 16, pl);
         if (more) {
-          tmem_ld_wait();
+          if constexpr (PREF) {
+            tmem_ld_wait();
 #pragma unroll
-          for (int i = 0; i < 32; ++i) v[i] = vn[i];
+            for (int i = 0; i < 32; ++i) v[i] = vn[i];
+          } else {
+            tmem_ld32(gcol + 32 * (grp + 1), v);
+            tmem_ld_wait();
+          }
         }
       }
       tmem_st_wait();
