@@ -12,10 +12,26 @@ namespace {
 // tile's largest |x| = m 2^k (m in [0.5, 1)) and takes e = 8 - k, so that 2^e |x| < 256
 // with the largest in [128, 256); pass 2 writes hi = fp16(2^e x) and
 // lo = fp16(2^e x - hi), zero-padded to d_pad (2^e x and the difference are exact in FP32,
-// so hi + lo holds 2^e x to 22 bits), and the squared norm of the unscaled FP32 row (FP64
-// accumulation).  tscale = 2^-e.  FP16 keeps its relative precision over the whole scaled
-// range: elements below 4 (of up to 256) only lose lo bits below 2^-24, i.e. an absolute
-// 2^-33 of the tile's largest value.
+// so hi + lo holds 2^e x to 22 bits), and the squared norm of the unscaled FP32 row.
+// tscale = 2^-e.  FP16 keeps its relative precision over the whole scaled range: elements
+// below 4 (of up to 256) only lose lo bits below 2^-24, i.e. an absolute 2^-33 of the
+// tile's largest value.
+// The norm is summed per lane in FP32 with the exact error of each square (FMA) and of
+// each addition (TwoSum) carried in a second FP32 word, then across lanes in FP64: FP64
+// accuracy for the few dozen terms of a lane at FP32 speed (this GPU's FP64 unit is about
+// 1/64 of its FP32 rate).  VEC: rows 16-byte aligned with d a multiple of 4, loaded as
+// float4 and stored as pairs of half2.
+__device__ __forceinline__ void sq_accumulate(float x, float& s, float& c) {
+  const float p = x * x;
+  const float pe = fmaf(x, x, -p);        // x^2 = p + pe exactly
+  const float t = s + p;
+  const float bp = t - s;
+  const float err = (s - (t - bp)) + (p - bp);   // s + p = t + err exactly (TwoSum)
+  s = t;
+  c += err + pe;
+}
+
+template <bool VEC>
 __global__ void prep_rows_split_kernel(const float* __restrict__ X, int64_t ldX, int64_t rows, int d, int d_pad,
                                        __half* __restrict__ hi, __half* __restrict__ lo, float* __restrict__ norms,
                                        float* __restrict__ tscale) {
@@ -25,8 +41,17 @@ __global__ void prep_rows_split_kernel(const float* __restrict__ X, int64_t ldX,
   __shared__ int e_s;
   float mx = 0.f;
   for (int rr = warp; rr < 128 && r0 + rr < rows; rr += 8) {
+    if constexpr (VEC) {
+      const float4* xr = reinterpret_cast<const float4*>(X + (r0 + rr) * ldX);
+#pragma unroll 2
+      for (int c4 = lane; c4 < d / 4; c4 += 32) {
+        const float4 v = xr[c4];
+        mx = fmaxf(mx, fmaxf(fmaxf(fabsf(v.x), fabsf(v.y)), fmaxf(fabsf(v.z), fabsf(v.w))));
+      }
+    } else {
 #pragma unroll 4
-    for (int col = lane; col < d; col += 32) mx = fmaxf(mx, fabsf(X[(r0 + rr) * ldX + col]));
+      for (int col = lane; col < d; col += 32) mx = fmaxf(mx, fabsf(X[(r0 + rr) * ldX + col]));
+    }
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
@@ -43,20 +68,58 @@ __global__ void prep_rows_split_kernel(const float* __restrict__ X, int64_t ldX,
   const float sc = pow2i(e_s);
   for (int rr = warp; rr < 128; rr += 8) {
     const int64_t row = r0 + rr;
-    double acc = 0.0;
+    float s = 0.f, c = 0.f;
+    if constexpr (VEC) {
+      const float4* xr = reinterpret_cast<const float4*>(X + row * ldX);
+      __half2* h2 = reinterpret_cast<__half2*>(hi + row * d_pad);
+      __half2* l2 = reinterpret_cast<__half2*>(lo + row * d_pad);
+#pragma unroll 2
+      for (int c4 = lane; c4 < d_pad / 4; c4 += 32) {
+        const float4 v = (row < rows && c4 < d / 4) ? xr[c4] : make_float4(0.f, 0.f, 0.f, 0.f);
+        sq_accumulate(v.x, s, c);
+        sq_accumulate(v.y, s, c);
+        sq_accumulate(v.z, s, c);
+        sq_accumulate(v.w, s, c);
+        const float a0 = v.x * sc, a1 = v.y * sc, a2 = v.z * sc, a3 = v.w * sc;
+        const __half2 hA = __floats2half2_rn(a0, a1), hB = __floats2half2_rn(a2, a3);
+        const float2 fA = __half22float2(hA), fB = __half22float2(hB);
+        h2[2 * c4] = hA;
+        h2[2 * c4 + 1] = hB;
+        l2[2 * c4] = __floats2half2_rn(a0 - fA.x, a1 - fA.y);
+        l2[2 * c4 + 1] = __floats2half2_rn(a2 - fB.x, a3 - fB.y);
+      }
+    } else {
 #pragma unroll 4
-    for (int col = lane; col < d_pad; col += 32) {
-      const float x = (row < rows && col < d) ? X[row * ldX + col] : 0.f;
-      const float xs = x * sc;
-      const __half h = __float2half_rn(xs);
-      hi[row * d_pad + col] = h;
-      lo[row * d_pad + col] = __float2half_rn(xs - __half2float(h));
-      acc += static_cast<double>(x) * x;
+      for (int col = lane; col < d_pad; col += 32) {
+        const float x = (row < rows && col < d) ? X[row * ldX + col] : 0.f;
+        const float xs = x * sc;
+        const __half h = __float2half_rn(xs);
+        hi[row * d_pad + col] = h;
+        lo[row * d_pad + col] = __float2half_rn(xs - __half2float(h));
+        sq_accumulate(x, s, c);
+      }
     }
+    double acc = static_cast<double>(s) + static_cast<double>(c);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
     if (lane == 0) norms[row] = static_cast<float>(acc);
   }
+}
+
+// The split-row preparation of rows_pad / 128 tiles, with 16-byte row loads where the
+// rows allow them.
+void launch_prep_split(const float* X, int64_t ldX, int64_t rows, int d, int64_t rows_pad, int d_pad,
+                       void* hi, void* lo, float* norms, float* tscale, cudaStream_t stream) {
+  const bool vec = (d % 4) == 0 && (ldX % 4) == 0 && (reinterpret_cast<uintptr_t>(X) % 16) == 0;
+  const unsigned grid = static_cast<unsigned>(rows_pad / kRowTile);
+  __half* h = reinterpret_cast<__half*>(hi);
+  __half* l = reinterpret_cast<__half*>(lo);
+  if (vec)
+    prep_rows_split_kernel<true><<<grid, 256, 0, stream>>>(X, ldX, rows, d, d_pad, h, l, norms, tscale),
+        ::itergp::note_launch();
+  else
+    prep_rows_split_kernel<false><<<grid, 256, 0, stream>>>(X, ldX, rows, d, d_pad, h, l, norms, tscale),
+        ::itergp::note_launch();
 }
 
 // BF16 rows (one warp per row): BF16 copies zero-padded to d_pad and the squared norm of
@@ -156,8 +219,7 @@ int prepare_rows_into(int precision, const float* X, int64_t rows, int d, int64_
   if (precision_tf32_rows(precision))
     prep_rows_tf32_kernel<<<blocks, 256, 0, stream>>>(X, ldX, rows, d, rows_pad, d_pad, reinterpret_cast<float*>(hi), norms), ::itergp::note_launch();
   else if (precision_splits_rows(precision))
-    prep_rows_split_kernel<<<static_cast<unsigned>(rows_pad / kRowTile), 256, 0, stream>>>(
-        X, ldX, rows, d, d_pad, reinterpret_cast<__half*>(hi), reinterpret_cast<__half*>(lo), norms, tscale), ::itergp::note_launch();
+    launch_prep_split(X, ldX, rows, d, rows_pad, d_pad, hi, lo, norms, tscale, stream);
   else
     prep_rows_kernel<<<blocks, 256, 0, stream>>>(X, ldX, rows, d, rows_pad, d_pad, hi, norms), ::itergp::note_launch();
   ITERGP_CUDA_TRY(cudaGetLastError());
@@ -216,8 +278,7 @@ int prepare_rows(int precision, const float* X, int64_t rows, int d, int64_t ldX
     prep_rows_tf32_kernel<<<blocks, 256, 0, stream>>>(X, ldX, rows, d, op->rows_pad, op->d_pad,
                                                       reinterpret_cast<float*>(hi), norms), ::itergp::note_launch();
   else if (lo)
-    prep_rows_split_kernel<<<static_cast<unsigned>(op->rows_pad / kRowTile), 256, 0, stream>>>(
-        X, ldX, rows, d, op->d_pad, reinterpret_cast<__half*>(hi), reinterpret_cast<__half*>(lo), norms, tscale), ::itergp::note_launch();
+    launch_prep_split(X, ldX, rows, d, op->rows_pad, op->d_pad, hi, lo, norms, tscale, stream);
   else
     prep_rows_kernel<<<blocks, 256, 0, stream>>>(X, ldX, rows, d, op->rows_pad, op->d_pad, hi, norms), ::itergp::note_launch();
   ITERGP_CUDA_TRY(cudaGetLastError());
