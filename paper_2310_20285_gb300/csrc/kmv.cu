@@ -131,14 +131,15 @@ __global__ void prep_rows_kernel(const float* __restrict__ X, int64_t ldX, int64
   const int64_t row = static_cast<int64_t>(blockIdx.x) * (blockDim.x / 32) + threadIdx.x / 32;
   const int lane = threadIdx.x % 32;
   if (row >= rows_pad) return;
-  double acc = 0.0;
+  float s = 0.f, c = 0.f;   // compensated FP32 (see sq_accumulate)
   for (int col = lane; col < d_pad; col += 32) {
     const float x = (row < rows && col < d) ? X[row * ldX + col] : 0.f;
     const __nv_bfloat16 h = __float2bfloat16_rn(x);
     const float hf = __bfloat162float(h);
     hi[row * d_pad + col] = h;
-    acc += static_cast<double>(hf) * hf;
+    sq_accumulate(hf, s, c);
   }
+  double acc = static_cast<double>(s) + static_cast<double>(c);
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
   if (lane == 0) norms[row] = static_cast<float>(acc);
@@ -163,12 +164,13 @@ __global__ void prep_rows_tf32_kernel(const float* __restrict__ X, int64_t ldX, 
   const int64_t row = static_cast<int64_t>(blockIdx.x) * (blockDim.x / 32) + threadIdx.x / 32;
   const int lane = threadIdx.x % 32;
   if (row >= rows_pad) return;
-  double acc = 0.0;
+  float s = 0.f, c = 0.f;   // compensated FP32 (see sq_accumulate)
   for (int col = lane; col < d_pad; col += 32) {
     const float x = round_tf32((row < rows && col < d) ? X[row * ldX + col] : 0.f);
     out[row * d_pad + col] = x;
-    acc += static_cast<double>(x) * x;
+    sq_accumulate(x, s, c);
   }
+  double acc = static_cast<double>(s) + static_cast<double>(c);
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
   if (lane == 0) norms[row] = static_cast<float>(acc);
@@ -180,11 +182,9 @@ __global__ void row_norms_kernel(const float* __restrict__ X, int64_t ldX, int64
   const int64_t row = static_cast<int64_t>(blockIdx.x) * (blockDim.x / 32) + threadIdx.x / 32;
   const int lane = threadIdx.x % 32;
   if (row >= rows) return;
-  double acc = 0.0;
-  for (int col = lane; col < d; col += 32) {
-    const float x = X[row * ldX + col];
-    acc += static_cast<double>(x) * x;
-  }
+  float s = 0.f, c = 0.f;   // compensated FP32 (see sq_accumulate)
+  for (int col = lane; col < d; col += 32) sq_accumulate(X[row * ldX + col], s, c);
+  double acc = static_cast<double>(s) + static_cast<double>(c);
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
   if (lane == 0) norms[row] = static_cast<float>(acc);
