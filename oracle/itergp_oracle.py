@@ -487,7 +487,7 @@ class FitResult:
 def iterncgp_fit(X, lik, C: int, kern: Kernel, max_newton: int = 10, max_iters: int = 50,
                  R: int | None = None, policy: int = CG, tol_newton: float | None = None,
                  tol_abs: float = 1e-5, tol_rel: float = 1e-5, recycle: bool = True,
-                 project_contrasts: bool = False, f0=None):
+                 project_contrasts: bool = False, f0=None, product_noise=None):
     """Alg. 1: Newton's method as a sequence of GP regression problems, each solved by
     IterGP (Alg. 2) with recycled actions (Alg. 3).  Prior mean m = 0 (App. C.3),
     f_0 = m, empty buffers.  tol_newton=None runs exactly ``max_newton`` steps.
@@ -495,7 +495,11 @@ def iterncgp_fit(X, lik, C: int, kern: Kernel, max_newton: int = 10, max_iters: 
     residual under the residual (CG) policy (the CUDA path's stabilisation; the identity
     in exact arithmetic, where those vectors already lie in range(I kron P)).
     f0 (N x C) replaces the starting iterate f_0 = m (used to start a step from a given
-    iterate); the objective of step 0 is then reported with v = 0 as for f_0 = m."""
+    iterate); the objective of step 0 is then reported with v = 0 as for f_0 = m.
+    product_noise=(eps, rng) models an inexact kernel product: every application of K
+    (each solver product and f = K v) returns (K W)(1 + eps z) with z standard normal,
+    drawn fresh from rng per call, as rounding of relative size eps would.  Off (None) by
+    default; tests use it to measure how far rounding of a given size moves a fit."""
     X = np.asarray(X, dtype=np.float64)
     N = X.shape[0]
     m = np.zeros((N, C))
@@ -509,10 +513,17 @@ def iterncgp_fit(X, lik, C: int, kern: Kernel, max_newton: int = 10, max_iters: 
     kx = None if per_class else kernel_matrix(X, X, kern)
     kxs = [kernel_matrix(X, X, kc) for kc in kernels_per_class(kern, C)] if per_class else None
 
-    def kprod(W):   # K applied to an N x C block (k kron I_C, or class c's kernel on column c)
+    def kprod_exact(W):   # K applied to an N x C block (k kron I_C, or class c's kernel on column c)
         if not per_class:
             return kx @ W
         return np.stack([kxs[c] @ W[:, c] for c in range(C)], axis=1)
+
+    def kprod(W):
+        Y = kprod_exact(W)
+        if product_noise is None:
+            return Y
+        eps, rng = product_noise
+        return Y * (1.0 + eps * rng.standard_normal(Y.shape))
 
     def kmv(w):
         return kprod(w.reshape(N, C)).reshape(-1)

@@ -609,6 +609,37 @@ def test_restart_from_an_iterate_reproduces_the_next_step():
         assert np.allclose(step.f, full.fs[i + 1], rtol=0, atol=1e-12 * np.abs(full.fs[i + 1]).max())
 
 
+def test_product_noise_off_is_the_exact_fit_and_enters_each_product_linearly():
+    """The inexact-product option that the batched GPU tests use to measure a fit's
+    sensitivity to rounding.  eps = 0 is bitwise the exact fit; every kernel product draws
+    its own noise (Alg. 2 as the oracle runs it: K v for the residual r_{j-1} and K s_j per
+    iteration, then f = K v once per Newton step, Alg. 1); and for a small eps the fit moves
+    linearly in eps (the same draws at 2 eps move it twice as far)."""
+    X, y, _ = datagen.blobs(60, 2, 3, 21)
+    kern = O.Kernel(O.RBF, 1.0, 1.0)
+    kw = dict(max_newton=3, max_iters=5, R=10, tol_abs=0, tol_rel=0)
+    exact = O.iterncgp_fit(X, O.Softmax(y, 3), 3, kern, **kw)
+    zero = O.iterncgp_fit(X, O.Softmax(y, 3), 3, kern, product_noise=(0.0, np.random.default_rng(1)), **kw)
+    assert np.array_equal(exact.f, zero.f)
+
+    class Counting:
+        def __init__(self, seed):
+            self.g, self.calls = np.random.default_rng(seed), 0
+
+        def standard_normal(self, shape):
+            self.calls += 1
+            return self.g.standard_normal(shape)
+
+    rng = Counting(0)
+    res = O.iterncgp_fit(X, O.Softmax(y, 3), 3, kern, product_noise=(1e-8, rng), **kw)
+    assert rng.calls == sum(2 * inf.iters + 1 for inf in res.infos) == 33
+
+    d1 = O.iterncgp_fit(X, O.Softmax(y, 3), 3, kern, product_noise=(1e-8, np.random.default_rng(1)), **kw).f - exact.f
+    d2 = O.iterncgp_fit(X, O.Softmax(y, 3), 3, kern, product_noise=(2e-8, np.random.default_rng(1)), **kw).f - exact.f
+    assert 0 < np.linalg.norm(d1) <= 1e-6 * np.linalg.norm(exact.f)
+    assert np.linalg.norm(d2 - 2.0 * d1) <= 1e-3 * np.linalg.norm(d2)
+
+
 # ------------------------------------------------------ one-latent likelihoods (App. A, C)
 
 def one_latent_problem(kind, n=12, seed=3):
