@@ -347,7 +347,12 @@ __device__ __noinline__ int issue_gemm1(uint32_t gt, int nk, int klast, uint64_t
 // GEMM2 of one chunk: O (+)= P . S with P (the chunk's kernel values, 16-bit hi/lo pairs
 // packed in the G buffer's TMEM columns) as the A operand and the chunk's transposed
 // weights from shared memory as B; CW / 16 K steps of 16 rows, 3 MMAs each for split
-// weights.
+// weights.  Packed (pk2: one CTA, split weights, P tiles <= 32): the weight tile holds each
+// 64-row box's hi and lo planes back to back, so one MMA of N = 2P multiplies P's hi plane
+// by both (O columns [0, P) take hi.hi, [P, 2P) hi.lo) and a second of N = P adds lo.hi
+// into [P, 2P): 2 MMAs per K step instead of 3.  The hi.hi sum then takes one accumulation
+// per K step (not three) and the correction terms are summed apart at their own magnitude;
+// the flush adds the two column halves.
 // Waits for the epilogue's P (pfull, parity par of its G buffer) and the weight tile (sfull,
 // parity spar of its slot); releases the weight tile (sempty) and, at the end of a flush
 // group, hands O to the epilogue (ofull).
@@ -357,7 +362,7 @@ template <int NT2, bool PAIR, int CW>
 __device__ __noinline__ bool issue_gemm2(uint32_t tb, uint32_t a_col0, uint32_t o_col, uint32_t par, uint32_t spar,
                                          bool first, bool last, uint64_t* pfull_b, uint64_t* sfull_b, uint64_t* sempty_b,
                                          uint64_t* ofull_b, volatile int* ab, uint64_t dS0, uint64_t sbox16,
-                                         uint32_t idesc2, uint64_t lim) {
+                                         uint32_t idesc2, uint32_t idesc2w, bool pk2, uint32_t p_pad, uint64_t lim) {
   if constexpr (PAIR) {   // both CTAs' epilogue warps arrive on pfull
     if (!mbar_try_wait_cluster(pfull_b, par) && !mbar_wait_cluster_slow(pfull_b, par, ab, lim)) return false;
   } else {
@@ -365,6 +370,19 @@ __device__ __noinline__ bool issue_gemm2(uint32_t tb, uint32_t a_col0, uint32_t 
   }
   if (!mbar_try_wait(sfull_b, spar) && !mbar_wait_slow(sfull_b, spar, ab, lim)) return false;
   tc_fence_after();   // P was written by the epilogue's tcgen05.st
+  if (NT2 == 3 && !PAIR && pk2) {
+#pragma unroll
+    for (int ks2 = 0; ks2 < CW / 16; ++ks2) {
+      const int grp = ks2 >> 1, h = ks2 & 1;
+      const uint32_t a_hi = tb + a_col0 + static_cast<uint32_t>(32 * grp + 8 * h);
+      const uint64_t dSh = dS0 + static_cast<uint64_t>(ks2 >> 2) * 2 * sbox16 + static_cast<uint64_t>((ks2 & 3) * 2);
+      mma_ts_x<PAIR>(tb + o_col, a_hi, dSh, idesc2w, (first && ks2 == 0) ? 0u : 1u);
+      mma_ts_x<PAIR>(tb + o_col + p_pad, a_hi + 16, dSh, idesc2, 1u);
+    }
+    commit_x<PAIR>(sempty_b);
+    if (last) commit_x<PAIR>(ofull_b);
+    return true;
+  }
 #pragma unroll
   for (int ks2 = 0; ks2 < CW / 16; ++ks2) {
     const int grp = ks2 >> 1, h = ks2 & 1;
@@ -418,8 +436,10 @@ kmv_tc_kernel(const __grid_constant__ CUtensorMap mAh, const __grid_constant__ C
   constexpr uint32_t SB = ARES ? (NT1 == 3 ? 2u : 1u) * B_PART : stage_bytes(NT1, PAIR, CW);
   const int ng = O2REG ? 2 : g_bufs(args.p_pad);         // G buffers
   const int nsl = args.w_slots;                          // weight-tile slots (1 .. 3)
+  // packed GEMM2 (see issue_gemm2): O takes 2P columns, so O2 moves to 384 + 2P (<= 448)
+  const bool pk2 = NT2 == 3 && !PAIR && CW == BN && args.p_pad <= 32;
   const uint32_t ocol = O2REG ? 2u * CW : ng == 3 ? 384u : kOCol;
-  const uint32_t o2col = ng == 3 ? 384u + static_cast<uint32_t>(args.p_pad) : kO2Col;   // TMEM O2 forms
+  const uint32_t o2col = ng == 3 ? 384u + static_cast<uint32_t>((pk2 ? 2 : 1) * args.p_pad) : kO2Col;   // TMEM O2 forms
   const uint32_t SBOX = s_box_bytes(args.p_pad, PAIR);
   const uint32_t SBUF = s_buf_bytes(NT2, args.p_pad, PAIR, CW);
   uint8_t* a_region = smem + NSTAGE * SB;                        // ARES only
@@ -591,11 +611,13 @@ kmv_tc_kernel(const __grid_constant__ CUtensorMap mAh, const __grid_constant__ C
             if (NT2 == 3) tma_load_2d_pair(sbase + (CW / 64 + bx) * SBOX, &mSl, fb, j0 + 64 * bx, srow);
           }
         } else {
+          // plain order hi0 hi1 lo0 lo1; packed GEMM2 hi0 lo0 hi1 lo1
+          const uint32_t hs = pk2 ? 2u : 1u, lo0 = pk2 ? 1u : 2u;
           tma_load_2d(sbase, &mSh, &sfull[sb], j0, args.s_row0);
-          tma_load_2d(sbase + SBOX, &mSh, &sfull[sb], j0 + 64, args.s_row0);
+          tma_load_2d(sbase + hs * SBOX, &mSh, &sfull[sb], j0 + 64, args.s_row0);
           if (NT2 == 3) {
-            tma_load_2d(sbase + 2 * SBOX, &mSl, &sfull[sb], j0, args.s_row0);
-            tma_load_2d(sbase + 3 * SBOX, &mSl, &sfull[sb], j0 + 64, args.s_row0);
+            tma_load_2d(sbase + lo0 * SBOX, &mSl, &sfull[sb], j0, args.s_row0);
+            tma_load_2d(sbase + (lo0 + hs) * SBOX, &mSl, &sfull[sb], j0 + 64, args.s_row0);
           }
         }
       }
@@ -612,6 +634,7 @@ kmv_tc_kernel(const __grid_constant__ CUtensorMap mAh, const __grid_constant__ C
       // split weights are FP16 hi/lo (kernel values too), single weights BF16
       const uint32_t idesc2 = NT2 == 3 ? idesc_f16_f32(TM, static_cast<uint32_t>(args.p_pad))
                                        : idesc_bf16_f32(TM, static_cast<uint32_t>(args.p_pad));
+      const uint32_t idesc2w = idesc_f16_f32(TM, static_cast<uint32_t>(2 * args.p_pad));   // pk2 only
       // shared-memory descriptors of stage 0, the resident A and the weight buffers; the
       // start-address field (bits 0-13, 16-byte units) takes offsets by plain addition
       // because every operand lies below 256 KB of the shared window
@@ -658,7 +681,7 @@ kmv_tc_kernel(const __grid_constant__ CUtensorMap mAh, const __grid_constant__ C
         return issue_gemm2<NT2, PAIR, CW>(tb, static_cast<uint32_t>(gb) * CW, ocol, par, wpar, first, last, &pfull[gb],
                                       &sfull[wb], &sempty[wb], &ofull, ab,
                                       dS_base + static_cast<uint64_t>(wb) * (SBUF >> 4), sbox16, idesc2,
-                                      args.wait_ns);
+                                      idesc2w, pk2, static_cast<uint32_t>(args.p_pad), args.wait_ns);
       };
       Walker wk1 = walk0;    // GEMM1 steps (segment boundaries for the resident A)
       int64_t aseg = -1;
@@ -937,6 +960,13 @@ kmv_tc_kernel(const __grid_constant__ CUtensorMap mAh, const __grid_constant__ C
         for (int c16 = hc; !O2REG && c16 < args.p_pad / 16; c16 += NH) {
           uint32_t o[16];
           tmem_ld16(tb + lane_base + ocol + 16 * c16, o);
+          if (pk2) {   // the correction half (hi.lo + lo.hi) of the packed GEMM2's columns
+            uint32_t ox[16];
+            tmem_ld16(tb + lane_base + ocol + static_cast<uint32_t>(args.p_pad) + 16 * c16, ox);
+            tmem_ld_wait();
+#pragma unroll
+            for (int i = 0; i < 16; ++i) o[i] = __float_as_uint(__uint_as_float(o[i]) + __uint_as_float(ox[i]));
+          }
           if (sub_in_seg > 0) {
             uint32_t o2[16];
             tmem_ld16(tb + lane_base + o2col + 16 * c16, o2);
