@@ -8,8 +8,11 @@
 // fit runs without a host round trip.  Scalars (alpha, eta, norms, objective) are
 // reduced in FP64 with a fixed block order, so results are deterministic.
 #include <algorithm>
+#include <mutex>
+#include <utility>
 #include <vector>
 
+#include <cooperative_groups.h>
 #include <cuda_fp16.h>
 
 #include "internal.h"
@@ -374,38 +377,66 @@ __device__ __forceinline__ void rr_pair(int k, int r, int m, int* lo, int* hi) {
   *hi = p < q ? q : p;
 }
 
+// CL > 1: the eigenproblem is shared by the CL CTAs of a cluster (one SM each), so the
+// rounds' FP64 updates run on CL SMs' FP64 units.  The rank-0 CTA holds the rotation arrays
+// (cs, sn, plo, phi: addresses in its shared memory), computes the norms, the stopping test
+// and each round's rotations exactly as one CTA would, and the round's block and V updates
+// are split over all CL x blockDim threads, which reach A, V and the rotations through
+// distributed shared memory (A and V may also be global).  Cluster barriers stand where one
+// CTA has block barriers; every thread of every CTA passes the same sequence of them, and
+// each element is still computed by one thread from the same operands, so the result is
+// bitwise the one-CTA result.  The caller maps the pointers of a rank > 0 CTA to rank 0.
+template <int CL>
 __device__ void jacobi_eig(double* A, double* V, int n, int ld, double* cs, double* sn, int* plo, int* phi,
                            double* sh) {
+  namespace cg = cooperative_groups;
+  const int rank = CL > 1 ? static_cast<int>(cg::this_cluster().block_rank()) : 0;
+  const bool lead = rank == 0;
   const int tid = threadIdx.x, nt = blockDim.x;
+  const int gtid = rank * nt + tid, gnt = CL * nt;   // the team's threads for the updates
+  auto team_sync = [&]() {
+    if constexpr (CL > 1) cg::this_cluster().sync(); else __syncthreads();
+  };
   const int m = (n + 1) / 2 * 2;   // even number of players (index n is a dummy if n odd)
   const int h = m / 2;
-  for (int e = tid; e < n * n; e += nt) V[(e / n) * ld + e % n] = (e / n == e % n) ? 1.0 : 0.0;
-  double fro = 0.0;
-  for (int e = tid; e < n * n; e += nt) {
-    const double a = A[(e / n) * ld + e % n];
-    fro += a * a;
-  }
-  fro = block_reduce_sum(fro, sh);
   __shared__ double fro_s, off_s;
-  if (tid == 0) fro_s = fro;
-  __syncthreads();
-  const double tol2 = fro_s * 1e-30;
-  for (int sweep = 0; sweep < 40; ++sweep) {
-    double off = 0.0;
+  __shared__ int stop_s;
+  int* stop = &stop_s;
+  if constexpr (CL > 1) stop = cg::this_cluster().map_shared_rank(&stop_s, 0);
+  double tol2 = 0.0;
+  if (lead) {
+    for (int e = tid; e < n * n; e += nt) V[(e / n) * ld + e % n] = (e / n == e % n) ? 1.0 : 0.0;
+    double fro = 0.0;
     for (int e = tid; e < n * n; e += nt) {
-      const int i = e / n, j = e % n;
-      if (i < j) {
-        const double a = A[i * ld + j];
-        off += 2.0 * a * a;
+      const double a = A[(e / n) * ld + e % n];
+      fro += a * a;
+    }
+    fro = block_reduce_sum(fro, sh);
+    if (tid == 0) fro_s = fro;
+    __syncthreads();
+    tol2 = fro_s * 1e-30;
+  }
+  for (int sweep = 0; sweep < 40; ++sweep) {
+    if (lead) {
+      double off = 0.0;
+      for (int e = tid; e < n * n; e += nt) {
+        const int i = e / n, j = e % n;
+        if (i < j) {
+          const double a = A[i * ld + j];
+          off += 2.0 * a * a;
+        }
+      }
+      off = block_reduce_sum(off, sh);
+      if (tid == 0) {
+        off_s = off;
+        stop_s = (off <= tol2 || off == 0.0) ? 1 : 0;
       }
     }
-    off = block_reduce_sum(off, sh);
-    if (tid == 0) off_s = off;
-    __syncthreads();
-    if (off_s <= tol2 || off_s == 0.0) break;
+    team_sync();
+    if (*stop) break;
     for (int r = 0; r < m - 1; ++r) {
       // the round's pairs and rotations; sn = 0 marks a pair left as it is
-      for (int k = tid; k < h; k += nt) {
+      for (int k = tid; lead && k < h; k += nt) {
         int lo, hi;
         rr_pair(k, r, m, &lo, &hi);
         plo[k] = lo;
@@ -426,10 +457,10 @@ __device__ void jacobi_eig(double* A, double* V, int n, int ld, double* cs, doub
         cs[k] = c;
         sn[k] = s;
       }
-      __syncthreads();
+      team_sync();
       // A <- J^T A J by 2 x 2 blocks (a <= b, enumerated densely: e = b (b + 1) / 2 + a),
       // mirrored; V <- V J (rows x pairs)
-      for (int e = tid; e < h * (h + 1) / 2; e += nt) {
+      for (int e = gtid; e < h * (h + 1) / 2; e += gnt) {
         int b = static_cast<int>((sqrtf(8.f * static_cast<float>(e) + 1.f) - 1.f) * 0.5f);
         if ((b + 1) * (b + 2) / 2 <= e) ++b;
         if (b * (b + 1) / 2 > e) --b;
@@ -473,7 +504,7 @@ __device__ void jacobi_eig(double* A, double* V, int n, int ld, double* cs, doub
           A[q2 * ld + q1] = z11;
         }
       }
-      for (int e = tid; e < n * h; e += nt) {
+      for (int e = gtid; e < n * h; e += gnt) {
         const int row = e / h, k = e % h;
         const double s = sn[k];
         if (s == 0.0) continue;
@@ -483,9 +514,11 @@ __device__ void jacobi_eig(double* A, double* V, int n, int ld, double* cs, doub
         V[row * ld + lo] = c * x - s * y;
         V[row * ld + hi] = s * x + c * y;
       }
-      __syncthreads();
+      team_sync();
     }
   }
+  // the other CTAs have read the stop flag and made their last accesses to rank 0's memory
+  if constexpr (CL > 1) team_sync();
 }
 
 // Sort eigenpairs descending (ties by index): order[k] = index of the k-th largest.
@@ -512,6 +545,58 @@ inline size_t eig_smem_bytes(int b, bool ab_smem = false) {
 }
 // Buffers up to this size keep A and V in shared memory (200 KB at 112).
 constexpr int kEigSmemMax = 112;
+// CTAs per eigenproblem when a few problems leave SMs idle (portable cluster size).
+constexpr int kEigCluster = 8;
+
+// Launch as clusters of cl CTAs, `groups` clusters.
+template <typename... P, typename... Args>
+cudaError_t launch_clustered(void (*fn)(P...), int groups, int cl, int threads, size_t smem, cudaStream_t st,
+                             Args&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(static_cast<unsigned>(groups * cl));
+  cfg.blockDim = dim3(static_cast<unsigned>(threads));
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = static_cast<unsigned>(cl);
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, fn, std::forward<Args>(args)...);
+}
+
+// True when clusters of kEigCluster CTAs of fn (threads, smem) can be resident; sets fn's
+// dynamic shared-memory limit to smem.
+template <typename... P>
+bool eig_cluster_fits(void (*fn)(P...), int threads, size_t smem) {
+  if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(kEigCluster);
+  cfg.blockDim = dim3(static_cast<unsigned>(threads));
+  cfg.dynamicSmemBytes = smem;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = kEigCluster;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  int n = 0;
+  if (cudaOccupancyMaxActiveClusters(&n, fn, &cfg) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return n > 0;
+}
+
+// The fit's eigen step: whether clusters fit with the largest layout (A and V of a
+// kEigSmemMax buffer in shared memory), asked once per device.
+bool vsr_eig_cluster_ok(const DeviceContext* ctx);
 
 // Sum Gram partials, symmetrise, eigendecompose, drop lambda <= 1e-12 lambda_max, keep
 // the R largest (Alg. 3), write rotation W[b][k] = U[b][k] lambda_k^-1/2 (FP32) and
@@ -519,8 +604,13 @@ constexpr int kEigSmemMax = 112;
 // shared memory.  (V stays FP64: a kept eigenvalue may be 1e-12 of the largest, and the
 // rotation W = U lambda^-1/2 magnifies an eigenvector's error by up to lambda_max /
 // lambda_k in the K-hat inner products of the compressed buffer.)
+// CL > 1: launched as clusters of CL CTAs per problem (A and V in shared memory only); the
+// rank-0 CTA does all but the eigendecomposition's rounds, which the cluster shares.
+template <int CL>
 __global__ void vsr_eig_kernel(const ProbDev* __restrict__ probs, int splits, int rank, int step, int ab_smem) {
-  const ProbDev& P = probs[blockIdx.x];
+  namespace cg = cooperative_groups;
+  const ProbDev& P = probs[blockIdx.x / CL];
+  const bool lead = CL == 1 || cg::this_cluster().block_rank() == 0;
   FitState* st = P.st;
   const double* __restrict__ part = P.pg;
   const int bcap = P.bcap;
@@ -528,10 +618,12 @@ __global__ void vsr_eig_kernel(const ProbDev* __restrict__ probs, int splits, in
   double* __restrict__ Vmat = P.Vm;
   float* __restrict__ W = P.W;
   float* __restrict__ sq = P.sq;
+  // every CTA of a cluster reads the same flags: rank 0 writes st->B only after the
+  // eigendecomposition's first cluster barrier, which the others reach after these reads
   if (!st->newton_active) return;
   const int B = st->B;
   if (B == 0) {
-    if (threadIdx.x == 0 && step < ITERGP_MAX_REPORT_STEPS) st->kept[step] = 0;
+    if (lead && threadIdx.x == 0 && step < ITERGP_MAX_REPORT_STEPS) st->kept[step] = 0;
     return;
   }
   extern __shared__ __align__(16) uint8_t esh[];
@@ -549,6 +641,16 @@ __global__ void vsr_eig_kernel(const ProbDev* __restrict__ probs, int splits, in
     V = A + B * B;
     ld = B;
   }
+  if constexpr (CL > 1) {
+    if (!lead) {   // the cluster's other CTAs work on rank 0's arrays, then leave
+      auto cl = cg::this_cluster();
+      double* A0 = ab_smem ? cl.map_shared_rank(A, 0) : A;
+      double* V0 = ab_smem ? cl.map_shared_rank(V, 0) : V;
+      jacobi_eig<CL>(A0, V0, B, ld, cl.map_shared_rank(cs, 0), cl.map_shared_rank(sn, 0),
+                     cl.map_shared_rank(plo, 0), cl.map_shared_rank(phi, 0), red);
+      return;
+    }
+  }
   for (int e = threadIdx.x; e < B * B; e += blockDim.x) {
     const int a = e / B, b = e % B;
     double s1 = 0.0, s2 = 0.0;
@@ -559,7 +661,7 @@ __global__ void vsr_eig_kernel(const ProbDev* __restrict__ probs, int splits, in
     A[a * ld + b] = 0.5 * (s1 + s2);
   }
   __syncthreads();
-  jacobi_eig(A, V, B, ld, cs, sn, plo, phi, red);
+  jacobi_eig<CL>(A, V, B, ld, cs, sn, plo, phi, red);
   eig_order(A, B, ld, order);
   __shared__ int keep_s;
   if (threadIdx.x == 0) {
@@ -581,6 +683,17 @@ __global__ void vsr_eig_kernel(const ProbDev* __restrict__ probs, int splits, in
   }
   for (int k = threadIdx.x; k < keep; k += blockDim.x)
     sq[k] = static_cast<float>(sqrt(A[order[k] * ld + order[k]]));
+}
+
+bool vsr_eig_cluster_ok(const DeviceContext* ctx) {
+  static std::mutex mu;
+  static signed char known[64] = {};   // 0 not asked, 1 yes, -1 no
+  const int dev = ctx->device;
+  if (dev < 0 || dev >= 64) return false;
+  std::lock_guard<std::mutex> lk(mu);
+  if (known[dev] == 0)
+    known[dev] = eig_cluster_fits(vsr_eig_kernel<kEigCluster>, 512, eig_smem_bytes(kEigSmemMax, true)) ? 1 : -1;
+  return known[dev] > 0;
 }
 
 // Q[:, k] = sum_b S[:, b] W[b][k];  KQ[:, k] = sum_b T[:, b] W[b][k]   (k < B_new, b < B_old)
@@ -1050,8 +1163,11 @@ __global__ void pseudo_targets_kernel(const float* __restrict__ f, const int32_t
   }
 }
 
+// CL > 1: one cluster of CL CTAs (A and V global, the rotations in rank 0's shared memory).
+template <int CL>
 __global__ void sym_eig_kernel(const double* __restrict__ M, int b, double* __restrict__ lam,
                                double* __restrict__ U, double* __restrict__ A, double* __restrict__ V) {
+  namespace cg = cooperative_groups;
   extern __shared__ __align__(16) uint8_t esh[];
   double* cs = reinterpret_cast<double*>(esh);
   double* sn = cs + b / 2 + 1;
@@ -1059,12 +1175,20 @@ __global__ void sym_eig_kernel(const double* __restrict__ M, int b, double* __re
   int* plo = reinterpret_cast<int*>(red + 32);
   int* phi = plo + b + 1;
   int* order = phi + b + 1;
+  if constexpr (CL > 1) {
+    if (cg::this_cluster().block_rank() != 0) {
+      auto cl = cg::this_cluster();
+      jacobi_eig<CL>(A, V, b, b, cl.map_shared_rank(cs, 0), cl.map_shared_rank(sn, 0),
+                     cl.map_shared_rank(plo, 0), cl.map_shared_rank(phi, 0), red);
+      return;
+    }
+  }
   for (int e = threadIdx.x; e < b * b; e += blockDim.x) {
     const int i = e / b, j = e % b;
     A[i * b + j] = 0.5 * (M[i * b + j] + M[j * b + i]);
   }
   __syncthreads();
-  jacobi_eig(A, V, b, b, cs, sn, plo, phi, red);
+  jacobi_eig<CL>(A, V, b, b, cs, sn, plo, phi, red);
   eig_order(A, b, b, order);
   for (int e = threadIdx.x; e < b * b; e += blockDim.x) {
     const int i = e / b, k = e % b;
@@ -1451,8 +1575,11 @@ int fit_run_batch(DeviceContext* ctx, const std::vector<FitProblem>& probs, cuda
   const bool eig_ab_smem = max_bcap <= kEigSmemMax;
   const size_t eig_smem = eig_smem_bytes(max_bcap, eig_ab_smem);
   const int eig_threads = 512;
-  ITERGP_CUDA_TRY(cudaFuncSetAttribute(vsr_eig_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  ITERGP_CUDA_TRY(cudaFuncSetAttribute(vsr_eig_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        static_cast<int>(eig_smem)));
+  // a few problems: each eigendecomposition on a cluster of SMs (bitwise the same result)
+  const bool eig_cl = eig_ab_smem && eig_threads == 512 && static_cast<int64_t>(np) * kEigCluster <= ctx->num_sms &&
+                      vsr_eig_cluster_ok(ctx);
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   // The schedule is captured on a private stream (the caller's may be the legacy default
@@ -1479,8 +1606,14 @@ int fit_run_batch(DeviceContext* ctx, const std::vector<FitProblem>& probs, cuda
       copy_int_kernel<<<np, 32, 0, stream>>>(pdev), ::itergp::note_launch();
       vsr_z_kernel<<<dim3(eb, np), 256, 0, stream>>>(pdev), ::itergp::note_launch();
       gram_partial_kernel<<<dim3(tiles * tiles, gram_splits, np), 256, 0, stream>>>(pdev, tiles), ::itergp::note_launch();
-      vsr_eig_kernel<<<np, eig_threads, eig_smem, stream>>>(pdev, gram_splits, prm.rank, step, eig_ab_smem ? 1 : 0),
-          ::itergp::note_launch();
+      if (eig_cl)
+        rc = launch_clustered(vsr_eig_kernel<kEigCluster>, np, kEigCluster, eig_threads, eig_smem, stream,
+                              static_cast<const ProbDev*>(pdev), gram_splits, prm.rank, step, 1) == cudaSuccess
+                 ? ITERGP_OK : ITERGP_ECUDA;
+      else
+        vsr_eig_kernel<1><<<np, eig_threads, eig_smem, stream>>>(pdev, gram_splits, prm.rank, step, eig_ab_smem ? 1 : 0);
+      ::itergp::note_launch();
+      if (rc != ITERGP_OK) break;
       vsr_rotate_kernel<<<dim3(eb, np), 256, 0, stream>>>(pdev), ::itergp::note_launch();
       vsr_rescale_kernel<<<dim3(eb, np), 256, 0, stream>>>(pdev), ::itergp::note_launch();
       // v0 = Q0 (Q0^T b), u0 = K v0 = KQ0 (Q0^T b)
@@ -1589,7 +1722,11 @@ int sym_eig_launch(DeviceContext* ctx, const double* M, int b, double* lam, doub
   double* A = ws.as<double>();
   double* V = A + static_cast<size_t>(b) * b;
   const size_t smem = eig_smem_bytes(b);
-  sym_eig_kernel<<<1, 512, smem, s>>>(M, b, lam, U, A, V), ::itergp::note_launch();
+  if (eig_cluster_fits(sym_eig_kernel<kEigCluster>, 512, smem))
+    ITERGP_CUDA_TRY(launch_clustered(sym_eig_kernel<kEigCluster>, 1, kEigCluster, 512, smem, s, M, b, lam, U, A, V));
+  else
+    sym_eig_kernel<1><<<1, 512, smem, s>>>(M, b, lam, U, A, V);
+  ::itergp::note_launch();
   ITERGP_CUDA_TRY(cudaGetLastError());
   return ITERGP_OK;
 }
