@@ -378,11 +378,13 @@ __device__ __forceinline__ void rr_pair(int k, int r, int m, int* lo, int* hi) {
 }
 
 // CL > 1: the eigenproblem is shared by the CL CTAs of a cluster (one SM each), so the
-// rounds' FP64 updates run on CL SMs' FP64 units.  The rank-0 CTA holds the rotation arrays
-// (cs, sn, plo, phi: addresses in its shared memory), computes the norms, the stopping test
-// and each round's rotations exactly as one CTA would, and the round's block and V updates
-// are split over all CL x blockDim threads, which reach A, V and the rotations through
-// distributed shared memory (A and V may also be global).  Cluster barriers stand where one
+// rounds' FP64 updates run on several SMs' FP64 units.  The rank-0 CTA holds the rotation
+// arrays (cs, sn, plo, phi: addresses in its shared memory), computes the norms, the
+// stopping test and each round's rotations exactly as one CTA would, and applies the
+// round's 2 x 2 block updates of A (about half the round's FP64 work) on its own memory;
+// the V rotations (the other half) are split over the threads of the other CTAs, which
+// reach V and the rotations through distributed shared memory (A and V may also be
+// global).  Remote accesses cost far more than local ones, so A stays with rank 0.  Cluster barriers stand where one
 // CTA has block barriers; every thread of every CTA passes the same sequence of them, and
 // each element is still computed by one thread from the same operands, so the result is
 // bitwise the one-CTA result.  The caller maps the pointers of a rank > 0 CTA to rank 0.
@@ -393,7 +395,8 @@ __device__ void jacobi_eig(double* A, double* V, int n, int ld, double* cs, doub
   const int rank = CL > 1 ? static_cast<int>(cg::this_cluster().block_rank()) : 0;
   const bool lead = rank == 0;
   const int tid = threadIdx.x, nt = blockDim.x;
-  const int gtid = rank * nt + tid, gnt = CL * nt;   // the team's threads for the updates
+  // the V rotations' threads: those of ranks 1 .. CL - 1 (one CTA: all of its threads)
+  const int vtid = CL > 1 ? (rank - 1) * nt + tid : tid, vnt = CL > 1 ? (CL - 1) * nt : nt;
   auto team_sync = [&]() {
     if constexpr (CL > 1) cg::this_cluster().sync(); else __syncthreads();
   };
@@ -460,7 +463,7 @@ __device__ void jacobi_eig(double* A, double* V, int n, int ld, double* cs, doub
       team_sync();
       // A <- J^T A J by 2 x 2 blocks (a <= b, enumerated densely: e = b (b + 1) / 2 + a),
       // mirrored; V <- V J (rows x pairs)
-      for (int e = gtid; e < h * (h + 1) / 2; e += gnt) {
+      for (int e = tid; lead && e < h * (h + 1) / 2; e += nt) {
         int b = static_cast<int>((sqrtf(8.f * static_cast<float>(e) + 1.f) - 1.f) * 0.5f);
         if ((b + 1) * (b + 2) / 2 <= e) ++b;
         if (b * (b + 1) / 2 > e) --b;
@@ -504,7 +507,7 @@ __device__ void jacobi_eig(double* A, double* V, int n, int ld, double* cs, doub
           A[q2 * ld + q1] = z11;
         }
       }
-      for (int e = gtid; e < n * h; e += gnt) {
+      for (int e = vtid; (CL == 1 || !lead) && e < n * h; e += vnt) {
         const int row = e / h, k = e % h;
         const double s = sn[k];
         if (s == 0.0) continue;
