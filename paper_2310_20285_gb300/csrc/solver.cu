@@ -1609,11 +1609,14 @@ int fit_run_batch(DeviceContext* ctx, const std::vector<FitProblem>& probs, cuda
       copy_int_kernel<<<np, 32, 0, stream>>>(pdev), ::itergp::note_launch();
       vsr_z_kernel<<<dim3(eb, np), 256, 0, stream>>>(pdev), ::itergp::note_launch();
       gram_partial_kernel<<<dim3(tiles * tiles, gram_splits, np), 256, 0, stream>>>(pdev, tiles), ::itergp::note_launch();
-      if (eig_cl)
-        rc = launch_clustered(vsr_eig_kernel<kEigCluster>, np, kEigCluster, eig_threads, eig_smem, stream,
-                              static_cast<const ProbDev*>(pdev), gram_splits, prm.rank, step, 1) == cudaSuccess
-                 ? ITERGP_OK : ITERGP_ECUDA;
-      else
+      if (eig_cl) {
+        const cudaError_t le = launch_clustered(vsr_eig_kernel<kEigCluster>, np, kEigCluster, eig_threads, eig_smem,
+                                                stream, static_cast<const ProbDev*>(pdev), gram_splits, prm.rank, step, 1);
+        if (le != cudaSuccess) {
+          ::itergp::record_cuda_error(le, "vsr_eig_kernel cluster launch", __FILE__, __LINE__);
+          rc = ITERGP_ECUDA;
+        }
+      } else
         vsr_eig_kernel<1><<<np, eig_threads, eig_smem, stream>>>(pdev, gram_splits, prm.rank, step, eig_ab_smem ? 1 : 0);
       ::itergp::note_launch();
       if (rc != ITERGP_OK) break;

@@ -240,3 +240,21 @@ def test_a_failing_problem_fails_alone(native, prec):
         b.free()
     with pytest.raises(native.ItergpError):
         native.fit_batch(mixed, precision=prec, graph=True, **SCHED)
+
+
+def test_cluster_eigensolver_gives_the_one_cta_fits(native):
+    """With few problems (problems x 8 <= SMs) each eigendecomposition of the virtual solver
+    run (Alg. 3) runs on a cluster of 8 CTAs; one problem more puts every problem's on one
+    CTA.  A problem's fit does not depend on the rest of its batch, and the cluster form
+    computes every element as one CTA does, so the shared problems' fits are bitwise equal."""
+    k = torch.cuda.get_device_properties(DEV).multi_processor_count // 8
+    probs = datagen.batch_problems(count=k + 1, seed=13, n_lo=100, n_hi=300, dims=(2, 8), c_lo=2,
+                                   c_hi=4, ell_lo=0.8, ell_hi=2.0, n_test=4)
+    few = native.fit_batch(to_dev(probs[:k]), precision="fp32", graph=True, **SCHED)
+    many = native.fit_batch(to_dev(probs), precision="fp32", graph=True, **SCHED)
+    for a, b in zip(few, many[:k]):
+        assert a.report.kept[1] > 0   # the virtual solver run kept columns
+        for key in ("f", "v"):
+            assert torch.equal(a.arrays()[key], b.arrays()[key]), key
+    for m in few + many:
+        m.free()
