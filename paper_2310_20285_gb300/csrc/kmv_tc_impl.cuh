@@ -43,7 +43,8 @@ constexpr uint32_t kO2Col = 384;   // FP32 running sum of flushed O (IEEE round-
 // G buffers (and weight-tile slots): 3 for P tiles <= 48, else 2.  With three, GEMM2 of a
 // chunk is issued two chunks behind its GEMM1, so the epilogue of chunk t overlaps GEMM1
 // of t + 1 and t + 2 (at small D the epilogue is longer than one GEMM1).  TMEM then holds
-// G 3 x 128 columns, O at 384 and O2 at 384 + P.
+// G 3 x 128 columns, O at 384 and O2 at 384 + P (384 + 2P when GEMM2 runs packed, see
+// issue_gemm2).
 __host__ __device__ constexpr int g_bufs(int p_pad) { return p_pad <= 48 ? 3 : 2; }
 constexpr int kFlushChunks = 4;    // O is flushed into O2 at least every 4 chunks (512 rows)
 // Chunks per flush group for a chunk width: 4 x 128 or 3 x 192 rows of B.
@@ -347,7 +348,7 @@ __device__ __noinline__ int issue_gemm1(uint32_t gt, int nk, int klast, uint64_t
 // GEMM2 of one chunk: O (+)= P . S with P (the chunk's kernel values, 16-bit hi/lo pairs
 // packed in the G buffer's TMEM columns) as the A operand and the chunk's transposed
 // weights from shared memory as B; CW / 16 K steps of 16 rows, 3 MMAs each for split
-// weights.  Packed (pk2: one CTA, split weights, P tiles <= 32): the weight tile holds each
+// weights (hi.hi, hi.lo, lo.hi).  Packed (pk2: one CTA, split weights, P tiles <= 32): the weight tile holds each
 // 64-row box's hi and lo planes back to back, so one MMA of N = 2P multiplies P's hi plane
 // by both (O columns [0, P) take hi.hi, [P, 2P) hi.lo) and a second of N = P adds lo.hi
 // into [P, 2P): 2 MMAs per K step instead of 3.  The hi.hi sum then takes one accumulation
