@@ -1500,8 +1500,6 @@ int fit_run_batch(DeviceContext* ctx, const std::vector<FitProblem>& probs, cuda
   }
 
   // tables of the batched product, uploaded once
-  SSource* src_lit = nullptr;
-  std::vector<TcProb> tcp_lit;
   if (batched) {
     for (int i = 0; i < np; ++i) {
       float* wsc_i = precision_is_tensor(prm.precision) ? reinterpret_cast<float*>(base + o_wsc) + i * bp.p16 : nullptr;
@@ -1541,8 +1539,6 @@ int fit_run_batch(DeviceContext* ctx, const std::vector<FitProblem>& probs, cuda
     }
     if (prm.literal_kv) return ITERGP_EINVAL;   // batched fits carry K v (validated by the API)
   }
-  (void)src_lit;
-  (void)tcp_lit;
 
   // the kernel products of an iteration: t_cur = K s_cur for every active problem
   // K w for one problem's N x C block (one kernel per class: C grouped products)
